@@ -1,0 +1,190 @@
+"""Oracle operators: A, Y, L, U and the block eigenvalues, from their definitions (FP64).
+
+Test infrastructure only (see the package docstring).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+from scipy.linalg import toeplitz
+
+
+def _axes(prob):
+    return list(prob.m), list(prob.h)
+
+
+def laplacian_1d(m: int, h: float) -> sp.csr_matrix:
+    """L = -Delta_h in 1-D: the central-difference Dirichlet Laplacian, tridiag(-1, 2, -1)/h^2.
+
+    Sec. 5.2 (central differences on a uniform grid, zero boundary values; Delta_h is symmetric
+    negative definite, so L is SPD).
+    """
+    e = np.ones(m)
+    return sp.diags([-e[:-1], 2.0 * e, -e[:-1]], [-1, 0, 1], format="csr") / (h * h)
+
+
+def laplacian(prob) -> sp.csr_matrix:
+    """L = -Delta_h on the tensor grid, lexicographic order with x fastest (Sec. 5.2).
+
+    The d-dimensional operator is the Kronecker sum of the 1-D ones; axis 0 (x) is the fastest.
+    """
+    ms, hs = _axes(prob)
+    M = int(np.prod(ms))
+    L = sp.csr_matrix((M, M))
+    for ax in range(prob.d):
+        inner = int(np.prod(ms[:ax]))            # axes faster than this one
+        outer = int(np.prod(ms[ax + 1:]))        # axes slower than this one
+        term = sp.kron(sp.identity(outer), sp.kron(laplacian_1d(ms[ax], hs[ax]), sp.identity(inner)))
+        L = L + term
+    return L.tocsr()
+
+
+def dst1_matrix(m: int) -> np.ndarray:
+    """Normalised DST-I matrix S[j, k] = sqrt(2/(m+1)) sin(pi (j+1)(k+1)/(m+1)).
+
+    It is the orthogonal U that diagonalises every block for the paper's examples (Sec. 5.1: the
+    blocks are diagonalised by the discrete sine transform).  S is symmetric and S @ S = I.
+    """
+    j = np.arange(1, m + 1)
+    return np.sqrt(2.0 / (m + 1)) * np.sin(np.pi * np.outer(j, j) / (m + 1))
+
+
+def laplacian_eigenvalues(prob) -> np.ndarray:
+    """Eigenvalues mu_i of L in the order of U's columns (lexicographic, x fastest).
+
+    Per axis the 1-D eigenvalue of column k is (4/h^2) sin^2(pi (k+1) / (2 (m+1))) (textbook);
+    the d-dimensional ones are their sums over the axes.
+    """
+    ms, hs = _axes(prob)
+    mu = np.zeros(1)
+    for ax in range(prob.d):            # build with x fastest: later axes are slower
+        k = np.arange(1, ms[ax] + 1)
+        mu1 = 4.0 / hs[ax] ** 2 * np.sin(np.pi * k / (2.0 * (ms[ax] + 1))) ** 2
+        mu = (mu1[:, None] + mu[None, :]).reshape(-1)
+    return mu
+
+
+def apply_U(prob, V: np.ndarray) -> np.ndarray:
+    """Apply I_N (x) U to a time-major array V of shape (N, M): the DST-I along every spatial axis.
+
+    U = S_z (x) S_y (x) S_x (x fastest) is symmetric and orthogonal, so this is also U^T.
+    Used for Steps 1 and 3 of the preconditioner solve (Sec. 5.1).
+    """
+    ms = list(prob.m)
+    N = V.shape[0]
+    X = V.reshape((N,) + tuple(reversed(ms)))        # (N, [z], [y], x)
+    for ax in range(prob.d):
+        S = dst1_matrix(ms[ax])
+        arr_axis = X.ndim - 1 - ax                    # x is the last array axis
+        X = np.moveaxis(np.tensordot(X, S, axes=([arr_axis], [0])), -1, arr_axis)
+    return X.reshape(N, -1)
+
+
+def block_eigenvalues(prob) -> np.ndarray:
+    """lambda_i^(k) = a_k + b_k mu_i, the eigenvalues of A_(k) = U Lambda_k U^T (Sec. 3).
+
+    Returns an (N, M) array: row k holds the diagonal of Lambda_k.
+    """
+    mu = laplacian_eigenvalues(prob)
+    return prob.a[:, None] + prob.b[:, None] * mu[None, :]
+
+
+def assumption_margin(prob) -> float:
+    """c0 = min_i (lambda_i^(0) - sum_{j>=1} |lambda_i^(j)|) (Proposition after Lemma 3.1).
+
+    Assumption 1(ii) holds iff this is positive.  Evaluated over every mode.
+    """
+    lam = block_eigenvalues(prob)
+    return float(np.min(lam[0] - np.abs(lam[1:]).sum(axis=0)))
+
+
+def bltt_matvec(prob, z: np.ndarray, flip: bool = False) -> np.ndarray:
+    """y = A z (or Y A z when flip), A the BLTT matrix of eq. amatdef, computed directly.
+
+    Block row n of A z is sum_{k=0}^{n} A_(k) z_{n-k} = sum_k a_k z_{n-k} + L sum_k b_k z_{n-k}.
+    With Z the (N, M) time-major array, the two time sums are the lower-triangular Toeplitz
+    products T_a Z and T_b Z (O(N^2 M), a library matmul as the step), and L acts per time slice.
+    Y = Y_N (x) I_M reverses the order of the time blocks (Sec. 2).
+    """
+    N, M = prob.N, prob.M
+    Z = np.asarray(z, dtype=np.float64).reshape(N, M)
+    Ta = toeplitz(prob.a, np.zeros(N))
+    Yv = Ta @ Z
+    if np.any(prob.b != 0):
+        Tb = toeplitz(prob.b, np.zeros(N))
+        W = Tb @ Z
+        L = laplacian(prob)
+        Yv = Yv + (L @ W.T).T
+    if flip:
+        Yv = Yv[::-1]
+    return np.ascontiguousarray(Yv).reshape(-1)
+
+
+def bltt_matvec_entry(prob, z: np.ndarray, n: int, i: int, flip: bool = False) -> float:
+    """One entry of A z (or Y A z): block row n, spatial index i, by the block sum itself.
+
+    Used for sampled checks at sizes where the full product is too slow.
+    """
+    N, M = prob.N, prob.M
+    Z = np.asarray(z).reshape(N, M)
+    row = N - 1 - n if flip else n
+    ms = list(prob.m)
+    # neighbours of i in the Laplacian stencil
+    coords = []
+    r = i
+    for ax in range(prob.d):
+        coords.append(r % ms[ax])
+        r //= ms[ax]
+    acc = 0.0
+    for k in range(row + 1):
+        zk = Z[row - k]
+        if prob.a[k] != 0.0:
+            acc += prob.a[k] * zk[i]
+        if prob.b[k] != 0.0:
+            lz = 0.0
+            stride = 1
+            for ax in range(prob.d):
+                h2 = prob.h[ax] ** 2
+                lz += 2.0 * zk[i] / h2
+                if coords[ax] > 0:
+                    lz -= zk[i - stride] / h2
+                if coords[ax] < ms[ax] - 1:
+                    lz -= zk[i + stride] / h2
+                stride *= ms[ax]
+            acc += prob.b[k] * lz
+    return acc
+
+
+def assemble_A(prob) -> np.ndarray:
+    """Dense A of eq. amatdef: block (p, q) is A_(p-q) for p >= q, zero above (tiny sizes only)."""
+    N, M = prob.N, prob.M
+    L = laplacian(prob).toarray()
+    I = np.eye(M)
+    A = np.zeros((N * M, N * M))
+    for p in range(N):
+        for q in range(p + 1):
+            k = p - q
+            A[p * M:(p + 1) * M, q * M:(q + 1) * M] = prob.a[k] * I + prob.b[k] * L
+    return A
+
+
+def assemble_Y(N: int, M: int) -> np.ndarray:
+    """Dense Y = Y_N (x) I_M, Y_N the anti-identity (Sec. 2)."""
+    return np.kron(np.fliplr(np.eye(N)), np.eye(M))
+
+
+def assemble_C_alpha(prob, alpha: float) -> np.ndarray:
+    """Dense block alpha-circulant C_alpha = I_N (x) A_(0) + sum_k H_alpha^(k) (x) A_(k) (eq. tensordef2calpha).
+
+    H_alpha^(k) = [[0, alpha I_k], [I_{N-k}, 0]] (Sec. 3).
+    """
+    N, M = prob.N, prob.M
+    L = laplacian(prob).toarray()
+    I = np.eye(M)
+    C = np.kron(np.eye(N), prob.a[0] * I + prob.b[0] * L)
+    for k in range(1, N):
+        H = np.zeros((N, N))
+        H[:k, N - k:] = alpha * np.eye(k)
+        H[k:, :N - k] = np.eye(N - k)
+        C += np.kron(H, prob.a[k] * I + prob.b[k] * L)
+    return C

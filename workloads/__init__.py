@@ -1,0 +1,218 @@
+"""Seeded synthetic inputs for block lower triangular Toeplitz (BLTT) all-at-once systems.
+
+This module defines *problems*, not the solver: the block coefficients of the BLTT matrix that a
+time discretisation produces (Sec. 5: backward Euler / Crank-Nicolson heat equations, the L1
+scheme for the time-fractional sub-diffusion equation) and seeded right-hand sides.  It holds none
+of the solver's arithmetic (no transforms, no preconditioner, no Krylov recurrences).  Both the
+CPU oracle and the CUDA path take their inputs from here, so neither depends on the other.
+
+Conventions (Sec. 5 and Sec. 2):
+  * every block is A_(k) = a_k I + b_k L, with L = -Delta_h the SPD finite-difference Dirichlet
+    Laplacian on a uniform grid with m interior points per axis, h = length/(m+1);
+  * unknowns are time-major: u[n*M + i], n = 0..N-1 the time step, i the lexicographic spatial
+    index with x fastest; M = m**d.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "Problem", "l1_weights", "fractional_problem", "heat_bdf_problem", "heat_cn_problem",
+    "rhs_uniform", "rhs_smoothed_field", "WORKLOADS", "workload", "batched_systems",
+    "alpha_training_problems",
+]
+
+
+@dataclass
+class Problem:
+    """One BLTT system A u = f with blocks A_(k) = a[k] I + b[k] L (eq. amatdef)."""
+    N: int                      # number of time steps (blocks per block row)
+    d: int                      # spatial dimension (1, 2 or 3)
+    m: tuple                    # interior points per axis, length d
+    h: tuple                    # grid spacing per axis, length d
+    a: np.ndarray               # (N,) identity coefficients of the blocks
+    b: np.ndarray               # (N,) Laplacian coefficients of the blocks
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def M(self) -> int:
+        return int(np.prod(self.m))
+
+    @property
+    def n(self) -> int:
+        return self.N * self.M
+
+
+def l1_weights(gamma: float, N: int) -> np.ndarray:
+    """L1-scheme weights l_k^(gamma), k = 0..N-1 (Sec. 5.2, the L1 discretisation).
+
+    l_0 = 1/Gamma(2-gamma);  l_k = [(k+1)^(1-gamma) - 2 k^(1-gamma) + (k-1)^(1-gamma)]/Gamma(2-gamma).
+    At k = 1 the term 0^(1-gamma) is taken as 0 for every gamma in (0, 1]; this is also its
+    gamma -> 1 limit, under which the weights become (1, -1, 0, ...), the backward-Euler ones.
+    """
+    if not (0.0 < gamma <= 1.0):
+        raise ValueError("gamma must lie in (0, 1]")
+    p = 1.0 - gamma
+    k = np.arange(N, dtype=np.float64)
+
+    def pw(x):
+        out = np.zeros_like(x)
+        pos = x > 0
+        out[pos] = x[pos] ** p
+        return out
+
+    g = math.gamma(2.0 - gamma)
+    l = (pw(k + 1) - 2.0 * pw(k) + pw(k - 1)) / g
+    l[0] = 1.0 / g
+    return l
+
+
+def _grid(d, m, length):
+    m = tuple([m] * d) if np.isscalar(m) else tuple(m)
+    if len(m) != d:
+        raise ValueError("m must have d entries")
+    h = tuple(length / (mi + 1) for mi in m)
+    return m, h
+
+
+def fractional_problem(d, m, N, gamma, T=1.0, length=1.0, name=None) -> Problem:
+    """L1-scheme time-fractional sub-diffusion: A_(0) = l_0/tau^g I + L, A_(k) = l_k/tau^g I."""
+    m, h = _grid(d, m, length)
+    tau = T / N
+    a = l1_weights(gamma, N) / tau ** gamma
+    b = np.zeros(N)
+    b[0] = 1.0
+    return Problem(N, d, m, h, a, b, name or f"frac{d}d_N{N}_m{m[0]}_g{gamma}",
+                   dict(kind="fractional", gamma=gamma, tau=tau))
+
+
+def heat_bdf_problem(d, m, N, T=1.0, length=1.0, name=None) -> Problem:
+    """Backward-Euler heat equation: A_(0) = I/tau + L, A_(1) = -I/tau (Sec. 5.1, BDF)."""
+    m, h = _grid(d, m, length)
+    tau = T / N
+    a = np.zeros(N)
+    a[0] = 1.0 / tau
+    if N > 1:
+        a[1] = -1.0 / tau
+    b = np.zeros(N)
+    b[0] = 1.0
+    return Problem(N, d, m, h, a, b, name or f"heat{d}d_bdf_N{N}_m{m[0]}",
+                   dict(kind="heat_bdf", gamma=1.0, tau=tau))
+
+
+def heat_cn_problem(d, m, N, T=1.0, length=1.0, name=None) -> Problem:
+    """Crank-Nicolson heat equation: A_(0) = I/tau + L/2, A_(1) = -I/tau + L/2 (Sec. 5.1, CN)."""
+    m, h = _grid(d, m, length)
+    tau = T / N
+    a = np.zeros(N)
+    b = np.zeros(N)
+    a[0], b[0] = 1.0 / tau, 0.5
+    if N > 1:
+        a[1], b[1] = -1.0 / tau, 0.5
+    return Problem(N, d, m, h, a, b, name or f"heat{d}d_cn_N{N}_m{m[0]}",
+                   dict(kind="heat_cn", gamma=1.0, tau=tau))
+
+
+def rhs_uniform(n: int, seed: int) -> np.ndarray:
+    """Seeded U[-1, 1] right-hand side of length n (float64)."""
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, n)
+
+
+def rhs_smoothed_field(N: int, d: int, m, seed: int, sigma: float = 2.0) -> np.ndarray:
+    """Seeded Gaussian-smoothed random field, one independent field per time slice.
+
+    iid N(0,1) per grid point, separable Gaussian smoothing in space (sigma grid cells,
+    truncated at 3 sigma, zero outside the domain), normalised to unit RMS over the whole vector.
+    """
+    from scipy.ndimage import gaussian_filter1d
+    m = tuple([m] * d) if np.isscalar(m) else tuple(m)
+    rng = np.random.default_rng(seed)
+    shape = (N,) + tuple(reversed(m))          # (time, z, y, x): x fastest
+    f = rng.standard_normal(shape)
+    for ax in range(1, f.ndim):
+        gaussian_filter1d(f, sigma, axis=ax, mode="constant", cval=0.0, truncate=3.0, output=f)
+    f /= np.sqrt(np.mean(f * f))
+    return f.reshape(-1)
+
+
+# Named workloads, each with its sizes.  A workload bundles a problem, its right-hand-side recipe
+# and the seed; the solver tolerance is 1e-8 relative residual throughout.
+def _w_frac1d():
+    p = fractional_problem(1, 63, 64, 0.5)
+    return p, (lambda: rhs_uniform(p.n, 1))
+
+
+def _w_frac2d():
+    p = fractional_problem(2, 255, 1024, 0.7)
+    return p, (lambda: rhs_uniform(p.n, 2))
+
+
+def _w_heat3d():
+    p = heat_bdf_problem(3, 127, 256)
+    return p, (lambda: rhs_smoothed_field(p.N, 3, p.m, 3))
+
+
+WORKLOADS = {
+    "frac1d_N64_m63_g0.5": _w_frac1d,      # 1-D L1 fractional, 4,032 unknowns
+    "frac2d_N1024_m255_g0.7": _w_frac2d,   # 2-D L1 fractional, 66,585,600 unknowns
+    "heat3d_bdf_N256_m127": _w_heat3d,     # 3-D backward-Euler heat, 524,386,048 unknowns
+}
+
+
+def workload(name: str):
+    """Return (Problem, rhs_factory) for a named workload."""
+    return WORKLOADS[name]()
+
+
+_BATCH_N = (128, 256, 512, 1024, 2048)
+_BATCH_SPACE = ((1, 127), (2, 63), (2, 127), (2, 255))   # M = 127, 63^2, 127^2, 255^2
+
+
+def batched_systems(nsys: int = 96, nrhs: int = 4, seed: int = 4, scale: float = 1.0):
+    """Mixed batch of L1 fractional systems with uneven N and M, nrhs seeded U[-1,1] RHS each.
+
+    Draws N from {128,...,2048}, the space from {1-D m=127, 2-D m=63, 127, 255} and
+    gamma ~ U[0.2, 0.9] from default_rng(seed); RHS r of system s uses seed + 1000 s + r.
+    `scale` < 1 shrinks N (never below 8) for reduced test batches.
+    Returns a list of (Problem, [rhs factories]).
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for s in range(nsys):
+        N = int(rng.choice(_BATCH_N))
+        d, m = _BATCH_SPACE[int(rng.integers(len(_BATCH_SPACE)))]
+        gamma = float(rng.uniform(0.2, 0.9))
+        if scale != 1.0:
+            N = max(8, int(N * scale))
+        p = fractional_problem(d, m, N, gamma, name=f"batch{s}_{d}d_N{N}_m{m}_g{gamma:.3f}")
+        rhs = [(lambda p=p, r=r, s=s: rhs_uniform(p.n, seed + 1000 * s + r)) for r in range(nrhs)]
+        out.append((p, rhs))
+    return out
+
+
+def alpha_training_problems(count: int, seed: int = 5):
+    """Problems for learning alpha: half 1-D L1 fractional, half 3-D backward-Euler heat.
+
+    1-D fractional: m in {31, 63, 127, 255}, N in {32, ..., 1024}, gamma ~ U[0.2, 0.9].
+    3-D heat:       m in {15, 31, 63},       N in {32, ..., 256}  (gamma := 1 as a feature).
+    Each comes with a seeded U[-1,1] right-hand side.  Returns a list of (Problem, rhs_factory).
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for j in range(count):
+        if j % 2 == 0:
+            m = int(rng.choice((31, 63, 127, 255)))
+            N = int(rng.choice((32, 64, 128, 256, 512, 1024)))
+            gamma = float(rng.uniform(0.2, 0.9))
+            p = fractional_problem(1, m, N, gamma)
+        else:
+            m = int(rng.choice((15, 31, 63)))
+            N = int(rng.choice((32, 64, 128, 256)))
+            p = heat_bdf_problem(3, m, N)
+        sd = int(rng.integers(1 << 30))
+        out.append((p, (lambda p=p, sd=sd: rhs_uniform(p.n, sd))))
+    return out
