@@ -1,0 +1,156 @@
+/*
+ * bltt.h - C ABI of libbltt: preconditioned MINRES for block lower triangular Toeplitz (BLTT)
+ * all-at-once systems A u = f, on one GB300 GPU (sm_103a).
+ *
+ * Method (arXiv 2307.07749): time-reverse the system to the symmetric indefinite form
+ * Y A u = Y f (Sec. 2, eq. symmetrizedblttsys) and solve it by preconditioned MINRES with the
+ * absolute-value block alpha-circulant preconditioner P_alpha = |C_alpha| (Sec. 3, eqs.
+ * tensordef2calpha, calphaabsdef, precdef), applied as in Sec. 5.1.
+ *
+ * Problem class: blocks A_(k) = a_k I + b_k L, k = 0..N-1 (eq. amatdef), L = -Delta_h the
+ * central-difference Dirichlet Laplacian on a uniform d-dimensional grid (d = 1, 2, 3), which the
+ * normalised DST-I diagonalises (Sec. 5.1).  The blocks commute (Assumption 1 (i)) by construction.
+ *
+ * Vector layout everywhere: time-major, u[n*M + i], n = 0..N-1 the time step, i the lexicographic
+ * spatial index with x fastest; M = m[0]*...*m[d-1].  Vectors are contiguous FP64.
+ *
+ * Conventions shared by every entry point:
+ *  - Memory: vector arguments named *_dev are caller-owned device pointers (e.g. torch tensors),
+ *    8-byte aligned, length N*M; the library never frees them.  All other pointers are host memory.
+ *    The library owns its tables and workspace (allocated in bltt_create / on first use).
+ *  - Streams: work is issued on the handle's stream (bltt_set_stream; default: the legacy
+ *    stream).  bltt_matvec and bltt_precond_apply are asynchronous; bltt_minres_solve synchronises
+ *    on that stream to fill its info struct.
+ *  - Errors: every call returns a bltt_status; nothing aborts, exits or traps.  A failed call
+ *    leaves outputs unspecified; bltt_last_error(h) returns a message for the last failure on h.
+ *  - Threads: a handle is not thread-safe; distinct handles may be used from distinct threads.
+ *  - Sizes: N and every m[ax]+1 must be powers of two with 2 <= N <= 4096 and
+ *    2 <= m[ax]+1 <= 4096; other sizes return BLTT_ERR_UNSUPPORTED.
+ */
+#ifndef BLTT_H
+#define BLTT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bltt_ctx* bltt_handle;
+
+typedef enum {
+  BLTT_OK = 0,
+  BLTT_ERR_INVALID_ARG = 1,   /* null pointer, alpha outside (0,1], bad sizes or flags        */
+  BLTT_ERR_ASSUMPTION = 2,    /* Assumption 1 (ii) fails: c0 = min_i(l_i^(0) - sum|l_i^(k)|) <= 0 */
+  BLTT_ERR_OOM = 3,           /* device allocation failed                                      */
+  BLTT_ERR_CUDA = 4,          /* a CUDA runtime call failed                                    */
+  BLTT_ERR_NUMERIC = 5,       /* NaN/Inf in the data or <z, v> < 0 (MINRES breakdown)           */
+  BLTT_ERR_NOT_CONVERGED = 6, /* maxit reached before the stopping rule held                   */
+  BLTT_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up                            */
+  BLTT_ERR_UNSUPPORTED = 8    /* sizes outside the supported set                               */
+} bltt_status;
+
+/* Spatial grid: ndim in {1,2,3}, m[ax] interior points and spacing h[ax] per axis (x first).
+ * L = -Delta_h with zero Dirichlet values (Sec. 5.2). Unused axes are ignored. */
+typedef struct {
+  int ndim;
+  int m[3];
+  double h[3];
+} bltt_space;
+
+/* The BLTT matrix: N blocks A_(k) = a[k] I + b[k] L (eq. amatdef).  a, b: host arrays of length N,
+ * copied by bltt_create. */
+typedef struct {
+  int N;
+  const double* a;
+  const double* b;
+  bltt_space space;
+} bltt_blocks;
+
+/* Precision of the preconditioner apply (the matvec, the Lanczos recurrences and the true
+ * residual are always FP64). */
+enum { BLTT_PREC_F64 = 64, BLTT_PREC_F32 = 32 };
+
+/* Basis the MINRES vectors live in during the iteration.  SPECTRAL: the DST-I basis of the
+ * blocks (U is orthogonal and symmetric, Sec. 3), so the loop needs no DST; the iterates are the
+ * physical ones multiplied by I (x) U.  PHYSICAL: the textbook form, DSTs inside P_alpha^{-1}.
+ * AUTO picks SPECTRAL for FP64 and PHYSICAL for FP32 preconditioners. */
+enum { BLTT_BASIS_AUTO = 0, BLTT_BASIS_SPECTRAL = 1, BLTT_BASIS_PHYSICAL = 2 };
+
+/* Preconditioner kind: ABAC P_alpha (alpha = 1 gives the absolute-value block circulant P_1),
+ * or none (MINRES-I, the paper's unpreconditioned comparison solver, Sec. 5.2). */
+enum { BLTT_PRECOND_ABAC = 0, BLTT_PRECOND_NONE = 1 };
+
+typedef struct {
+  int precision;     /* BLTT_PREC_F64 (default when 0) or BLTT_PREC_F32                        */
+  int basis;         /* BLTT_BASIS_*                                                            */
+  int precond;       /* BLTT_PRECOND_*                                                          */
+  int sync_every;    /* iterations issued between host checks of the device state (0: 2)        */
+} bltt_solve_opts;
+
+typedef struct {
+  int iters;              /* MINRES iterations (one matvec + one preconditioner apply each)    */
+  double relres_est;      /* |eta_j| / eta_0: P^{-1}-norm residual estimate of the recurrence  */
+  double relres_true;     /* ||Y f - Y A u||_2 / ||Y f||_2, recomputed in FP64 at the end      */
+  double alpha_used;
+  int alpha_source;       /* 0: caller, 1: learned predictor, 2: fallback rule alpha = 1e-8    */
+  int precision;          /* preconditioner precision used (64 or 32)                          */
+  int basis;              /* basis used (BLTT_BASIS_SPECTRAL or BLTT_BASIS_PHYSICAL)           */
+  double t_setup_ms;      /* per-alpha preconditioner set-up (device time)                     */
+  double t_solve_ms;      /* whole solve incl. set-up, device time on the handle's stream      */
+  long long kernel_launches; /* kernels issued by the solve                                    */
+  int status;             /* bltt_status of the solve                                          */
+} bltt_solve_info;
+
+/* Create a handle for the BLTT matrix `blocks` with N time steps and M spatial unknowns
+ * (M must equal prod(m)).  Checks Assumption 1 (ii) (Proposition after Lemma 3.1): with
+ * mu_i the eigenvalues of L, c0 = min_i (a_0 + b_0 mu_i - sum_{k>=1} |a_k + b_k mu_i|) must be
+ * > 0, else BLTT_ERR_ASSUMPTION.  Builds the matvec spectra FFT_{2N}([a;0]), FFT_{2N}([b;0])
+ * (Sec. 5.1, the FFT matvec) and the per-axis eigenvalue tables; allocates no vector workspace.
+ * *out receives the handle (NULL on failure). */
+bltt_status bltt_create(const bltt_blocks* blocks, int N, long long M, bltt_handle* out);
+
+/* Release the handle, its tables and workspace.  NULL is accepted. */
+bltt_status bltt_destroy(bltt_handle h);
+
+/* Issue all later work of h on `cuda_stream` (a cudaStream_t; NULL = legacy default stream). */
+bltt_status bltt_set_stream(bltt_handle h, void* cuda_stream);
+
+/* y = A x (flip = 0) or y = Y A x (flip = 1), A the BLTT matrix (eq. amatdef), Y = Y_N (x) I_M
+ * the time reversal (Sec. 2).  The time convolution runs as a 2N zero-padded circulant
+ * product with FFTs along time, or as a direct shifted sum when a and b have at most 4 leading
+ * nonzeros (Sec. 5.1, the O(MN log N) matvec); L acts as the 2d+1 point stencil.  FP64.
+ * x_dev and y_dev must not overlap. */
+bltt_status bltt_matvec(bltt_handle h, const double* x_dev, double* y_dev, int flip);
+
+/* z = P_alpha^{-1} v = C_alpha^{-1/2} (C_alpha^{-1/2})^* v (Sec. 5.1): DST-I of every time slice,
+ * per spatial mode the alpha-scaled time pass D F conj(Lambda)^{-1/2} F^* D^{-1} followed by
+ * D^{-1} F Lambda^{-1/2} F^* D (eqs. hatcalphaidiagform, sqrtcalphabdiagform), inverse DST-I.
+ * 0 < alpha <= 1.  precision: 64 or 32 (arithmetic of the whole apply; v and z stay FP64).
+ * v_dev and z_dev may be equal (in place). */
+bltt_status bltt_precond_apply(bltt_handle h, double alpha, const double* v_dev, double* z_dev,
+                               int precision);
+
+/* Solve A u = f through MINRES on Y A u = Y f with P_alpha (Sec. 2-3, Sec. 5).  Zero initial
+ * guess (Sec. 5.2).  Stops when the recurrence estimate |eta_j|/eta_0 <= tol and then the true
+ * relative residual ||Yf - YAu||/||Yf|| <= tol (both FP64); otherwise iterates on, up to maxit.
+ * f_dev: the unflipped right-hand side; u_dev: the solution (may not alias f_dev).
+ * opts may be NULL (FP64, AUTO basis, ABAC).  info (host, may be NULL) receives the statistics.
+ * Returns BLTT_OK, BLTT_ERR_NOT_CONVERGED (u holds the last iterate), BLTT_ERR_NUMERIC, ... */
+bltt_status bltt_minres_solve_ex(bltt_handle h, const double* f_dev, double alpha, double tol,
+                                 int maxit, const bltt_solve_opts* opts, double* u_dev,
+                                 bltt_solve_info* info);
+
+/* Same as bltt_minres_solve_ex with opts = {precision, AUTO, ABAC, 0}. */
+bltt_status bltt_minres_solve(bltt_handle h, const double* f_dev, double alpha, double tol,
+                              int maxit, int precision, double* u_dev, bltt_solve_info* info);
+
+/* Message for the last failed call on h ("" if none); for h == NULL, the last failure of
+ * bltt_create on this thread.  The string stays valid until the next call on h. */
+const char* bltt_last_error(bltt_handle h);
+
+/* Library version string. */
+const char* bltt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BLTT_H */

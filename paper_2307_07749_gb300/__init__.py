@@ -1,0 +1,228 @@
+"""GB300-native preconditioned MINRES for block lower triangular Toeplitz systems (arXiv 2307.07749).
+
+Thin Python binding of libbltt (C ABI in include/bltt.h): argument marshalling only.  Every step of
+the solver runs in the library's CUDA kernels; PyTorch supplies device memory and streams.  There
+is no CPU fallback: if libbltt.so is missing or cannot load, importing the binding raises.
+
+The functions carry the C names (bltt_create, bltt_matvec, bltt_precond_apply, bltt_minres_solve,
+...) and take torch tensors (float64, contiguous, on a CUDA device) where the C calls take device
+pointers.  `Solver` wraps a handle for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbltt.so")
+
+BLTT_OK = 0
+STATUS_NAMES = {
+    0: "BLTT_OK", 1: "BLTT_ERR_INVALID_ARG", 2: "BLTT_ERR_ASSUMPTION", 3: "BLTT_ERR_OOM",
+    4: "BLTT_ERR_CUDA", 5: "BLTT_ERR_NUMERIC", 6: "BLTT_ERR_NOT_CONVERGED", 7: "BLTT_ERR_TIMEOUT",
+    8: "BLTT_ERR_UNSUPPORTED",
+}
+PREC_F64, PREC_F32 = 64, 32
+BASIS_AUTO, BASIS_SPECTRAL, BASIS_PHYSICAL = 0, 1, 2
+PRECOND_ABAC, PRECOND_NONE = 0, 1
+
+
+class BlttError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class bltt_space(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("m", ctypes.c_int * 3), ("h", ctypes.c_double * 3)]
+
+
+class bltt_blocks(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("a", ctypes.POINTER(ctypes.c_double)),
+                ("b", ctypes.POINTER(ctypes.c_double)), ("space", bltt_space)]
+
+
+class bltt_solve_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("basis", ctypes.c_int), ("precond", ctypes.c_int),
+                ("sync_every", ctypes.c_int)]
+
+
+class bltt_solve_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("relres_est", ctypes.c_double),
+                ("relres_true", ctypes.c_double), ("alpha_used", ctypes.c_double),
+                ("alpha_source", ctypes.c_int), ("precision", ctypes.c_int),
+                ("basis", ctypes.c_int), ("t_setup_ms", ctypes.c_double),
+                ("t_solve_ms", ctypes.c_double), ("kernel_launches", ctypes.c_longlong),
+                ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# C signatures: name -> (restype, argtypes)
+_P = ctypes.c_void_p
+_SIGS = {
+    "bltt_create": (ctypes.c_int, [ctypes.POINTER(bltt_blocks), ctypes.c_int, ctypes.c_longlong,
+                                   ctypes.POINTER(_P)]),
+    "bltt_destroy": (ctypes.c_int, [_P]),
+    "bltt_set_stream": (ctypes.c_int, [_P, _P]),
+    "bltt_matvec": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
+    "bltt_precond_apply": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, ctypes.c_int]),
+    "bltt_minres_solve_ex": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                            ctypes.POINTER(bltt_solve_opts), _P,
+                                            ctypes.POINTER(bltt_solve_info)]),
+    "bltt_minres_solve": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                         ctypes.c_int, _P, ctypes.POINTER(bltt_solve_info)]),
+    "bltt_last_error": (ctypes.c_char_p, [_P]),
+    "bltt_version": (ctypes.c_char_p, []),
+}
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libbltt.so (raises OSError if it is missing: build it with build.build())."""
+    if not os.path.exists(path):
+        raise OSError(f"libbltt.so not found at {path}; run paper_2307_07749_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+def _check(status, handle=None):
+    if status != BLTT_OK:
+        msg = lib().bltt_last_error(handle)
+        raise BlttError(status, msg.decode() if msg else "")
+
+
+def _ptr(t, name="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# --------------------------------------------------------------------------------------------
+# functions with the C names
+
+def bltt_create(a, b, N, ndim, m, h):
+    """Create a handle for blocks A_(k) = a[k] I + b[k] L on the grid (ndim, m, h)."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    m = list(m) + [1] * (3 - len(m))
+    h = list(h) + [1.0] * (3 - len(h))
+    sp = bltt_space(ndim, (ctypes.c_int * 3)(*m), (ctypes.c_double * 3)(*h))
+    blk = bltt_blocks(N, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                      b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), sp)
+    M = int(np.prod(m[:ndim]))
+    out = ctypes.c_void_p()
+    _check(lib().bltt_create(ctypes.byref(blk), N, M, ctypes.byref(out)))
+    return out
+
+
+def bltt_destroy(handle):
+    _check(lib().bltt_destroy(handle))
+
+
+def bltt_set_stream(handle, stream):
+    """stream: a torch.cuda.Stream (or an int cudaStream_t)."""
+    s = getattr(stream, "cuda_stream", stream)
+    _check(lib().bltt_set_stream(handle, ctypes.c_void_p(int(s) if s else 0)), handle)
+
+
+def bltt_matvec(handle, x, y, flip=1):
+    _check(lib().bltt_matvec(handle, _ptr(x, "x"), _ptr(y, "y"), int(flip)), handle)
+
+
+def bltt_precond_apply(handle, alpha, v, z, precision=PREC_F64):
+    _check(lib().bltt_precond_apply(handle, float(alpha), _ptr(v, "v"), _ptr(z, "z"),
+                                    int(precision)), handle)
+
+
+def bltt_minres_solve_ex(handle, f, alpha, tol, maxit, u, precision=PREC_F64, basis=BASIS_AUTO,
+                         precond=PRECOND_ABAC, sync_every=0, raise_on_error=True):
+    opts = bltt_solve_opts(precision, basis, precond, sync_every)
+    info = bltt_solve_info()
+    st = lib().bltt_minres_solve_ex(handle, _ptr(f, "f"), float(alpha), float(tol), int(maxit),
+                                    ctypes.byref(opts), _ptr(u, "u"), ctypes.byref(info))
+    if raise_on_error and st not in (BLTT_OK, 6):
+        _check(st, handle)
+    return st, info.as_dict()
+
+
+def bltt_minres_solve(handle, f, alpha, tol, maxit, precision, u):
+    info = bltt_solve_info()
+    st = lib().bltt_minres_solve(handle, _ptr(f, "f"), float(alpha), float(tol), int(maxit),
+                                 int(precision), _ptr(u, "u"), ctypes.byref(info))
+    return st, info.as_dict()
+
+
+def bltt_version():
+    return lib().bltt_version().decode()
+
+
+# --------------------------------------------------------------------------------------------
+class Solver:
+    """A BLTT system on the GPU: wraps one libbltt handle.
+
+    prob: any object with N, d, m, h, a, b (e.g. workloads.Problem).
+    """
+
+    def __init__(self, prob, stream=None):
+        self.N, self.d = int(prob.N), int(prob.d)
+        self.m = tuple(int(v) for v in prob.m)
+        self.M = int(np.prod(self.m))
+        self.n = self.N * self.M
+        self.handle = bltt_create(prob.a, prob.b, self.N, self.d, self.m, tuple(prob.h))
+        if stream is not None:
+            bltt_set_stream(self.handle, stream)
+
+    def close(self):
+        if self.handle:
+            bltt_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        bltt_set_stream(self.handle, stream)
+
+    def matvec(self, x, y=None, flip=True):
+        import torch
+        y = torch.empty_like(x) if y is None else y
+        bltt_matvec(self.handle, x, y, 1 if flip else 0)
+        return y
+
+    def precond_apply(self, alpha, v, z=None, precision=PREC_F64):
+        import torch
+        z = torch.empty_like(v) if z is None else z
+        bltt_precond_apply(self.handle, alpha, v, z, precision)
+        return z
+
+    def solve(self, f, alpha=1e-8, tol=1e-8, maxit=200, precision=PREC_F64, basis=BASIS_AUTO,
+              precond=PRECOND_ABAC, u=None, sync_every=0, raise_on_error=True):
+        import torch
+        u = torch.empty_like(f) if u is None else u
+        st, info = bltt_minres_solve_ex(self.handle, f, alpha, tol, maxit, u, precision, basis,
+                                        precond, sync_every, raise_on_error)
+        info["status_name"] = STATUS_NAMES.get(st, st)
+        return u, info

@@ -1,0 +1,618 @@
+// bltt_api.cu - the C ABI of libbltt (declared in include/bltt.h): handle life cycle, set-up of
+// the spectral tables, the physical-basis matvec and preconditioner entry points and the MINRES
+// driver (device-resident scalar state, host checks every few iterations).
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/bltt.h"
+#include "internal.h"
+
+using namespace bltt;
+using cd = std::complex<double>;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// ---------------------------------------------------------------------------------------------
+// host-side transforms for the set-up (O(N log N), FP64 with long-double twiddles)
+void twiddle_table(int L, std::vector<double2>& out) {
+  out.resize(L);
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  for (int k = 0; k < L; ++k) {
+    long double ang = two_pi * (long double)k / (long double)L;
+    out[k] = make_double2((double)cosl(ang), (double)(-sinl(ang)));
+  }
+}
+
+// forward DFT X_k = sum_j x_j exp(-2 pi i jk/L), L a power of two (iterative radix 2)
+void host_fft(std::vector<cd>& a) {
+  const int n = (int)a.size();
+  for (int i = 1, j = 0; i < n; ++i) {
+    int bit = n >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) std::swap(a[i], a[j]);
+  }
+  std::vector<double2> tw;
+  twiddle_table(n, tw);
+  for (int len = 2; len <= n; len <<= 1) {
+    const int step = n / len;
+    for (int i = 0; i < n; i += len)
+      for (int k = 0; k < len / 2; ++k) {
+        cd w(tw[k * step].x, tw[k * step].y);
+        cd u = a[i + k], v = a[i + k + len / 2] * w;
+        a[i + k] = u + v;
+        a[i + k + len / 2] = u - v;
+      }
+  }
+}
+
+bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2i(long long v) { int l = 0; while ((1LL << l) < v) ++l; return l; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+struct bltt_ctx {
+  int N = 0, d = 0, m[3] = {1, 1, 1};
+  long long M = 0, n = 0;
+  double h[3] = {1, 1, 1};
+  std::vector<double> a, b;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  OpTables op{};
+  // owned device allocations
+  std::vector<void*> allocs;
+  // workspace
+  double* ws = nullptr;          // 10 vectors of n doubles
+  size_t ws_vectors = 0;
+  double* partials[2] = {nullptr, nullptr};
+  MinresDev* state = nullptr;
+  MinresDev* state_host = nullptr;   // pinned
+  double* scal = nullptr;            // device scalar scratch
+  double* scal_host = nullptr;       // pinned
+  // per-alpha preconditioner cache
+  double pc_alpha = -1.0;
+  bool pc_has64 = false, pc_has32 = false;
+  double* pc_dinv = nullptr;
+  double* pc_d2 = nullptr;
+  double2* pc_g64 = nullptr;
+  float2* pc_ahat32 = nullptr;
+  float2* pc_bhat32 = nullptr;
+  double2* pc_ahat64 = nullptr;
+  double2* pc_bhat64 = nullptr;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  long long launches = 0;
+
+  ~bltt_ctx() {
+    if (stream_sync_ok) cudaStreamSynchronize(stream);
+    for (void* p : allocs) cudaFree(p);
+    if (state_host) cudaFreeHost(state_host);
+    if (scal_host) cudaFreeHost(scal_host);
+    for (auto& e : ev) if (e) cudaEventDestroy(e);
+  }
+  bool stream_sync_ok = true;
+
+  template <typename T>
+  cudaError_t alloc(T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) { *p = nullptr; return e; }
+    allocs.push_back(q);
+    *p = reinterpret_cast<T*>(q);
+    return cudaSuccess;
+  }
+  void release(void* p) {
+    if (!p) return;
+    auto it = std::find(allocs.begin(), allocs.end(), p);
+    if (it != allocs.end()) { cudaFree(p); allocs.erase(it); }
+  }
+};
+
+namespace {
+
+bltt_status fail(bltt_ctx* h, bltt_status s, const std::string& msg) {
+  if (h) h->err = msg; else g_create_error = msg;
+  return s;
+}
+bltt_status cuda_fail(bltt_ctx* h, cudaError_t e, const char* where) {
+  bltt_status s = (e == cudaErrorMemoryAllocation) ? BLTT_ERR_OOM : BLTT_ERR_CUDA;
+  return fail(h, s, std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define CK(h, call, where)                                   \
+  do {                                                       \
+    cudaError_t e__ = (call);                                \
+    if (e__ != cudaSuccess) return cuda_fail((h), e__, where); \
+  } while (0)
+
+template <typename T>
+cudaError_t upload(bltt_ctx* h, T** dst, const T* src, size_t count) {
+  cudaError_t e = h->alloc(dst, count);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+cudaError_t upload_twiddles(bltt_ctx* h, int L, const double2** d64, const float2** d32) {
+  std::vector<double2> tw;
+  twiddle_table(L, tw);
+  std::vector<float2> tw32(L);
+  for (int k = 0; k < L; ++k) tw32[k] = make_float2((float)tw[k].x, (float)tw[k].y);
+  double2* p64;
+  float2* p32;
+  cudaError_t e = upload(h, &p64, tw.data(), L);
+  if (e != cudaSuccess) return e;
+  e = upload(h, &p32, tw32.data(), L);
+  if (e != cudaSuccess) return e;
+  *d64 = p64;
+  if (d32) *d32 = p32;
+  return cudaSuccess;
+}
+
+// ensure the solve workspace: 10 vectors of n doubles, partial sums, device scalar state
+bltt_status ensure_workspace(bltt_ctx* h) {
+  if (h->ws) return BLTT_OK;
+  const size_t nv = 10;
+  CK(h, h->alloc(&h->ws, nv * (size_t)h->n + 2), "workspace allocation");
+  h->ws_vectors = nv;
+  CK(h, h->alloc(&h->partials[0], (size_t)kMaxPartials), "partials");
+  CK(h, h->alloc(&h->partials[1], (size_t)kMaxPartials), "partials");
+  CK(h, h->alloc(&h->state, 1), "state");
+  CK(h, h->alloc(&h->scal, 8), "scalars");
+  if (!h->state_host) CK(h, cudaMallocHost(&h->state_host, sizeof(MinresDev)), "pinned state");
+  if (!h->scal_host) CK(h, cudaMallocHost(&h->scal_host, 8 * sizeof(double)), "pinned scalars");
+  return BLTT_OK;
+}
+
+double* vec(bltt_ctx* h, int k) { return h->ws + (size_t)k * h->n; }
+
+// per-alpha tables: D_alpha scalings, ahat = FFT_N(D a), bhat = FFT_N(D b) and, for the FP64
+// preconditioner, the table lambda^{-1/2}/(2N) over (k <= N/2, mode i)
+bltt_status prepare_precond(bltt_ctx* h, double alpha, int prec) {
+  const int N = h->N;
+  if (h->pc_alpha != alpha) {
+    h->pc_has64 = h->pc_has32 = false;
+    std::vector<double> dinv(N), d2(N);
+    std::vector<cd> ah(N), bh(N);
+    for (int j = 0; j < N; ++j) {
+      double dj = std::pow(alpha, (double)j / N);
+      dinv[j] = 1.0 / dj;
+      d2[j] = dj * dj;
+      ah[j] = cd(dj * h->a[j], 0.0);
+      bh[j] = cd(dj * h->b[j], 0.0);
+    }
+    host_fft(ah);
+    host_fft(bh);
+    if (!h->pc_dinv) {
+      CK(h, h->alloc(&h->pc_dinv, N), "alloc dinv");
+      CK(h, h->alloc(&h->pc_d2, N), "alloc d2");
+      CK(h, h->alloc(&h->pc_ahat64, N / 2 + 1), "alloc ahat");
+      CK(h, h->alloc(&h->pc_bhat64, N / 2 + 1), "alloc bhat");
+      CK(h, h->alloc(&h->pc_ahat32, N / 2 + 1), "alloc ahat32");
+      CK(h, h->alloc(&h->pc_bhat32, N / 2 + 1), "alloc bhat32");
+    }
+    std::vector<double2> a64(N / 2 + 1), b64(N / 2 + 1);
+    std::vector<float2> a32(N / 2 + 1), b32(N / 2 + 1);
+    for (int k = 0; k <= N / 2; ++k) {
+      a64[k] = make_double2(ah[k].real(), ah[k].imag());
+      b64[k] = make_double2(bh[k].real(), bh[k].imag());
+      a32[k] = make_float2((float)ah[k].real(), (float)ah[k].imag());
+      b32[k] = make_float2((float)bh[k].real(), (float)bh[k].imag());
+    }
+    CK(h, cudaMemcpyAsync(h->pc_dinv, dinv.data(), N * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy dinv");
+    CK(h, cudaMemcpyAsync(h->pc_d2, d2.data(), N * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy d2");
+    CK(h, cudaMemcpyAsync(h->pc_ahat64, a64.data(), a64.size() * sizeof(double2), cudaMemcpyHostToDevice, h->stream), "copy ahat");
+    CK(h, cudaMemcpyAsync(h->pc_bhat64, b64.data(), b64.size() * sizeof(double2), cudaMemcpyHostToDevice, h->stream), "copy bhat");
+    CK(h, cudaMemcpyAsync(h->pc_ahat32, a32.data(), a32.size() * sizeof(float2), cudaMemcpyHostToDevice, h->stream), "copy ahat32");
+    CK(h, cudaMemcpyAsync(h->pc_bhat32, b32.data(), b32.size() * sizeof(float2), cudaMemcpyHostToDevice, h->stream), "copy bhat32");
+    // the host vectors die at return: wait for the copies
+    CK(h, cudaStreamSynchronize(h->stream), "sync after table upload");
+    h->pc_alpha = alpha;
+    h->pc_has32 = true;
+  }
+  if (prec == 64 && !h->pc_has64) {
+    if (!h->pc_g64) CK(h, h->alloc(&h->pc_g64, (size_t)(N / 2 + 1) * h->M), "alloc g64 table");
+    CK(h, launch_setup_g64(h->op, h->pc_ahat64, h->pc_bhat64, h->pc_g64, h->stream), "setup g64");
+    h->launches++;
+    h->pc_has64 = true;
+  }
+  return BLTT_OK;
+}
+
+PrecTables prec_tables(bltt_ctx* h, int none) {
+  PrecTables pt{};
+  pt.alpha = h->pc_alpha;
+  pt.dinv = h->pc_dinv;
+  pt.d2 = h->pc_d2;
+  pt.g64 = h->pc_g64;
+  pt.ahat32 = h->pc_ahat32;
+  pt.bhat32 = h->pc_bhat32;
+  pt.none = none;
+  return pt;
+}
+
+// z = P^{-1} (combined input), in the spectral basis (time pass only) or the physical basis
+// (DST-I of every slice, time pass, inverse DST-I); fused dot with `dot_with` into partials.
+bltt_status precond_chain(bltt_ctx* h, int spectral, int prec, const PrecTables& pt,
+                          const Combine& in, double* out, const double* dot_with,
+                          double* partials, int* nparts, const int* phase) {
+  const OpTables& op = h->op;
+  if (pt.none || spectral) {
+    CK(h, launch_timepass(op, pt, prec, in, out, dot_with, partials, nparts, phase, h->stream), "time pass");
+    h->launches++;
+    return BLTT_OK;
+  }
+  for (int ax = 0; ax < op.d; ++ax) {
+    Combine c{};
+    if (ax == 0) c = in; else c.in0 = out;
+    CK(h, launch_dst(op, ax, prec, c, out, 0, nullptr, nullptr, nullptr, phase, h->stream), "dst");
+    h->launches++;
+  }
+  Combine c{};
+  c.in0 = out;
+  CK(h, launch_timepass(op, pt, prec, c, out, nullptr, nullptr, nullptr, phase, h->stream), "time pass");
+  h->launches++;
+  for (int ax = 0; ax < op.d; ++ax) {
+    Combine c2{};
+    c2.in0 = out;
+    const bool last = (ax == op.d - 1);
+    CK(h, launch_dst(op, ax, prec, c2, out, 0, last ? dot_with : nullptr, last ? partials : nullptr,
+                     last ? nparts : nullptr, phase, h->stream), "dst");
+    h->launches++;
+  }
+  return BLTT_OK;
+}
+
+// out = (I (x) U) in, optionally time-reversed (first pass out of place), with ||out||^2 partials
+bltt_status dst_all(bltt_ctx* h, const double* in, double* out, int flip, double* partials,
+                    int* nparts) {
+  const OpTables& op = h->op;
+  for (int ax = 0; ax < op.d; ++ax) {
+    Combine c{};
+    c.in0 = (ax == 0) ? in : out;
+    const bool last = (ax == op.d - 1);
+    CK(h, launch_dst(op, ax, 64, c, out, ax == 0 ? flip : 0, last && partials ? out : nullptr,
+                     last ? partials : nullptr, last ? nparts : nullptr, nullptr, h->stream), "dst");
+    h->launches++;
+  }
+  return BLTT_OK;
+}
+
+bltt_status check_handle(bltt_ctx* h) {
+  if (!h) return BLTT_ERR_INVALID_ARG;
+  return BLTT_OK;
+}
+
+}  // namespace
+
+// =============================================================================================
+extern "C" {
+
+const char* bltt_version(void) { return "bltt-gb300 0.1 (sm_103a)"; }
+
+const char* bltt_last_error(bltt_handle h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+bltt_status bltt_create(const bltt_blocks* blocks, int N, long long M, bltt_handle* out) {
+  if (out) *out = nullptr;
+  if (!blocks || !out || !blocks->a || !blocks->b)
+    return fail(nullptr, BLTT_ERR_INVALID_ARG, "null argument");
+  if (blocks->N != N || N < 2)
+    return fail(nullptr, BLTT_ERR_INVALID_ARG, "N mismatch or N < 2");
+  const bltt_space& sp = blocks->space;
+  if (sp.ndim < 1 || sp.ndim > 3) return fail(nullptr, BLTT_ERR_INVALID_ARG, "ndim must be 1, 2 or 3");
+  long long prodm = 1;
+  for (int ax = 0; ax < sp.ndim; ++ax) {
+    if (sp.m[ax] < 1 || !(sp.h[ax] > 0.0) || !std::isfinite(sp.h[ax]))
+      return fail(nullptr, BLTT_ERR_INVALID_ARG, "bad m or h");
+    prodm *= sp.m[ax];
+  }
+  if (prodm != M) return fail(nullptr, BLTT_ERR_INVALID_ARG, "M != prod(m)");
+  if (!is_pow2(N) || N > 4096) return fail(nullptr, BLTT_ERR_UNSUPPORTED, "N must be a power of two <= 4096");
+  for (int ax = 0; ax < sp.ndim; ++ax)
+    if (!is_pow2(sp.m[ax] + 1) || sp.m[ax] + 1 > 4096)
+      return fail(nullptr, BLTT_ERR_UNSUPPORTED, "m+1 must be a power of two <= 4096");
+  for (int k = 0; k < N; ++k)
+    if (!std::isfinite(blocks->a[k]) || !std::isfinite(blocks->b[k]))
+      return fail(nullptr, BLTT_ERR_NUMERIC, "non-finite block coefficient");
+
+  bltt_ctx* h = new bltt_ctx();
+  h->N = N; h->d = sp.ndim; h->M = M; h->n = (long long)N * M;
+  for (int ax = 0; ax < 3; ++ax) { h->m[ax] = ax < sp.ndim ? sp.m[ax] : 1; h->h[ax] = ax < sp.ndim ? sp.h[ax] : 1.0; }
+  h->a.assign(blocks->a, blocks->a + N);
+  h->b.assign(blocks->b, blocks->b + N);
+
+  // per-axis eigenvalues of L: (4/h^2) sin^2(pi (k+1) / (2(m+1)))
+  std::vector<std::vector<double>> mu(3);
+  double mu_min = 0.0, mu_max = 0.0;
+  for (int ax = 0; ax < sp.ndim; ++ax) {
+    mu[ax].resize(h->m[ax]);
+    for (int k = 0; k < h->m[ax]; ++k) {
+      long double s = sinl(3.141592653589793238462643383279502884L * (k + 1) / (2.0L * (h->m[ax] + 1)));
+      mu[ax][k] = (double)(4.0L / ((long double)h->h[ax] * h->h[ax]) * s * s);
+    }
+    mu_min += mu[ax].front();
+    mu_max += mu[ax].back();
+  }
+  // Assumption 1 (ii): c0(mu) = a0 + b0 mu - sum_k |a_k + b_k mu| is concave in mu, so its minimum
+  // over [mu_min, mu_max] sits at an end point.
+  auto c0_at = [&](double muv) {
+    double v = h->a[0] + h->b[0] * muv;
+    for (int k = 1; k < N; ++k) v -= std::fabs(h->a[k] + h->b[k] * muv);
+    return v;
+  };
+  const double c0 = std::min(c0_at(mu_min), c0_at(mu_max));
+  if (!(c0 > 0.0)) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "Assumption 1 (ii) fails: c0 = %.6g <= 0", c0);
+    delete h;
+    return fail(nullptr, BLTT_ERR_ASSUMPTION, buf);
+  }
+
+  OpTables& op = h->op;
+  op.N = N; op.log2N = ilog2i(N); op.d = h->d; op.M = M;
+  for (int ax = 0; ax < 3; ++ax) { op.m[ax] = h->m[ax]; op.h2inv[ax] = 1.0 / (h->h[ax] * h->h[ax]); }
+  cudaError_t e = cudaSuccess;
+  for (int ax = 0; ax < h->d && e == cudaSuccess; ++ax) {
+    double* p;
+    e = upload(h, &p, mu[ax].data(), mu[ax].size());
+    op.mu_axis[ax] = p;
+    std::vector<float> m32(mu[ax].begin(), mu[ax].end());
+    float* q;
+    if (e == cudaSuccess) e = upload(h, &q, m32.data(), m32.size());
+    op.mu_axis32[ax] = q;
+  }
+  // matvec spectra FFT_2N([a;0]) / (2N), FFT_2N([b;0]) / (2N), k = 0..N
+  std::vector<cd> A2(2 * N, cd(0, 0)), B2(2 * N, cd(0, 0));
+  for (int k = 0; k < N; ++k) { A2[k] = cd(h->a[k], 0); B2[k] = cd(h->b[k], 0); }
+  host_fft(A2);
+  host_fft(B2);
+  std::vector<double2> Ah(N + 1), Bh(N + 1);
+  for (int k = 0; k <= N; ++k) {
+    Ah[k] = make_double2(A2[k].real() / (2.0 * N), A2[k].imag() / (2.0 * N));
+    Bh[k] = make_double2(B2[k].real() / (2.0 * N), B2[k].imag() / (2.0 * N));
+  }
+  double2 *pA = nullptr, *pB = nullptr;
+  if (e == cudaSuccess) e = upload(h, &pA, Ah.data(), Ah.size());
+  if (e == cudaSuccess) e = upload(h, &pB, Bh.data(), Bh.size());
+  op.Ahat = pA; op.Bhat = pB;
+  // b = b0 e_0 ?
+  bool b_e0 = true;
+  for (int k = 1; k < N; ++k) if (h->b[k] != 0.0) b_e0 = false;
+  op.b_kind = b_e0 ? 0 : 1;
+  op.b0 = h->b[0];
+  int last_nz = 0;
+  for (int k = 0; k < N; ++k) if (h->a[k] != 0.0 || h->b[k] != 0.0) last_nz = k;
+  op.ntaps = (last_nz < 4) ? last_nz + 1 : 0;
+  double *pa = nullptr, *pb = nullptr;
+  if (e == cudaSuccess) e = upload(h, &pa, h->a.data(), N);
+  if (e == cudaSuccess) e = upload(h, &pb, h->b.data(), N);
+  op.a_dev = pa; op.b_dev = pb;
+  if (e == cudaSuccess) e = upload_twiddles(h, 2 * N, &op.tw_2N, nullptr);
+  if (e == cudaSuccess) e = upload_twiddles(h, N, &op.tw_N, &op.tw_N32);
+  for (int ax = 0; ax < h->d && e == cudaSuccess; ++ax)
+    e = upload_twiddles(h, 2 * (h->m[ax] + 1), &op.tw_dst[ax], &op.tw_dst32[ax]);
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&h->ev[i]);
+  if (e != cudaSuccess) {
+    bltt_status s = (e == cudaErrorMemoryAllocation) ? BLTT_ERR_OOM : BLTT_ERR_CUDA;
+    std::string msg = std::string("bltt_create: ") + cudaGetErrorString(e);
+    h->stream_sync_ok = false;
+    delete h;
+    return fail(nullptr, s, msg);
+  }
+  *out = h;
+  return BLTT_OK;
+}
+
+bltt_status bltt_destroy(bltt_handle h) {
+  if (!h) return BLTT_OK;
+  delete h;
+  return BLTT_OK;
+}
+
+bltt_status bltt_set_stream(bltt_handle h, void* s) {
+  if (!h) return BLTT_ERR_INVALID_ARG;
+  h->stream = reinterpret_cast<cudaStream_t>(s);
+  return BLTT_OK;
+}
+
+bltt_status bltt_matvec(bltt_handle h, const double* x, double* y, int flip) {
+  if (!h) return BLTT_ERR_INVALID_ARG;
+  if (!x || !y) return fail(h, BLTT_ERR_INVALID_ARG, "null vector");
+  if (x == y) return fail(h, BLTT_ERR_INVALID_ARG, "x and y must not overlap");
+  double* tmp = nullptr;
+  if (h->op.b_kind == 1 && h->op.ntaps == 0) {
+    bltt_status s = ensure_workspace(h);
+    if (s != BLTT_OK) return s;
+    tmp = vec(h, 9);
+  }
+  CK(h, launch_matvec(h->op, 0, x, nullptr, y, flip ? 1 : 0, MV_STORE, nullptr, nullptr, nullptr,
+                      nullptr, tmp, h->stream), "matvec");
+  return BLTT_OK;
+}
+
+bltt_status bltt_precond_apply(bltt_handle h, double alpha, const double* v, double* z,
+                               int precision) {
+  if (!h) return BLTT_ERR_INVALID_ARG;
+  if (!v || !z) return fail(h, BLTT_ERR_INVALID_ARG, "null vector");
+  if (!(alpha > 0.0 && alpha <= 1.0)) return fail(h, BLTT_ERR_INVALID_ARG, "alpha must lie in (0, 1]");
+  if (precision != 64 && precision != 32) return fail(h, BLTT_ERR_INVALID_ARG, "precision must be 64 or 32");
+  bltt_status s = prepare_precond(h, alpha, precision);
+  if (s != BLTT_OK) return s;
+  PrecTables pt = prec_tables(h, 0);
+  Combine c{};
+  c.in0 = v;
+  return precond_chain(h, 0, precision, pt, c, z, nullptr, nullptr, nullptr, nullptr);
+}
+
+bltt_status bltt_minres_solve_ex(bltt_handle h, const double* f, double alpha, double tol,
+                                 int maxit, const bltt_solve_opts* opts, double* u,
+                                 bltt_solve_info* info) {
+  if (!h) return BLTT_ERR_INVALID_ARG;
+  if (info) { std::memset(info, 0, sizeof *info); info->status = BLTT_ERR_INVALID_ARG; }
+  if (!f || !u) return fail(h, BLTT_ERR_INVALID_ARG, "null vector");
+  if (f == u) return fail(h, BLTT_ERR_INVALID_ARG, "u must not alias f");
+  bltt_solve_opts o{};
+  if (opts) o = *opts;
+  if (o.precision == 0) o.precision = 64;
+  if (o.precision != 64 && o.precision != 32) return fail(h, BLTT_ERR_INVALID_ARG, "precision must be 64 or 32");
+  if (o.precond != BLTT_PRECOND_ABAC && o.precond != BLTT_PRECOND_NONE) return fail(h, BLTT_ERR_INVALID_ARG, "bad precond");
+  const bool none = (o.precond == BLTT_PRECOND_NONE);
+  if (!none && !(alpha > 0.0 && alpha <= 1.0)) return fail(h, BLTT_ERR_INVALID_ARG, "alpha must lie in (0, 1]");
+  if (!(tol >= 0.0) || maxit < 1) return fail(h, BLTT_ERR_INVALID_ARG, "tol must be >= 0 and maxit >= 1");
+  int basis = o.basis;
+  if (basis == BLTT_BASIS_AUTO) basis = (o.precision == 64) ? BLTT_BASIS_SPECTRAL : BLTT_BASIS_PHYSICAL;
+  if (basis != BLTT_BASIS_SPECTRAL && basis != BLTT_BASIS_PHYSICAL) return fail(h, BLTT_ERR_INVALID_ARG, "bad basis");
+  const int spectral = (basis == BLTT_BASIS_SPECTRAL) ? 1 : 0;
+  const int sync_every = o.sync_every > 0 ? o.sync_every : 2;
+
+  bltt_status s = ensure_workspace(h);
+  if (s != BLTT_OK) return s;
+  h->launches = 0;
+  const OpTables& op = h->op;
+  cudaStream_t st = h->stream;
+  CK(h, cudaEventRecord(h->ev[0], st), "event");
+  if (!none) {
+    s = prepare_precond(h, alpha, o.precision);
+    if (s != BLTT_OK) return s;
+  }
+  CK(h, cudaEventRecord(h->ev[1], st), "event");
+  PrecTables pt = prec_tables(h, none ? 1 : 0);
+
+  double* bvec = vec(h, 0);
+  double* vbuf[2] = {vec(h, 1), vec(h, 2)};
+  double* zbuf[2] = {vec(h, 3), vec(h, 4)};
+  double* wbuf[2] = {vec(h, 5), vec(h, 6)};
+  double* q = vec(h, 7);
+  double* x = spectral ? vec(h, 8) : u;
+  double* tmp = vec(h, 9);
+  const long long n = h->n;
+
+  // state: tol, maxit
+  MinresDev* sh = h->state_host;
+  std::memset(sh, 0, sizeof *sh);
+  sh->tol = tol;
+  sh->maxit = maxit;
+  sh->phase = PH_RUN;
+  CK(h, cudaMemcpyAsync(h->state, sh, sizeof *sh, cudaMemcpyHostToDevice, st), "state upload");
+  int* phase = &h->state->phase;
+
+  // b = Y f (spectral: Y (I (x) U) f) with ||b||^2
+  int nb = 0, nzv = 0, np = 0;
+  if (spectral) {
+    s = dst_all(h, f, bvec, 1, h->partials[1], &nb);
+    if (s != BLTT_OK) return s;
+  } else {
+    CK(h, launch_flip_copy(f, bvec, h->N, h->M, h->partials[1], &nb, st), "flip");
+    h->launches++;
+  }
+  const int cur0 = 0;
+  int cur = cur0;
+  // v_1 = b (copied into vbuf[cur]), z_1 = P^{-1} v_1, <z_1, v_1>
+  {
+    Combine c{};
+    c.in0 = bvec;
+    c.vout = vbuf[cur];
+    s = precond_chain(h, spectral, o.precision, pt, c, zbuf[cur], vbuf[cur], h->partials[0], &nzv, nullptr);
+    if (s != BLTT_OK) return s;
+  }
+  CK(h, cudaMemsetAsync(x, 0, n * sizeof(double), st), "memset x");
+  CK(h, cudaMemsetAsync(vbuf[1 - cur], 0, n * sizeof(double), st), "memset v0");
+  CK(h, cudaMemsetAsync(wbuf[0], 0, n * sizeof(double), st), "memset w0");
+  CK(h, cudaMemsetAsync(wbuf[1], 0, n * sizeof(double), st), "memset w1");
+  CK(h, launch_scalar_init(h->state, h->partials[0], nzv, h->partials[1], nb, st), "scalar init");
+  h->launches++;
+
+  int issued = 0;
+  for (;;) {
+    const int prv = 1 - cur;
+    // q = Y A z_j  (z_j = z_u / gamma_j), delta_j = <q, z_j>
+    CK(h, launch_matvec(op, spectral, zbuf[cur], &h->state->inv_gamma, q, 1, MV_STORE, nullptr,
+                        h->partials[0], &np, phase, tmp, st), "matvec");
+    h->launches += (op.b_kind == 1 && op.ntaps == 0 && !spectral) ? 2 : 1;
+    CK(h, launch_scalar_delta(h->state, h->partials[0], np, st), "scalar delta");
+    h->launches++;
+    // v_{j+1} = q - (delta/gamma) v_j - (gamma/gamma_prev) v_{j-1} (over v_{j-1});
+    // z_{j+1} = P^{-1} v_{j+1} (over z_{j-1}); <z_{j+1}, v_{j+1}>
+    {
+      Combine c{};
+      c.in0 = q; c.in1 = vbuf[cur]; c.in2 = vbuf[prv];
+      c.coef = h->state->coef; c.vout = vbuf[prv];
+      s = precond_chain(h, spectral, o.precision, pt, c, zbuf[prv], vbuf[prv], h->partials[1], &np, phase);
+      if (s != BLTT_OK) return s;
+    }
+    CK(h, launch_scalar_gamma(h->state, h->partials[1], np, st), "scalar gamma");
+    h->launches++;
+    CK(h, launch_w_update(h->state, zbuf[cur], wbuf[prv], wbuf[cur], x, n, st), "w update");
+    h->launches++;
+    // true residual when the estimate says so
+    CK(h, launch_matvec(op, spectral, x, nullptr, nullptr, 1, MV_RESID, bvec, h->partials[0], &np,
+                        phase, tmp, st), "residual");
+    h->launches += (op.b_kind == 1 && op.ntaps == 0 && !spectral) ? 2 : 1;
+    CK(h, launch_scalar_check(h->state, h->partials[0], np, st), "scalar check");
+    h->launches++;
+    std::swap(vbuf[0], vbuf[1]);
+    std::swap(zbuf[0], zbuf[1]);
+    std::swap(wbuf[0], wbuf[1]);
+    ++issued;
+    if (issued % sync_every == 0 || issued >= maxit) {
+      CK(h, cudaMemcpyAsync(sh, h->state, sizeof *sh, cudaMemcpyDeviceToHost, st), "state download");
+      CK(h, cudaStreamSynchronize(st), "sync");
+      if (sh->phase != PH_RUN || issued >= maxit) break;
+    }
+  }
+  double relres_phys = sh->relres_true;
+  if (spectral) {
+    // u = (I (x) U) x_hat, then ||f - A u|| / ||f|| in the physical basis
+    s = dst_all(h, x, u, 0, nullptr, nullptr);
+    if (s != BLTT_OK) return s;
+    int nr = 0;
+    CK(h, launch_matvec(op, 0, u, nullptr, nullptr, 0, MV_RESID, f, h->partials[0], &nr, nullptr,
+                        tmp, st), "final residual");
+    h->launches += (op.b_kind == 1 && op.ntaps == 0) ? 2 : 1;
+    CK(h, launch_sum_partials(h->partials[0], nr, h->scal, st), "sum");
+    h->launches++;
+    CK(h, cudaMemcpyAsync(h->scal_host, h->scal, sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
+  }
+  CK(h, cudaEventRecord(h->ev[2], st), "event");
+  CK(h, cudaStreamSynchronize(st), "sync");
+  if (spectral && sh->normb > 0) relres_phys = std::sqrt(h->scal_host[0]) / sh->normb;
+  float t_all = 0.f, t_setup = 0.f;
+  cudaEventElapsedTime(&t_all, h->ev[0], h->ev[2]);
+  cudaEventElapsedTime(&t_setup, h->ev[0], h->ev[1]);
+  bltt_status result;
+  if (sh->phase == PH_DONE) result = (sh->status == 0) ? BLTT_OK : BLTT_ERR_NOT_CONVERGED;
+  else if (sh->phase == PH_FAIL) result = BLTT_ERR_NUMERIC;
+  else result = BLTT_ERR_NOT_CONVERGED;
+  if (info) {
+    info->iters = sh->iter;
+    info->relres_est = sh->relres_est;
+    info->relres_true = relres_phys;
+    info->alpha_used = none ? 0.0 : alpha;
+    info->alpha_source = 0;
+    info->precision = o.precision;
+    info->basis = basis;
+    info->t_setup_ms = t_setup;
+    info->t_solve_ms = t_all;
+    info->kernel_launches = h->launches;
+    info->status = result;
+  }
+  if (result == BLTT_ERR_NUMERIC) h->err = "MINRES breakdown: <z, v> negative or non-finite";
+  else if (result == BLTT_ERR_NOT_CONVERGED) h->err = "maxit reached before the stopping rule held";
+  return result;
+}
+
+bltt_status bltt_minres_solve(bltt_handle h, const double* f, double alpha, double tol, int maxit,
+                              int precision, double* u, bltt_solve_info* info) {
+  bltt_solve_opts o{};
+  o.precision = precision;
+  return bltt_minres_solve_ex(h, f, alpha, tol, maxit, &o, u, info);
+}
+
+}  // extern "C"

@@ -1,0 +1,97 @@
+// internal.h - declarations shared by the libbltt translation units (host side).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bltt {
+
+constexpr int kThreads = 512;      // threads of every FFT tile kernel
+constexpr int kCap = 8192;         // complex points per FFT tile (128 KB of FP64 smem)
+constexpr int kMaxPartials = 1 << 20;
+
+// MINRES scalar state, resident on the device for the whole solve.
+enum Phase { PH_RUN = 0, PH_CHECK = 1, PH_DONE = 2, PH_FAIL = 3, PH_MAXIT = 4 };
+
+struct MinresDev {
+  double gamma, gamma_prev, delta, eta, eta0;
+  double s, s_prev, c, c_prev;
+  double inv_gamma;      // 1/gamma_j: normalises z_j where the matvec reads it
+  double coef[3];        // v_{j+1} = coef0 q + coef1 v_j + coef2 v_{j-1}
+  double w_inv_gamma;    // 1/gamma_j for the w update of iteration j
+  double w_a1inv, w_a2, w_a3, w_ceta;
+  double normb, relres_est, relres_true, tol;
+  double gamma_new;
+  int iter, maxit, phase, status, wpending, pad;
+};
+
+// Operator data handed to the kernels (device pointers).
+struct OpTables {
+  int N, log2N, d, m[3];
+  long long M;
+  double h2inv[3];            // 1/h^2 per axis
+  const double* mu_axis[3];   // per-axis eigenvalues of L (device, length m[ax])
+  const float* mu_axis32[3];
+  // matvec: Ahat, Bhat = FFT_2N([a;0]), FFT_2N([b;0]) scaled by 1/(2N), k = 0..N (device)
+  const double2* Ahat;
+  const double2* Bhat;
+  int b_kind;                 // 0: b = b0 e_0; 1: general b
+  double b0;
+  int ntaps;                  // >0: a and b vanish beyond ntaps (direct matvec), else FFT matvec
+  const double* a_dev;        // a, b (device, length N) for the direct matvec
+  const double* b_dev;
+  const double2* tw_2N;       // twiddles for length 2N
+  const double2* tw_N;
+  const float2* tw_N32;
+  const double2* tw_dst[3];   // twiddles for length 2(m_ax+1)
+  const float2* tw_dst32[3];
+};
+
+// Per-alpha preconditioner data.
+struct PrecTables {
+  double alpha;
+  const double* dinv;    // 1/d_j, d_j = alpha^{j/N}
+  const double* d2;      // d_j^2
+  const double2* g64;    // [(N/2+1)][M]: lambda^{-1/2}/(2N), FP64 form
+  const float2* ahat32;  // [N/2+1]: FFT_N(D a), FP32 form
+  const float2* bhat32;
+  int none;              // 1: identity preconditioner (MINRES-I)
+};
+
+// A fused "v = c0*in0 + c1*in1 + c2*in2" load (coefficients from device memory).
+struct Combine {
+  const double* in0;
+  const double* in1;     // may be null
+  const double* in2;     // may be null
+  const double* coef;    // device, 3 doubles; null means (1, 0, 0)
+  double* vout;          // if set, the combined value is stored here
+};
+
+// launchers (kernels.cu); all return cudaGetLastError()
+cudaError_t launch_dst(const OpTables& op, int axis, int prec, const Combine& in, double* out,
+                       int flip, const double* dot_with, double* partials, int* nparts,
+                       const int* phase, cudaStream_t st);
+cudaError_t launch_timepass(const OpTables& op, const PrecTables& pt, int prec, const Combine& in,
+                            double* out, const double* dot_with, double* partials, int* nparts,
+                            const int* phase, cudaStream_t st);
+// matvec modes
+enum MvMode { MV_STORE = 0, MV_RESID = 1 };
+cudaError_t launch_matvec(const OpTables& op, int spectral, const double* x, const double* xscale,
+                          double* y, int flip, int mode, const double* rhs, double* partials,
+                          int* nparts, const int* phase, double* tmp, cudaStream_t st);
+cudaError_t launch_setup_g64(const OpTables& op, const double2* ahat, const double2* bhat,
+                             double2* g64, cudaStream_t st);
+cudaError_t launch_flip_copy(const double* f, double* b, int N, long long M, double* partials,
+                             int* nparts, cudaStream_t st);
+cudaError_t launch_scalar_init(MinresDev* s, const double* partials_zv, int nzv,
+                               const double* partials_b, int nb, cudaStream_t st);
+cudaError_t launch_scalar_delta(MinresDev* s, const double* partials, int np, cudaStream_t st);
+cudaError_t launch_scalar_gamma(MinresDev* s, const double* partials, int np, cudaStream_t st);
+cudaError_t launch_scalar_check(MinresDev* s, const double* partials, int np, cudaStream_t st);
+cudaError_t launch_w_update(MinresDev* s, const double* z, double* w_prev, const double* w,
+                            double* x, long long n, cudaStream_t st);
+cudaError_t launch_copy_scaled_check(const double* src, double* dst, long long n, cudaStream_t st);
+cudaError_t launch_sum_partials(const double* partials, int np, double* out, cudaStream_t st);
+
+int tile_columns(long long nlines, int Lfft);   // complex columns per tile for a line batch
+
+}  // namespace bltt

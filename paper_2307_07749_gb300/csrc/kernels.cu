@@ -1,0 +1,735 @@
+// kernels.cu - sm_103a kernels of libbltt: DST-I along a spatial axis, the alpha-scaled time pass
+// of the ABAC preconditioner, the BLTT matvec (2N circulant embedding or direct taps), the
+// preconditioner set-up and the MINRES vector/scalar kernels.
+#include <math.h>
+#include "common.cuh"
+#include "internal.h"
+
+namespace bltt {
+
+// ============================================================================================
+// helpers
+__device__ __forceinline__ bool skip_phase(const int* phase, int want) {
+  return phase != nullptr && *phase != want;
+}
+
+__device__ __forceinline__ void load_coef(const Combine& cb, double& c0, double& c1, double& c2) {
+  if (cb.coef) { c0 = cb.coef[0]; c1 = cb.coef[1]; c2 = cb.coef[2]; }
+  else { c0 = 1.0; c1 = 0.0; c2 = 0.0; }
+}
+
+// v = c0 in0[e] + c1 in1[e] + c2 in2[e]; optionally stored to vout[e] (vout may alias in1/in2:
+// the same thread reads before it writes).
+__device__ __forceinline__ double combine_at(const Combine& cb, long long e, double c0, double c1,
+                                             double c2) {
+  double v = c0 * cb.in0[e];
+  if (cb.in1) v = fma(c1, cb.in1[e], v);
+  if (cb.in2) v = fma(c2, cb.in2[e], v);
+  if (cb.vout) cb.vout[e] = v;
+  return v;
+}
+
+// eigenvalue of L for spatial mode i (x fastest): sum over axes of the 1-D eigenvalues
+__device__ __forceinline__ double mode_mu(const OpTables& op, long long i) {
+  long long r = i / op.m[0];
+  double mu = op.mu_axis[0][i - r * op.m[0]];
+  if (op.d > 1) {
+    long long r2 = r / op.m[1];
+    mu += op.mu_axis[1][r - r2 * op.m[1]];
+    if (op.d > 2) mu += op.mu_axis[2][r2];
+  }
+  return mu;
+}
+__device__ __forceinline__ float mode_mu32(const OpTables& op, long long i) {
+  long long r = i / op.m[0];
+  float mu = op.mu_axis32[0][i - r * op.m[0]];
+  if (op.d > 1) {
+    long long r2 = r / op.m[1];
+    mu += op.mu_axis32[1][r - r2 * op.m[1]];
+    if (op.d > 2) mu += op.mu_axis32[2][r2];
+  }
+  return mu;
+}
+
+// (L x)[i] on the time slice starting at x_t: the 2d+1 point Dirichlet stencil (Sec. 5.2)
+__device__ __forceinline__ double stencil_at(const OpTables& op, const double* __restrict__ x_t,
+                                             long long i) {
+  const double xi = x_t[i];
+  double acc = 0.0;
+  long long r = i, stride = 1;
+#pragma unroll 1
+  for (int ax = 0; ax < op.d; ++ax) {
+    const int mm = op.m[ax];
+    long long q = r / mm;
+    int c = (int)(r - q * mm);
+    r = q;
+    double s = 2.0 * xi;
+    if (c > 0) s -= x_t[i - stride];
+    if (c < mm - 1) s -= x_t[i + stride];
+    acc = fma(s, op.h2inv[ax], acc);
+    stride *= mm;
+  }
+  return acc;
+}
+
+// principal (x + i y)^{-1/2} for x > 0, by the half-angle form of the square root:
+// sqrt(z) = s + i y/(2s), s = sqrt((|z| + x)/2), and 1/sqrt(z) = conj(sqrt(z)) / |z|.
+template <typename T>
+__device__ __forceinline__ C<T> inv_sqrt_principal(T x, T y) {
+  T r = hypot(x, y);
+  T s = sqrt(T(0.5) * (r + x));
+  T t = y / (T(2) * s);
+  T ir = T(1) / r;
+  return mk<T>(s * ir, -t * ir);
+}
+
+template <typename K>
+static cudaError_t set_smem(K kern, size_t bytes) {
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+int tile_columns(long long nlines, int Lfft) {
+  int nc = kCap / Lfft;
+  if (nc < 1) nc = 1;
+  long long pairs = (nlines + 1) / 2;
+  while (nc > 1 && (pairs + nc - 1) / nc < 2 * 152) nc >>= 1;
+  return nc;
+}
+
+static int ilog2(long long v) { int l = 0; while ((1LL << l) < v) ++l; return l; }
+
+// ============================================================================================
+// DST-I along one spatial axis (Steps 1 and 3 of Sec. 5.1).  Two real lines x_a, x_b share one
+// complex FFT of length 2P (P = m+1) of their odd extensions [0, x, 0, -rev(x)]; then
+// S x_a = -Im(Z_{k+1}) / sqrt(2P) and S x_b = Re(Z_{k+1}) / sqrt(2P), S the normalised DST-I.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_dst(Lines ln, int P, int log2L, int NC, Combine cb, double* out, int flip, int N, long long M,
+      const double* dot_with, double* partials, const C<T>* __restrict__ tw, const int* phase,
+      int want) {
+  if (skip_phase(phase, want)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
+  T* bufs = reinterpret_cast<T*>(smem_raw);
+  __shared__ double red[32];
+  const int L = 2 * P, m = ln.len, W = 2 * NC;
+  const long long g0 = (long long)blockIdx.x * W;
+  double c0, c1, c2;
+  load_coef(cb, c0, c1, c2);
+  const bool contiguous = (ln.inner == 1);
+  const int total = m * W;
+  for (int e = threadIdx.x; e < total; e += kThreads) {
+    int c, p;
+    if (contiguous) { c = e / m; p = e - c * m; } else { p = e / W; c = e - p * W; }
+    long long g = g0 + c;
+    T val = T(0);
+    if (g < ln.nlines) val = (T)combine_at(cb, ln.base(g) + (long long)p * ln.inner, c0, c1, c2);
+    const int cc = c >> 1, comp = c & 1;
+    bufs[((p + 1) * NC + cc) * 2 + comp] = val;
+    bufs[((L - 1 - p) * NC + cc) * 2 + comp] = -val;
+  }
+  for (int e = threadIdx.x; e < 2 * NC; e += kThreads) {
+    const int cc = e >> 1, which = e & 1;
+    buf[(which ? P : 0) * NC + cc] = mk<T>(T(0), T(0));
+  }
+  __syncthreads();
+  fft_columns<T, kThreads, kCap, false>(buf, L, log2L, NC, tw);
+  const double scale = rsqrt((double)L);
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < total; e += kThreads) {
+    int c, k;
+    if (contiguous) { c = e / m; k = e - c * m; } else { k = e / W; c = e - k * W; }
+    long long g = g0 + c;
+    if (g < ln.nlines) {
+      C<T> z = buf[(k + 1) * NC + (c >> 1)];
+      double val = ((c & 1) ? (double)z.x : -(double)z.y) * scale;
+      long long idx = ln.base(g) + (long long)k * ln.inner;
+      if (flip) {
+        long long t = idx / M;
+        idx += (long long)(N - 1 - 2 * t) * M;
+      }
+      out[idx] = val;
+      if (dot_with) acc = fma(val, dot_with[idx], acc);
+    }
+  }
+  if (partials) {
+    double s = block_sum<kThreads>(acc, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  }
+}
+
+// ============================================================================================
+// Time pass of P_alpha^{-1} for a tile of 2*NC spatial modes (Step 2 and its second half,
+// Sec. 5.1): per mode, s1 = v/d, s2 = F conj(Lambda)^{-1/2} F^* s1, s3 = d^2 s2,
+// s4 = F Lambda^{-1/2} F^* s3, z = s4/d.  Two real modes share one complex FFT of length N; the
+// per-mode spectra are split and re-merged in the frequency domain (Lemma 3.1 makes each mode's
+// spectrum conjugate-symmetric, so both inverse transforms are real).
+
+// G for the modes ia, ia+1 at frequency k: lambda^{-1/2}/(2N), lambda = ahat_k + bhat_k mu_i
+template <typename T> struct GSrc;
+template <> struct GSrc<double> {
+  static __device__ __forceinline__ C<double> get(const OpTables& op, const PrecTables& pt, int k,
+                                                 long long i) {
+    return pt.g64[(long long)k * op.M + i];
+  }
+};
+template <> struct GSrc<float> {
+  static __device__ __forceinline__ C<float> get(const OpTables& op, const PrecTables& pt, int k,
+                                                long long i) {
+    float mu = mode_mu32(op, i);
+    float2 a = pt.ahat32[k], b = pt.bhat32[k];
+    C<float> g = inv_sqrt_principal<float>(fmaf(b.x, mu, a.x), fmaf(b.y, mu, a.y));
+    const float sc = 0.5f / (float)op.N;
+    return mk<float>(g.x * sc, g.y * sc);
+  }
+};
+
+template <typename T, bool CONJ>
+__device__ __forceinline__ void tp_freq_mul(C<T>* buf, const OpTables& op, const PrecTables& pt,
+                                            int NC, long long g0) {
+  const int N = op.N, half = N >> 1;
+  const int items = NC * (half + 1);
+  for (int it = threadIdx.x; it < items; it += kThreads) {
+    const int cc = it % NC, k = it / NC;
+    const long long ia = g0 + 2 * cc, ib = ia + 1;
+    C<T> Ga = mk<T>(T(0), T(0)), Gb = Ga;
+    if (ia < op.M) Ga = GSrc<T>::get(op, pt, k, ia);
+    if (ib < op.M) Gb = GSrc<T>::get(op, pt, k, ib);
+    if (CONJ) { Ga = cconj<T>(Ga); Gb = cconj<T>(Gb); }
+    const int kb = (N - k) & (N - 1);
+    C<T> A = buf[k * NC + cc], B = buf[kb * NC + cc];
+    C<T> Bc = cconj<T>(B);
+    C<T> U1 = cmul<T>(Ga, cadd<T>(A, Bc));
+    C<T> U2 = cmul<T>(Gb, csub<T>(A, Bc));
+    buf[k * NC + cc] = cadd<T>(U1, U2);
+    if (kb != k) buf[kb * NC + cc] = cconj<T>(csub<T>(U1, U2));
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_timepass(OpTables op, PrecTables pt, Combine cb, double* out, const double* dot_with,
+           double* partials, const int* phase, int want, int NC) {
+  if (skip_phase(phase, want)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
+  T* bufs = reinterpret_cast<T*>(smem_raw);
+  __shared__ double red[32];
+  const int N = op.N, W = 2 * NC;
+  const long long M = op.M;
+  const long long g0 = (long long)blockIdx.x * W;
+  const C<T>* tw = reinterpret_cast<const C<T>*>(sizeof(T) == 8 ? (const void*)op.tw_N
+                                                                 : (const void*)op.tw_N32);
+  double c0, c1, c2;
+  load_coef(cb, c0, c1, c2);
+  const int total = N * W;
+  for (int e = threadIdx.x; e < total; e += kThreads) {
+    const int p = e / W, c = e - p * W;
+    const long long i = g0 + c;
+    T val = T(0);
+    if (i < M) val = (T)(combine_at(cb, (long long)p * M + i, c0, c1, c2) * pt.dinv[p]);
+    bufs[(p * NC + (c >> 1)) * 2 + (c & 1)] = val;
+  }
+  __syncthreads();
+  fft_columns<T, kThreads, kCap, false>(buf, N, op.log2N, NC, tw);
+  tp_freq_mul<T, true>(buf, op, pt, NC, g0);
+  __syncthreads();
+  fft_columns<T, kThreads, kCap, true>(buf, N, op.log2N, NC, tw);
+  for (int e = threadIdx.x; e < N * NC; e += kThreads) {
+    const int p = e / NC;
+    const T s = (T)pt.d2[p];
+    C<T> v = buf[e];
+    buf[e] = mk<T>(v.x * s, v.y * s);
+  }
+  __syncthreads();
+  fft_columns<T, kThreads, kCap, false>(buf, N, op.log2N, NC, tw);
+  tp_freq_mul<T, false>(buf, op, pt, NC, g0);
+  __syncthreads();
+  fft_columns<T, kThreads, kCap, true>(buf, N, op.log2N, NC, tw);
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < total; e += kThreads) {
+    const int p = e / W, c = e - p * W;
+    const long long i = g0 + c;
+    if (i < M) {
+      const long long idx = (long long)p * M + i;
+      const double z = (double)bufs[(p * NC + (c >> 1)) * 2 + (c & 1)] * pt.dinv[p];
+      out[idx] = z;
+      if (dot_with) acc = fma(z, dot_with[idx], acc);
+    }
+  }
+  if (partials) {
+    double s = block_sum<kThreads>(acc, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  }
+}
+
+// identity preconditioner (MINRES-I): z = v, with the same fused load and dot
+__global__ void k_precond_identity(Combine cb, double* out, long long n, const double* dot_with,
+                                   double* partials, const int* phase, int want) {
+  if (skip_phase(phase, want)) return;
+  __shared__ double red[32];
+  double c0, c1, c2;
+  load_coef(cb, c0, c1, c2);
+  double acc = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    double v = combine_at(cb, e, c0, c1, c2);
+    out[e] = v;
+    if (dot_with) acc = fma(v, dot_with[e], acc);
+  }
+  if (partials) {
+    double s = block_sum<256>(acc, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  }
+}
+
+// ============================================================================================
+// BLTT matvec along time by the 2N zero-padded circulant embedding (Sec. 5.1): per spatial point,
+// y = first N entries of IFFT_2N(H .* FFT_2N([x; 0])), H = FFT_2N([a; 0]) (+ mu_i FFT_2N([b;0]) in
+// the spectral basis).  Two real columns share one complex FFT.  The flip Y, the b_0 L (or b_0 mu)
+// term, the normalisation of x and the dot product / residual are fused into load and store.
+//   spectral: 1 -> lines are DST modes (matvec of (I (x) U) A (I (x) U)), 0 -> physical points.
+//   which:    0 -> y = conv_a + extra term; 1 -> y = conv_b only (physical general-b first pass).
+//   st_src:   source of the physical stencil term (x itself when b = b0 e_0, else conv_b(x)).
+__global__ void __launch_bounds__(kThreads)
+k_conv(OpTables op, int spectral, int which, const double* x, const double* xscale, double* y,
+       int flip, int mode, const double* rhs, double* partials, const int* phase, int want,
+       const double* st_src, int NC) {
+  if (skip_phase(phase, want)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* buf = reinterpret_cast<double2*>(smem_raw);
+  double* bufs = reinterpret_cast<double*>(smem_raw);
+  __shared__ double red[32];
+  const int N = op.N, L = 2 * N, W = 2 * NC;
+  const long long M = op.M;
+  const long long g0 = (long long)blockIdx.x * W;
+  const double s = xscale ? *xscale : 1.0;
+  const int total = N * W;
+  for (int e = threadIdx.x; e < total; e += kThreads) {
+    const int p = e / W, c = e - p * W;
+    const long long i = g0 + c;
+    double val = 0.0;
+    if (i < M) val = x[(long long)p * M + i] * s;
+    bufs[(p * NC + (c >> 1)) * 2 + (c & 1)] = val;
+  }
+  for (int e = threadIdx.x; e < N * NC; e += kThreads) buf[N * NC + e] = make_double2(0.0, 0.0);
+  __syncthreads();
+  fft_columns<double, kThreads, kCap, false>(buf, L, op.log2N + 1, NC, op.tw_2N);
+  const bool split = spectral && op.b_kind == 1;
+  if (!split) {
+    const double2* H = which ? op.Bhat : op.Ahat;
+    for (int e = threadIdx.x; e < L * NC; e += kThreads) {
+      const int k = e / NC;
+      double2 h = (k <= N) ? H[k] : cconj<double>(H[L - k]);
+      buf[e] = cmul<double>(buf[e], h);
+    }
+  } else {
+    // per-mode H_i = Ahat + mu_i Bhat; split the packed spectra (extra factor 1/2)
+    const int items = NC * (N + 1);
+    for (int it = threadIdx.x; it < items; it += kThreads) {
+      const int cc = it % NC, k = it / NC;
+      const long long ia = g0 + 2 * cc, ib = ia + 1;
+      const double mua = ia < M ? mode_mu(op, ia) : 0.0, mub = ib < M ? mode_mu(op, ib) : 0.0;
+      const double2 A_ = op.Ahat[k], B_ = op.Bhat[k];
+      double2 Ha = make_double2(0.5 * fma(mua, B_.x, A_.x), 0.5 * fma(mua, B_.y, A_.y));
+      double2 Hb = make_double2(0.5 * fma(mub, B_.x, A_.x), 0.5 * fma(mub, B_.y, A_.y));
+      const int kb = (L - k) & (L - 1);
+      double2 Av = buf[k * NC + cc], Bv = buf[kb * NC + cc];
+      double2 Bc = cconj<double>(Bv);
+      double2 U1 = cmul<double>(Ha, cadd<double>(Av, Bc));
+      double2 U2 = cmul<double>(Hb, csub<double>(Av, Bc));
+      buf[k * NC + cc] = cadd<double>(U1, U2);
+      if (kb != k) buf[kb * NC + cc] = cconj<double>(csub<double>(U1, U2));
+    }
+  }
+  __syncthreads();
+  fft_columns<double, kThreads, kCap, true>(buf, L, op.log2N + 1, NC, op.tw_2N);
+  double acc = 0.0;
+  const bool extra_mu = spectral && op.b_kind == 0 && which == 0;
+  const bool extra_st = !spectral && which == 0 && st_src != nullptr;
+  const double st_coef = (op.b_kind == 0) ? op.b0 * s : 1.0;
+  for (int e = threadIdx.x; e < total; e += kThreads) {
+    const int t = e / W, c = e - t * W;
+    const long long i = g0 + c;
+    if (i >= M) continue;
+    double val = bufs[(t * NC + (c >> 1)) * 2 + (c & 1)];
+    if (extra_mu) val = fma(op.b0 * mode_mu(op, i), x[(long long)t * M + i] * s, val);
+    if (extra_st) val = fma(st_coef, stencil_at(op, st_src + (long long)t * M, i), val);
+    const int to = flip ? (N - 1 - t) : t;
+    const long long idx = (long long)to * M + i;
+    if (mode == MV_STORE) {
+      y[idx] = val;
+      if (partials) acc = fma(val, x[idx] * s, acc);
+    } else {
+      const double r = rhs[idx] - val;
+      if (y) y[idx] = r;
+      acc = fma(r, r, acc);
+    }
+  }
+  if (partials) {
+    double sum = block_sum<kThreads>(acc, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = sum;
+  }
+}
+
+// Direct matvec for blocks that vanish beyond ntaps (heat BDF / CN): y_t = sum_{k<ntaps}
+// (a_k x_{t-k} + b_k [mu_i | L] x_{t-k}), same fused epilogues as k_conv.
+__global__ void __launch_bounds__(256)
+k_direct(OpTables op, int spectral, const double* x, const double* xscale, double* y, int flip,
+         int mode, const double* rhs, double* partials, const int* phase, int want) {
+  if (skip_phase(phase, want)) return;
+  __shared__ double red[32];
+  const int N = op.N, K = op.ntaps;
+  const long long M = op.M, n = (long long)N * M;
+  const double s = xscale ? *xscale : 1.0;
+  double acc = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int t = (int)(e / M);
+    const long long i = e - (long long)t * M;
+    const double mu = spectral ? mode_mu(op, i) : 0.0;
+    double val = 0.0;
+    for (int k = 0; k < K && k <= t; ++k) {
+      const double ak = op.a_dev[k], bk = op.b_dev[k];
+      const long long base = (long long)(t - k) * M;
+      if (ak != 0.0) val = fma(ak, x[base + i], val);
+      if (bk != 0.0) val = fma(bk, spectral ? mu * x[base + i] : stencil_at(op, x + base, i), val);
+    }
+    val *= s;
+    const int to = flip ? (N - 1 - t) : t;
+    const long long idx = (long long)to * M + i;
+    if (mode == MV_STORE) {
+      y[idx] = val;
+      if (partials) acc = fma(val, x[idx] * s, acc);
+    } else {
+      const double r = rhs[idx] - val;
+      if (y) y[idx] = r;
+      acc = fma(r, r, acc);
+    }
+  }
+  if (partials) {
+    double sum = block_sum<256>(acc, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = sum;
+  }
+}
+
+// physical general-b second pass: y += L tmp (only used when b has more than one nonzero and the
+// FFT matvec is chosen; the stencil term is then folded in by k_conv with st_src = tmp)
+
+// ============================================================================================
+// Set-up of the FP64 time-pass table: g(k, i) = lambda_i(k)^{-1/2} / (2N), k = 0..N/2, with
+// lambda_i(k) = ahat_k + bhat_k mu_i the eigenvalues of eq. hatcalphaieigvaldef (principal branch,
+// Def. 2; Re lambda > 0 by diagonal dominance, Sec. 3).
+__global__ void k_setup_g64(OpTables op, const double2* ahat, const double2* bhat, double2* g) {
+  const int half = op.N / 2;
+  const long long total = (long long)(half + 1) * op.M;
+  const double sc = 0.5 / op.N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e / op.M);
+    const long long i = e - (long long)k * op.M;
+    const double mu = mode_mu(op, i);
+    const double2 a = ahat[k], b = bhat[k];
+    double2 v = inv_sqrt_principal<double>(fma(b.x, mu, a.x), fma(b.y, mu, a.y));
+    g[e] = make_double2(v.x * sc, v.y * sc);
+  }
+}
+
+// b = Y f (time reversal, Sec. 2) and partial sums of ||b||^2
+__global__ void k_flip_copy(const double* f, double* b, int N, long long M, double* partials) {
+  __shared__ double red[32];
+  const long long n = (long long)N * M;
+  double acc = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int t = (int)(e / M);
+    const long long i = e - (long long)t * M;
+    const double v = f[(long long)(N - 1 - t) * M + i];
+    b[e] = v;
+    acc = fma(v, v, acc);
+  }
+  double s = block_sum<256>(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// ============================================================================================
+// MINRES scalar recurrences (one block; partial sums reduced in a fixed order)
+__device__ double reduce_partials(const double* p, int n, double* scratch) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) acc += p[i];
+  return block_sum<256>(acc, scratch);
+}
+
+__global__ void __launch_bounds__(256) k_scalar_init(MinresDev* st, const double* pzv, int nzv,
+                                                     const double* pb, int nb) {
+  __shared__ double red[32];
+  double g2 = reduce_partials(pzv, nzv, red);
+  __syncthreads();
+  double nb2 = reduce_partials(pb, nb, red);
+  if (threadIdx.x != 0) return;
+  st->normb = sqrt(nb2);
+  st->iter = 0;
+  st->wpending = 0;
+  st->relres_est = 1.0;
+  st->relres_true = 1.0;
+  st->gamma_new = 0.0;
+  if (!(g2 >= 0.0) || !isfinite(g2) || !isfinite(nb2)) {
+    st->phase = PH_FAIL; st->status = 5; return;
+  }
+  const double g = sqrt(g2);
+  st->gamma = g; st->gamma_prev = 1.0; st->eta = g; st->eta0 = g;
+  st->s = 0.0; st->s_prev = 0.0; st->c = 1.0; st->c_prev = 1.0;
+  st->inv_gamma = g > 0.0 ? 1.0 / g : 0.0;
+  st->status = 0;
+  if (g == 0.0) { st->phase = PH_DONE; st->relres_est = 0.0; st->relres_true = 0.0; }
+  else st->phase = PH_RUN;
+}
+
+__global__ void __launch_bounds__(256) k_scalar_delta(MinresDev* st, const double* p, int np) {
+  if (st->phase != PH_RUN) return;
+  __shared__ double red[32];
+  double delta = reduce_partials(p, np, red);
+  if (threadIdx.x != 0) return;
+  if (!isfinite(delta)) { st->phase = PH_FAIL; st->status = 5; return; }
+  st->delta = delta;
+  st->coef[0] = 1.0;
+  st->coef[1] = -delta / st->gamma;
+  st->coef[2] = -st->gamma / st->gamma_prev;
+}
+
+__global__ void __launch_bounds__(256) k_scalar_gamma(MinresDev* st, const double* p, int np) {
+  if (st->phase != PH_RUN) return;
+  __shared__ double red[32];
+  double g2 = reduce_partials(p, np, red);
+  if (threadIdx.x != 0) return;
+  if (!(g2 >= 0.0) || !isfinite(g2)) { st->phase = PH_FAIL; st->status = 5; return; }
+  const double gn = sqrt(g2);
+  const double delta = st->delta, gamma = st->gamma;
+  const double c = st->c, c_prev = st->c_prev, s = st->s, s_prev = st->s_prev;
+  const double a0 = c * delta - c_prev * s * gamma;
+  const double a1 = sqrt(a0 * a0 + gn * gn);
+  const double a2 = s * delta + c_prev * c * gamma;
+  const double a3 = s_prev * gamma;
+  const double cn = a0 / a1, sn = gn / a1;
+  st->w_inv_gamma = st->inv_gamma;
+  st->w_a1inv = 1.0 / a1;
+  st->w_a2 = a2;
+  st->w_a3 = a3;
+  st->w_ceta = cn * st->eta;
+  st->eta = -sn * st->eta;
+  st->gamma_prev = gamma;
+  st->gamma = gn;
+  st->gamma_new = gn;
+  st->inv_gamma = gn > 0.0 ? 1.0 / gn : 0.0;
+  st->s_prev = s; st->s = sn;
+  st->c_prev = c; st->c = cn;
+  st->iter += 1;
+  st->wpending = 1;
+  st->relres_est = fabs(st->eta) / st->eta0;
+  if (gn == 0.0 || st->relres_est <= st->tol || st->iter >= st->maxit) st->phase = PH_CHECK;
+}
+
+__global__ void __launch_bounds__(256) k_scalar_check(MinresDev* st, const double* p, int np) {
+  __shared__ double red[32];
+  const bool check = (st->phase == PH_CHECK);
+  double r2 = check ? reduce_partials(p, np, red) : 0.0;
+  if (threadIdx.x != 0) return;
+  st->wpending = 0;
+  if (!check) return;
+  const double rr = sqrt(r2) / st->normb;
+  st->relres_true = rr;
+  if (!isfinite(rr)) { st->phase = PH_FAIL; st->status = 5; return; }
+  if (rr <= st->tol || st->gamma_new == 0.0) {
+    st->phase = PH_DONE; st->status = (rr <= st->tol) ? 0 : 6;
+  } else if (st->iter >= st->maxit) {
+    st->phase = PH_MAXIT; st->status = 6;
+  } else {
+    st->phase = PH_RUN;
+  }
+}
+
+// w_{j+1} = (z_j - a3 w_{j-1} - a2 w_j)/a1 (written over w_{j-1}); x += c_{j+1} eta w_{j+1}
+__global__ void __launch_bounds__(256) k_w_update(const MinresDev* st, const double* z,
+                                                  double* w_prev, const double* w, double* x,
+                                                  long long n) {
+  if (!st->wpending) return;
+  const double ig = st->w_inv_gamma, a1i = st->w_a1inv, a2 = st->w_a2, a3 = st->w_a3,
+               ce = st->w_ceta;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += stride) {
+    const double wn = (z[e] * ig - a3 * w_prev[e] - a2 * w[e]) * a1i;
+    w_prev[e] = wn;
+    x[e] = fma(ce, wn, x[e]);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_sum_partials(const double* p, int np, double* out) {
+  __shared__ double red[32];
+  double s = reduce_partials(p, np, red);
+  if (threadIdx.x == 0) *out = s;
+}
+
+// ============================================================================================
+// launchers
+static int grid_stream(long long n, int threads) {
+  long long g = (n + threads - 1) / threads;
+  long long cap = 152LL * 8;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+template <typename T>
+static cudaError_t ensure_smem_dst() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = set_smem(k_dst<T>, kCap * sizeof(C<T>));
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+template <typename T>
+static cudaError_t ensure_smem_tp() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = set_smem(k_timepass<T>, kCap * sizeof(C<T>));
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+static cudaError_t ensure_smem_conv() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = set_smem(k_conv, kCap * sizeof(double2));
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+cudaError_t launch_dst(const OpTables& op, int axis, int prec, const Combine& in, double* out,
+                       int flip, const double* dot_with, double* partials, int* nparts,
+                       const int* phase, cudaStream_t st) {
+  Lines ln;
+  ln.len = op.m[axis];
+  long long inner = 1;
+  for (int a = 0; a < axis; ++a) inner *= op.m[a];
+  ln.inner = inner;
+  ln.nlines = (long long)op.N * op.M / op.m[axis];
+  const int P = op.m[axis] + 1;
+  const int L = 2 * P;
+  const int NC = tile_columns(ln.nlines, L);
+  const long long grid = (ln.nlines + 2 * NC - 1) / (2 * NC);
+  if (nparts) *nparts = (int)grid;
+  if (prec == 64) {
+    cudaError_t e = ensure_smem_dst<double>();
+    if (e != cudaSuccess) return e;
+    k_dst<double><<<(unsigned)grid, kThreads, kCap * sizeof(double2), st>>>(
+        ln, P, ilog2(L), NC, in, out, flip, op.N, op.M, dot_with, partials, op.tw_dst[axis],
+        phase, PH_RUN);
+  } else {
+    cudaError_t e = ensure_smem_dst<float>();
+    if (e != cudaSuccess) return e;
+    k_dst<float><<<(unsigned)grid, kThreads, kCap * sizeof(float2), st>>>(
+        ln, P, ilog2(L), NC, in, out, flip, op.N, op.M, dot_with, partials, op.tw_dst32[axis],
+        phase, PH_RUN);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_timepass(const OpTables& op, const PrecTables& pt, int prec, const Combine& in,
+                            double* out, const double* dot_with, double* partials, int* nparts,
+                            const int* phase, cudaStream_t st) {
+  if (pt.none) {
+    long long n = (long long)op.N * op.M;
+    int g = grid_stream(n, 256);
+    if (nparts) *nparts = g;
+    k_precond_identity<<<g, 256, 0, st>>>(in, out, n, dot_with, partials, phase, PH_RUN);
+    return cudaGetLastError();
+  }
+  const int NC = tile_columns(op.M, op.N);
+  const long long grid = (op.M + 2 * NC - 1) / (2 * NC);
+  if (nparts) *nparts = (int)grid;
+  if (prec == 64) {
+    cudaError_t e = ensure_smem_tp<double>();
+    if (e != cudaSuccess) return e;
+    k_timepass<double><<<(unsigned)grid, kThreads, kCap * sizeof(double2), st>>>(
+        op, pt, in, out, dot_with, partials, phase, PH_RUN, NC);
+  } else {
+    cudaError_t e = ensure_smem_tp<float>();
+    if (e != cudaSuccess) return e;
+    k_timepass<float><<<(unsigned)grid, kThreads, kCap * sizeof(float2), st>>>(
+        op, pt, in, out, dot_with, partials, phase, PH_RUN, NC);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_matvec(const OpTables& op, int spectral, const double* x, const double* xscale,
+                          double* y, int flip, int mode, const double* rhs, double* partials,
+                          int* nparts, const int* phase, double* tmp, cudaStream_t st) {
+  const int want = (mode == MV_RESID) ? PH_CHECK : PH_RUN;
+  if (op.ntaps > 0) {
+    long long n = (long long)op.N * op.M;
+    int g = grid_stream(n, 256);
+    if (nparts) *nparts = g;
+    k_direct<<<g, 256, 0, st>>>(op, spectral, x, xscale, y, flip, mode, rhs, partials, phase,
+                                want);
+    return cudaGetLastError();
+  }
+  cudaError_t e = ensure_smem_conv();
+  if (e != cudaSuccess) return e;
+  const int NC = tile_columns(op.M, 2 * op.N);
+  const long long grid = (op.M + 2 * NC - 1) / (2 * NC);
+  if (nparts) *nparts = (int)grid;
+  const double* st_src = x;
+  if (!spectral && op.b_kind == 1) {
+    // conv_b(x) first (scaled like x), then y = conv_a(x) + L conv_b(x)
+    k_conv<<<(unsigned)grid, kThreads, kCap * sizeof(double2), st>>>(
+        op, 0, 1, x, xscale, tmp, 0, MV_STORE, nullptr, nullptr, phase, want, nullptr, NC);
+    st_src = tmp;
+  }
+  k_conv<<<(unsigned)grid, kThreads, kCap * sizeof(double2), st>>>(
+      op, spectral, 0, x, xscale, y, flip, mode, rhs, partials, phase, want, st_src, NC);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_setup_g64(const OpTables& op, const double2* ahat, const double2* bhat,
+                             double2* g64, cudaStream_t st) {
+  long long total = (long long)(op.N / 2 + 1) * op.M;
+  k_setup_g64<<<grid_stream(total, 256), 256, 0, st>>>(op, ahat, bhat, g64);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flip_copy(const double* f, double* b, int N, long long M, double* partials,
+                             int* nparts, cudaStream_t st) {
+  long long n = (long long)N * M;
+  int g = grid_stream(n, 256);
+  if (nparts) *nparts = g;
+  k_flip_copy<<<g, 256, 0, st>>>(f, b, N, M, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scalar_init(MinresDev* s, const double* pzv, int nzv, const double* pb, int nb,
+                               cudaStream_t st) {
+  k_scalar_init<<<1, 256, 0, st>>>(s, pzv, nzv, pb, nb);
+  return cudaGetLastError();
+}
+cudaError_t launch_scalar_delta(MinresDev* s, const double* p, int np, cudaStream_t st) {
+  k_scalar_delta<<<1, 256, 0, st>>>(s, p, np);
+  return cudaGetLastError();
+}
+cudaError_t launch_scalar_gamma(MinresDev* s, const double* p, int np, cudaStream_t st) {
+  k_scalar_gamma<<<1, 256, 0, st>>>(s, p, np);
+  return cudaGetLastError();
+}
+cudaError_t launch_scalar_check(MinresDev* s, const double* p, int np, cudaStream_t st) {
+  k_scalar_check<<<1, 256, 0, st>>>(s, p, np);
+  return cudaGetLastError();
+}
+cudaError_t launch_w_update(MinresDev* s, const double* z, double* w_prev, const double* w,
+                            double* x, long long n, cudaStream_t st) {
+  k_w_update<<<grid_stream(n, 256), 256, 0, st>>>(s, z, w_prev, w, x, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_sum_partials(const double* partials, int np, double* out, cudaStream_t st) {
+  k_sum_partials<<<1, 256, 0, st>>>(partials, np, out);
+  return cudaGetLastError();
+}
+
+}  // namespace bltt

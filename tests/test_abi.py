@@ -1,0 +1,75 @@
+"""The C ABI without a GPU: the library builds and loads, exports every declared symbol, and
+rejects bad arguments on the host before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            txt = open(os.path.join(inc, f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(bltt_[a-z0-9_]+)\s*\(", txt))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2307_07749_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_exports_every_declared_symbol(lib):
+    syms = declared_symbols()
+    assert "bltt_create" in syms and "bltt_minres_solve" in syms
+    for s in syms:
+        assert hasattr(lib, s), s
+
+
+def test_version(lib):
+    import paper_2307_07749_gb300 as B
+    assert "sm_103a" in B.bltt_version()
+
+
+def _create(a, b, N, d, m, h):
+    import paper_2307_07749_gb300 as B
+    with pytest.raises(B.BlttError) as ei:
+        B.bltt_create(a, b, N, d, m, h)
+    return ei.value.status
+
+
+def test_host_validation(lib):
+    from workloads import fractional_problem
+    p = fractional_problem(1, 7, 8, 0.5)
+    # N not a power of two
+    assert _create(np.ones(6), np.r_[1.0, np.zeros(5)], 6, 1, (7,), (0.125,)) == 8
+    # m + 1 not a power of two
+    assert _create(p.a, p.b, 8, 1, (6,), (1 / 7,)) == 8
+    # bad dimension
+    assert _create(p.a, p.b, 8, 4, (7,), (0.125,)) == 1
+    # Assumption 1 (ii) violated: |A_(1)| outweighs A_(0) on the high modes
+    b = p.b.copy()
+    b[1] = -2.0
+    assert _create(p.a, b, 8, 1, (7,), (0.125,)) == 2
+    # non-finite coefficient
+    a = p.a.copy()
+    a[3] = np.nan
+    assert _create(a, p.b, 8, 1, (7,), (0.125,)) == 5
+
+
+def test_null_handle_calls(lib):
+    import paper_2307_07749_gb300 as B
+    L = B.lib()
+    assert L.bltt_destroy(None) == 0
+    assert L.bltt_matvec(None, None, None, 1) == 1
+    assert L.bltt_precond_apply(None, 0.5, None, None, 64) == 1
+    assert L.bltt_set_stream(None, None) == 1

@@ -1,0 +1,170 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, element by element.
+
+Sizes span several tiles with a ragged tail (M odd everywhere), every spatial dimension, both
+matvec paths (2N FFT embedding and direct taps), general b (two convolutions), the edge sizes
+N = 2 / M = 1 and the largest supported N.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from workloads import (Problem, fractional_problem, heat_bdf_problem, heat_cn_problem, l1_weights,
+                       rhs_uniform)
+from _gpu_helpers import precond_tol, rel, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2307_07749_gb300 import build
+    build.build()
+    import paper_2307_07749_gb300 as mod
+    return mod
+
+
+def general_b_problem(N=32, m=(15, 7)):
+    """L1 blocks plus a decaying Laplacian coefficient in every block (b with N taps)."""
+    p = fractional_problem(2, m, N, 0.6)
+    b = 0.3 * (0.5 ** np.arange(N))
+    b[0] = 1.0
+    return Problem(p.N, p.d, p.m, p.h, p.a, b, name=f"generalb2d_N{N}", meta={})
+
+
+def problems():
+    return [
+        fractional_problem(1, 63, 64, 0.5),            # 1-D L1, 4,032 unknowns
+        fractional_problem(2, 31, 32, 0.7),            # 2-D L1, ragged M = 961
+        fractional_problem(3, (7, 15, 3), 16, 0.3),    # 3-D, unequal axes
+        heat_bdf_problem(3, (15, 7, 3), 16),           # direct 2-tap matvec
+        heat_cn_problem(2, (15, 31), 32),              # direct, two Laplacian taps
+        general_b_problem(),                           # FFT matvec with two convolutions
+        fractional_problem(1, 1, 2, 0.5),              # N = 2, M = 1
+        fractional_problem(1, 3, 4096, 0.4),           # largest N
+    ]
+
+
+IDS = [p.name for p in problems()]
+
+
+@pytest.mark.parametrize("prob", problems(), ids=IDS)
+@pytest.mark.parametrize("flip", [0, 1])
+def test_matvec_parity(B, prob, flip):
+    s = B.Solver(prob)
+    z = np.random.default_rng(21).standard_normal(prob.n)
+    y = to_host(s.matvec(to_dev(z), flip=bool(flip)))
+    ref = O.bltt_matvec(prob, z, flip=bool(flip))
+    assert rel(y, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("prob", problems(), ids=IDS)
+@pytest.mark.parametrize("alpha", [1.0, 1e-2, 1e-4, 1e-8])
+def test_precond_parity_f64(B, prob, alpha):
+    s = B.Solver(prob)
+    v = np.random.default_rng(22).standard_normal(prob.n)
+    z = to_host(s.precond_apply(alpha, to_dev(v), precision=64))
+    ref = O.precond_apply(prob, alpha, v)
+    assert rel(z, ref) <= precond_tol(prob.N, alpha, 64)
+
+
+@pytest.mark.parametrize("prob", problems()[:6], ids=IDS[:6])
+@pytest.mark.parametrize("alpha", [1.0, 1e-2, 1e-3])
+def test_precond_parity_f32(B, prob, alpha):
+    s = B.Solver(prob)
+    v = np.random.default_rng(23).standard_normal(prob.n)
+    z = to_host(s.precond_apply(alpha, to_dev(v), precision=32))
+    ref = O.precond_apply(prob, alpha, v)
+    assert rel(z, ref) <= precond_tol(prob.N, alpha, 32)
+
+
+def test_precond_in_place(B):
+    prob = fractional_problem(2, 31, 32, 0.7)
+    s = B.Solver(prob)
+    v = np.random.default_rng(24).standard_normal(prob.n)
+    t = to_dev(v)
+    s.precond_apply(1e-4, t, t)
+    assert rel(to_host(t), O.precond_apply(prob, 1e-4, v)) <= precond_tol(32, 1e-4)
+
+
+SOLVE_PROBLEMS = [
+    fractional_problem(1, 63, 64, 0.5),
+    fractional_problem(2, 31, 32, 0.7),
+    heat_bdf_problem(3, 15, 16),
+    heat_cn_problem(2, 31, 32),
+    general_b_problem(),
+]
+
+
+@pytest.mark.parametrize("prob", SOLVE_PROBLEMS, ids=[p.name for p in SOLVE_PROBLEMS])
+@pytest.mark.parametrize("basis", [1, 2])
+def test_solve_parity_f64(B, prob, basis):
+    f = rhs_uniform(prob.n, 31)
+    ref = O.solve(prob, f, alpha=1e-8, tol=1e-8)
+    s = B.Solver(prob)
+    u, info = s.solve(to_dev(f), alpha=1e-8, tol=1e-8, maxit=100, precision=64, basis=basis)
+    assert info["status"] == 0, info
+    assert abs(info["iters"] - ref["iters"]) <= 1, (info["iters"], ref["iters"])
+    assert info["relres_true"] <= 1e-8
+    uh = to_host(u)
+    assert rel(O.bltt_matvec(prob, uh), f) <= 1e-8          # true residual, oracle's matvec
+    assert rel(uh, ref["x"]) <= 1e-6
+
+
+@pytest.mark.parametrize("prob", SOLVE_PROBLEMS[:3], ids=[p.name for p in SOLVE_PROBLEMS[:3]])
+@pytest.mark.parametrize("basis", [1, 2])
+def test_solve_f32_preconditioner(B, prob, basis):
+    f = rhs_uniform(prob.n, 32)
+    alpha = 1e-3
+    ref = O.solve(prob, f, alpha=alpha, tol=1e-8)
+    s = B.Solver(prob)
+    u, info = s.solve(to_dev(f), alpha=alpha, tol=1e-8, maxit=100, precision=32, basis=basis)
+    assert info["status"] == 0, info
+    assert info["relres_true"] <= 1e-8
+    assert rel(O.bltt_matvec(prob, to_host(u)), f) <= 1e-8
+    assert info["iters"] <= ref["iters"] + 4, (info["iters"], ref["iters"])
+
+
+@pytest.mark.parametrize("precond,alpha", [(0, 1.0), (1, 0.0)])
+def test_comparison_solvers(B, precond, alpha):
+    # MINRES-P_1 (alpha = 1) and MINRES-I (no preconditioner), Sec. 5.2
+    prob = fractional_problem(1, 15, 32, 0.5)
+    f = rhs_uniform(prob.n, 33)
+    ref = O.solve(prob, f, alpha=alpha if precond == 0 else 1.0, tol=1e-8, maxit=2000,
+                  precond="one" if precond == 0 else "none")
+    s = B.Solver(prob)
+    u, info = s.solve(to_dev(f), alpha=alpha, tol=1e-8, maxit=2000, precision=64, basis=2,
+                      precond=precond)
+    assert info["status"] == 0
+    assert abs(info["iters"] - ref["iters"]) <= max(1, ref["iters"] // 50), (info["iters"], ref["iters"])
+    assert info["relres_true"] <= 1e-8
+
+
+def test_errors(B):
+    prob = fractional_problem(1, 15, 16, 0.5)
+    s = B.Solver(prob)
+    f = to_dev(rhs_uniform(prob.n, 34))
+    with pytest.raises(B.BlttError) as e:
+        s.solve(f, alpha=0.0)
+    assert e.value.status == 1
+    with pytest.raises(B.BlttError) as e:
+        s.solve(f, alpha=1.5)
+    assert e.value.status == 1
+    bad = f.clone()
+    bad[5] = float("nan")
+    with pytest.raises(B.BlttError) as e:
+        s.solve(bad, alpha=1e-8)
+    assert e.value.status == 5
+    u, info = s.solve(f, alpha=1.0, maxit=2, precond=1, raise_on_error=False)
+    assert info["status"] == 6 and info["iters"] == 2
+    # zero right-hand side: zero solution, no iterations
+    u, info = s.solve(f * 0, alpha=1e-8)
+    assert info["iters"] == 0 and float(u.abs().max()) == 0.0
+
+
+def test_solve_matches_time_stepping(B):
+    prob = fractional_problem(2, 31, 64, 0.6)
+    f = rhs_uniform(prob.n, 35)
+    s = B.Solver(prob)
+    u, info = s.solve(to_dev(f), alpha=1e-8, tol=1e-10, maxit=50)
+    ustar = O.timestep_solve(prob, f)
+    assert rel(to_host(u), ustar) <= 1e-8
