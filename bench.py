@@ -1,0 +1,419 @@
+#!/usr/bin/env python
+"""Benchmark: preconditioned MINRES (ABAC preconditioner) on the 2-D L1 time-fractional workload.
+
+Workload: L1 scheme, gamma = 0.7, N = 1024 time steps, m = 255 (M = 65,025 = 255^2, 5-point
+Laplacian), 66,585,600 unknowns, f ~ U[-1, 1] (seed 2), tolerance 1e-8 relative residual.
+A step is one whole solve through the C ABI: the per-alpha preconditioner set-up (tables rebuilt
+every step), the entry transform, the MINRES iterations, the exit transform and the FP64 true
+residual.  Metric: unknown-iterations/s = n * iterations / solve time.
+
+Two forms are timed: the chosen form (FP32 preconditioner, FP64 matvec/Lanczos/true residual,
+alpha = 1e-3, physical basis) and the plain FP64 form (alpha = 1e-8, the paper's rule, spectral
+basis).  `value` is the chosen form; the plain form is reported beside it with both
+time-to-solution figures.
+
+Every vector is 533 MB (> 129 MB L2), so no L2 flush is needed between steps.
+
+Multi-GPU (torchrun, N > 1): independent replicas, one solve per rank per step (weak scaling);
+torch.distributed is used only for the barrier and the max-over-ranks time.
+
+--impl reference: the CPU oracle, as it stands, timed on the host cores: each step is one
+MINRES iteration's operator work (one Y A z and one P_alpha^{-1} apply) on the full workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "frac2d_N1024_m255_g0.7"
+TOL = 1e-8
+ALPHA_F64 = 1e-8          # the paper's alpha rule (Sec. 5.2)
+ALPHA_F32 = 1e-3          # FP32 preconditioner: alpha raised so that FP32 rounding stays below tol
+FP64_PEAK_TFLOPS = 1.259  # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (measured 1.20 at 1995 MHz)
+FP32_PEAK_TFLOPS = 80.6   # 128 FFMA/clk/SM x 152 SMs x 2.07 GHz (measured 69.8 at 1995 MHz)
+
+
+def peaks():
+    p = {"hbm_gbs": 6695.5, "source": "fallback"}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            j = json.load(fh)
+        p["hbm_gbs"] = float(j["hbm_gbs"])
+        p["source"] = "measured"
+    except Exception:
+        p["hbm_gbs"] = 6800.0
+    return p
+
+
+# --------------------------------------------------------------------------------------------
+# algorithmic cost per unknown of each kernel family (the design doc derives these)
+def kernel_cost(name, N, m, d):
+    """(bound, bytes per unknown, flops per unknown) of one launch, per unknown it processes."""
+    l2N = np.log2(2 * N)
+    lN = np.log2(N)
+    if name == "conv":      # FP64: real FFT 2N fwd + inv (2 x 2.5 * 2N log2 2N / N), 6 mul, 4 epilogue
+        return "alu64", 16.0, 10.0 * l2N + 10.0
+    if name == "direct":
+        return "hbm", 16.0, 6.0
+    if name in ("timepass64", "timepass32"):   # 4 real FFTs of N, 2 spectral products, 3 scalings
+        b = 16.0 + (8.0 if name == "timepass64" else 0.0)
+        return ("alu64" if name == "timepass64" else "hbm"), b, 10.0 * lN + 15.0
+    if name in ("dst64", "dst32"):   # one complex FFT of 2(m+1) per two lines
+        return ("alu64" if name == "dst64" else "hbm"), 16.0, 5.0 * np.log2(2 * (m + 1)) * (m + 1) / m
+    if name == "w_update":
+        return "hbm", 48.0, 6.0
+    return "hbm", 0.0, 0.0
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    def __init__(self, index=0):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        self.cmd = ["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                    "-lms", "200"]
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(self.cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        sm = [r[0] for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 0, 1
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    return rank, local, ws
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, ws):
+    if ws <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(v, ws):
+    if ws <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------------------------
+def time_form(B, solver, fd, steps, warmup, alpha, precision, basis, ws, stream, profile):
+    """Time `steps` whole solves (after `warmup`) on the device; returns a result dict."""
+    import torch
+    for _ in range(warmup):
+        u, info = solver.solve(fd, alpha=alpha, tol=TOL, maxit=200, precision=precision,
+                               basis=basis, rebuild=True)
+    torch.cuda.synchronize()
+    if profile:
+        solver.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    infos = []
+    e0.record(stream)
+    for _ in range(steps):
+        u, info = solver.solve(fd, alpha=alpha, tol=TOL, maxit=200, precision=precision,
+                               basis=basis, rebuild=True)
+        infos.append(info)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = e0.elapsed_time(e1)
+    prof = solver.profile_read() if profile else {}
+    if profile:
+        solver.profile(False)
+    return {"ms_total": ms, "infos": infos, "profile": prof, "u": u}
+
+
+def time_e2e(B, solver, f_host, steps, alpha, precision, basis, stream):
+    """Same metric through the public API with host buffers: H2D of f, solve, D2H of u."""
+    import torch
+    fd = torch.empty(f_host.shape, dtype=torch.float64, device="cuda")
+    ud = torch.empty_like(fd)
+    u_host = torch.empty(f_host.shape, dtype=torch.float64, pin_memory=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    iters = 0
+    e0.record(stream)
+    for _ in range(steps):
+        fd.copy_(f_host, non_blocking=True)
+        u, info = solver.solve(fd, alpha=alpha, tol=TOL, maxit=200, precision=precision,
+                               basis=basis, u=ud, rebuild=True)
+        u_host.copy_(ud, non_blocking=True)
+        iters += info["iters"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), iters
+
+
+def cpu_baseline_sample(prob, f, alpha):
+    """The oracle, as it stands, on one iteration's operator work of the full workload."""
+    import oracle as O
+    t0 = time.perf_counter()
+    y = O.bltt_matvec(prob, f, flip=True)
+    t1 = time.perf_counter()
+    O.precond_apply(prob, alpha, y)
+    t2 = time.perf_counter()
+    return t2 - t0, t1 - t0, t2 - t1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from workloads import workload
+    prob, rf = workload(WORKLOAD)
+    f = rf()
+    for _ in range(args.warmup):
+        cpu_baseline_sample(prob, f, ALPHA_F32)
+    times = []
+    for _ in range(args.steps):
+        times.append(cpu_baseline_sample(prob, f, ALPHA_F32)[0])
+    tot = sum(times)
+    value = prob.n * args.steps / tot
+    cores = os.cpu_count()
+    sample = ("one MINRES iteration's operator work (one Y A z by the direct Toeplitz product and "
+              "one P_alpha^{-1} apply by the paper's three steps, alpha = 1e-3) on the full "
+              f"{prob.n}-unknown workload per step")
+    line = {
+        "impl": "reference", "metric": "unknown-iterations/s to relres<=1e-8 (CPU oracle, "
+        "operator work per iteration)", "value": value, "unit": "unknown-iter/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": prob.N, "m": prob.m[0], "d": prob.d, "gamma": 0.7,
+                   "unknowns": prob.n, "tol": TOL},
+        "cpu_baseline": {"value": value, "unit": "unknown-iter/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "unknown-iter/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    args.warmup = max(args.warmup, 3)
+
+    rank, local, ws = dist_init()
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2307_07749_gb300 import build
+    if rank == 0:
+        build.build()
+    barrier(ws)
+    import paper_2307_07749_gb300 as B
+    from workloads import workload, rhs_uniform
+
+    prob, _ = workload(WORKLOAD)
+    f = rhs_uniform(prob.n, 2 + 100 * rank)      # rank r solves its own right-hand side
+    stream = torch.cuda.Stream()
+    solver = B.Solver(prob, stream=stream)
+    fd = torch.from_numpy(f).to("cuda")
+    torch.cuda.synchronize()
+
+    forms = {
+        "chosen": dict(alpha=ALPHA_F32, precision=32, basis=B.BASIS_PHYSICAL),
+        "plain_f64": dict(alpha=ALPHA_F64, precision=64, basis=B.BASIS_SPECTRAL),
+    }
+    res = {}
+    with torch.cuda.stream(stream):
+        for key, fm in forms.items():
+            sampler = ClockSampler(local) if key == "chosen" else None
+            if sampler:
+                sampler.__enter__()
+            try:
+                r = time_form(B, solver, fd, args.steps, args.warmup, fm["alpha"], fm["precision"],
+                              fm["basis"], ws, stream, profile=True)
+            finally:
+                if sampler:
+                    sampler.__exit__()
+            r["clocks"] = sampler.summary() if sampler else None
+            res[key] = r
+
+    def summarise(r):
+        ms = max_over_ranks(r["ms_total"], ws)
+        iters = [i["iters"] for i in r["infos"]]
+        units = sum_over_ranks(float(prob.n * sum(iters)), ws)
+        return {
+            "value": units / (ms / 1e3), "ms_per_step": ms / args.steps,
+            "iters": iters[-1], "relres_true": max(i["relres_true"] for i in r["infos"]),
+            "status": max(i["status"] for i in r["infos"]),
+            "launches": sum(i["kernel_launches"] for i in r["infos"]),
+            "setup_ms": float(np.mean([i["t_setup_ms"] for i in r["infos"]])),
+        }
+
+    ch = summarise(res["chosen"])
+    pl = summarise(res["plain_f64"])
+
+    # roofline of the dominant kernel of the chosen form (live CUDA-event durations)
+    pk = peaks()
+    prof = res["chosen"]["profile"]
+    kern = []
+    for name, (launches, tot_ms) in prof.items():
+        bound, bpu, fpu = kernel_cost(name, prob.N, prob.m[0], prob.d)
+        avg_ms = tot_ms / max(launches, 1)
+        units = prob.n
+        if bound == "alu64":
+            ach = fpu * units / (avg_ms / 1e3) / 1e12
+            kern.append(dict(name=name, launches=launches, total_ms=tot_ms, bound="alu",
+                             achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s (FP64)",
+                             frac=ach / FP64_PEAK_TFLOPS, bytes_per_unit=bpu, flops_per_unit=fpu))
+        elif bpu > 0:
+            ach = bpu * units / (avg_ms / 1e3) / 1e9
+            kern.append(dict(name=name, launches=launches, total_ms=tot_ms, bound="hbm",
+                             achieved=ach, peak=pk["hbm_gbs"], unit="GB/s",
+                             frac=ach / pk["hbm_gbs"], bytes_per_unit=bpu, flops_per_unit=fpu))
+    kern.sort(key=lambda k: -k["total_ms"])
+    dom = kern[0] if kern else None
+    roof = None
+    if dom:
+        roof = {"kernel": dom["name"], "bound": dom["bound"], "achieved": round(dom["achieved"], 4),
+                "peak": dom["peak"], "unit": dom["unit"], "frac": round(dom["frac"], 4),
+                "traffic": None,
+                "peak_source": ("derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz, confirmed by a "
+                                "measured 1.20 TFLOP/s FP64 FMA loop" if dom["bound"] == "alu"
+                                else pk["source"] + " hbm_gbs")}
+
+    e2e = None
+    if not args.no_e2e:
+        f_host = torch.from_numpy(f).pin_memory()
+        with torch.cuda.stream(stream):
+            e_ms, e_iters = time_e2e(B, solver, f_host, args.steps, ALPHA_F32, 32,
+                                     B.BASIS_PHYSICAL, stream)
+        e_ms = max_over_ranks(e_ms, ws)
+        e_units = sum_over_ranks(float(prob.n * e_iters), ws)
+        e2e = {"value": e_units / (e_ms / 1e3), "unit": "unknown-iter/s",
+               "h2d_bytes_per_step": prob.n * 8, "d2h_bytes_per_step": prob.n * 8,
+               "ms_per_step": e_ms / args.steps}
+
+    # accuracy of the chosen form against the plain FP64 GPU solve (error stated per result)
+    uc = res["chosen"]["u"]
+    up = res["plain_f64"]["u"]
+    err_vs_f64 = float(torch.linalg.norm(uc - up) / torch.linalg.norm(up))
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        t, tmv, tpc = cpu_baseline_sample(prob, f, ALPHA_F32)
+        cpu = {"value": prob.n / t, "unit": "unknown-iter/s", "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": ("one MINRES iteration's operator work on the full workload: one Y A z "
+                          f"({tmv:.1f} s) and one P_alpha^-1 apply ({tpc:.1f} s), numpy/scipy FP64")}
+
+    if rank == 0:
+        line = {
+            "metric": "unknown-iterations/s to relres<=1e-8 (chosen form: FP32 preconditioner, "
+                      "FP64 matvec/Lanczos/true residual)",
+            "value": ch["value"], "unit": "unknown-iter/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ch["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+            "data": "synthetic (seeded U[-1,1] right-hand side)",
+            "config": {"workload": WORKLOAD, "d": 2, "N": prob.N, "m": prob.m[0], "M": prob.M,
+                       "gamma": 0.7, "unknowns": prob.n, "tol": TOL, "alpha": ALPHA_F32,
+                       "precond_precision": "fp32", "basis": "physical",
+                       "l2": "inputs larger than L2 (533 MB per vector), no flush",
+                       "parallelism": f"replicas x{ws}"},
+            "iters": ch["iters"], "relres_true": ch["relres_true"],
+            "time_to_solution_ms": ch["ms_per_step"], "setup_ms": ch["setup_ms"],
+            "err_vs_plain_f64_solution": err_vs_f64,
+            "plain_f64": {"value": pl["value"], "unit": "unknown-iter/s", "iters": pl["iters"],
+                          "relres_true": pl["relres_true"], "time_to_solution_ms": pl["ms_per_step"],
+                          "alpha": ALPHA_F64, "basis": "spectral", "dtype": "f64",
+                          "setup_ms": pl["setup_ms"]},
+            "roofline": roof,
+            "kernels": [{k: (round(v, 5) if isinstance(v, float) else v) for k, v in kk.items()}
+                        for kk in kern],
+            "kernels_plain_f64": {k: [int(v[0]), round(v[1], 4)] for k, v in res["plain_f64"]["profile"].items()},
+            "e2e": e2e,
+            "gpu_launches": ch["launches"],
+            "clocks": res["chosen"]["clocks"],
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

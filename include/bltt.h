@@ -84,6 +84,7 @@ typedef struct {
   int basis;         /* BLTT_BASIS_*                                                            */
   int precond;       /* BLTT_PRECOND_*                                                          */
   int sync_every;    /* iterations issued between host checks of the device state (0: 2)        */
+  int rebuild;       /* 1: rebuild the per-alpha preconditioner tables even if cached            */
 } bltt_solve_opts;
 
 typedef struct {
@@ -142,6 +143,21 @@ bltt_status bltt_minres_solve_ex(bltt_handle h, const double* f_dev, double alph
 /* Same as bltt_minres_solve_ex with opts = {precision, AUTO, ABAC, 0}. */
 bltt_status bltt_minres_solve(bltt_handle h, const double* f_dev, double alpha, double tol,
                               int maxit, int precision, double* u_dev, bltt_solve_info* info);
+
+/* Per-kernel device time, collected with CUDA events around every launch on the handle's
+ * stream while profiling is enabled (tracing aid; adds two event records per launch). */
+typedef struct {
+  char name[24];          /* kernel family: conv, direct, dst64, dst32, timepass64, ...        */
+  long long launches;
+  double total_ms;
+} bltt_kernel_stat;
+
+/* Enable (1) or disable (0) per-launch timing on h; either way the counters are reset. */
+bltt_status bltt_profile_enable(bltt_handle h, int enable);
+
+/* Synchronise h's stream and copy up to max_entries statistics to out (host array).  Returns the
+ * number of kernel families recorded (may exceed max_entries), or -1 for a NULL handle. */
+int bltt_profile_read(bltt_handle h, bltt_kernel_stat* out, int max_entries);
 
 /* Message for the last failed call on h ("" if none); for h == NULL, the last failure of
  * bltt_create on this thread.  The string stays valid until the next call on h. */

@@ -46,7 +46,7 @@ class bltt_blocks(ctypes.Structure):
 
 class bltt_solve_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("basis", ctypes.c_int), ("precond", ctypes.c_int),
-                ("sync_every", ctypes.c_int)]
+                ("sync_every", ctypes.c_int), ("rebuild", ctypes.c_int)]
 
 
 class bltt_solve_info(ctypes.Structure):
@@ -59,6 +59,11 @@ class bltt_solve_info(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class bltt_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_longlong),
+                ("total_ms", ctypes.c_double)]
 
 
 # C signatures: name -> (restype, argtypes)
@@ -75,6 +80,8 @@ _SIGS = {
                                             ctypes.POINTER(bltt_solve_info)]),
     "bltt_minres_solve": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                          ctypes.c_int, _P, ctypes.POINTER(bltt_solve_info)]),
+    "bltt_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "bltt_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(bltt_kernel_stat), ctypes.c_int]),
     "bltt_last_error": (ctypes.c_char_p, [_P]),
     "bltt_version": (ctypes.c_char_p, []),
 }
@@ -155,8 +162,8 @@ def bltt_precond_apply(handle, alpha, v, z, precision=PREC_F64):
 
 
 def bltt_minres_solve_ex(handle, f, alpha, tol, maxit, u, precision=PREC_F64, basis=BASIS_AUTO,
-                         precond=PRECOND_ABAC, sync_every=0, raise_on_error=True):
-    opts = bltt_solve_opts(precision, basis, precond, sync_every)
+                         precond=PRECOND_ABAC, sync_every=0, raise_on_error=True, rebuild=0):
+    opts = bltt_solve_opts(precision, basis, precond, sync_every, rebuild)
     info = bltt_solve_info()
     st = lib().bltt_minres_solve_ex(handle, _ptr(f, "f"), float(alpha), float(tol), int(maxit),
                                     ctypes.byref(opts), _ptr(u, "u"), ctypes.byref(info))
@@ -170,6 +177,19 @@ def bltt_minres_solve(handle, f, alpha, tol, maxit, precision, u):
     st = lib().bltt_minres_solve(handle, _ptr(f, "f"), float(alpha), float(tol), int(maxit),
                                  int(precision), _ptr(u, "u"), ctypes.byref(info))
     return st, info.as_dict()
+
+
+def bltt_profile_enable(handle, enable=True):
+    _check(lib().bltt_profile_enable(handle, 1 if enable else 0), handle)
+
+
+def bltt_profile_read(handle):
+    """{kernel family: (launches, total_ms)} recorded since profiling was enabled."""
+    arr = (bltt_kernel_stat * 64)()
+    k = lib().bltt_profile_read(handle, arr, 64)
+    if k < 0:
+        raise BlttError(1, "null handle")
+    return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms) for i in range(min(k, 64))}
 
 
 def bltt_version():
@@ -203,6 +223,12 @@ class Solver:
         except Exception:
             pass
 
+    def profile(self, enable=True):
+        bltt_profile_enable(self.handle, enable)
+
+    def profile_read(self):
+        return bltt_profile_read(self.handle)
+
     def set_stream(self, stream):
         bltt_set_stream(self.handle, stream)
 
@@ -219,10 +245,10 @@ class Solver:
         return z
 
     def solve(self, f, alpha=1e-8, tol=1e-8, maxit=200, precision=PREC_F64, basis=BASIS_AUTO,
-              precond=PRECOND_ABAC, u=None, sync_every=0, raise_on_error=True):
+              precond=PRECOND_ABAC, u=None, sync_every=0, raise_on_error=True, rebuild=False):
         import torch
         u = torch.empty_like(f) if u is None else u
         st, info = bltt_minres_solve_ex(self.handle, f, alpha, tol, maxit, u, precision, basis,
-                                        precond, sync_every, raise_on_error)
+                                        precond, sync_every, raise_on_error, int(rebuild))
         info["status_name"] = STATUS_NAMES.get(st, st)
         return u, info

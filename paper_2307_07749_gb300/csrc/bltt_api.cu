@@ -6,6 +6,7 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -89,6 +90,13 @@ struct bltt_ctx {
   double2* pc_bhat64 = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   long long launches = 0;
+  // per-launch profiling
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  struct Pending { const char* name; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  std::map<std::string, std::pair<long long, double>> stats;
 
   ~bltt_ctx() {
     if (stream_sync_ok) cudaStreamSynchronize(stream);
@@ -96,6 +104,7 @@ struct bltt_ctx {
     if (state_host) cudaFreeHost(state_host);
     if (scal_host) cudaFreeHost(scal_host);
     for (auto& e : ev) if (e) cudaEventDestroy(e);
+    for (auto& e : ev_pool) cudaEventDestroy(e);
   }
   bool stream_sync_ok = true;
 
@@ -129,6 +138,16 @@ bltt_status cuda_fail(bltt_ctx* h, cudaError_t e, const char* where) {
   do {                                                       \
     cudaError_t e__ = (call);                                \
     if (e__ != cudaSuccess) return cuda_fail((h), e__, where); \
+  } while (0)
+
+cudaEvent_t prof_begin(bltt_ctx* h);
+void prof_end(bltt_ctx* h, const char* name, cudaEvent_t a);
+#define PCK(h, name, call, where)                            \
+  do {                                                       \
+    cudaEvent_t pa__ = prof_begin(h);                        \
+    cudaError_t e__ = (call);                                \
+    if (e__ != cudaSuccess) return cuda_fail((h), e__, where); \
+    prof_end((h), (name), pa__);                             \
   } while (0)
 
 template <typename T>
@@ -217,7 +236,9 @@ bltt_status prepare_precond(bltt_ctx* h, double alpha, int prec) {
   }
   if (prec == 64 && !h->pc_has64) {
     if (!h->pc_g64) CK(h, h->alloc(&h->pc_g64, (size_t)(N / 2 + 1) * h->M), "alloc g64 table");
+    cudaEvent_t pa = prof_begin(h);
     CK(h, launch_setup_g64(h->op, h->pc_ahat64, h->pc_bhat64, h->pc_g64, h->stream), "setup g64");
+    prof_end(h, "setup_g64", pa);
     h->launches++;
     h->pc_has64 = true;
   }
@@ -242,27 +263,37 @@ bltt_status precond_chain(bltt_ctx* h, int spectral, int prec, const PrecTables&
                           const Combine& in, double* out, const double* dot_with,
                           double* partials, int* nparts, const int* phase) {
   const OpTables& op = h->op;
+  const char* tp_name = pt.none ? "identity" : (prec == 64 ? "timepass64" : "timepass32");
+  const char* dst_name = prec == 64 ? "dst64" : "dst32";
   if (pt.none || spectral) {
+    cudaEvent_t pa = prof_begin(h);
     CK(h, launch_timepass(op, pt, prec, in, out, dot_with, partials, nparts, phase, h->stream), "time pass");
+    prof_end(h, tp_name, pa);
     h->launches++;
     return BLTT_OK;
   }
   for (int ax = 0; ax < op.d; ++ax) {
     Combine c{};
     if (ax == 0) c = in; else c.in0 = out;
+    cudaEvent_t pa = prof_begin(h);
     CK(h, launch_dst(op, ax, prec, c, out, 0, nullptr, nullptr, nullptr, phase, h->stream), "dst");
+    prof_end(h, dst_name, pa);
     h->launches++;
   }
   Combine c{};
   c.in0 = out;
+  cudaEvent_t pt0 = prof_begin(h);
   CK(h, launch_timepass(op, pt, prec, c, out, nullptr, nullptr, nullptr, phase, h->stream), "time pass");
+  prof_end(h, tp_name, pt0);
   h->launches++;
   for (int ax = 0; ax < op.d; ++ax) {
     Combine c2{};
     c2.in0 = out;
     const bool last = (ax == op.d - 1);
+    cudaEvent_t pa = prof_begin(h);
     CK(h, launch_dst(op, ax, prec, c2, out, 0, last ? dot_with : nullptr, last ? partials : nullptr,
                      last ? nparts : nullptr, phase, h->stream), "dst");
+    prof_end(h, dst_name, pa);
     h->launches++;
   }
   return BLTT_OK;
@@ -276,16 +307,51 @@ bltt_status dst_all(bltt_ctx* h, const double* in, double* out, int flip, double
     Combine c{};
     c.in0 = (ax == 0) ? in : out;
     const bool last = (ax == op.d - 1);
+    cudaEvent_t pa = prof_begin(h);
     CK(h, launch_dst(op, ax, 64, c, out, ax == 0 ? flip : 0, last && partials ? out : nullptr,
                      last ? partials : nullptr, last ? nparts : nullptr, nullptr, h->stream), "dst");
+    prof_end(h, "dst64", pa);
     h->launches++;
   }
   return BLTT_OK;
 }
 
-bltt_status check_handle(bltt_ctx* h) {
-  if (!h) return BLTT_ERR_INVALID_ARG;
-  return BLTT_OK;
+cudaEvent_t prof_event(bltt_ctx* h) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    h->ev_pool.push_back(e);
+  }
+  return h->ev_pool[h->ev_used++];
+}
+
+// record an event before a launch when profiling (returns null otherwise)
+cudaEvent_t prof_begin(bltt_ctx* h) {
+  if (!h->prof) return nullptr;
+  cudaEvent_t a = prof_event(h);
+  if (a) cudaEventRecord(a, h->stream);
+  return a;
+}
+void prof_end(bltt_ctx* h, const char* name, cudaEvent_t a) {
+  if (!h->prof || !a) return;
+  cudaEvent_t b = prof_event(h);
+  if (!b) return;
+  cudaEventRecord(b, h->stream);
+  h->pending.push_back({name, a, b});
+}
+void prof_harvest(bltt_ctx* h) {
+  if (h->pending.empty()) { h->ev_used = 0; return; }
+  cudaStreamSynchronize(h->stream);
+  for (auto& p : h->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      auto& st = h->stats[p.name];
+      st.first += 1;
+      st.second += ms;
+    }
+  }
+  h->pending.clear();
+  h->ev_used = 0;
 }
 
 }  // namespace
@@ -432,7 +498,7 @@ bltt_status bltt_matvec(bltt_handle h, const double* x, double* y, int flip) {
     if (s != BLTT_OK) return s;
     tmp = vec(h, 9);
   }
-  CK(h, launch_matvec(h->op, 0, x, nullptr, y, flip ? 1 : 0, MV_STORE, nullptr, nullptr, nullptr,
+  PCK(h, (h->op.ntaps > 0 ? "direct" : "conv"), launch_matvec(h->op, 0, x, nullptr, y, flip ? 1 : 0, MV_STORE, nullptr, nullptr, nullptr,
                       nullptr, tmp, h->stream), "matvec");
   return BLTT_OK;
 }
@@ -478,6 +544,7 @@ bltt_status bltt_minres_solve_ex(bltt_handle h, const double* f, double alpha, d
   const OpTables& op = h->op;
   cudaStream_t st = h->stream;
   CK(h, cudaEventRecord(h->ev[0], st), "event");
+  if (o.rebuild) h->pc_alpha = -1.0;
   if (!none) {
     s = prepare_precond(h, alpha, o.precision);
     if (s != BLTT_OK) return s;
@@ -509,7 +576,7 @@ bltt_status bltt_minres_solve_ex(bltt_handle h, const double* f, double alpha, d
     s = dst_all(h, f, bvec, 1, h->partials[1], &nb);
     if (s != BLTT_OK) return s;
   } else {
-    CK(h, launch_flip_copy(f, bvec, h->N, h->M, h->partials[1], &nb, st), "flip");
+    PCK(h, "flip", launch_flip_copy(f, bvec, h->N, h->M, h->partials[1], &nb, st), "flip");
     h->launches++;
   }
   const int cur0 = 0;
@@ -526,17 +593,17 @@ bltt_status bltt_minres_solve_ex(bltt_handle h, const double* f, double alpha, d
   CK(h, cudaMemsetAsync(vbuf[1 - cur], 0, n * sizeof(double), st), "memset v0");
   CK(h, cudaMemsetAsync(wbuf[0], 0, n * sizeof(double), st), "memset w0");
   CK(h, cudaMemsetAsync(wbuf[1], 0, n * sizeof(double), st), "memset w1");
-  CK(h, launch_scalar_init(h->state, h->partials[0], nzv, h->partials[1], nb, st), "scalar init");
+  PCK(h, "scalar", launch_scalar_init(h->state, h->partials[0], nzv, h->partials[1], nb, st), "scalar init");
   h->launches++;
 
   int issued = 0;
   for (;;) {
     const int prv = 1 - cur;
     // q = Y A z_j  (z_j = z_u / gamma_j), delta_j = <q, z_j>
-    CK(h, launch_matvec(op, spectral, zbuf[cur], &h->state->inv_gamma, q, 1, MV_STORE, nullptr,
+    PCK(h, (h->op.ntaps > 0 ? "direct" : "conv"), launch_matvec(op, spectral, zbuf[cur], &h->state->inv_gamma, q, 1, MV_STORE, nullptr,
                         h->partials[0], &np, phase, tmp, st), "matvec");
     h->launches += (op.b_kind == 1 && op.ntaps == 0 && !spectral) ? 2 : 1;
-    CK(h, launch_scalar_delta(h->state, h->partials[0], np, st), "scalar delta");
+    PCK(h, "scalar", launch_scalar_delta(h->state, h->partials[0], np, st), "scalar delta");
     h->launches++;
     // v_{j+1} = q - (delta/gamma) v_j - (gamma/gamma_prev) v_{j-1} (over v_{j-1});
     // z_{j+1} = P^{-1} v_{j+1} (over z_{j-1}); <z_{j+1}, v_{j+1}>
@@ -547,15 +614,15 @@ bltt_status bltt_minres_solve_ex(bltt_handle h, const double* f, double alpha, d
       s = precond_chain(h, spectral, o.precision, pt, c, zbuf[prv], vbuf[prv], h->partials[1], &np, phase);
       if (s != BLTT_OK) return s;
     }
-    CK(h, launch_scalar_gamma(h->state, h->partials[1], np, st), "scalar gamma");
+    PCK(h, "scalar", launch_scalar_gamma(h->state, h->partials[1], np, st), "scalar gamma");
     h->launches++;
-    CK(h, launch_w_update(h->state, zbuf[cur], wbuf[prv], wbuf[cur], x, n, st), "w update");
+    PCK(h, "w_update", launch_w_update(h->state, zbuf[cur], wbuf[prv], wbuf[cur], x, n, st), "w update");
     h->launches++;
     // true residual when the estimate says so
-    CK(h, launch_matvec(op, spectral, x, nullptr, nullptr, 1, MV_RESID, bvec, h->partials[0], &np,
+    PCK(h, (h->op.ntaps > 0 ? "direct" : "conv"), launch_matvec(op, spectral, x, nullptr, nullptr, 1, MV_RESID, bvec, h->partials[0], &np,
                         phase, tmp, st), "residual");
     h->launches += (op.b_kind == 1 && op.ntaps == 0 && !spectral) ? 2 : 1;
-    CK(h, launch_scalar_check(h->state, h->partials[0], np, st), "scalar check");
+    PCK(h, "scalar", launch_scalar_check(h->state, h->partials[0], np, st), "scalar check");
     h->launches++;
     std::swap(vbuf[0], vbuf[1]);
     std::swap(zbuf[0], zbuf[1]);
@@ -573,16 +640,17 @@ bltt_status bltt_minres_solve_ex(bltt_handle h, const double* f, double alpha, d
     s = dst_all(h, x, u, 0, nullptr, nullptr);
     if (s != BLTT_OK) return s;
     int nr = 0;
-    CK(h, launch_matvec(op, 0, u, nullptr, nullptr, 0, MV_RESID, f, h->partials[0], &nr, nullptr,
+    PCK(h, (h->op.ntaps > 0 ? "direct" : "conv"), launch_matvec(op, 0, u, nullptr, nullptr, 0, MV_RESID, f, h->partials[0], &nr, nullptr,
                         tmp, st), "final residual");
     h->launches += (op.b_kind == 1 && op.ntaps == 0) ? 2 : 1;
-    CK(h, launch_sum_partials(h->partials[0], nr, h->scal, st), "sum");
+    PCK(h, "scalar", launch_sum_partials(h->partials[0], nr, h->scal, st), "sum");
     h->launches++;
     CK(h, cudaMemcpyAsync(h->scal_host, h->scal, sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
   }
   CK(h, cudaEventRecord(h->ev[2], st), "event");
   CK(h, cudaStreamSynchronize(st), "sync");
   if (spectral && sh->normb > 0) relres_phys = std::sqrt(h->scal_host[0]) / sh->normb;
+  prof_harvest(h);
   float t_all = 0.f, t_setup = 0.f;
   cudaEventElapsedTime(&t_all, h->ev[0], h->ev[2]);
   cudaEventElapsedTime(&t_setup, h->ev[0], h->ev[1]);
@@ -606,6 +674,30 @@ bltt_status bltt_minres_solve_ex(bltt_handle h, const double* f, double alpha, d
   if (result == BLTT_ERR_NUMERIC) h->err = "MINRES breakdown: <z, v> negative or non-finite";
   else if (result == BLTT_ERR_NOT_CONVERGED) h->err = "maxit reached before the stopping rule held";
   return result;
+}
+
+bltt_status bltt_profile_enable(bltt_handle h, int enable) {
+  if (!h) return BLTT_ERR_INVALID_ARG;
+  prof_harvest(h);
+  h->stats.clear();
+  h->prof = enable != 0;
+  return BLTT_OK;
+}
+
+int bltt_profile_read(bltt_handle h, bltt_kernel_stat* out, int max_entries) {
+  if (!h) return -1;
+  prof_harvest(h);
+  int k = 0;
+  for (auto& kv : h->stats) {
+    if (out && k < max_entries) {
+      std::memset(&out[k], 0, sizeof out[k]);
+      std::strncpy(out[k].name, kv.first.c_str(), sizeof out[k].name - 1);
+      out[k].launches = kv.second.first;
+      out[k].total_ms = kv.second.second;
+    }
+    ++k;
+  }
+  return k;
 }
 
 bltt_status bltt_minres_solve(bltt_handle h, const double* f, double alpha, double tol, int maxit,
