@@ -7,10 +7,12 @@ A step is one whole solve through the C ABI: the per-alpha preconditioner set-up
 every step), the entry transform, the MINRES iterations, the exit transform and the FP64 true
 residual.  Metric: unknown-iterations/s = n * iterations / solve time.
 
-Two forms are timed: the chosen form (FP32 preconditioner, FP64 matvec/Lanczos/true residual,
-alpha = 1e-3, physical basis) and the plain FP64 form (alpha = 1e-8, the paper's rule, spectral
-basis).  `value` is the chosen form; the plain form is reported beside it with both
-time-to-solution figures.
+Forms timed: the chosen form (FP32 preconditioner with alpha = 1e-3; the matvec and the entry/exit
+DSTs FP64-accurate in double-float on the FP32 pipes; Lanczos and true residual in FP64; DST
+basis), the plain FP64 form (alpha = 1e-8, the paper's rule, everything native FP64) and two
+more (all FP64-accurate stages in double-float at alpha = 1e-8; the chosen form in the physical
+basis).  `value` is the chosen form; the others are reported beside it, each with its
+time-to-solution.
 
 Every vector is 533 MB (> 129 MB L2), so no L2 flush is needed between steps.
 
@@ -40,6 +42,24 @@ ALPHA_F64 = 1e-8          # the paper's alpha rule (Sec. 5.2)
 ALPHA_F32 = 1e-3          # FP32 preconditioner: alpha raised so that FP32 rounding stays below tol
 FP64_PEAK_TFLOPS = 1.259  # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (measured 1.20 at 1995 MHz)
 FP32_PEAK_TFLOPS = 80.6   # 128 FFMA/clk/SM x 152 SMs x 2.07 GHz (measured 69.8 at 1995 MHz)
+FP32_PEAK_TOPS = 40.28    # FP32 pipe: 128 instructions/clk/SM x 152 SMs x 2.07 GHz
+
+
+def df_fft_ops(L):
+    """FP32 operations of one double-float complex FFT of length L, per point (radix 4, plus one
+    radix-2 pass when log2 L is odd): df add = 11 ops, df complex multiply = 2 dot2 = 38 ops."""
+    lg = int(np.log2(L))
+    ops = 0.0
+    if lg % 2:
+        ops += 2 * 22.0 / 2          # radix-2 pass: 2 complex add/sub per 2 points
+    ops += (lg // 2) * (3 * 38.0 + 8 * 22.0) / 4   # radix-4 passes: 3 twiddle muls, 8 adds
+    return ops
+
+
+def df_conv_ops(N):
+    """FP32 operations per unknown of the double-float matvec: forward + inverse FFT of 2N per
+    complex column (one complex point per real unknown), the spectral product, the epilogue."""
+    return 2 * df_fft_ops(2 * N) + 38.0 + 4.0
 
 
 def peaks():
@@ -62,6 +82,8 @@ def kernel_cost(name, N, m, d):
     lN = np.log2(N)
     if name == "conv":      # FP64: real FFT 2N fwd + inv (2 x 2.5 * 2N log2 2N / N), 6 mul, 4 epilogue
         return "alu64", 16.0, 10.0 * l2N + 10.0
+    if name == "conv_df":   # same algorithm in double-float on the FP32 pipes (FP32 operations)
+        return "alu32", 16.0, df_conv_ops(N)
     if name == "direct":
         return "hbm", 16.0, 6.0
     if name in ("timepass64", "timepass32"):   # 4 real FFTs of N, 2 spectral products, 3 scalings
@@ -69,6 +91,10 @@ def kernel_cost(name, N, m, d):
         return ("alu64" if name == "timepass64" else "hbm"), b, 10.0 * lN + 15.0
     if name in ("dst64", "dst32"):   # one complex FFT of 2(m+1) per two lines
         return ("alu64" if name == "dst64" else "hbm"), 16.0, 5.0 * np.log2(2 * (m + 1)) * (m + 1) / m
+    if name == "dst_df":
+        return "alu32", 16.0, df_fft_ops(2 * (m + 1)) * (m + 1) / m
+    if name == "timepass_df":
+        return "alu32", 24.0, 4 * df_fft_ops(N) / 2 + 2 * 82.0 / 2 + 3 * 14.0
     if name == "w_update":
         return "hbm", 48.0, 6.0
     return "hbm", 0.0, 0.0
@@ -166,12 +192,12 @@ def sum_over_ranks(v, ws):
 
 
 # --------------------------------------------------------------------------------------------
-def time_form(B, solver, fd, steps, warmup, alpha, precision, basis, ws, stream, profile):
+def time_form(B, solver, fd, steps, warmup, alpha, precision, basis, arith, ws, stream, profile):
     """Time `steps` whole solves (after `warmup`) on the device; returns a result dict."""
     import torch
     for _ in range(warmup):
         u, info = solver.solve(fd, alpha=alpha, tol=TOL, maxit=200, precision=precision,
-                               basis=basis, rebuild=True)
+                               basis=basis, rebuild=True, matvec_arith=arith)
     torch.cuda.synchronize()
     if profile:
         solver.profile(True)
@@ -182,7 +208,7 @@ def time_form(B, solver, fd, steps, warmup, alpha, precision, basis, ws, stream,
     e0.record(stream)
     for _ in range(steps):
         u, info = solver.solve(fd, alpha=alpha, tol=TOL, maxit=200, precision=precision,
-                               basis=basis, rebuild=True)
+                               basis=basis, rebuild=True, matvec_arith=arith)
         infos.append(info)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -194,7 +220,7 @@ def time_form(B, solver, fd, steps, warmup, alpha, precision, basis, ws, stream,
     return {"ms_total": ms, "infos": infos, "profile": prof, "u": u}
 
 
-def time_e2e(B, solver, f_host, steps, alpha, precision, basis, stream):
+def time_e2e(B, solver, f_host, steps, alpha, precision, basis, arith, stream):
     """Same metric through the public API with host buffers: H2D of f, solve, D2H of u."""
     import torch
     fd = torch.empty(f_host.shape, dtype=torch.float64, device="cuda")
@@ -207,7 +233,7 @@ def time_e2e(B, solver, f_host, steps, alpha, precision, basis, stream):
     for _ in range(steps):
         fd.copy_(f_host, non_blocking=True)
         u, info = solver.solve(fd, alpha=alpha, tol=TOL, maxit=200, precision=precision,
-                               basis=basis, u=ud, rebuild=True)
+                               basis=basis, u=ud, rebuild=True, matvec_arith=arith)
         u_host.copy_(ud, non_blocking=True)
         iters += info["iters"]
     e1.record(stream)
@@ -292,8 +318,12 @@ def main():
     torch.cuda.synchronize()
 
     forms = {
-        "chosen": dict(alpha=ALPHA_F32, precision=32, basis=B.BASIS_PHYSICAL),
-        "plain_f64": dict(alpha=ALPHA_F64, precision=64, basis=B.BASIS_SPECTRAL),
+        "chosen": dict(alpha=ALPHA_F32, precision=32, basis=B.BASIS_SPECTRAL, arith=B.ARITH_F32X2),
+        "plain_f64": dict(alpha=ALPHA_F64, precision=64, basis=B.BASIS_SPECTRAL, arith=B.ARITH_F64),
+        "f32x2_all": dict(alpha=ALPHA_F64, precision=96, basis=B.BASIS_SPECTRAL,
+                          arith=B.ARITH_F32X2),
+        "f32_physical": dict(alpha=ALPHA_F32, precision=32, basis=B.BASIS_PHYSICAL,
+                             arith=B.ARITH_F32X2),
     }
     res = {}
     with torch.cuda.stream(stream):
@@ -303,7 +333,7 @@ def main():
                 sampler.__enter__()
             try:
                 r = time_form(B, solver, fd, args.steps, args.warmup, fm["alpha"], fm["precision"],
-                              fm["basis"], ws, stream, profile=True)
+                              fm["basis"], fm["arith"], ws, stream, profile=True)
             finally:
                 if sampler:
                     sampler.__exit__()
@@ -324,12 +354,13 @@ def main():
 
     ch = summarise(res["chosen"])
     pl = summarise(res["plain_f64"])
+    others = {k: summarise(res[k]) for k in ("f32x2_all", "f32_physical")}
 
     # roofline of the dominant kernel of the chosen form (live CUDA-event durations)
     pk = peaks()
     prof = res["chosen"]["profile"]
     kern = []
-    for name, (launches, tot_ms) in prof.items():
+    for name, (all_launches, all_ms, launches, tot_ms) in prof.items():
         bound, bpu, fpu = kernel_cost(name, prob.N, prob.m[0], prob.d)
         avg_ms = tot_ms / max(launches, 1)
         units = prob.n
@@ -338,6 +369,11 @@ def main():
             kern.append(dict(name=name, launches=launches, total_ms=tot_ms, bound="alu",
                              achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s (FP64)",
                              frac=ach / FP64_PEAK_TFLOPS, bytes_per_unit=bpu, flops_per_unit=fpu))
+        elif bound == "alu32":
+            ach = fpu * units / (avg_ms / 1e3) / 1e12
+            kern.append(dict(name=name, launches=launches, total_ms=tot_ms, bound="alu",
+                             achieved=ach, peak=FP32_PEAK_TOPS, unit="Tops/s (FP32 pipe)",
+                             frac=ach / FP32_PEAK_TOPS, bytes_per_unit=bpu, flops_per_unit=fpu))
         elif bpu > 0:
             ach = bpu * units / (avg_ms / 1e3) / 1e9
             kern.append(dict(name=name, launches=launches, total_ms=tot_ms, bound="hbm",
@@ -350,16 +386,18 @@ def main():
         roof = {"kernel": dom["name"], "bound": dom["bound"], "achieved": round(dom["achieved"], 4),
                 "peak": dom["peak"], "unit": dom["unit"], "frac": round(dom["frac"], 4),
                 "traffic": None,
-                "peak_source": ("derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz, confirmed by a "
-                                "measured 1.20 TFLOP/s FP64 FMA loop" if dom["bound"] == "alu"
-                                else pk["source"] + " hbm_gbs")}
+                "peak_source": (("derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz, confirmed by a "
+                                 "measured 1.20 TFLOP/s FP64 FMA loop") if dom["unit"].endswith("(FP64)")
+                                else ("derived: 128 FP32 ops/clk/SM x 152 SMs x 2.07 GHz, confirmed "
+                                      "by a measured 69.8 TFLOP/s FP32 FMA loop")
+                                if dom["bound"] == "alu" else pk["source"] + " hbm_gbs")}
 
     e2e = None
     if not args.no_e2e:
         f_host = torch.from_numpy(f).pin_memory()
         with torch.cuda.stream(stream):
             e_ms, e_iters = time_e2e(B, solver, f_host, args.steps, ALPHA_F32, 32,
-                                     B.BASIS_PHYSICAL, stream)
+                                     B.BASIS_SPECTRAL, B.ARITH_F32X2, stream)
         e_ms = max_over_ranks(e_ms, ws)
         e_units = sum_over_ranks(float(prob.n * e_iters), ws)
         e2e = {"value": e_units / (e_ms / 1e3), "unit": "unknown-iter/s",
@@ -382,14 +420,15 @@ def main():
     if rank == 0:
         line = {
             "metric": "unknown-iterations/s to relres<=1e-8 (chosen form: FP32 preconditioner, "
-                      "FP64 matvec/Lanczos/true residual)",
+                      "FP64-accurate matvec (double-float on FP32 pipes), FP64 Lanczos/true residual)",
             "value": ch["value"], "unit": "unknown-iter/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ch["ms_per_step"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32 (f32x2 matvec)",
             "data": "synthetic (seeded U[-1,1] right-hand side)",
             "config": {"workload": WORKLOAD, "d": 2, "N": prob.N, "m": prob.m[0], "M": prob.M,
                        "gamma": 0.7, "unknowns": prob.n, "tol": TOL, "alpha": ALPHA_F32,
-                       "precond_precision": "fp32", "basis": "physical",
+                       "precond_precision": "fp32", "basis": "spectral (DST-I basis)",
+                       "matvec_arith": "f32x2 (double-float)",
                        "l2": "inputs larger than L2 (533 MB per vector), no flush",
                        "parallelism": f"replicas x{ws}"},
             "iters": ch["iters"], "relres_true": ch["relres_true"],
@@ -399,10 +438,16 @@ def main():
                           "relres_true": pl["relres_true"], "time_to_solution_ms": pl["ms_per_step"],
                           "alpha": ALPHA_F64, "basis": "spectral", "dtype": "f64",
                           "setup_ms": pl["setup_ms"]},
+            "other_forms": {k: {"value": v["value"], "unit": "unknown-iter/s", "iters": v["iters"],
+                                "relres_true": v["relres_true"],
+                                "time_to_solution_ms": v["ms_per_step"],
+                                "form": {kk: (vv if not isinstance(vv, float) else vv)
+                                         for kk, vv in forms[k].items()}}
+                            for k, v in others.items()},
             "roofline": roof,
             "kernels": [{k: (round(v, 5) if isinstance(v, float) else v) for k, v in kk.items()}
                         for kk in kern],
-            "kernels_plain_f64": {k: [int(v[0]), round(v[1], 4)] for k, v in res["plain_f64"]["profile"].items()},
+            "kernels_plain_f64": {k: [int(v[2]), round(v[3], 4)] for k, v in res["plain_f64"]["profile"].items()},
             "e2e": e2e,
             "gpu_launches": ch["launches"],
             "clocks": res["chosen"]["clocks"],

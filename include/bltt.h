@@ -65,19 +65,27 @@ typedef struct {
   bltt_space space;
 } bltt_blocks;
 
-/* Precision of the preconditioner apply (the matvec, the Lanczos recurrences and the true
- * residual are always FP64). */
-enum { BLTT_PREC_F64 = 64, BLTT_PREC_F32 = 32 };
+/* Arithmetic of the preconditioner apply: FP64, FP32, or double-float (F32X2: FP64-accurate to
+ * about 1e-14 relative, computed on the FP32 pipes).  The matvec, the Lanczos recurrences and the
+ * true residual stay FP64-accurate whatever this is; vectors are FP64 in memory throughout. */
+enum { BLTT_PREC_F64 = 64, BLTT_PREC_F32 = 32, BLTT_PREC_F32X2 = 96 };
 
 /* Basis the MINRES vectors live in during the iteration.  SPECTRAL: the DST-I basis of the
  * blocks (U is orthogonal and symmetric, Sec. 3), so the loop needs no DST; the iterates are the
  * physical ones multiplied by I (x) U.  PHYSICAL: the textbook form, DSTs inside P_alpha^{-1}.
- * AUTO picks SPECTRAL for FP64 and PHYSICAL for FP32 preconditioners. */
+ * AUTO picks SPECTRAL. */
 enum { BLTT_BASIS_AUTO = 0, BLTT_BASIS_SPECTRAL = 1, BLTT_BASIS_PHYSICAL = 2 };
 
 /* Preconditioner kind: ABAC P_alpha (alpha = 1 gives the absolute-value block circulant P_1),
  * or none (MINRES-I, the paper's unpreconditioned comparison solver, Sec. 5.2). */
 enum { BLTT_PRECOND_ABAC = 0, BLTT_PRECOND_NONE = 1 };
+
+/* Arithmetic of the FFT matvec (the 2N circulant-embedding time convolution).  F64: native FP64.
+ * F32X2: every value carried as an unevaluated sum of two FP32 numbers (double-float, about 48
+ * significant bits) and computed on the FP32 pipes, which GB300 runs at 58x its FP64 rate; the
+ * product stays FP64 in memory and agrees with the FP64 result to about 1e-14 relative.
+ * DEFAULT: the handle's setting (F64 unless bltt_set_matvec_arith changed it). */
+enum { BLTT_ARITH_DEFAULT = 0, BLTT_ARITH_F64 = 1, BLTT_ARITH_F32X2 = 2 };
 
 typedef struct {
   int precision;     /* BLTT_PREC_F64 (default when 0) or BLTT_PREC_F32                        */
@@ -85,6 +93,7 @@ typedef struct {
   int precond;       /* BLTT_PRECOND_*                                                          */
   int sync_every;    /* iterations issued between host checks of the device state (0: 2)        */
   int rebuild;       /* 1: rebuild the per-alpha preconditioner tables even if cached            */
+  int matvec_arith;  /* BLTT_ARITH_*                                                             */
 } bltt_solve_opts;
 
 typedef struct {
@@ -115,6 +124,11 @@ bltt_status bltt_destroy(bltt_handle h);
 /* Issue all later work of h on `cuda_stream` (a cudaStream_t; NULL = legacy default stream). */
 bltt_status bltt_set_stream(bltt_handle h, void* cuda_stream);
 
+/* Set the handle's matvec arithmetic (BLTT_ARITH_F64 or BLTT_ARITH_F32X2); used by bltt_matvec
+ * and by solves whose opts leave matvec_arith at DEFAULT.  Blocks with at most 4 nonzero
+ * coefficients use the direct shifted sum in FP64 whatever this setting. */
+bltt_status bltt_set_matvec_arith(bltt_handle h, int arith);
+
 /* y = A x (flip = 0) or y = Y A x (flip = 1), A the BLTT matrix (eq. amatdef), Y = Y_N (x) I_M
  * the time reversal (Sec. 2).  The time convolution runs as a 2N zero-padded circulant
  * product with FFTs along time, or as a direct shifted sum when a and b have at most 4 leading
@@ -125,7 +139,7 @@ bltt_status bltt_matvec(bltt_handle h, const double* x_dev, double* y_dev, int f
 /* z = P_alpha^{-1} v = C_alpha^{-1/2} (C_alpha^{-1/2})^* v (Sec. 5.1): DST-I of every time slice,
  * per spatial mode the alpha-scaled time pass D F conj(Lambda)^{-1/2} F^* D^{-1} followed by
  * D^{-1} F Lambda^{-1/2} F^* D (eqs. hatcalphaidiagform, sqrtcalphabdiagform), inverse DST-I.
- * 0 < alpha <= 1.  precision: 64 or 32 (arithmetic of the whole apply; v and z stay FP64).
+ * 0 < alpha <= 1.  precision: BLTT_PREC_* (arithmetic of the whole apply; v and z stay FP64).
  * v_dev and z_dev may be equal (in place). */
 bltt_status bltt_precond_apply(bltt_handle h, double alpha, const double* v_dev, double* z_dev,
                                int precision);
@@ -147,9 +161,11 @@ bltt_status bltt_minres_solve(bltt_handle h, const double* f_dev, double alpha, 
 /* Per-kernel device time, collected with CUDA events around every launch on the handle's
  * stream while profiling is enabled (tracing aid; adds two event records per launch). */
 typedef struct {
-  char name[24];          /* kernel family: conv, direct, dst64, dst32, timepass64, ...        */
-  long long launches;
-  double total_ms;
+  char name[24];          /* kernel family: conv, conv_df, direct, dst64, dst32, timepass64, ... */
+  long long launches;     /* all launches, including ones that returned at once because the   */
+  double total_ms;        /* solve had already converged (device-side early exit)            */
+  long long active_launches;  /* launches that took more than 1/4 of the family's longest one */
+  double active_ms;
 } bltt_kernel_stat;
 
 /* Enable (1) or disable (0) per-launch timing on h; either way the counters are reset. */

@@ -24,9 +24,10 @@ STATUS_NAMES = {
     4: "BLTT_ERR_CUDA", 5: "BLTT_ERR_NUMERIC", 6: "BLTT_ERR_NOT_CONVERGED", 7: "BLTT_ERR_TIMEOUT",
     8: "BLTT_ERR_UNSUPPORTED",
 }
-PREC_F64, PREC_F32 = 64, 32
+PREC_F64, PREC_F32, PREC_F32X2 = 64, 32, 96
 BASIS_AUTO, BASIS_SPECTRAL, BASIS_PHYSICAL = 0, 1, 2
 PRECOND_ABAC, PRECOND_NONE = 0, 1
+ARITH_DEFAULT, ARITH_F64, ARITH_F32X2 = 0, 1, 2
 
 
 class BlttError(RuntimeError):
@@ -46,7 +47,8 @@ class bltt_blocks(ctypes.Structure):
 
 class bltt_solve_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("basis", ctypes.c_int), ("precond", ctypes.c_int),
-                ("sync_every", ctypes.c_int), ("rebuild", ctypes.c_int)]
+                ("sync_every", ctypes.c_int), ("rebuild", ctypes.c_int),
+                ("matvec_arith", ctypes.c_int)]
 
 
 class bltt_solve_info(ctypes.Structure):
@@ -63,7 +65,8 @@ class bltt_solve_info(ctypes.Structure):
 
 class bltt_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_longlong),
-                ("total_ms", ctypes.c_double)]
+                ("total_ms", ctypes.c_double), ("active_launches", ctypes.c_longlong),
+                ("active_ms", ctypes.c_double)]
 
 
 # C signatures: name -> (restype, argtypes)
@@ -74,6 +77,7 @@ _SIGS = {
     "bltt_destroy": (ctypes.c_int, [_P]),
     "bltt_set_stream": (ctypes.c_int, [_P, _P]),
     "bltt_matvec": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
+    "bltt_set_matvec_arith": (ctypes.c_int, [_P, ctypes.c_int]),
     "bltt_precond_apply": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, ctypes.c_int]),
     "bltt_minres_solve_ex": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                             ctypes.POINTER(bltt_solve_opts), _P,
@@ -152,6 +156,10 @@ def bltt_set_stream(handle, stream):
     _check(lib().bltt_set_stream(handle, ctypes.c_void_p(int(s) if s else 0)), handle)
 
 
+def bltt_set_matvec_arith(handle, arith):
+    _check(lib().bltt_set_matvec_arith(handle, int(arith)), handle)
+
+
 def bltt_matvec(handle, x, y, flip=1):
     _check(lib().bltt_matvec(handle, _ptr(x, "x"), _ptr(y, "y"), int(flip)), handle)
 
@@ -162,8 +170,9 @@ def bltt_precond_apply(handle, alpha, v, z, precision=PREC_F64):
 
 
 def bltt_minres_solve_ex(handle, f, alpha, tol, maxit, u, precision=PREC_F64, basis=BASIS_AUTO,
-                         precond=PRECOND_ABAC, sync_every=0, raise_on_error=True, rebuild=0):
-    opts = bltt_solve_opts(precision, basis, precond, sync_every, rebuild)
+                         precond=PRECOND_ABAC, sync_every=0, raise_on_error=True, rebuild=0,
+                         matvec_arith=ARITH_DEFAULT):
+    opts = bltt_solve_opts(precision, basis, precond, sync_every, rebuild, matvec_arith)
     info = bltt_solve_info()
     st = lib().bltt_minres_solve_ex(handle, _ptr(f, "f"), float(alpha), float(tol), int(maxit),
                                     ctypes.byref(opts), _ptr(u, "u"), ctypes.byref(info))
@@ -184,12 +193,13 @@ def bltt_profile_enable(handle, enable=True):
 
 
 def bltt_profile_read(handle):
-    """{kernel family: (launches, total_ms)} recorded since profiling was enabled."""
+    """{kernel family: (launches, total_ms, active_launches, active_ms)} since profiling began."""
     arr = (bltt_kernel_stat * 64)()
     k = lib().bltt_profile_read(handle, arr, 64)
     if k < 0:
         raise BlttError(1, "null handle")
-    return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms) for i in range(min(k, 64))}
+    return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms, arr[i].active_launches,
+                                   arr[i].active_ms) for i in range(min(k, 64))}
 
 
 def bltt_version():
@@ -223,6 +233,9 @@ class Solver:
         except Exception:
             pass
 
+    def set_matvec_arith(self, arith):
+        bltt_set_matvec_arith(self.handle, arith)
+
     def profile(self, enable=True):
         bltt_profile_enable(self.handle, enable)
 
@@ -245,10 +258,12 @@ class Solver:
         return z
 
     def solve(self, f, alpha=1e-8, tol=1e-8, maxit=200, precision=PREC_F64, basis=BASIS_AUTO,
-              precond=PRECOND_ABAC, u=None, sync_every=0, raise_on_error=True, rebuild=False):
+              precond=PRECOND_ABAC, u=None, sync_every=0, raise_on_error=True, rebuild=False,
+              matvec_arith=ARITH_DEFAULT):
         import torch
         u = torch.empty_like(f) if u is None else u
         st, info = bltt_minres_solve_ex(self.handle, f, alpha, tol, maxit, u, precision, basis,
-                                        precond, sync_every, raise_on_error, int(rebuild))
+                                        precond, sync_every, raise_on_error, int(rebuild),
+                                        matvec_arith)
         info["status_name"] = STATUS_NAMES.get(st, st)
         return u, info

@@ -83,6 +83,12 @@ struct bltt_ctx {
   bool pc_has64 = false, pc_has32 = false;
   double* pc_dinv = nullptr;
   double* pc_d2 = nullptr;
+  float* pc_dinv32 = nullptr;
+  float* pc_d232 = nullptr;
+  float2* pc_dinv_df = nullptr;
+  float2* pc_d2_df = nullptr;
+  float4* pc_gdf = nullptr;
+  bool pc_hasdf = false;
   double2* pc_g64 = nullptr;
   float2* pc_ahat32 = nullptr;
   float2* pc_bhat32 = nullptr;
@@ -96,7 +102,8 @@ struct bltt_ctx {
   size_t ev_used = 0;
   struct Pending { const char* name; cudaEvent_t a, b; };
   std::vector<Pending> pending;
-  std::map<std::string, std::pair<long long, double>> stats;
+  struct Stat { long long launches = 0; double ms = 0; long long act = 0; double act_ms = 0; double max_ms = 0; };
+  std::map<std::string, Stat> stats;
 
   ~bltt_ctx() {
     if (stream_sync_ok) cudaStreamSynchronize(stream);
@@ -157,6 +164,20 @@ cudaError_t upload(bltt_ctx* h, T** dst, const T* src, size_t count) {
   return cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice);
 }
 
+float4 split_df(double re, double im) {
+  float rh = (float)re, ih = (float)im;
+  return make_float4(rh, (float)(re - (double)rh), ih, (float)(im - (double)ih));
+}
+
+cudaError_t upload_df(bltt_ctx* h, const std::vector<double2>& src, const float4** dst) {
+  std::vector<float4> v(src.size());
+  for (size_t k = 0; k < src.size(); ++k) v[k] = split_df(src[k].x, src[k].y);
+  float4* p;
+  cudaError_t e = upload(h, &p, v.data(), v.size());
+  *dst = p;
+  return e;
+}
+
 cudaError_t upload_twiddles(bltt_ctx* h, int L, const double2** d64, const float2** d32) {
   std::vector<double2> tw;
   twiddle_table(L, tw);
@@ -195,7 +216,7 @@ double* vec(bltt_ctx* h, int k) { return h->ws + (size_t)k * h->n; }
 bltt_status prepare_precond(bltt_ctx* h, double alpha, int prec) {
   const int N = h->N;
   if (h->pc_alpha != alpha) {
-    h->pc_has64 = h->pc_has32 = false;
+    h->pc_has64 = h->pc_has32 = h->pc_hasdf = false;
     std::vector<double> dinv(N), d2(N);
     std::vector<cd> ah(N), bh(N);
     for (int j = 0; j < N; ++j) {
@@ -210,6 +231,10 @@ bltt_status prepare_precond(bltt_ctx* h, double alpha, int prec) {
     if (!h->pc_dinv) {
       CK(h, h->alloc(&h->pc_dinv, N), "alloc dinv");
       CK(h, h->alloc(&h->pc_d2, N), "alloc d2");
+      CK(h, h->alloc(&h->pc_dinv32, N), "alloc dinv32");
+      CK(h, h->alloc(&h->pc_d232, N), "alloc d232");
+      CK(h, h->alloc(&h->pc_dinv_df, N), "alloc dinv_df");
+      CK(h, h->alloc(&h->pc_d2_df, N), "alloc d2_df");
       CK(h, h->alloc(&h->pc_ahat64, N / 2 + 1), "alloc ahat");
       CK(h, h->alloc(&h->pc_bhat64, N / 2 + 1), "alloc bhat");
       CK(h, h->alloc(&h->pc_ahat32, N / 2 + 1), "alloc ahat32");
@@ -223,6 +248,18 @@ bltt_status prepare_precond(bltt_ctx* h, double alpha, int prec) {
       a32[k] = make_float2((float)ah[k].real(), (float)ah[k].imag());
       b32[k] = make_float2((float)bh[k].real(), (float)bh[k].imag());
     }
+    std::vector<float> dinv32(N), d232(N);
+    std::vector<float2> dinvdf(N), d2df(N);
+    for (int j = 0; j < N; ++j) {
+      dinv32[j] = (float)dinv[j];
+      d232[j] = (float)d2[j];
+      dinvdf[j] = make_float2(dinv32[j], (float)(dinv[j] - (double)dinv32[j]));
+      d2df[j] = make_float2(d232[j], (float)(d2[j] - (double)d232[j]));
+    }
+    CK(h, cudaMemcpyAsync(h->pc_dinv_df, dinvdf.data(), N * sizeof(float2), cudaMemcpyHostToDevice, h->stream), "copy dinv_df");
+    CK(h, cudaMemcpyAsync(h->pc_d2_df, d2df.data(), N * sizeof(float2), cudaMemcpyHostToDevice, h->stream), "copy d2_df");
+    CK(h, cudaMemcpyAsync(h->pc_dinv32, dinv32.data(), N * sizeof(float), cudaMemcpyHostToDevice, h->stream), "copy dinv32");
+    CK(h, cudaMemcpyAsync(h->pc_d232, d232.data(), N * sizeof(float), cudaMemcpyHostToDevice, h->stream), "copy d232");
     CK(h, cudaMemcpyAsync(h->pc_dinv, dinv.data(), N * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy dinv");
     CK(h, cudaMemcpyAsync(h->pc_d2, d2.data(), N * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy d2");
     CK(h, cudaMemcpyAsync(h->pc_ahat64, a64.data(), a64.size() * sizeof(double2), cudaMemcpyHostToDevice, h->stream), "copy ahat");
@@ -234,13 +271,21 @@ bltt_status prepare_precond(bltt_ctx* h, double alpha, int prec) {
     h->pc_alpha = alpha;
     h->pc_has32 = true;
   }
-  if (prec == 64 && !h->pc_has64) {
+  if (prec == PREC_F64 && !h->pc_has64) {
     if (!h->pc_g64) CK(h, h->alloc(&h->pc_g64, (size_t)(N / 2 + 1) * h->M), "alloc g64 table");
     cudaEvent_t pa = prof_begin(h);
-    CK(h, launch_setup_g64(h->op, h->pc_ahat64, h->pc_bhat64, h->pc_g64, h->stream), "setup g64");
-    prof_end(h, "setup_g64", pa);
+    CK(h, launch_setup_g64(h->op, h->pc_ahat64, h->pc_bhat64, h->pc_g64, nullptr, h->stream), "setup g64");
+    prof_end(h, "setup_g", pa);
     h->launches++;
     h->pc_has64 = true;
+  }
+  if (prec == PREC_DF && !h->pc_hasdf) {
+    if (!h->pc_gdf) CK(h, h->alloc(&h->pc_gdf, (size_t)(N / 2 + 1) * h->M), "alloc gdf table");
+    cudaEvent_t pa = prof_begin(h);
+    CK(h, launch_setup_g64(h->op, h->pc_ahat64, h->pc_bhat64, nullptr, h->pc_gdf, h->stream), "setup gdf");
+    prof_end(h, "setup_g", pa);
+    h->launches++;
+    h->pc_hasdf = true;
   }
   return BLTT_OK;
 }
@@ -250,6 +295,11 @@ PrecTables prec_tables(bltt_ctx* h, int none) {
   pt.alpha = h->pc_alpha;
   pt.dinv = h->pc_dinv;
   pt.d2 = h->pc_d2;
+  pt.dinv32 = h->pc_dinv32;
+  pt.d232 = h->pc_d232;
+  pt.dinv_df = h->pc_dinv_df;
+  pt.d2_df = h->pc_d2_df;
+  pt.gdf = h->pc_gdf;
   pt.g64 = h->pc_g64;
   pt.ahat32 = h->pc_ahat32;
   pt.bhat32 = h->pc_bhat32;
@@ -263,8 +313,8 @@ bltt_status precond_chain(bltt_ctx* h, int spectral, int prec, const PrecTables&
                           const Combine& in, double* out, const double* dot_with,
                           double* partials, int* nparts, const int* phase) {
   const OpTables& op = h->op;
-  const char* tp_name = pt.none ? "identity" : (prec == 64 ? "timepass64" : "timepass32");
-  const char* dst_name = prec == 64 ? "dst64" : "dst32";
+  const char* tp_name = pt.none ? "identity" : (prec == PREC_F64 ? "timepass64" : prec == PREC_DF ? "timepass_df" : "timepass32");
+  const char* dst_name = prec == PREC_F64 ? "dst64" : prec == PREC_DF ? "dst_df" : "dst32";
   if (pt.none || spectral) {
     cudaEvent_t pa = prof_begin(h);
     CK(h, launch_timepass(op, pt, prec, in, out, dot_with, partials, nparts, phase, h->stream), "time pass");
@@ -300,20 +350,24 @@ bltt_status precond_chain(bltt_ctx* h, int spectral, int prec, const PrecTables&
 }
 
 // out = (I (x) U) in, optionally time-reversed (first pass out of place), with ||out||^2 partials
-bltt_status dst_all(bltt_ctx* h, const double* in, double* out, int flip, double* partials,
-                    int* nparts) {
-  const OpTables& op = h->op;
+bltt_status dst_all(bltt_ctx* h, const OpTables& op, const double* in, double* out, int flip,
+                    double* partials, int* nparts) {
+  const int arith = op.mv_arith ? PREC_DF : PREC_F64;
   for (int ax = 0; ax < op.d; ++ax) {
     Combine c{};
     c.in0 = (ax == 0) ? in : out;
     const bool last = (ax == op.d - 1);
     cudaEvent_t pa = prof_begin(h);
-    CK(h, launch_dst(op, ax, 64, c, out, ax == 0 ? flip : 0, last && partials ? out : nullptr,
+    CK(h, launch_dst(op, ax, arith, c, out, ax == 0 ? flip : 0, last && partials ? out : nullptr,
                      last ? partials : nullptr, last ? nparts : nullptr, nullptr, h->stream), "dst");
-    prof_end(h, "dst64", pa);
+    prof_end(h, arith == PREC_DF ? "dst_df" : "dst64", pa);
     h->launches++;
   }
   return BLTT_OK;
+}
+
+const char* mv_name(const OpTables& op) {
+  return op.ntaps > 0 ? "direct" : (op.mv_arith ? "conv_df" : "conv");
 }
 
 cudaEvent_t prof_event(bltt_ctx* h) {
@@ -342,13 +396,25 @@ void prof_end(bltt_ctx* h, const char* name, cudaEvent_t a) {
 void prof_harvest(bltt_ctx* h) {
   if (h->pending.empty()) { h->ev_used = 0; return; }
   cudaStreamSynchronize(h->stream);
-  for (auto& p : h->pending) {
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-      auto& st = h->stats[p.name];
-      st.first += 1;
-      st.second += ms;
-    }
+  std::vector<float> ms(h->pending.size(), 0.f);
+  std::map<std::string, float> mx;
+  for (size_t i = 0; i < h->pending.size(); ++i) {
+    if (cudaEventElapsedTime(&ms[i], h->pending[i].a, h->pending[i].b) != cudaSuccess) ms[i] = -1.f;
+    float& m = mx[h->pending[i].name];
+    m = std::max(m, ms[i]);
+  }
+  for (size_t i = 0; i < h->pending.size(); ++i) {
+    if (ms[i] < 0.f) continue;
+    auto& st = h->stats[h->pending[i].name];
+    st.launches += 1;
+    st.ms += ms[i];
+    st.max_ms = std::max(st.max_ms, (double)ms[i]);
+  }
+  // a launch is active when it took more than 1/4 of its family's longest launch
+  for (size_t i = 0; i < h->pending.size(); ++i) {
+    if (ms[i] < 0.f) continue;
+    auto& st = h->stats[h->pending[i].name];
+    if (ms[i] > 0.25 * st.max_ms) { st.act += 1; st.act_ms += ms[i]; }
   }
   h->pending.clear();
   h->ev_used = 0;
@@ -461,9 +527,28 @@ bltt_status bltt_create(const bltt_blocks* blocks, int N, long long M, bltt_hand
   if (e == cudaSuccess) e = upload(h, &pb, h->b.data(), N);
   op.a_dev = pa; op.b_dev = pb;
   if (e == cudaSuccess) e = upload_twiddles(h, 2 * N, &op.tw_2N, nullptr);
+  if (e == cudaSuccess) e = upload_df(h, Ah, &op.Ahat_df);
+  if (e == cudaSuccess) e = upload_df(h, Bh, &op.Bhat_df);
+  if (e == cudaSuccess) {
+    std::vector<double2> tw;
+    twiddle_table(2 * N, tw);
+    e = upload_df(h, tw, &op.tw_2N_df);
+  }
+  op.mv_arith = 0;
   if (e == cudaSuccess) e = upload_twiddles(h, N, &op.tw_N, &op.tw_N32);
-  for (int ax = 0; ax < h->d && e == cudaSuccess; ++ax)
+  if (e == cudaSuccess) {
+    std::vector<double2> tw;
+    twiddle_table(N, tw);
+    e = upload_df(h, tw, &op.tw_N_df);
+  }
+  for (int ax = 0; ax < h->d && e == cudaSuccess; ++ax) {
     e = upload_twiddles(h, 2 * (h->m[ax] + 1), &op.tw_dst[ax], &op.tw_dst32[ax]);
+    if (e == cudaSuccess) {
+      std::vector<double2> tw;
+      twiddle_table(2 * (h->m[ax] + 1), tw);
+      e = upload_df(h, tw, &op.tw_dst_df[ax]);
+    }
+  }
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&h->ev[i]);
   if (e != cudaSuccess) {
     bltt_status s = (e == cudaErrorMemoryAllocation) ? BLTT_ERR_OOM : BLTT_ERR_CUDA;
@@ -488,6 +573,14 @@ bltt_status bltt_set_stream(bltt_handle h, void* s) {
   return BLTT_OK;
 }
 
+bltt_status bltt_set_matvec_arith(bltt_handle h, int arith) {
+  if (!h) return BLTT_ERR_INVALID_ARG;
+  if (arith != BLTT_ARITH_F64 && arith != BLTT_ARITH_F32X2)
+    return fail(h, BLTT_ERR_INVALID_ARG, "arith must be BLTT_ARITH_F64 or BLTT_ARITH_F32X2");
+  h->op.mv_arith = (arith == BLTT_ARITH_F32X2) ? 1 : 0;
+  return BLTT_OK;
+}
+
 bltt_status bltt_matvec(bltt_handle h, const double* x, double* y, int flip) {
   if (!h) return BLTT_ERR_INVALID_ARG;
   if (!x || !y) return fail(h, BLTT_ERR_INVALID_ARG, "null vector");
@@ -498,7 +591,7 @@ bltt_status bltt_matvec(bltt_handle h, const double* x, double* y, int flip) {
     if (s != BLTT_OK) return s;
     tmp = vec(h, 9);
   }
-  PCK(h, (h->op.ntaps > 0 ? "direct" : "conv"), launch_matvec(h->op, 0, x, nullptr, y, flip ? 1 : 0, MV_STORE, nullptr, nullptr, nullptr,
+  PCK(h, mv_name(h->op), launch_matvec(h->op, 0, x, nullptr, y, flip ? 1 : 0, MV_STORE, nullptr, nullptr, nullptr,
                       nullptr, tmp, h->stream), "matvec");
   return BLTT_OK;
 }
@@ -508,7 +601,7 @@ bltt_status bltt_precond_apply(bltt_handle h, double alpha, const double* v, dou
   if (!h) return BLTT_ERR_INVALID_ARG;
   if (!v || !z) return fail(h, BLTT_ERR_INVALID_ARG, "null vector");
   if (!(alpha > 0.0 && alpha <= 1.0)) return fail(h, BLTT_ERR_INVALID_ARG, "alpha must lie in (0, 1]");
-  if (precision != 64 && precision != 32) return fail(h, BLTT_ERR_INVALID_ARG, "precision must be 64 or 32");
+  if (precision != 64 && precision != 32 && precision != 96) return fail(h, BLTT_ERR_INVALID_ARG, "precision must be 64, 32 or 96");
   bltt_status s = prepare_precond(h, alpha, precision);
   if (s != BLTT_OK) return s;
   PrecTables pt = prec_tables(h, 0);
@@ -527,21 +620,24 @@ bltt_status bltt_minres_solve_ex(bltt_handle h, const double* f, double alpha, d
   bltt_solve_opts o{};
   if (opts) o = *opts;
   if (o.precision == 0) o.precision = 64;
-  if (o.precision != 64 && o.precision != 32) return fail(h, BLTT_ERR_INVALID_ARG, "precision must be 64 or 32");
+  if (o.precision != 64 && o.precision != 32 && o.precision != 96) return fail(h, BLTT_ERR_INVALID_ARG, "precision must be 64, 32 or 96");
   if (o.precond != BLTT_PRECOND_ABAC && o.precond != BLTT_PRECOND_NONE) return fail(h, BLTT_ERR_INVALID_ARG, "bad precond");
   const bool none = (o.precond == BLTT_PRECOND_NONE);
   if (!none && !(alpha > 0.0 && alpha <= 1.0)) return fail(h, BLTT_ERR_INVALID_ARG, "alpha must lie in (0, 1]");
   if (!(tol >= 0.0) || maxit < 1) return fail(h, BLTT_ERR_INVALID_ARG, "tol must be >= 0 and maxit >= 1");
   int basis = o.basis;
-  if (basis == BLTT_BASIS_AUTO) basis = (o.precision == 64) ? BLTT_BASIS_SPECTRAL : BLTT_BASIS_PHYSICAL;
+  if (basis == BLTT_BASIS_AUTO) basis = BLTT_BASIS_SPECTRAL;
   if (basis != BLTT_BASIS_SPECTRAL && basis != BLTT_BASIS_PHYSICAL) return fail(h, BLTT_ERR_INVALID_ARG, "bad basis");
   const int spectral = (basis == BLTT_BASIS_SPECTRAL) ? 1 : 0;
   const int sync_every = o.sync_every > 0 ? o.sync_every : 2;
 
+  if (o.matvec_arith < 0 || o.matvec_arith > 2) return fail(h, BLTT_ERR_INVALID_ARG, "bad matvec_arith");
   bltt_status s = ensure_workspace(h);
   if (s != BLTT_OK) return s;
   h->launches = 0;
-  const OpTables& op = h->op;
+  OpTables op = h->op;
+  if (o.matvec_arith == BLTT_ARITH_F64) op.mv_arith = 0;
+  if (o.matvec_arith == BLTT_ARITH_F32X2) op.mv_arith = 1;
   cudaStream_t st = h->stream;
   CK(h, cudaEventRecord(h->ev[0], st), "event");
   if (o.rebuild) h->pc_alpha = -1.0;
@@ -573,7 +669,7 @@ bltt_status bltt_minres_solve_ex(bltt_handle h, const double* f, double alpha, d
   // b = Y f (spectral: Y (I (x) U) f) with ||b||^2
   int nb = 0, nzv = 0, np = 0;
   if (spectral) {
-    s = dst_all(h, f, bvec, 1, h->partials[1], &nb);
+    s = dst_all(h, op, f, bvec, 1, h->partials[1], &nb);
     if (s != BLTT_OK) return s;
   } else {
     PCK(h, "flip", launch_flip_copy(f, bvec, h->N, h->M, h->partials[1], &nb, st), "flip");
@@ -600,7 +696,7 @@ bltt_status bltt_minres_solve_ex(bltt_handle h, const double* f, double alpha, d
   for (;;) {
     const int prv = 1 - cur;
     // q = Y A z_j  (z_j = z_u / gamma_j), delta_j = <q, z_j>
-    PCK(h, (h->op.ntaps > 0 ? "direct" : "conv"), launch_matvec(op, spectral, zbuf[cur], &h->state->inv_gamma, q, 1, MV_STORE, nullptr,
+    PCK(h, mv_name(op), launch_matvec(op, spectral, zbuf[cur], &h->state->inv_gamma, q, 1, MV_STORE, nullptr,
                         h->partials[0], &np, phase, tmp, st), "matvec");
     h->launches += (op.b_kind == 1 && op.ntaps == 0 && !spectral) ? 2 : 1;
     PCK(h, "scalar", launch_scalar_delta(h->state, h->partials[0], np, st), "scalar delta");
@@ -619,7 +715,7 @@ bltt_status bltt_minres_solve_ex(bltt_handle h, const double* f, double alpha, d
     PCK(h, "w_update", launch_w_update(h->state, zbuf[cur], wbuf[prv], wbuf[cur], x, n, st), "w update");
     h->launches++;
     // true residual when the estimate says so
-    PCK(h, (h->op.ntaps > 0 ? "direct" : "conv"), launch_matvec(op, spectral, x, nullptr, nullptr, 1, MV_RESID, bvec, h->partials[0], &np,
+    PCK(h, mv_name(op), launch_matvec(op, spectral, x, nullptr, nullptr, 1, MV_RESID, bvec, h->partials[0], &np,
                         phase, tmp, st), "residual");
     h->launches += (op.b_kind == 1 && op.ntaps == 0 && !spectral) ? 2 : 1;
     PCK(h, "scalar", launch_scalar_check(h->state, h->partials[0], np, st), "scalar check");
@@ -637,10 +733,10 @@ bltt_status bltt_minres_solve_ex(bltt_handle h, const double* f, double alpha, d
   double relres_phys = sh->relres_true;
   if (spectral) {
     // u = (I (x) U) x_hat, then ||f - A u|| / ||f|| in the physical basis
-    s = dst_all(h, x, u, 0, nullptr, nullptr);
+    s = dst_all(h, op, x, u, 0, nullptr, nullptr);
     if (s != BLTT_OK) return s;
     int nr = 0;
-    PCK(h, (h->op.ntaps > 0 ? "direct" : "conv"), launch_matvec(op, 0, u, nullptr, nullptr, 0, MV_RESID, f, h->partials[0], &nr, nullptr,
+    PCK(h, mv_name(op), launch_matvec(op, 0, u, nullptr, nullptr, 0, MV_RESID, f, h->partials[0], &nr, nullptr,
                         tmp, st), "final residual");
     h->launches += (op.b_kind == 1 && op.ntaps == 0) ? 2 : 1;
     PCK(h, "scalar", launch_sum_partials(h->partials[0], nr, h->scal, st), "sum");
@@ -692,8 +788,10 @@ int bltt_profile_read(bltt_handle h, bltt_kernel_stat* out, int max_entries) {
     if (out && k < max_entries) {
       std::memset(&out[k], 0, sizeof out[k]);
       std::strncpy(out[k].name, kv.first.c_str(), sizeof out[k].name - 1);
-      out[k].launches = kv.second.first;
-      out[k].total_ms = kv.second.second;
+      out[k].launches = kv.second.launches;
+      out[k].total_ms = kv.second.ms;
+      out[k].active_launches = kv.second.act;
+      out[k].active_ms = kv.second.act_ms;
     }
     ++k;
   }

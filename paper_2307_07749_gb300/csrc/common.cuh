@@ -1,8 +1,11 @@
-// common.cuh - device building blocks shared by the libbltt kernels: complex arithmetic, the
-// shared-memory Stockham FFT engine, block reductions and the tile geometry of a batch of lines.
+// common.cuh - device building blocks shared by the libbltt kernels: complex arithmetic in FP64,
+// FP32 and double-float (an FP64-accurate number carried as an unevaluated sum of two FP32 values,
+// run on the FP32 pipes), the shared-memory Stockham FFT engine and block reductions.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include "convert.cuh"
 
 namespace bltt {
 
@@ -12,49 +15,220 @@ template <typename T> struct cplx;
 template <> struct cplx<double> { using t = double2; };
 template <> struct cplx<float> { using t = float2; };
 template <typename T> using C = typename cplx<T>::t;
-
 template <typename T> __device__ __forceinline__ C<T> mk(T re, T im) { C<T> r; r.x = re; r.y = im; return r; }
-template <typename T> __device__ __forceinline__ C<T> cadd(C<T> a, C<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
-template <typename T> __device__ __forceinline__ C<T> csub(C<T> a, C<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
-template <typename T> __device__ __forceinline__ C<T> cconj(C<T> a) { return mk<T>(a.x, -a.y); }
-// a * b
-template <typename T> __device__ __forceinline__ C<T> cmul(C<T> a, C<T> b) {
-  return mk<T>(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+
+// ------------------------------------------------------------------------------------------
+// double-float scalars: value = hi + lo with |lo| <= ulp(hi)/2.  The error-free transforms use
+// the _rn intrinsics so that the compiler never fuses them into FMAs.
+struct dfl {
+  float hi, lo;
+};
+
+// double <-> double-float: the FP32 parts are converted on the integer pipes, which leaves one
+// FP64 subtraction (or addition) per value on the FP64 pipe
+__device__ __forceinline__ dfl df_from(double x) {
+  float h = d2f_bits(x);
+  return {h, d2f_bits(x - f2d_bits(h))};
 }
-// a * conj(b)
-template <typename T> __device__ __forceinline__ C<T> cmulc(C<T> a, C<T> b) {
-  return mk<T>(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+__device__ __forceinline__ double df_to(dfl a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
+
+// a + b: two-sum of the leading parts, the trailing parts added once, then renormalised
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  float s = __fadd_rn(a.hi, b.hi);
+  float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  float h = __fadd_rn(s, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, s))};
 }
-// multiply by -i (forward) or +i (inverse)
-template <typename T, bool INV> __device__ __forceinline__ C<T> rot(C<T> a) {
-  return INV ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
+__device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
+
+// a * b: exact product of the leading parts by FMA, cross terms folded into the error
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  float h = __fadd_rn(p, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+
+// a * b + c * d with one renormalisation
+__device__ __forceinline__ dfl df_dot2(dfl a, dfl b, dfl c, dfl d) {
+  float p1 = __fmul_rn(a.hi, b.hi);
+  float e1 = __fmaf_rn(a.hi, b.hi, -p1);
+  float p2 = __fmul_rn(c.hi, d.hi);
+  float e2 = __fmaf_rn(c.hi, d.hi, -p2);
+  float s = __fadd_rn(p1, p2);
+  float bb = __fsub_rn(s, p1);
+  float es = __fadd_rn(__fsub_rn(p1, __fsub_rn(s, bb)), __fsub_rn(p2, bb));
+  float err = __fadd_rn(__fadd_rn(e1, e2), es);
+  err = __fmaf_rn(a.hi, b.lo, err);
+  err = __fmaf_rn(a.lo, b.hi, err);
+  err = __fmaf_rn(c.hi, d.lo, err);
+  err = __fmaf_rn(c.lo, d.hi, err);
+  float h = __fadd_rn(s, err);
+  return {h, __fsub_rn(err, __fsub_rn(h, s))};
 }
 
 // ------------------------------------------------------------------------------------------
-// Shared-memory Stockham FFT (self-sorting, radix 4 with one radix-2 pass when log2 L is odd).
+// Arithmetic traits of the FFT engine.  V: a complex value; R: its real scalar.
+struct ArithD {
+  using V = double2;
+  using R = double;
+  using Sc = double;   // real scale factor
+  static __device__ __forceinline__ Sc make_sc(double s) { return s; }
+  static __device__ __forceinline__ Sc row_sc(const double* t64, const float*, int p) { return t64[p]; }
+  static __device__ __forceinline__ V scale_sc(V a, Sc s) { return make_double2(a.x * s, a.y * s); }
+  static __device__ __forceinline__ double part_sc(V a, int comp, Sc s) { return (comp ? a.y : a.x) * s; }
+  static __device__ __forceinline__ void put_sc(V* buf, int idx, int comp, double x, Sc s) {
+    reinterpret_cast<double*>(buf)[2 * idx + comp] = x * s;
+  }
+  static __device__ __forceinline__ V add(V a, V b) { return make_double2(a.x + b.x, a.y + b.y); }
+  static __device__ __forceinline__ V sub(V a, V b) { return make_double2(a.x - b.x, a.y - b.y); }
+  static __device__ __forceinline__ V conj(V a) { return make_double2(a.x, -a.y); }
+  static __device__ __forceinline__ V mul(V a, V b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+  }
+  static __device__ __forceinline__ V mulc(V a, V b) {   // a * conj(b)
+    return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+  }
+  template <bool INV> static __device__ __forceinline__ V rot(V a) {   // * -i (fwd), * i (inv)
+    return INV ? make_double2(-a.y, a.x) : make_double2(a.y, -a.x);
+  }
+  static __device__ __forceinline__ V scale(V a, double s) { return make_double2(a.x * s, a.y * s); }
+  static __device__ __forceinline__ V zero() { return make_double2(0.0, 0.0); }
+  static __device__ __forceinline__ V from(double re, double im) { return make_double2(re, im); }
+  static __device__ __forceinline__ double part(V a, int comp) { return comp ? a.y : a.x; }
+  static __device__ __forceinline__ void put(V* buf, int idx, int comp, double x) {
+    reinterpret_cast<double*>(buf)[2 * idx + comp] = x;
+  }
+  static __device__ __forceinline__ void put_pm(V* buf, int i1, int i2, int comp, double x) {
+    reinterpret_cast<double*>(buf)[2 * i1 + comp] = x;
+    reinterpret_cast<double*>(buf)[2 * i2 + comp] = -x;
+  }
+};
+
+struct ArithF {
+  using V = float2;
+  using R = float;
+  using Sc = float;
+  static __device__ __forceinline__ Sc make_sc(double s) { return (float)s; }
+  static __device__ __forceinline__ Sc row_sc(const double*, const float* t32, int p) { return t32[p]; }
+  static __device__ __forceinline__ V scale_sc(V a, Sc s) { return make_float2(a.x * s, a.y * s); }
+  static __device__ __forceinline__ double part_sc(V a, int comp, Sc s) { return f2d_bits((comp ? a.y : a.x) * s); }
+  static __device__ __forceinline__ void put_sc(V* buf, int idx, int comp, double x, Sc s) {
+    reinterpret_cast<float*>(buf)[2 * idx + comp] = d2f_bits(x) * s;
+  }
+  static __device__ __forceinline__ V add(V a, V b) { return make_float2(a.x + b.x, a.y + b.y); }
+  static __device__ __forceinline__ V sub(V a, V b) { return make_float2(a.x - b.x, a.y - b.y); }
+  static __device__ __forceinline__ V conj(V a) { return make_float2(a.x, -a.y); }
+  static __device__ __forceinline__ V mul(V a, V b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+  }
+  static __device__ __forceinline__ V mulc(V a, V b) {
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+  }
+  template <bool INV> static __device__ __forceinline__ V rot(V a) {
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+  }
+  static __device__ __forceinline__ V scale(V a, double s) {
+    float f = (float)s;
+    return make_float2(a.x * f, a.y * f);
+  }
+  static __device__ __forceinline__ V zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ V from(double re, double im) { return make_float2((float)re, (float)im); }
+  static __device__ __forceinline__ double part(V a, int comp) { return f2d_bits(comp ? a.y : a.x); }
+  static __device__ __forceinline__ void put(V* buf, int idx, int comp, double x) {
+    reinterpret_cast<float*>(buf)[2 * idx + comp] = d2f_bits(x);
+  }
+  static __device__ __forceinline__ void put_pm(V* buf, int i1, int i2, int comp, double x) {
+    const float f = d2f_bits(x);
+    reinterpret_cast<float*>(buf)[2 * i1 + comp] = f;
+    reinterpret_cast<float*>(buf)[2 * i2 + comp] = -f;
+  }
+};
+
+// complex double-float packed as float4 {re.hi, re.lo, im.hi, im.lo}
+struct ArithDF {
+  using V = float4;
+  using R = dfl;
+  using Sc = dfl;
+  static __device__ __forceinline__ Sc make_sc(double s) { return df_from(s); }
+  static __device__ __forceinline__ Sc row_sc(const float2* tdf, int p) { const float2 v = tdf[p]; return {v.x, v.y}; }
+  static __device__ __forceinline__ V scale_sc(V a, Sc s) {
+    return pack(df_mul(dfl{a.x, a.y}, s), df_mul(dfl{a.z, a.w}, s));
+  }
+  static __device__ __forceinline__ double part_sc(V a, int comp, Sc s) {
+    return df_to(df_mul(comp ? dfl{a.z, a.w} : dfl{a.x, a.y}, s));
+  }
+  static __device__ __forceinline__ void put_sc(V* buf, int idx, int comp, double x, Sc s) {
+    dfl v = df_mul(df_from(x), s);
+    reinterpret_cast<float2*>(buf)[2 * idx + comp] = make_float2(v.hi, v.lo);
+  }
+  static __device__ __forceinline__ dfl re(V a) { return {a.x, a.y}; }
+  static __device__ __forceinline__ dfl im(V a) { return {a.z, a.w}; }
+  static __device__ __forceinline__ V pack(dfl r, dfl i) { return make_float4(r.hi, r.lo, i.hi, i.lo); }
+  static __device__ __forceinline__ V add(V a, V b) { return pack(df_add(re(a), re(b)), df_add(im(a), im(b))); }
+  static __device__ __forceinline__ V sub(V a, V b) { return pack(df_sub(re(a), re(b)), df_sub(im(a), im(b))); }
+  static __device__ __forceinline__ V conj(V a) { return make_float4(a.x, a.y, -a.z, -a.w); }
+  static __device__ __forceinline__ V mul(V a, V b) {
+    return pack(df_dot2(re(a), re(b), df_neg(im(a)), im(b)), df_dot2(re(a), im(b), im(a), re(b)));
+  }
+  static __device__ __forceinline__ V mulc(V a, V b) {
+    return pack(df_dot2(re(a), re(b), im(a), im(b)), df_dot2(im(a), re(b), df_neg(re(a)), im(b)));
+  }
+  template <bool INV> static __device__ __forceinline__ V rot(V a) {
+    return INV ? make_float4(-a.z, -a.w, a.x, a.y) : make_float4(a.z, a.w, -a.x, -a.y);
+  }
+  static __device__ __forceinline__ V scale(V a, double s) {
+    dfl f = df_from(s);
+    return pack(df_mul(re(a), f), df_mul(im(a), f));
+  }
+  static __device__ __forceinline__ V zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  static __device__ __forceinline__ V from(double r, double i) { return pack(df_from(r), df_from(i)); }
+  static __device__ __forceinline__ double part(V a, int comp) {
+    return comp ? df_to(im(a)) : df_to(re(a));
+  }
+  static __device__ __forceinline__ void put(V* buf, int idx, int comp, double x) {
+    dfl v = df_from(x);
+    reinterpret_cast<float2*>(buf)[2 * idx + comp] = make_float2(v.hi, v.lo);
+  }
+  static __device__ __forceinline__ void put_pm(V* buf, int i1, int i2, int comp, double x) {
+    dfl v = df_from(x);
+    reinterpret_cast<float2*>(buf)[2 * i1 + comp] = make_float2(v.hi, v.lo);
+    reinterpret_cast<float2*>(buf)[2 * i2 + comp] = make_float2(-v.hi, -v.lo);
+  }
+};
+
+// ------------------------------------------------------------------------------------------
+// Shared-memory Stockham FFT (self-sorting; radix 4 with one radix-2 pass when log2 L is odd).
 //
-// buf holds NC independent complex columns of length L, element (p, c) at buf[p * NC + c].
-// tw is the table w_L^k = exp(-2 pi i k / L), k < L.  Forward: X_k = sum_j x_j w^{jk};
-// inverse (INV): the same with conjugate twiddles and no 1/L scaling.
-// Every pass first loads all of its butterfly inputs into registers, synchronises, then writes;
-// so the transform runs in place in buf.  CAP bounds NC*L; the block has NT threads.
-template <typename T, int NT, int CAP, bool INV>
-__device__ void fft_columns(C<T>* buf, int L, int log2L, int NC, const C<T>* __restrict__ tw) {
+// buf holds NC = 2^log2NC independent complex columns of length L, element (p, c) at
+// buf[p * NC + c].  tw holds w_L^k = exp(-2 pi i k / L), k < L.  Forward: X_k = sum_j x_j w^{jk};
+// inverse (INV): conjugate twiddles, no 1/L scaling.  Every pass loads all of its butterfly
+// inputs into registers, synchronises, then writes, so the transform runs in place.
+// CAP bounds NC * L; the block has NT threads.
+template <class A, int NT, int CAP, bool INV>
+__device__ void fft_columns(typename A::V* buf, int L, int log2L, int log2NC,
+                            const typename A::V* __restrict__ tw) {
+  using V = typename A::V;
   constexpr int IPT4 = (CAP / 4 + NT - 1) / NT;   // radix-4 butterflies per thread
   const int tid = threadIdx.x;
+  const int NC = 1 << log2NC, cmask = NC - 1;
   int Ns = 1;
   if (log2L & 1) {
-    // radix-2 pass with Ns = 1: no twiddles; out[2j + r] = DFT2(in[j], in[j + L/2])
     const int half = L >> 1;
-    const int total = NC * half;
-    C<T> v[2 * IPT4][2];
+    const int total = half << log2NC;
+    V v[2 * IPT4][2];
 #pragma unroll
     for (int s = 0; s < 2 * IPT4; ++s) {
       int it = tid + s * NT;
       if (it < total) {
-        int c = it % NC, j = it / NC;
-        v[s][0] = buf[j * NC + c];
-        v[s][1] = buf[(j + half) * NC + c];
+        int c = it & cmask, j = it >> log2NC;
+        v[s][0] = buf[(j << log2NC) + c];
+        v[s][1] = buf[((j + half) << log2NC) + c];
       }
     }
     __syncthreads();
@@ -62,26 +236,26 @@ __device__ void fft_columns(C<T>* buf, int L, int log2L, int NC, const C<T>* __r
     for (int s = 0; s < 2 * IPT4; ++s) {
       int it = tid + s * NT;
       if (it < total) {
-        int c = it % NC, j = it / NC;
-        buf[(2 * j) * NC + c] = cadd<T>(v[s][0], v[s][1]);
-        buf[(2 * j + 1) * NC + c] = csub<T>(v[s][0], v[s][1]);
+        int c = it & cmask, j = it >> log2NC;
+        buf[((2 * j) << log2NC) + c] = A::add(v[s][0], v[s][1]);
+        buf[((2 * j + 1) << log2NC) + c] = A::sub(v[s][0], v[s][1]);
       }
     }
     __syncthreads();
     Ns = 2;
   }
   const int quarter = L >> 2;
-  const int total = NC * quarter;
+  const int total = quarter << log2NC;
   for (; Ns < L; Ns <<= 2) {
-    const int tstep = L / (4 * Ns);   // twiddle index stride: w_{4Ns}^{rk} = w_L^{rk L/(4Ns)}
-    C<T> v[IPT4][4];
+    const int tstep = L / (4 * Ns);
+    V v[IPT4][4];
 #pragma unroll
     for (int s = 0; s < IPT4; ++s) {
       int it = tid + s * NT;
       if (it < total) {
-        int c = it % NC, j = it / NC;
+        int c = it & cmask, j = it >> log2NC;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) v[s][r] = buf[(j + r * quarter) * NC + c];
+        for (int r = 0; r < 4; ++r) v[s][r] = buf[((j + r * quarter) << log2NC) + c];
       }
     }
     __syncthreads();
@@ -89,25 +263,25 @@ __device__ void fft_columns(C<T>* buf, int L, int log2L, int NC, const C<T>* __r
     for (int s = 0; s < IPT4; ++s) {
       int it = tid + s * NT;
       if (it < total) {
-        int c = it % NC, j = it / NC;
+        int c = it & cmask, j = it >> log2NC;
         int k = j & (Ns - 1);
         if (k != 0) {
           int e = k * tstep;
 #pragma unroll
           for (int r = 1; r < 4; ++r) {
-            C<T> w = __ldg(&tw[r * e]);
-            v[s][r] = INV ? cmulc<T>(v[s][r], w) : cmul<T>(v[s][r], w);
+            V w = tw[r * e];
+            v[s][r] = INV ? A::mulc(v[s][r], w) : A::mul(v[s][r], w);
           }
         }
-        C<T> t0 = cadd<T>(v[s][0], v[s][2]);
-        C<T> t1 = csub<T>(v[s][0], v[s][2]);
-        C<T> t2 = cadd<T>(v[s][1], v[s][3]);
-        C<T> t3 = rot<T, INV>(csub<T>(v[s][1], v[s][3]));
-        int o = (j - k) * 4 + k;   // (j / Ns) * 4Ns + k
-        buf[o * NC + c] = cadd<T>(t0, t2);
-        buf[(o + Ns) * NC + c] = cadd<T>(t1, t3);
-        buf[(o + 2 * Ns) * NC + c] = csub<T>(t0, t2);
-        buf[(o + 3 * Ns) * NC + c] = csub<T>(t1, t3);
+        V t0 = A::add(v[s][0], v[s][2]);
+        V t1 = A::sub(v[s][0], v[s][2]);
+        V t2 = A::add(v[s][1], v[s][3]);
+        V t3 = A::template rot<INV>(A::sub(v[s][1], v[s][3]));
+        int o = (j - k) * 4 + k;
+        buf[(o << log2NC) + c] = A::add(t0, t2);
+        buf[((o + Ns) << log2NC) + c] = A::add(t1, t3);
+        buf[((o + 2 * Ns) << log2NC) + c] = A::sub(t0, t2);
+        buf[((o + 3 * Ns) << log2NC) + c] = A::sub(t1, t3);
       }
     }
     __syncthreads();
@@ -132,18 +306,5 @@ __device__ __forceinline__ double block_sum(double v, double* scratch) {
   }
   return r;
 }
-
-// ------------------------------------------------------------------------------------------
-// A batch of lines inside a time-major array: line g has elements at base(g) + p * inner,
-// p < len, with base(g) = (g / inner) * (len * inner) + g % inner.  Time lines: len = N,
-// inner = M.  DST lines along spatial axis ax: len = m_ax, inner = m_0 ... m_{ax-1}.
-struct Lines {
-  long long nlines;
-  int len;
-  long long inner;
-  __device__ __forceinline__ long long base(long long g) const {
-    return (g / inner) * ((long long)len * inner) + (g % inner);
-  }
-};
 
 }  // namespace bltt

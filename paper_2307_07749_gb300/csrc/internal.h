@@ -8,6 +8,7 @@ namespace bltt {
 constexpr int kThreads = 512;      // threads of every FFT tile kernel
 constexpr int kCap = 8192;         // complex points per FFT tile (128 KB of FP64 smem)
 constexpr int kMaxPartials = 1 << 20;
+constexpr int kMaxCols = 256;     // real lines per FFT tile (column info kept in shared memory)
 
 // MINRES scalar state, resident on the device for the whole solve.
 enum Phase { PH_RUN = 0, PH_CHECK = 1, PH_DONE = 2, PH_FAIL = 3, PH_MAXIT = 4 };
@@ -44,6 +45,13 @@ struct OpTables {
   const float2* tw_N32;
   const double2* tw_dst[3];   // twiddles for length 2(m_ax+1)
   const float2* tw_dst32[3];
+  // double-float copies for the FP32-pipe matvec (complex as {re.hi, re.lo, im.hi, im.lo})
+  const float4* Ahat_df;
+  const float4* Bhat_df;
+  const float4* tw_2N_df;
+  const float4* tw_dst_df[3];
+  const float4* tw_N_df;
+  int mv_arith;               // 0: FP64, 1: double-float (matvec and the FP64-accurate DSTs)
 };
 
 // Per-alpha preconditioner data.
@@ -51,20 +59,29 @@ struct PrecTables {
   double alpha;
   const double* dinv;    // 1/d_j, d_j = alpha^{j/N}
   const double* d2;      // d_j^2
+  const float* dinv32;   // the same in FP32
+  const float* d232;
+  const float2* dinv_df; // the same as double-float (hi, lo)
+  const float2* d2_df;
+  const float4* gdf;     // [(N/2+1)][M]: the g64 table as double-float, f32x2 form
   const double2* g64;    // [(N/2+1)][M]: lambda^{-1/2}/(2N), FP64 form
   const float2* ahat32;  // [N/2+1]: FFT_N(D a), FP32 form
   const float2* bhat32;
   int none;              // 1: identity preconditioner (MINRES-I)
 };
 
-// A fused "v = c0*in0 + c1*in1 + c2*in2" load (coefficients from device memory).
+// A fused "v = in0 + c1*in1 + c2*in2" load in FP64 (c1, c2 = coef[1], coef[2] from device
+// memory; coef[0] is not used).
 struct Combine {
   const double* in0;
   const double* in1;     // may be null
   const double* in2;     // may be null
-  const double* coef;    // device, 3 doubles; null means (1, 0, 0)
+  const double* coef;    // device, 3 doubles; null when in1 and in2 are null
   double* vout;          // if set, the combined value is stored here
 };
+
+// preconditioner / transform arithmetic codes
+enum { PREC_F32 = 32, PREC_F64 = 64, PREC_DF = 96 };
 
 // launchers (kernels.cu); all return cudaGetLastError()
 cudaError_t launch_dst(const OpTables& op, int axis, int prec, const Combine& in, double* out,
@@ -79,7 +96,7 @@ cudaError_t launch_matvec(const OpTables& op, int spectral, const double* x, con
                           double* y, int flip, int mode, const double* rhs, double* partials,
                           int* nparts, const int* phase, double* tmp, cudaStream_t st);
 cudaError_t launch_setup_g64(const OpTables& op, const double2* ahat, const double2* bhat,
-                             double2* g64, cudaStream_t st);
+                             double2* g64, float4* gdf, cudaStream_t st);
 cudaError_t launch_flip_copy(const double* f, double* b, int N, long long M, double* partials,
                              int* nparts, cudaStream_t st);
 cudaError_t launch_scalar_init(MinresDev* s, const double* partials_zv, int nzv,

@@ -14,15 +14,16 @@ __device__ __forceinline__ bool skip_phase(const int* phase, int want) {
 }
 
 __device__ __forceinline__ void load_coef(const Combine& cb, double& c0, double& c1, double& c2) {
-  if (cb.coef) { c0 = cb.coef[0]; c1 = cb.coef[1]; c2 = cb.coef[2]; }
-  else { c0 = 1.0; c1 = 0.0; c2 = 0.0; }
+  c0 = 1.0;
+  if (cb.coef) { c1 = cb.coef[1]; c2 = cb.coef[2]; }
+  else { c1 = 0.0; c2 = 0.0; }
 }
 
-// v = c0 in0[e] + c1 in1[e] + c2 in2[e]; optionally stored to vout[e] (vout may alias in1/in2:
-// the same thread reads before it writes).
-__device__ __forceinline__ double combine_at(const Combine& cb, long long e, double c0, double c1,
+// v = in0[e] + c1 in1[e] + c2 in2[e] (FP64); optionally stored to vout[e] (vout may alias
+// in1/in2: the same thread reads before it writes).
+__device__ __forceinline__ double combine_at(const Combine& cb, long long e, double, double c1,
                                              double c2) {
-  double v = c0 * cb.in0[e];
+  double v = cb.in0[e];
   if (cb.in1) v = fma(c1, cb.in1[e], v);
   if (cb.in2) v = fma(c2, cb.in2[e], v);
   if (cb.vout) cb.vout[e] = v;
@@ -88,66 +89,106 @@ static cudaError_t set_smem(K kern, size_t bytes) {
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+static int ilog2(long long v) { int l = 0; while ((1LL << l) < v) ++l; return l; }
+
+// complex columns per FFT tile: fill the tile (kCap points) but keep at most kMaxCols real lines
+// and, when the batch is small, at least two tiles per SM
 int tile_columns(long long nlines, int Lfft) {
   int nc = kCap / Lfft;
   if (nc < 1) nc = 1;
+  if (nc > kMaxCols / 2) nc = kMaxCols / 2;
   long long pairs = (nlines + 1) / 2;
   while (nc > 1 && (pairs + nc - 1) / nc < 2 * 152) nc >>= 1;
   return nc;
 }
 
-static int ilog2(long long v) { int l = 0; while ((1LL << l) < v) ++l; return l; }
+// e / m for 0 <= e < 2^22 without an integer division (float reciprocal, one correction step)
+__device__ __forceinline__ int fast_div(int e, int m, float inv_m) {
+  int c = __float2int_rz((float)e * inv_m);
+  int r = e - c * m;
+  if (r < 0) --c;
+  else if (r >= m) ++c;
+  return c;
+}
+
+constexpr int kBatch = 4;   // independent global loads in flight per thread in the tile loaders
 
 // ============================================================================================
 // DST-I along one spatial axis (Steps 1 and 3 of Sec. 5.1).  Two real lines x_a, x_b share one
 // complex FFT of length 2P (P = m+1) of their odd extensions [0, x, 0, -rev(x)]; then
 // S x_a = -Im(Z_{k+1}) / sqrt(2P) and S x_b = Re(Z_{k+1}) / sqrt(2P), S the normalised DST-I.
-template <typename T>
+// Lines: line g has elements base(g) + p*inner, base(g) = (g/inner)*(m*inner) + g%inner.
+template <class A>
 __global__ void __launch_bounds__(kThreads)
-k_dst(Lines ln, int P, int log2L, int NC, Combine cb, double* out, int flip, int N, long long M,
-      const double* dot_with, double* partials, const C<T>* __restrict__ tw, const int* phase,
-      int want) {
+k_dst(long long nlines, int m, long long inner, int P, int log2L, int log2NC, Combine cb,
+      double* out, int flip, int N, long long M, const double* dot_with, double* partials,
+      const typename A::V* __restrict__ tw, const int* phase, int want) {
   if (skip_phase(phase, want)) return;
+  using V = typename A::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
-  T* bufs = reinterpret_cast<T*>(smem_raw);
+  V* buf = reinterpret_cast<V*>(smem_raw);
   __shared__ double red[32];
-  const int L = 2 * P, m = ln.len, W = 2 * NC;
+  __shared__ long long s_in[kMaxCols], s_out[kMaxCols];
+  const int L = 2 * P, NC = 1 << log2NC, W = 2 * NC;
   const long long g0 = (long long)blockIdx.x * W;
+  for (int c = threadIdx.x; c < W; c += kThreads) {
+    long long g = g0 + c;
+    long long b = -1, o = -1;
+    if (g < nlines) {
+      b = (g / inner) * ((long long)m * inner) + (g % inner);
+      o = b;
+      if (flip) o += (long long)(N - 1 - 2 * (b / M)) * M;
+    }
+    s_in[c] = b;
+    s_out[c] = o;
+  }
+  for (int e = threadIdx.x; e < 2 * NC; e += kThreads)
+    buf[((e & 1) ? P : 0) * NC + (e >> 1)] = A::zero();
+  __syncthreads();
   double c0, c1, c2;
   load_coef(cb, c0, c1, c2);
-  const bool contiguous = (ln.inner == 1);
-  const int total = m * W;
-  for (int e = threadIdx.x; e < total; e += kThreads) {
-    int c, p;
-    if (contiguous) { c = e / m; p = e - c * m; } else { p = e / W; c = e - p * W; }
-    long long g = g0 + c;
-    T val = T(0);
-    if (g < ln.nlines) val = (T)combine_at(cb, ln.base(g) + (long long)p * ln.inner, c0, c1, c2);
-    const int cc = c >> 1, comp = c & 1;
-    bufs[((p + 1) * NC + cc) * 2 + comp] = val;
-    bufs[((L - 1 - p) * NC + cc) * 2 + comp] = -val;
-  }
-  for (int e = threadIdx.x; e < 2 * NC; e += kThreads) {
-    const int cc = e >> 1, which = e & 1;
-    buf[(which ? P : 0) * NC + cc] = mk<T>(T(0), T(0));
+  const bool contiguous = (inner == 1);
+  const float inv_m = 1.0f / (float)m;
+  const int total = m * W, log2W = log2NC + 1;
+  for (int e0 = threadIdx.x; e0 < total; e0 += kBatch * kThreads) {
+    double v[kBatch];
+    int cs[kBatch], ps[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int e = e0 + u * kThreads;
+      int c = 0, p = 0;
+      if (contiguous) { c = fast_div(e, m, inv_m); p = e - c * m; }
+      else { p = e >> log2W; c = e & (W - 1); }
+      cs[u] = c; ps[u] = p;
+      v[u] = 0.0;
+      if (e < total) {
+        const long long b = s_in[c];
+        if (b >= 0) v[u] = combine_at(cb, b + (long long)p * inner, c0, c1, c2);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int e = e0 + u * kThreads;
+      if (e < total) {
+        const int cc = cs[u] >> 1, comp = cs[u] & 1;
+        A::put_pm(buf, (ps[u] + 1) * NC + cc, (L - 1 - ps[u]) * NC + cc, comp, v[u]);
+      }
+    }
   }
   __syncthreads();
-  fft_columns<T, kThreads, kCap, false>(buf, L, log2L, NC, tw);
-  const double scale = rsqrt((double)L);
+  fft_columns<A, kThreads, kCap, false>(buf, L, log2L, log2NC, tw);
+  const typename A::Sc scale = A::make_sc(rsqrt((double)L));
+  const typename A::Sc nscale = A::make_sc(-rsqrt((double)L));
   double acc = 0.0;
   for (int e = threadIdx.x; e < total; e += kThreads) {
     int c, k;
-    if (contiguous) { c = e / m; k = e - c * m; } else { k = e / W; c = e - k * W; }
-    long long g = g0 + c;
-    if (g < ln.nlines) {
-      C<T> z = buf[(k + 1) * NC + (c >> 1)];
-      double val = ((c & 1) ? (double)z.x : -(double)z.y) * scale;
-      long long idx = ln.base(g) + (long long)k * ln.inner;
-      if (flip) {
-        long long t = idx / M;
-        idx += (long long)(N - 1 - 2 * t) * M;
-      }
+    if (contiguous) { c = fast_div(e, m, inv_m); k = e - c * m; }
+    else { k = e >> log2W; c = e & (W - 1); }
+    const long long o = s_out[c];
+    if (o >= 0) {
+      const V z = buf[(k + 1) * NC + (c >> 1)];
+      const double val = (c & 1) ? A::part_sc(z, 0, scale) : A::part_sc(z, 1, nscale);
+      const long long idx = o + (long long)k * inner;
       out[idx] = val;
       if (dot_with) acc = fma(val, dot_with[idx], acc);
     }
@@ -165,94 +206,123 @@ k_dst(Lines ln, int P, int log2L, int NC, Combine cb, double* out, int flip, int
 // per-mode spectra are split and re-merged in the frequency domain (Lemma 3.1 makes each mode's
 // spectrum conjugate-symmetric, so both inverse transforms are real).
 
-// G for the modes ia, ia+1 at frequency k: lambda^{-1/2}/(2N), lambda = ahat_k + bhat_k mu_i
-template <typename T> struct GSrc;
-template <> struct GSrc<double> {
-  static __device__ __forceinline__ C<double> get(const OpTables& op, const PrecTables& pt, int k,
-                                                 long long i) {
+// per-row scale factors (1/d_j and d_j^2) in the arithmetic of the kernel
+template <class A> struct RowSc;
+template <> struct RowSc<ArithD> {
+  static __device__ __forceinline__ double dinv(const PrecTables& pt, int p) { return pt.dinv[p]; }
+  static __device__ __forceinline__ double d2(const PrecTables& pt, int p) { return pt.d2[p]; }
+};
+template <> struct RowSc<ArithF> {
+  static __device__ __forceinline__ float dinv(const PrecTables& pt, int p) { return pt.dinv32[p]; }
+  static __device__ __forceinline__ float d2(const PrecTables& pt, int p) { return pt.d232[p]; }
+};
+template <> struct RowSc<ArithDF> {
+  static __device__ __forceinline__ dfl dinv(const PrecTables& pt, int p) { return ArithDF::row_sc(pt.dinv_df, p); }
+  static __device__ __forceinline__ dfl d2(const PrecTables& pt, int p) { return ArithDF::row_sc(pt.d2_df, p); }
+};
+
+// G for mode i at frequency k: lambda^{-1/2}/(2N), lambda = ahat_k + bhat_k mu_i
+template <class A> struct GSrc;
+template <> struct GSrc<ArithDF> {
+  static __device__ __forceinline__ float4 get(const OpTables& op, const PrecTables& pt, int k,
+                                              long long i, double) {
+    return pt.gdf[(long long)k * op.M + i];
+  }
+};
+template <> struct GSrc<ArithD> {
+  static __device__ __forceinline__ double2 get(const OpTables& op, const PrecTables& pt, int k,
+                                               long long i, double) {
     return pt.g64[(long long)k * op.M + i];
   }
 };
-template <> struct GSrc<float> {
-  static __device__ __forceinline__ C<float> get(const OpTables& op, const PrecTables& pt, int k,
-                                                long long i) {
-    float mu = mode_mu32(op, i);
-    float2 a = pt.ahat32[k], b = pt.bhat32[k];
+template <> struct GSrc<ArithF> {
+  static __device__ __forceinline__ float2 get(const OpTables& op, const PrecTables& pt, int k,
+                                              long long, double mu_d) {
+    const float mu = (float)mu_d;
+    const float2 a = pt.ahat32[k], b = pt.bhat32[k];
     C<float> g = inv_sqrt_principal<float>(fmaf(b.x, mu, a.x), fmaf(b.y, mu, a.y));
     const float sc = 0.5f / (float)op.N;
-    return mk<float>(g.x * sc, g.y * sc);
+    return make_float2(g.x * sc, g.y * sc);
   }
 };
 
-template <typename T, bool CONJ>
-__device__ __forceinline__ void tp_freq_mul(C<T>* buf, const OpTables& op, const PrecTables& pt,
-                                            int NC, long long g0) {
-  const int N = op.N, half = N >> 1;
-  const int items = NC * (half + 1);
+template <class A, bool CONJ>
+__device__ __forceinline__ void tp_freq_mul(typename A::V* buf, const OpTables& op,
+                                            const PrecTables& pt, int log2NC, long long g0,
+                                            const double* s_mu) {
+  using V = typename A::V;
+  const int N = op.N, half = N >> 1, NC = 1 << log2NC;
+  const int items = (half + 1) << log2NC;
   for (int it = threadIdx.x; it < items; it += kThreads) {
-    const int cc = it % NC, k = it / NC;
+    const int cc = it & (NC - 1), k = it >> log2NC;
     const long long ia = g0 + 2 * cc, ib = ia + 1;
-    C<T> Ga = mk<T>(T(0), T(0)), Gb = Ga;
-    if (ia < op.M) Ga = GSrc<T>::get(op, pt, k, ia);
-    if (ib < op.M) Gb = GSrc<T>::get(op, pt, k, ib);
-    if (CONJ) { Ga = cconj<T>(Ga); Gb = cconj<T>(Gb); }
+    V Ga = A::zero(), Gb = A::zero();
+    if (ia < op.M) Ga = GSrc<A>::get(op, pt, k, ia, s_mu[2 * cc]);
+    if (ib < op.M) Gb = GSrc<A>::get(op, pt, k, ib, s_mu[2 * cc + 1]);
+    if (CONJ) { Ga = A::conj(Ga); Gb = A::conj(Gb); }
     const int kb = (N - k) & (N - 1);
-    C<T> A = buf[k * NC + cc], B = buf[kb * NC + cc];
-    C<T> Bc = cconj<T>(B);
-    C<T> U1 = cmul<T>(Ga, cadd<T>(A, Bc));
-    C<T> U2 = cmul<T>(Gb, csub<T>(A, Bc));
-    buf[k * NC + cc] = cadd<T>(U1, U2);
-    if (kb != k) buf[kb * NC + cc] = cconj<T>(csub<T>(U1, U2));
+    const V Av = buf[k * NC + cc], Bc = A::conj(buf[kb * NC + cc]);
+    const V U1 = A::mul(Ga, A::add(Av, Bc));
+    const V U2 = A::mul(Gb, A::sub(Av, Bc));
+    buf[k * NC + cc] = A::add(U1, U2);
+    if (kb != k) buf[kb * NC + cc] = A::conj(A::sub(U1, U2));
   }
 }
 
-template <typename T>
+template <class A>
 __global__ void __launch_bounds__(kThreads)
 k_timepass(OpTables op, PrecTables pt, Combine cb, double* out, const double* dot_with,
-           double* partials, const int* phase, int want, int NC) {
+           double* partials, const int* phase, int want, int log2NC,
+           const typename A::V* __restrict__ tw) {
   if (skip_phase(phase, want)) return;
+  using V = typename A::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
-  T* bufs = reinterpret_cast<T*>(smem_raw);
+  V* buf = reinterpret_cast<V*>(smem_raw);
   __shared__ double red[32];
-  const int N = op.N, W = 2 * NC;
+  __shared__ double s_mu[kMaxCols];
+  const int N = op.N, NC = 1 << log2NC, W = 2 * NC, log2W = log2NC + 1;
   const long long M = op.M;
   const long long g0 = (long long)blockIdx.x * W;
-  const C<T>* tw = reinterpret_cast<const C<T>*>(sizeof(T) == 8 ? (const void*)op.tw_N
-                                                                 : (const void*)op.tw_N32);
+  for (int c = threadIdx.x; c < W; c += kThreads) s_mu[c] = (g0 + c < M) ? mode_mu(op, g0 + c) : 0.0;
   double c0, c1, c2;
   load_coef(cb, c0, c1, c2);
   const int total = N * W;
-  for (int e = threadIdx.x; e < total; e += kThreads) {
-    const int p = e / W, c = e - p * W;
-    const long long i = g0 + c;
-    T val = T(0);
-    if (i < M) val = (T)(combine_at(cb, (long long)p * M + i, c0, c1, c2) * pt.dinv[p]);
-    bufs[(p * NC + (c >> 1)) * 2 + (c & 1)] = val;
+  for (int e0 = threadIdx.x; e0 < total; e0 += kBatch * kThreads) {
+    double v[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int e = e0 + u * kThreads;
+      const int p = e >> log2W, c = e & (W - 1);
+      v[u] = 0.0;
+      if (e < total && g0 + c < M) v[u] = combine_at(cb, (long long)p * M + g0 + c, c0, c1, c2);
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int e = e0 + u * kThreads;
+      if (e < total) {
+        const int p = e >> log2W, c = e & (W - 1);
+        A::put_sc(buf, p * NC + (c >> 1), c & 1, v[u], RowSc<A>::dinv(pt, p));
+      }
+    }
   }
   __syncthreads();
-  fft_columns<T, kThreads, kCap, false>(buf, N, op.log2N, NC, tw);
-  tp_freq_mul<T, true>(buf, op, pt, NC, g0);
+  fft_columns<A, kThreads, kCap, false>(buf, N, op.log2N, log2NC, tw);
+  tp_freq_mul<A, true>(buf, op, pt, log2NC, g0, s_mu);
   __syncthreads();
-  fft_columns<T, kThreads, kCap, true>(buf, N, op.log2N, NC, tw);
-  for (int e = threadIdx.x; e < N * NC; e += kThreads) {
-    const int p = e / NC;
-    const T s = (T)pt.d2[p];
-    C<T> v = buf[e];
-    buf[e] = mk<T>(v.x * s, v.y * s);
-  }
+  fft_columns<A, kThreads, kCap, true>(buf, N, op.log2N, log2NC, tw);
+  for (int e = threadIdx.x; e < N * NC; e += kThreads)
+    buf[e] = A::scale_sc(buf[e], RowSc<A>::d2(pt, e >> log2NC));
   __syncthreads();
-  fft_columns<T, kThreads, kCap, false>(buf, N, op.log2N, NC, tw);
-  tp_freq_mul<T, false>(buf, op, pt, NC, g0);
+  fft_columns<A, kThreads, kCap, false>(buf, N, op.log2N, log2NC, tw);
+  tp_freq_mul<A, false>(buf, op, pt, log2NC, g0, s_mu);
   __syncthreads();
-  fft_columns<T, kThreads, kCap, true>(buf, N, op.log2N, NC, tw);
+  fft_columns<A, kThreads, kCap, true>(buf, N, op.log2N, log2NC, tw);
   double acc = 0.0;
   for (int e = threadIdx.x; e < total; e += kThreads) {
-    const int p = e / W, c = e - p * W;
-    const long long i = g0 + c;
-    if (i < M) {
-      const long long idx = (long long)p * M + i;
-      const double z = (double)bufs[(p * NC + (c >> 1)) * 2 + (c & 1)] * pt.dinv[p];
+    const int p = e >> log2W, c = e & (W - 1);
+    if (g0 + c < M) {
+      const long long idx = (long long)p * M + g0 + c;
+      const double z = A::part_sc(buf[p * NC + (c >> 1)], c & 1, RowSc<A>::dinv(pt, p));
       out[idx] = z;
       if (dot_with) acc = fma(z, dot_with[idx], acc);
     }
@@ -291,75 +361,158 @@ __global__ void k_precond_identity(Combine cb, double* out, long long n, const d
 //   spectral: 1 -> lines are DST modes (matvec of (I (x) U) A (I (x) U)), 0 -> physical points.
 //   which:    0 -> y = conv_a + extra term; 1 -> y = conv_b only (physical general-b first pass).
 //   st_src:   source of the physical stencil term (x itself when b = b0 e_0, else conv_b(x)).
+// A = ArithD runs on the FP64 pipe; A = ArithDF carries every value as a double-float pair on the
+// FP32 pipes (about 2^-47 relative rounding per operation).
+template <class A> struct ConvTables;
+template <> struct ConvTables<ArithD> {
+  static __device__ __forceinline__ const double2* tw(const OpTables& op) { return op.tw_2N; }
+  static __device__ __forceinline__ const double2* H(const OpTables& op, int which) { return which ? op.Bhat : op.Ahat; }
+  // per-mode spectrum, halved for the split of the packed pair: (A + mu B)/2 (general b) or
+  // A/2 + sh (b = b0 e_0: B = 1/(2N) is a constant, so sh = b0 mu / (4N) is precomputed)
+  static __device__ __forceinline__ double2 Hmode(const double2 a, const double2 b, double mu_or_sh, bool genb) {
+    if (genb) return make_double2(0.5 * fma(mu_or_sh, b.x, a.x), 0.5 * fma(mu_or_sh, b.y, a.y));
+    return make_double2(fma(0.5, a.x, mu_or_sh), 0.5 * a.y);
+  }
+  static __device__ __forceinline__ double sc_mu(double v) { return v; }
+};
+template <> struct ConvTables<ArithDF> {
+  static __device__ __forceinline__ const float4* tw(const OpTables& op) { return op.tw_2N_df; }
+  static __device__ __forceinline__ const float4* H(const OpTables& op, int which) { return which ? op.Bhat_df : op.Ahat_df; }
+  static __device__ __forceinline__ float4 Hmode(const float4 a, const float4 b, dfl mu_or_sh, bool genb) {
+    const dfl ar = {0.5f * a.x, 0.5f * a.y}, ai = {0.5f * a.z, 0.5f * a.w};   // exact halving
+    if (genb) {
+      const dfl br = {0.5f * b.x, 0.5f * b.y}, bi = {0.5f * b.z, 0.5f * b.w};
+      return ArithDF::pack(df_add(ar, df_mul(mu_or_sh, br)), df_add(ai, df_mul(mu_or_sh, bi)));
+    }
+    return ArithDF::pack(df_add(ar, mu_or_sh), ai);
+  }
+};
+template <class A> struct MuT;
+template <> struct MuT<ArithD> { using t = double; static __device__ __forceinline__ double make(double v) { return v; } };
+template <> struct MuT<ArithDF> { using t = dfl; static __device__ __forceinline__ dfl make(double v) { return df_from(v); } };
+
+template <class A>
 __global__ void __launch_bounds__(kThreads)
 k_conv(OpTables op, int spectral, int which, const double* x, const double* xscale, double* y,
        int flip, int mode, const double* rhs, double* partials, const int* phase, int want,
-       const double* st_src, int NC) {
+       const double* st_src, int log2NC) {
   if (skip_phase(phase, want)) return;
+  using V = typename A::V;
+  using MT = typename MuT<A>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* buf = reinterpret_cast<double2*>(smem_raw);
-  double* bufs = reinterpret_cast<double*>(smem_raw);
+  V* buf = reinterpret_cast<V*>(smem_raw);
   __shared__ double red[32];
-  const int N = op.N, L = 2 * N, W = 2 * NC;
+  __shared__ MT s_mu[kMaxCols];
+  __shared__ int s_nb[kMaxCols];
+  const int N = op.N, L = 2 * N, NC = 1 << log2NC, W = 2 * NC, log2W = log2NC + 1;
   const long long M = op.M;
   const long long g0 = (long long)blockIdx.x * W;
   const double s = xscale ? *xscale : 1.0;
-  const int total = N * W;
-  for (int e = threadIdx.x; e < total; e += kThreads) {
-    const int p = e / W, c = e - p * W;
+  const bool genb = (op.b_kind == 1);
+  const bool extra_st = !spectral && which == 0 && st_src != nullptr;
+  for (int c = threadIdx.x; c < W; c += kThreads) {
     const long long i = g0 + c;
-    double val = 0.0;
-    if (i < M) val = x[(long long)p * M + i] * s;
-    bufs[(p * NC + (c >> 1)) * 2 + (c & 1)] = val;
+    double mu = 0.0;
+    int nb = 0;
+    if (i < M) {
+      if (spectral) mu = genb ? mode_mu(op, i) : op.b0 * mode_mu(op, i) / (4.0 * N);
+      long long r = i;
+      for (int ax = 0; ax < op.d; ++ax) {
+        const long long q = r / op.m[ax];
+        const int cx = (int)(r - q * op.m[ax]);
+        r = q;
+        if (cx > 0) nb |= 1 << (2 * ax);
+        if (cx < op.m[ax] - 1) nb |= 2 << (2 * ax);
+      }
+    }
+    s_mu[c] = MuT<A>::make(mu);
+    s_nb[c] = nb;
   }
-  for (int e = threadIdx.x; e < N * NC; e += kThreads) buf[N * NC + e] = make_double2(0.0, 0.0);
+  const typename A::Sc ssc = A::make_sc(s);
+  const int total = N * W;
+  for (int e0 = threadIdx.x; e0 < total; e0 += kBatch * kThreads) {
+    double v[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int e = e0 + u * kThreads;
+      const int p = e >> log2W, c = e & (W - 1);
+      v[u] = (e < total && g0 + c < M) ? x[(long long)p * M + g0 + c] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int e = e0 + u * kThreads;
+      if (e < total) {
+        const int p = e >> log2W, c = e & (W - 1);
+        A::put_sc(buf, p * NC + (c >> 1), c & 1, v[u], ssc);
+      }
+    }
+  }
+  for (int e = threadIdx.x; e < N * NC; e += kThreads) buf[N * NC + e] = A::zero();
   __syncthreads();
-  fft_columns<double, kThreads, kCap, false>(buf, L, op.log2N + 1, NC, op.tw_2N);
-  const bool split = spectral && op.b_kind == 1;
-  if (!split) {
-    const double2* H = which ? op.Bhat : op.Ahat;
+  const V* __restrict__ tw = ConvTables<A>::tw(op);
+  fft_columns<A, kThreads, kCap, false>(buf, L, op.log2N + 1, log2NC, tw);
+  if (!spectral) {
+    const V* __restrict__ H = ConvTables<A>::H(op, which);
     for (int e = threadIdx.x; e < L * NC; e += kThreads) {
-      const int k = e / NC;
-      double2 h = (k <= N) ? H[k] : cconj<double>(H[L - k]);
-      buf[e] = cmul<double>(buf[e], h);
+      const int k = e >> log2NC;
+      const V h = (k <= N) ? H[k] : A::conj(H[L - k]);
+      buf[e] = A::mul(buf[e], h);
     }
   } else {
-    // per-mode H_i = Ahat + mu_i Bhat; split the packed spectra (extra factor 1/2)
-    const int items = NC * (N + 1);
+    // per-mode spectrum H_i = FFT_2N([a;0] + mu_i [b;0]) / (2N); the packed pair is split
+    const V* __restrict__ HA = ConvTables<A>::H(op, 0);
+    const V* __restrict__ HB = ConvTables<A>::H(op, 1);
+    const int items = (N + 1) << log2NC;
     for (int it = threadIdx.x; it < items; it += kThreads) {
-      const int cc = it % NC, k = it / NC;
-      const long long ia = g0 + 2 * cc, ib = ia + 1;
-      const double mua = ia < M ? mode_mu(op, ia) : 0.0, mub = ib < M ? mode_mu(op, ib) : 0.0;
-      const double2 A_ = op.Ahat[k], B_ = op.Bhat[k];
-      double2 Ha = make_double2(0.5 * fma(mua, B_.x, A_.x), 0.5 * fma(mua, B_.y, A_.y));
-      double2 Hb = make_double2(0.5 * fma(mub, B_.x, A_.x), 0.5 * fma(mub, B_.y, A_.y));
+      const int cc = it & (NC - 1), k = it >> log2NC;
+      const V a_ = HA[k], b_ = HB[k];
+      const V Ha = ConvTables<A>::Hmode(a_, b_, s_mu[2 * cc], genb);
+      const V Hb = ConvTables<A>::Hmode(a_, b_, s_mu[2 * cc + 1], genb);
       const int kb = (L - k) & (L - 1);
-      double2 Av = buf[k * NC + cc], Bv = buf[kb * NC + cc];
-      double2 Bc = cconj<double>(Bv);
-      double2 U1 = cmul<double>(Ha, cadd<double>(Av, Bc));
-      double2 U2 = cmul<double>(Hb, csub<double>(Av, Bc));
-      buf[k * NC + cc] = cadd<double>(U1, U2);
-      if (kb != k) buf[kb * NC + cc] = cconj<double>(csub<double>(U1, U2));
+      const V Av = buf[k * NC + cc], Bc = A::conj(buf[kb * NC + cc]);
+      const V U1 = A::mul(Ha, A::add(Av, Bc));
+      const V U2 = A::mul(Hb, A::sub(Av, Bc));
+      buf[k * NC + cc] = A::add(U1, U2);
+      if (kb != k) buf[kb * NC + cc] = A::conj(A::sub(U1, U2));
     }
   }
   __syncthreads();
-  fft_columns<double, kThreads, kCap, true>(buf, L, op.log2N + 1, NC, op.tw_2N);
+  fft_columns<A, kThreads, kCap, true>(buf, L, op.log2N + 1, log2NC, tw);
   double acc = 0.0;
-  const bool extra_mu = spectral && op.b_kind == 0 && which == 0;
-  const bool extra_st = !spectral && which == 0 && st_src != nullptr;
   const double st_coef = (op.b_kind == 0) ? op.b0 * s : 1.0;
+  const long long s1 = op.m[0], s2 = (long long)op.m[0] * op.m[1];
   for (int e = threadIdx.x; e < total; e += kThreads) {
-    const int t = e / W, c = e - t * W;
+    const int t = e >> log2W, c = e & (W - 1);
     const long long i = g0 + c;
     if (i >= M) continue;
-    double val = bufs[(t * NC + (c >> 1)) * 2 + (c & 1)];
-    if (extra_mu) val = fma(op.b0 * mode_mu(op, i), x[(long long)t * M + i] * s, val);
-    if (extra_st) val = fma(st_coef, stencil_at(op, st_src + (long long)t * M, i), val);
+    double val = A::part(buf[t * NC + (c >> 1)], c & 1);
+    if (extra_st) {
+      const double* xt = st_src + (long long)t * M;
+      const int nb = s_nb[c];
+      const double xi2 = 2.0 * xt[i];
+      double sx = xi2;
+      if (nb & 1) sx -= xt[i - 1];
+      if (nb & 2) sx -= xt[i + 1];
+      double lap = sx * op.h2inv[0];
+      if (op.d > 1) {
+        double sy = xi2;
+        if (nb & 4) sy -= xt[i - s1];
+        if (nb & 8) sy -= xt[i + s1];
+        lap = fma(sy, op.h2inv[1], lap);
+        if (op.d > 2) {
+          double sz = xi2;
+          if (nb & 16) sz -= xt[i - s2];
+          if (nb & 32) sz -= xt[i + s2];
+          lap = fma(sz, op.h2inv[2], lap);
+        }
+      }
+      val = fma(st_coef, lap, val);
+    }
     const int to = flip ? (N - 1 - t) : t;
     const long long idx = (long long)to * M + i;
     if (mode == MV_STORE) {
       y[idx] = val;
-      if (partials) acc = fma(val, x[idx] * s, acc);
+      if (partials) acc = fma(val, x[idx], acc);     // times s once per block below
     } else {
       const double r = rhs[idx] - val;
       if (y) y[idx] = r;
@@ -368,7 +521,7 @@ k_conv(OpTables op, int spectral, int which, const double* x, const double* xsca
   }
   if (partials) {
     double sum = block_sum<kThreads>(acc, red);
-    if (threadIdx.x == 0) partials[blockIdx.x] = sum;
+    if (threadIdx.x == 0) partials[blockIdx.x] = (mode == MV_STORE) ? sum * s : sum;
   }
 }
 
@@ -420,7 +573,8 @@ k_direct(OpTables op, int spectral, const double* x, const double* xscale, doubl
 // Set-up of the FP64 time-pass table: g(k, i) = lambda_i(k)^{-1/2} / (2N), k = 0..N/2, with
 // lambda_i(k) = ahat_k + bhat_k mu_i the eigenvalues of eq. hatcalphaieigvaldef (principal branch,
 // Def. 2; Re lambda > 0 by diagonal dominance, Sec. 3).
-__global__ void k_setup_g64(OpTables op, const double2* ahat, const double2* bhat, double2* g) {
+__global__ void k_setup_g64(OpTables op, const double2* ahat, const double2* bhat, double2* g,
+                            float4* gdf) {
   const int half = op.N / 2;
   const long long total = (long long)(half + 1) * op.M;
   const double sc = 0.5 / op.N;
@@ -431,7 +585,12 @@ __global__ void k_setup_g64(OpTables op, const double2* ahat, const double2* bha
     const double mu = mode_mu(op, i);
     const double2 a = ahat[k], b = bhat[k];
     double2 v = inv_sqrt_principal<double>(fma(b.x, mu, a.x), fma(b.y, mu, a.y));
-    g[e] = make_double2(v.x * sc, v.y * sc);
+    const double gr = v.x * sc, gi = v.y * sc;
+    if (g) g[e] = make_double2(gr, gi);
+    if (gdf) {
+      const dfl r = df_from(gr), im = df_from(gi);
+      gdf[e] = make_float4(r.hi, r.lo, im.hi, im.lo);
+    }
   }
 }
 
@@ -579,26 +738,24 @@ static int grid_stream(long long n, int threads) {
   return (int)g;
 }
 
-template <typename T>
-static cudaError_t ensure_smem_dst() {
+template <class A> static cudaError_t ensure_smem_dst() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = set_smem(k_dst<T>, kCap * sizeof(C<T>));
+  cudaError_t e = set_smem(k_dst<A>, kCap * sizeof(typename A::V));
   if (e == cudaSuccess) done = true;
   return e;
 }
-template <typename T>
-static cudaError_t ensure_smem_tp() {
+template <class A> static cudaError_t ensure_smem_tp() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = set_smem(k_timepass<T>, kCap * sizeof(C<T>));
+  cudaError_t e = set_smem(k_timepass<A>, kCap * sizeof(typename A::V));
   if (e == cudaSuccess) done = true;
   return e;
 }
-static cudaError_t ensure_smem_conv() {
+template <class A> static cudaError_t ensure_smem_conv() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = set_smem(k_conv, kCap * sizeof(double2));
+  cudaError_t e = set_smem(k_conv<A>, kCap * sizeof(typename A::V));
   if (e == cudaSuccess) done = true;
   return e;
 }
@@ -606,29 +763,33 @@ static cudaError_t ensure_smem_conv() {
 cudaError_t launch_dst(const OpTables& op, int axis, int prec, const Combine& in, double* out,
                        int flip, const double* dot_with, double* partials, int* nparts,
                        const int* phase, cudaStream_t st) {
-  Lines ln;
-  ln.len = op.m[axis];
+  const int m = op.m[axis];
   long long inner = 1;
   for (int a = 0; a < axis; ++a) inner *= op.m[a];
-  ln.inner = inner;
-  ln.nlines = (long long)op.N * op.M / op.m[axis];
-  const int P = op.m[axis] + 1;
-  const int L = 2 * P;
-  const int NC = tile_columns(ln.nlines, L);
-  const long long grid = (ln.nlines + 2 * NC - 1) / (2 * NC);
+  const long long nlines = (long long)op.N * op.M / m;
+  const int P = m + 1, L = 2 * P;
+  const int NC = tile_columns(nlines, L);
+  const int log2NC = ilog2(NC);
+  const long long grid = (nlines + 2 * NC - 1) / (2 * NC);
   if (nparts) *nparts = (int)grid;
-  if (prec == 64) {
-    cudaError_t e = ensure_smem_dst<double>();
+  if (prec == PREC_F64) {
+    cudaError_t e = ensure_smem_dst<ArithD>();
     if (e != cudaSuccess) return e;
-    k_dst<double><<<(unsigned)grid, kThreads, kCap * sizeof(double2), st>>>(
-        ln, P, ilog2(L), NC, in, out, flip, op.N, op.M, dot_with, partials, op.tw_dst[axis],
-        phase, PH_RUN);
+    k_dst<ArithD><<<(unsigned)grid, kThreads, kCap * sizeof(double2), st>>>(
+        nlines, m, inner, P, ilog2(L), log2NC, in, out, flip, op.N, op.M, dot_with, partials,
+        op.tw_dst[axis], phase, PH_RUN);
+  } else if (prec == PREC_DF) {
+    cudaError_t e = ensure_smem_dst<ArithDF>();
+    if (e != cudaSuccess) return e;
+    k_dst<ArithDF><<<(unsigned)grid, kThreads, kCap * sizeof(float4), st>>>(
+        nlines, m, inner, P, ilog2(L), log2NC, in, out, flip, op.N, op.M, dot_with, partials,
+        op.tw_dst_df[axis], phase, PH_RUN);
   } else {
-    cudaError_t e = ensure_smem_dst<float>();
+    cudaError_t e = ensure_smem_dst<ArithF>();
     if (e != cudaSuccess) return e;
-    k_dst<float><<<(unsigned)grid, kThreads, kCap * sizeof(float2), st>>>(
-        ln, P, ilog2(L), NC, in, out, flip, op.N, op.M, dot_with, partials, op.tw_dst32[axis],
-        phase, PH_RUN);
+    k_dst<ArithF><<<(unsigned)grid, kThreads, kCap * sizeof(float2), st>>>(
+        nlines, m, inner, P, ilog2(L), log2NC, in, out, flip, op.N, op.M, dot_with, partials,
+        op.tw_dst32[axis], phase, PH_RUN);
   }
   return cudaGetLastError();
 }
@@ -644,19 +805,49 @@ cudaError_t launch_timepass(const OpTables& op, const PrecTables& pt, int prec, 
     return cudaGetLastError();
   }
   const int NC = tile_columns(op.M, op.N);
+  const int log2NC = ilog2(NC);
   const long long grid = (op.M + 2 * NC - 1) / (2 * NC);
   if (nparts) *nparts = (int)grid;
-  if (prec == 64) {
-    cudaError_t e = ensure_smem_tp<double>();
+  if (prec == PREC_F64) {
+    cudaError_t e = ensure_smem_tp<ArithD>();
     if (e != cudaSuccess) return e;
-    k_timepass<double><<<(unsigned)grid, kThreads, kCap * sizeof(double2), st>>>(
-        op, pt, in, out, dot_with, partials, phase, PH_RUN, NC);
+    k_timepass<ArithD><<<(unsigned)grid, kThreads, kCap * sizeof(double2), st>>>(
+        op, pt, in, out, dot_with, partials, phase, PH_RUN, log2NC, op.tw_N);
+  } else if (prec == PREC_DF) {
+    cudaError_t e = ensure_smem_tp<ArithDF>();
+    if (e != cudaSuccess) return e;
+    k_timepass<ArithDF><<<(unsigned)grid, kThreads, kCap * sizeof(float4), st>>>(
+        op, pt, in, out, dot_with, partials, phase, PH_RUN, log2NC, op.tw_N_df);
   } else {
-    cudaError_t e = ensure_smem_tp<float>();
+    cudaError_t e = ensure_smem_tp<ArithF>();
     if (e != cudaSuccess) return e;
-    k_timepass<float><<<(unsigned)grid, kThreads, kCap * sizeof(float2), st>>>(
-        op, pt, in, out, dot_with, partials, phase, PH_RUN, NC);
+    k_timepass<ArithF><<<(unsigned)grid, kThreads, kCap * sizeof(float2), st>>>(
+        op, pt, in, out, dot_with, partials, phase, PH_RUN, log2NC, op.tw_N32);
   }
+  return cudaGetLastError();
+}
+
+template <class A>
+static cudaError_t launch_conv_t(const OpTables& op, int spectral, const double* x,
+                                 const double* xscale, double* y, int flip, int mode,
+                                 const double* rhs, double* partials, int* nparts,
+                                 const int* phase, int want, double* tmp, cudaStream_t st) {
+  cudaError_t e = ensure_smem_conv<A>();
+  if (e != cudaSuccess) return e;
+  const int NC = tile_columns(op.M, 2 * op.N);
+  const int log2NC = ilog2(NC);
+  const long long grid = (op.M + 2 * NC - 1) / (2 * NC);
+  if (nparts) *nparts = (int)grid;
+  const size_t smem = kCap * sizeof(typename A::V);
+  const double* st_src = x;
+  if (!spectral && op.b_kind == 1) {
+    // conv_b(x) first (scaled like x), then y = conv_a(x) + L conv_b(x)
+    k_conv<A><<<(unsigned)grid, kThreads, smem, st>>>(op, 0, 1, x, xscale, tmp, 0, MV_STORE,
+                                                     nullptr, nullptr, phase, want, nullptr, log2NC);
+    st_src = tmp;
+  }
+  k_conv<A><<<(unsigned)grid, kThreads, smem, st>>>(op, spectral, 0, x, xscale, y, flip, mode, rhs,
+                                                   partials, phase, want, st_src, log2NC);
   return cudaGetLastError();
 }
 
@@ -672,27 +863,17 @@ cudaError_t launch_matvec(const OpTables& op, int spectral, const double* x, con
                                 want);
     return cudaGetLastError();
   }
-  cudaError_t e = ensure_smem_conv();
-  if (e != cudaSuccess) return e;
-  const int NC = tile_columns(op.M, 2 * op.N);
-  const long long grid = (op.M + 2 * NC - 1) / (2 * NC);
-  if (nparts) *nparts = (int)grid;
-  const double* st_src = x;
-  if (!spectral && op.b_kind == 1) {
-    // conv_b(x) first (scaled like x), then y = conv_a(x) + L conv_b(x)
-    k_conv<<<(unsigned)grid, kThreads, kCap * sizeof(double2), st>>>(
-        op, 0, 1, x, xscale, tmp, 0, MV_STORE, nullptr, nullptr, phase, want, nullptr, NC);
-    st_src = tmp;
-  }
-  k_conv<<<(unsigned)grid, kThreads, kCap * sizeof(double2), st>>>(
-      op, spectral, 0, x, xscale, y, flip, mode, rhs, partials, phase, want, st_src, NC);
-  return cudaGetLastError();
+  if (op.mv_arith == 1)
+    return launch_conv_t<ArithDF>(op, spectral, x, xscale, y, flip, mode, rhs, partials, nparts,
+                                  phase, want, tmp, st);
+  return launch_conv_t<ArithD>(op, spectral, x, xscale, y, flip, mode, rhs, partials, nparts,
+                               phase, want, tmp, st);
 }
 
 cudaError_t launch_setup_g64(const OpTables& op, const double2* ahat, const double2* bhat,
-                             double2* g64, cudaStream_t st) {
+                             double2* g64, float4* gdf, cudaStream_t st) {
   long long total = (long long)(op.N / 2 + 1) * op.M;
-  k_setup_g64<<<grid_stream(total, 256), 256, 0, st>>>(op, ahat, bhat, g64);
+  k_setup_g64<<<grid_stream(total, 256), 256, 0, st>>>(op, ahat, bhat, g64, gdf);
   return cudaGetLastError();
 }
 

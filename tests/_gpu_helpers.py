@@ -9,15 +9,15 @@ def rel(a, b):
 
 
 def precond_tol(N, alpha, prec=64):
-    """Tolerance for P_alpha^{-1} between two independent implementations.
+    """Tolerance for P_alpha^{-1} between two independent implementations (prec 96: double-float).
 
     The D_alpha similarity has condition number alpha^{-(N-1)/N}; each FP64 (or FP32) evaluation
     carries about eps * log2(N) * that relative error, so two of them differ by at most a small
     multiple of it.  FP64 never needs to be looser than 1e-12 when alpha is moderate.
     """
-    eps = 2.0 ** -52 if prec == 64 else 2.0 ** -23
+    eps = {64: 2.0 ** -52, 32: 2.0 ** -23, 96: 2.0 ** -45}[prec]
     kappa = alpha ** (-(N - 1) / N)
-    floor = 1e-12 if prec == 64 else 1e-5
+    floor = {64: 1e-12, 32: 1e-5, 96: 1e-12}[prec]
     return max(floor, 50.0 * eps * kappa)
 
 

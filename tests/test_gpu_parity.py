@@ -49,8 +49,10 @@ IDS = [p.name for p in problems()]
 
 @pytest.mark.parametrize("prob", problems(), ids=IDS)
 @pytest.mark.parametrize("flip", [0, 1])
-def test_matvec_parity(B, prob, flip):
+@pytest.mark.parametrize("arith", [1, 2], ids=["f64", "f32x2"])
+def test_matvec_parity(B, prob, flip, arith):
     s = B.Solver(prob)
+    s.set_matvec_arith(arith)
     z = np.random.default_rng(21).standard_normal(prob.n)
     y = to_host(s.matvec(to_dev(z), flip=bool(flip)))
     ref = O.bltt_matvec(prob, z, flip=bool(flip))
@@ -65,6 +67,16 @@ def test_precond_parity_f64(B, prob, alpha):
     z = to_host(s.precond_apply(alpha, to_dev(v), precision=64))
     ref = O.precond_apply(prob, alpha, v)
     assert rel(z, ref) <= precond_tol(prob.N, alpha, 64)
+
+
+@pytest.mark.parametrize("prob", problems(), ids=IDS)
+@pytest.mark.parametrize("alpha", [1.0, 1e-2, 1e-4, 1e-8])
+def test_precond_parity_f32x2(B, prob, alpha):
+    s = B.Solver(prob)
+    v = np.random.default_rng(22).standard_normal(prob.n)
+    z = to_host(s.precond_apply(alpha, to_dev(v), precision=96))
+    ref = O.precond_apply(prob, alpha, v)
+    assert rel(z, ref) <= precond_tol(prob.N, alpha, 96)
 
 
 @pytest.mark.parametrize("prob", problems()[:6], ids=IDS[:6])
@@ -97,11 +109,13 @@ SOLVE_PROBLEMS = [
 
 @pytest.mark.parametrize("prob", SOLVE_PROBLEMS, ids=[p.name for p in SOLVE_PROBLEMS])
 @pytest.mark.parametrize("basis", [1, 2])
-def test_solve_parity_f64(B, prob, basis):
+@pytest.mark.parametrize("arith", [1, 2], ids=["f64", "f32x2"])
+def test_solve_parity_f64(B, prob, basis, arith):
     f = rhs_uniform(prob.n, 31)
     ref = O.solve(prob, f, alpha=1e-8, tol=1e-8)
     s = B.Solver(prob)
-    u, info = s.solve(to_dev(f), alpha=1e-8, tol=1e-8, maxit=100, precision=64, basis=basis)
+    u, info = s.solve(to_dev(f), alpha=1e-8, tol=1e-8, maxit=100, precision=64, basis=basis,
+                      matvec_arith=arith)
     assert info["status"] == 0, info
     assert abs(info["iters"] - ref["iters"]) <= 1, (info["iters"], ref["iters"])
     assert info["relres_true"] <= 1e-8
@@ -112,16 +126,33 @@ def test_solve_parity_f64(B, prob, basis):
 
 @pytest.mark.parametrize("prob", SOLVE_PROBLEMS[:3], ids=[p.name for p in SOLVE_PROBLEMS[:3]])
 @pytest.mark.parametrize("basis", [1, 2])
-def test_solve_f32_preconditioner(B, prob, basis):
+@pytest.mark.parametrize("arith", [1, 2], ids=["f64", "f32x2"])
+def test_solve_f32_preconditioner(B, prob, basis, arith):
     f = rhs_uniform(prob.n, 32)
     alpha = 1e-3
     ref = O.solve(prob, f, alpha=alpha, tol=1e-8)
     s = B.Solver(prob)
-    u, info = s.solve(to_dev(f), alpha=alpha, tol=1e-8, maxit=100, precision=32, basis=basis)
+    u, info = s.solve(to_dev(f), alpha=alpha, tol=1e-8, maxit=100, precision=32, basis=basis,
+                      matvec_arith=arith)
     assert info["status"] == 0, info
     assert info["relres_true"] <= 1e-8
     assert rel(O.bltt_matvec(prob, to_host(u)), f) <= 1e-8
     assert info["iters"] <= ref["iters"] + 4, (info["iters"], ref["iters"])
+
+
+@pytest.mark.parametrize("prob", SOLVE_PROBLEMS, ids=[p.name for p in SOLVE_PROBLEMS])
+@pytest.mark.parametrize("basis", [1, 2])
+def test_solve_f32x2_preconditioner(B, prob, basis):
+    # every FP64-accurate stage (matvec, DSTs, preconditioner) in double-float on the FP32 pipes
+    f = rhs_uniform(prob.n, 36)
+    ref = O.solve(prob, f, alpha=1e-8, tol=1e-8)
+    s = B.Solver(prob)
+    u, info = s.solve(to_dev(f), alpha=1e-8, tol=1e-8, maxit=100, precision=96, basis=basis,
+                      matvec_arith=2)
+    assert info["status"] == 0, info
+    assert info["relres_true"] <= 1e-8
+    assert rel(O.bltt_matvec(prob, to_host(u)), f) <= 1e-8
+    assert abs(info["iters"] - ref["iters"]) <= 1, (info["iters"], ref["iters"])
 
 
 @pytest.mark.parametrize("precond,alpha", [(0, 1.0), (1, 0.0)])
