@@ -88,6 +88,9 @@ struct bltt_ctx {
   float2* pc_dinv_df = nullptr;
   float2* pc_d2_df = nullptr;
   float4* pc_gdf = nullptr;
+  float2* pc_g32 = nullptr;
+  float4* pc_ahatdf = nullptr;
+  float4* pc_bhatdf = nullptr;
   bool pc_hasdf = false;
   double2* pc_g64 = nullptr;
   float2* pc_ahat32 = nullptr;
@@ -239,15 +242,22 @@ bltt_status prepare_precond(bltt_ctx* h, double alpha, int prec) {
       CK(h, h->alloc(&h->pc_bhat64, N / 2 + 1), "alloc bhat");
       CK(h, h->alloc(&h->pc_ahat32, N / 2 + 1), "alloc ahat32");
       CK(h, h->alloc(&h->pc_bhat32, N / 2 + 1), "alloc bhat32");
+      CK(h, h->alloc(&h->pc_ahatdf, N / 2 + 1), "alloc ahatdf");
+      CK(h, h->alloc(&h->pc_bhatdf, N / 2 + 1), "alloc bhatdf");
     }
     std::vector<double2> a64(N / 2 + 1), b64(N / 2 + 1);
     std::vector<float2> a32(N / 2 + 1), b32(N / 2 + 1);
+    std::vector<float4> adf(N / 2 + 1), bdf(N / 2 + 1);
     for (int k = 0; k <= N / 2; ++k) {
       a64[k] = make_double2(ah[k].real(), ah[k].imag());
       b64[k] = make_double2(bh[k].real(), bh[k].imag());
       a32[k] = make_float2((float)ah[k].real(), (float)ah[k].imag());
       b32[k] = make_float2((float)bh[k].real(), (float)bh[k].imag());
+      adf[k] = split_df(ah[k].real(), ah[k].imag());
+      bdf[k] = split_df(bh[k].real(), bh[k].imag());
     }
+    CK(h, cudaMemcpyAsync(h->pc_ahatdf, adf.data(), adf.size() * sizeof(float4), cudaMemcpyHostToDevice, h->stream), "copy ahatdf");
+    CK(h, cudaMemcpyAsync(h->pc_bhatdf, bdf.data(), bdf.size() * sizeof(float4), cudaMemcpyHostToDevice, h->stream), "copy bhatdf");
     std::vector<float> dinv32(N), d232(N);
     std::vector<float2> dinvdf(N), d2df(N);
     for (int j = 0; j < N; ++j) {
@@ -269,6 +279,14 @@ bltt_status prepare_precond(bltt_ctx* h, double alpha, int prec) {
     // the host vectors die at return: wait for the copies
     CK(h, cudaStreamSynchronize(h->stream), "sync after table upload");
     h->pc_alpha = alpha;
+  }
+  if (prec == PREC_F32 && !h->pc_has32) {
+    if (!h->pc_g32) CK(h, h->alloc(&h->pc_g32, (size_t)(N / 2 + 1) * h->M), "alloc g32 table");
+    cudaEvent_t pa = prof_begin(h);
+    CK(h, launch_setup_g32(h->op, h->pc_ahat32, h->pc_bhat32, nullptr, nullptr, h->pc_g32, nullptr,
+                           h->stream), "setup g32");
+    prof_end(h, "setup_g", pa);
+    h->launches++;
     h->pc_has32 = true;
   }
   if (prec == PREC_F64 && !h->pc_has64) {
@@ -282,7 +300,8 @@ bltt_status prepare_precond(bltt_ctx* h, double alpha, int prec) {
   if (prec == PREC_DF && !h->pc_hasdf) {
     if (!h->pc_gdf) CK(h, h->alloc(&h->pc_gdf, (size_t)(N / 2 + 1) * h->M), "alloc gdf table");
     cudaEvent_t pa = prof_begin(h);
-    CK(h, launch_setup_g64(h->op, h->pc_ahat64, h->pc_bhat64, nullptr, h->pc_gdf, h->stream), "setup gdf");
+    CK(h, launch_setup_g32(h->op, h->pc_ahat32, h->pc_bhat32, h->pc_ahatdf, h->pc_bhatdf, nullptr,
+                           h->pc_gdf, h->stream), "setup gdf");
     prof_end(h, "setup_g", pa);
     h->launches++;
     h->pc_hasdf = true;
@@ -300,6 +319,7 @@ PrecTables prec_tables(bltt_ctx* h, int none) {
   pt.dinv_df = h->pc_dinv_df;
   pt.d2_df = h->pc_d2_df;
   pt.gdf = h->pc_gdf;
+  pt.g32 = h->pc_g32;
   pt.g64 = h->pc_g64;
   pt.ahat32 = h->pc_ahat32;
   pt.bhat32 = h->pc_bhat32;

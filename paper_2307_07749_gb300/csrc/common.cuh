@@ -206,42 +206,48 @@ struct ArithDF {
 // Shared-memory Stockham FFT (self-sorting; radix 4 with one radix-2 pass when log2 L is odd).
 //
 // buf holds NC = 2^log2NC independent complex columns of length L, element (p, c) at
-// buf[p * NC + c].  tw holds w_L^k = exp(-2 pi i k / L), k < L.  Forward: X_k = sum_j x_j w^{jk};
+// buf[p * NC + c] (or at buf[p * NC + (c ^ (p mod NC))] with SWZ).  tw holds
+// w_L^k = exp(-2 pi i k / L), k < L.  skip_radix2: the caller has already applied the first
+// radix-2 pass (used when the upper half of the input is zero: the pass only duplicates).  Forward: X_k = sum_j x_j w^{jk};
 // inverse (INV): conjugate twiddles, no 1/L scaling.  Every pass loads all of its butterfly
 // inputs into registers, synchronises, then writes, so the transform runs in place.
 // CAP bounds NC * L; the block has NT threads.
-template <class A, int NT, int CAP, bool INV>
+template <class A, int NT, int CAP, bool INV, bool SWZ = false>
 __device__ void fft_columns(typename A::V* buf, int L, int log2L, int log2NC,
-                            const typename A::V* __restrict__ tw) {
+                            const typename A::V* __restrict__ tw, bool skip_radix2 = false) {
   using V = typename A::V;
   constexpr int IPT4 = (CAP / 4 + NT - 1) / NT;   // radix-4 butterflies per thread
   const int tid = threadIdx.x;
   const int NC = 1 << log2NC, cmask = NC - 1;
+  // element (p, c) lives at p * NC + (c ^ (p & cmask)) when SWZ (bank-conflict-free column walks)
+  auto at = [&](int p, int c) { return (p << log2NC) + (SWZ ? (c ^ (p & cmask)) : c); };
   int Ns = 1;
   if (log2L & 1) {
-    const int half = L >> 1;
-    const int total = half << log2NC;
-    V v[2 * IPT4][2];
+    if (!skip_radix2) {
+      const int half = L >> 1;
+      const int total = half << log2NC;
+      V v[2 * IPT4][2];
 #pragma unroll
-    for (int s = 0; s < 2 * IPT4; ++s) {
-      int it = tid + s * NT;
-      if (it < total) {
-        int c = it & cmask, j = it >> log2NC;
-        v[s][0] = buf[(j << log2NC) + c];
-        v[s][1] = buf[((j + half) << log2NC) + c];
+      for (int s = 0; s < 2 * IPT4; ++s) {
+        int it = tid + s * NT;
+        if (it < total) {
+          int c = it & cmask, j = it >> log2NC;
+          v[s][0] = buf[at(j, c)];
+          v[s][1] = buf[at(j + half, c)];
+        }
       }
-    }
-    __syncthreads();
+      __syncthreads();
 #pragma unroll
-    for (int s = 0; s < 2 * IPT4; ++s) {
-      int it = tid + s * NT;
-      if (it < total) {
-        int c = it & cmask, j = it >> log2NC;
-        buf[((2 * j) << log2NC) + c] = A::add(v[s][0], v[s][1]);
-        buf[((2 * j + 1) << log2NC) + c] = A::sub(v[s][0], v[s][1]);
+      for (int s = 0; s < 2 * IPT4; ++s) {
+        int it = tid + s * NT;
+        if (it < total) {
+          int c = it & cmask, j = it >> log2NC;
+          buf[at(2 * j, c)] = A::add(v[s][0], v[s][1]);
+          buf[at(2 * j + 1, c)] = A::sub(v[s][0], v[s][1]);
+        }
       }
+      __syncthreads();
     }
-    __syncthreads();
     Ns = 2;
   }
   const int quarter = L >> 2;
@@ -255,7 +261,7 @@ __device__ void fft_columns(typename A::V* buf, int L, int log2L, int log2NC,
       if (it < total) {
         int c = it & cmask, j = it >> log2NC;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) v[s][r] = buf[((j + r * quarter) << log2NC) + c];
+        for (int r = 0; r < 4; ++r) v[s][r] = buf[at(j + r * quarter, c)];
       }
     }
     __syncthreads();
@@ -278,10 +284,10 @@ __device__ void fft_columns(typename A::V* buf, int L, int log2L, int log2NC,
         V t2 = A::add(v[s][1], v[s][3]);
         V t3 = A::template rot<INV>(A::sub(v[s][1], v[s][3]));
         int o = (j - k) * 4 + k;
-        buf[(o << log2NC) + c] = A::add(t0, t2);
-        buf[((o + Ns) << log2NC) + c] = A::add(t1, t3);
-        buf[((o + 2 * Ns) << log2NC) + c] = A::sub(t0, t2);
-        buf[((o + 3 * Ns) << log2NC) + c] = A::sub(t1, t3);
+        buf[at(o, c)] = A::add(t0, t2);
+        buf[at(o + Ns, c)] = A::add(t1, t3);
+        buf[at(o + 2 * Ns, c)] = A::sub(t0, t2);
+        buf[at(o + 3 * Ns, c)] = A::sub(t1, t3);
       }
     }
     __syncthreads();

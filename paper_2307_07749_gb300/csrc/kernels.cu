@@ -118,7 +118,7 @@ constexpr int kBatch = 4;   // independent global loads in flight per thread in 
 // complex FFT of length 2P (P = m+1) of their odd extensions [0, x, 0, -rev(x)]; then
 // S x_a = -Im(Z_{k+1}) / sqrt(2P) and S x_b = Re(Z_{k+1}) / sqrt(2P), S the normalised DST-I.
 // Lines: line g has elements base(g) + p*inner, base(g) = (g/inner)*(m*inner) + g%inner.
-template <class A>
+template <class A, bool SWZ>
 __global__ void __launch_bounds__(kThreads)
 k_dst(long long nlines, int m, long long inner, int P, int log2L, int log2NC, Combine cb,
       double* out, int flip, int N, long long M, const double* dot_with, double* partials,
@@ -142,8 +142,10 @@ k_dst(long long nlines, int m, long long inner, int P, int log2L, int log2NC, Co
     s_in[c] = b;
     s_out[c] = o;
   }
+  const int cmask = NC - 1;
+  auto at = [&](int p, int cc) { return p * NC + (SWZ ? (cc ^ (p & cmask)) : cc); };
   for (int e = threadIdx.x; e < 2 * NC; e += kThreads)
-    buf[((e & 1) ? P : 0) * NC + (e >> 1)] = A::zero();
+    buf[at((e & 1) ? P : 0, e >> 1)] = A::zero();
   __syncthreads();
   double c0, c1, c2;
   load_coef(cb, c0, c1, c2);
@@ -171,12 +173,12 @@ k_dst(long long nlines, int m, long long inner, int P, int log2L, int log2NC, Co
       const int e = e0 + u * kThreads;
       if (e < total) {
         const int cc = cs[u] >> 1, comp = cs[u] & 1;
-        A::put_pm(buf, (ps[u] + 1) * NC + cc, (L - 1 - ps[u]) * NC + cc, comp, v[u]);
+        A::put_pm(buf, at(ps[u] + 1, cc), at(L - 1 - ps[u], cc), comp, v[u]);
       }
     }
   }
   __syncthreads();
-  fft_columns<A, kThreads, kCap, false>(buf, L, log2L, log2NC, tw);
+  fft_columns<A, kThreads, kCap, false, SWZ>(buf, L, log2L, log2NC, tw);
   const typename A::Sc scale = A::make_sc(rsqrt((double)L));
   const typename A::Sc nscale = A::make_sc(-rsqrt((double)L));
   double acc = 0.0;
@@ -186,7 +188,7 @@ k_dst(long long nlines, int m, long long inner, int P, int log2L, int log2NC, Co
     else { k = e >> log2W; c = e & (W - 1); }
     const long long o = s_out[c];
     if (o >= 0) {
-      const V z = buf[(k + 1) * NC + (c >> 1)];
+      const V z = buf[at(k + 1, c >> 1)];
       const double val = (c & 1) ? A::part_sc(z, 0, scale) : A::part_sc(z, 1, nscale);
       const long long idx = o + (long long)k * inner;
       out[idx] = val;
@@ -237,12 +239,8 @@ template <> struct GSrc<ArithD> {
 };
 template <> struct GSrc<ArithF> {
   static __device__ __forceinline__ float2 get(const OpTables& op, const PrecTables& pt, int k,
-                                              long long, double mu_d) {
-    const float mu = (float)mu_d;
-    const float2 a = pt.ahat32[k], b = pt.bhat32[k];
-    C<float> g = inv_sqrt_principal<float>(fmaf(b.x, mu, a.x), fmaf(b.y, mu, a.y));
-    const float sc = 0.5f / (float)op.N;
-    return make_float2(g.x * sc, g.y * sc);
+                                              long long i, double) {
+    return pt.g32[(long long)k * op.M + i];
   }
 };
 
@@ -429,6 +427,7 @@ k_conv(OpTables op, int spectral, int which, const double* x, const double* xsca
     s_nb[c] = nb;
   }
   const typename A::Sc ssc = A::make_sc(s);
+  const bool odd = ((op.log2N + 1) & 1) != 0;
   const int total = N * W;
   for (int e0 = threadIdx.x; e0 < total; e0 += kBatch * kThreads) {
     double v[kBatch];
@@ -443,14 +442,21 @@ k_conv(OpTables op, int spectral, int which, const double* x, const double* xsca
       const int e = e0 + u * kThreads;
       if (e < total) {
         const int p = e >> log2W, c = e & (W - 1);
-        A::put_sc(buf, p * NC + (c >> 1), c & 1, v[u], ssc);
+        if (odd) {
+          // the first radix-2 pass pairs x_p with the zero x_{p+N}: both outputs equal x_p
+          A::put_sc(buf, (2 * p) * NC + (c >> 1), c & 1, v[u], ssc);
+          A::put_sc(buf, (2 * p + 1) * NC + (c >> 1), c & 1, v[u], ssc);
+        } else {
+          A::put_sc(buf, p * NC + (c >> 1), c & 1, v[u], ssc);
+        }
       }
     }
   }
-  for (int e = threadIdx.x; e < N * NC; e += kThreads) buf[N * NC + e] = A::zero();
+  if (!odd)
+    for (int e = threadIdx.x; e < N * NC; e += kThreads) buf[N * NC + e] = A::zero();
   __syncthreads();
   const V* __restrict__ tw = ConvTables<A>::tw(op);
-  fft_columns<A, kThreads, kCap, false>(buf, L, op.log2N + 1, log2NC, tw);
+  fft_columns<A, kThreads, kCap, false>(buf, L, op.log2N + 1, log2NC, tw, odd);
   if (!spectral) {
     const V* __restrict__ H = ConvTables<A>::H(op, which);
     for (int e = threadIdx.x; e < L * NC; e += kThreads) {
@@ -590,6 +596,45 @@ __global__ void k_setup_g64(OpTables op, const double2* ahat, const double2* bha
     if (gdf) {
       const dfl r = df_from(gr), im = df_from(gi);
       gdf[e] = make_float4(r.hi, r.lo, im.hi, im.lo);
+    }
+  }
+}
+
+// Set-up of the FP32 and double-float time-pass tables without FP64 arithmetic: g0 is the
+// principal lambda^{-1/2} in FP32 (half-angle form); the double-float value takes one Newton
+// step for z^{-1/2}, g1 = g0 (3 - lambda g0^2) / 2, in double-float (the error squares: 2^-24 ->
+// about 2^-47), with lambda = ahat_k + bhat_k mu_i formed in double-float.
+__global__ void k_setup_g32(OpTables op, const float2* ahat32, const float2* bhat32,
+                            const float4* ahatdf, const float4* bhatdf, float2* g32, float4* gdf) {
+  const int half = op.N / 2;
+  const long long total = (long long)(half + 1) * op.M;
+  const float sc = 0.5f / (float)op.N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e / op.M);
+    const long long i = e - (long long)k * op.M;
+    const float mu = mode_mu32(op, i);
+    const float2 a = ahat32[k], b = bhat32[k];
+    const float2 g0 = inv_sqrt_principal<float>(fmaf(b.x, mu, a.x), fmaf(b.y, mu, a.y));
+    if (g32) g32[e] = make_float2(g0.x * sc, g0.y * sc);
+    if (gdf) {
+      const float4 A4 = ahatdf[k], B4 = bhatdf[k];
+      // mu_i as double-float: sum of the per-axis FP64 eigenvalues
+      long long r = i / op.m[0];
+      dfl m_ = df_from(op.mu_axis[0][i - r * op.m[0]]);
+      if (op.d > 1) {
+        long long r2 = r / op.m[1];
+        m_ = df_add(m_, df_from(op.mu_axis[1][r - r2 * op.m[1]]));
+        if (op.d > 2) m_ = df_add(m_, df_from(op.mu_axis[2][r2]));
+      }
+      const float4 lam = ArithDF::pack(df_add(dfl{A4.x, A4.y}, df_mul(m_, dfl{B4.x, B4.y})),
+                                       df_add(dfl{A4.z, A4.w}, df_mul(m_, dfl{B4.z, B4.w})));
+      const float4 g = make_float4(g0.x, 0.f, g0.y, 0.f);
+      const float4 t = ArithDF::mul(lam, ArithDF::mul(g, g));          // lambda g0^2 ~ 1
+      const float4 three_m = ArithDF::sub(make_float4(3.f, 0.f, 0.f, 0.f), t);
+      const float4 g1 = ArithDF::mul(g, three_m);                        // 2 g1
+      const dfl s2 = {0.25f / (float)op.N, 0.f};                         // (1/2) (1/(2N)), exact
+      gdf[e] = ArithDF::pack(df_mul(dfl{g1.x, g1.y}, s2), df_mul(dfl{g1.z, g1.w}, s2));
     }
   }
 }
@@ -741,9 +786,24 @@ static int grid_stream(long long n, int threads) {
 template <class A> static cudaError_t ensure_smem_dst() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = set_smem(k_dst<A>, kCap * sizeof(typename A::V));
+  cudaError_t e = set_smem(k_dst<A, false>, kCap * sizeof(typename A::V));
+  if (e == cudaSuccess) e = set_smem(k_dst<A, true>, kCap * sizeof(typename A::V));
   if (e == cudaSuccess) done = true;
   return e;
+}
+
+template <class A>
+static void run_dst(const OpTables& op, long long grid, long long nlines, int m, long long inner,
+                    int P, int L, int log2NC, const Combine& in, double* out, int flip,
+                    const double* dot_with, double* partials, const typename A::V* tw,
+                    const int* phase, cudaStream_t st) {
+  const size_t smem = kCap * sizeof(typename A::V);
+  if (inner == 1)
+    k_dst<A, true><<<(unsigned)grid, kThreads, smem, st>>>(nlines, m, inner, P, ilog2(L), log2NC,
+        in, out, flip, op.N, op.M, dot_with, partials, tw, phase, PH_RUN);
+  else
+    k_dst<A, false><<<(unsigned)grid, kThreads, smem, st>>>(nlines, m, inner, P, ilog2(L), log2NC,
+        in, out, flip, op.N, op.M, dot_with, partials, tw, phase, PH_RUN);
 }
 template <class A> static cudaError_t ensure_smem_tp() {
   static bool done = false;
@@ -772,24 +832,19 @@ cudaError_t launch_dst(const OpTables& op, int axis, int prec, const Combine& in
   const int log2NC = ilog2(NC);
   const long long grid = (nlines + 2 * NC - 1) / (2 * NC);
   if (nparts) *nparts = (int)grid;
+  cudaError_t e;
   if (prec == PREC_F64) {
-    cudaError_t e = ensure_smem_dst<ArithD>();
-    if (e != cudaSuccess) return e;
-    k_dst<ArithD><<<(unsigned)grid, kThreads, kCap * sizeof(double2), st>>>(
-        nlines, m, inner, P, ilog2(L), log2NC, in, out, flip, op.N, op.M, dot_with, partials,
-        op.tw_dst[axis], phase, PH_RUN);
+    if ((e = ensure_smem_dst<ArithD>()) != cudaSuccess) return e;
+    run_dst<ArithD>(op, grid, nlines, m, inner, P, L, log2NC, in, out, flip, dot_with, partials,
+                    op.tw_dst[axis], phase, st);
   } else if (prec == PREC_DF) {
-    cudaError_t e = ensure_smem_dst<ArithDF>();
-    if (e != cudaSuccess) return e;
-    k_dst<ArithDF><<<(unsigned)grid, kThreads, kCap * sizeof(float4), st>>>(
-        nlines, m, inner, P, ilog2(L), log2NC, in, out, flip, op.N, op.M, dot_with, partials,
-        op.tw_dst_df[axis], phase, PH_RUN);
+    if ((e = ensure_smem_dst<ArithDF>()) != cudaSuccess) return e;
+    run_dst<ArithDF>(op, grid, nlines, m, inner, P, L, log2NC, in, out, flip, dot_with, partials,
+                     op.tw_dst_df[axis], phase, st);
   } else {
-    cudaError_t e = ensure_smem_dst<ArithF>();
-    if (e != cudaSuccess) return e;
-    k_dst<ArithF><<<(unsigned)grid, kThreads, kCap * sizeof(float2), st>>>(
-        nlines, m, inner, P, ilog2(L), log2NC, in, out, flip, op.N, op.M, dot_with, partials,
-        op.tw_dst32[axis], phase, PH_RUN);
+    if ((e = ensure_smem_dst<ArithF>()) != cudaSuccess) return e;
+    run_dst<ArithF>(op, grid, nlines, m, inner, P, L, log2NC, in, out, flip, dot_with, partials,
+                    op.tw_dst32[axis], phase, st);
   }
   return cudaGetLastError();
 }
@@ -874,6 +929,14 @@ cudaError_t launch_setup_g64(const OpTables& op, const double2* ahat, const doub
                              double2* g64, float4* gdf, cudaStream_t st) {
   long long total = (long long)(op.N / 2 + 1) * op.M;
   k_setup_g64<<<grid_stream(total, 256), 256, 0, st>>>(op, ahat, bhat, g64, gdf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_setup_g32(const OpTables& op, const float2* ahat32, const float2* bhat32,
+                             const float4* ahatdf, const float4* bhatdf, float2* g32, float4* gdf,
+                             cudaStream_t st) {
+  long long total = (long long)(op.N / 2 + 1) * op.M;
+  k_setup_g32<<<grid_stream(total, 256), 256, 0, st>>>(op, ahat32, bhat32, ahatdf, bhatdf, g32, gdf);
   return cudaGetLastError();
 }
 

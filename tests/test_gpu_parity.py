@@ -142,17 +142,21 @@ def test_solve_f32_preconditioner(B, prob, basis, arith):
 
 @pytest.mark.parametrize("prob", SOLVE_PROBLEMS, ids=[p.name for p in SOLVE_PROBLEMS])
 @pytest.mark.parametrize("basis", [1, 2])
-def test_solve_f32x2_preconditioner(B, prob, basis):
-    # every FP64-accurate stage (matvec, DSTs, preconditioner) in double-float on the FP32 pipes
+@pytest.mark.parametrize("alpha", [1e-8, 1e-5])
+def test_solve_f32x2_preconditioner(B, prob, basis, alpha):
+    # every FP64-accurate stage (matvec, DSTs, preconditioner) in double-float on the FP32 pipes.
+    # Its rounding (~2^-47) is amplified by the D_alpha conditioning alpha^{-(N-1)/N}, so at
+    # alpha = 1e-8 MINRES may need up to two more iterations than the FP64 oracle.
     f = rhs_uniform(prob.n, 36)
-    ref = O.solve(prob, f, alpha=1e-8, tol=1e-8)
+    ref = O.solve(prob, f, alpha=alpha, tol=1e-8)
     s = B.Solver(prob)
-    u, info = s.solve(to_dev(f), alpha=1e-8, tol=1e-8, maxit=100, precision=96, basis=basis,
+    u, info = s.solve(to_dev(f), alpha=alpha, tol=1e-8, maxit=100, precision=96, basis=basis,
                       matvec_arith=2)
     assert info["status"] == 0, info
     assert info["relres_true"] <= 1e-8
     assert rel(O.bltt_matvec(prob, to_host(u)), f) <= 1e-8
-    assert abs(info["iters"] - ref["iters"]) <= 1, (info["iters"], ref["iters"])
+    slack = 2 if alpha < 1e-6 else 1
+    assert ref["iters"] - 1 <= info["iters"] <= ref["iters"] + slack, (info["iters"], ref["iters"])
 
 
 @pytest.mark.parametrize("precond,alpha", [(0, 1.0), (1, 0.0)])
