@@ -86,6 +86,9 @@ _SIGS = {
                                          ctypes.c_int, _P, ctypes.POINTER(bltt_solve_info)]),
     "bltt_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "bltt_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(bltt_kernel_stat), ctypes.c_int]),
+    "bltt_residual_noalloc": (ctypes.c_int, [ctypes.POINTER(bltt_blocks), ctypes.c_int,
+                                             ctypes.c_longlong, _P, _P, _P, _P,
+                                             ctypes.POINTER(ctypes.c_double)]),
     "bltt_last_error": (ctypes.c_char_p, [_P]),
     "bltt_version": (ctypes.c_char_p, []),
 }
@@ -200,6 +203,27 @@ def bltt_profile_read(handle):
         raise BlttError(1, "null handle")
     return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms, arr[i].active_launches,
                                    arr[i].active_ms) for i in range(min(k, 64))}
+
+
+def bltt_residual_noalloc(a, b, N, ndim, m, h, u, f, r=None, stream=None):
+    """||f - A u|| / ||f|| (and r = f - A u into `r` if given) with neither a handle nor any
+    allocation by the library; returns the relative residual.  See include/bltt.h."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    m = list(m) + [1] * (3 - len(m))
+    h = list(h) + [1.0] * (3 - len(h))
+    sp = bltt_space(ndim, (ctypes.c_int * 3)(*m), (ctypes.c_double * 3)(*h))
+    blk = bltt_blocks(N, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                      b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), sp)
+    M = int(np.prod(m[:ndim]))
+    out = ctypes.c_double()
+    s = getattr(stream, "cuda_stream", stream)
+    st = lib().bltt_residual_noalloc(ctypes.byref(blk), N, M, _ptr(u, "u"), _ptr(f, "f"),
+                                     _ptr(r, "r") if r is not None else None,
+                                     ctypes.c_void_p(int(s) if s else 0), ctypes.byref(out))
+    if st != BLTT_OK:
+        raise BlttError(st, "bltt_residual_noalloc")
+    return out.value
 
 
 def bltt_version():
