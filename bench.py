@@ -171,24 +171,33 @@ def barrier(ws):
         dist.barrier()
 
 
-def max_over_ranks(v, ws):
+def _reduce(v, ws, op, device):
     if ws <= 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=op)
     return float(t.item())
 
 
-def sum_over_ranks(v, ws):
-    if ws <= 1:
-        return v
-    import torch
+def max_over_ranks(v, ws, device="cuda"):
+    """The timed region's length is the slowest rank's."""
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(v, ws, dist.ReduceOp.MAX if ws > 1 else None, device)
+
+
+def sum_over_ranks(v, ws, device="cuda"):
+    """Units (unknown-iterations) processed by all ranks together."""
+    import torch.distributed as dist
+    return _reduce(v, ws, dist.ReduceOp.SUM if ws > 1 else None, device)
+
+
+def replica_throughput(units_local, ms_local, ws, device="cuda"):
+    """Whole-job throughput of independent replicas: sum of units / max of times (weak scaling)."""
+    ms = max_over_ranks(ms_local, ws, device)
+    units = sum_over_ranks(units_local, ws, device)
+    return units / (ms / 1e3), ms, units
 
 
 # --------------------------------------------------------------------------------------------

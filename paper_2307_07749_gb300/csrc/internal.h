@@ -115,4 +115,65 @@ cudaError_t launch_sum_partials(const double* partials, int np, double* out, cud
 
 int tile_columns(long long nlines, int Lfft);   // complex columns per tile for a line batch
 
+// ---------------------------------------------------------------------------------------------
+// Multi-item ("wave") launches for batched solves: one launch covers the tiles of many items
+// (a system with one right-hand side each); persistent blocks stride over the concatenated tile
+// list, find their item by binary search in `prefix` (prefix[i] = tiles of items < i), skip items
+// whose phase differs from `want`, and run the same per-tile code as the single-item kernels.
+struct ConvItem {
+  OpTables op;
+  const double* x;
+  const double* xscale;   // device scalar or null
+  double* y;
+  const double* rhs;
+  double* partials;
+  const int* phase;
+  int want, flip, mode, spectral, log2NC, pad;
+};
+struct TpItem {
+  OpTables op;
+  PrecTables pt;
+  Combine cb;
+  double* out;
+  const double* dot_with;
+  double* partials;
+  const int* phase;
+  int want, log2NC;
+};
+struct DstItem {
+  long long nlines, inner, N, M;
+  int m, P, log2L, log2NC, flip, pad;
+  Combine cb;
+  double* out;
+  const double* dot_with;
+  double* partials;
+  const void* tw;
+};
+struct VecItem {            // element-wise MINRES update (w, x) of one item
+  const MinresDev* st;
+  const double* z;
+  double* w_prev;
+  const double* w;
+  double* x;
+  long long n;
+};
+struct ScalItem {           // scalar recurrence of one item
+  MinresDev* st;
+  const double* p0;         // partials for the first reduction
+  const double* p1;         // partials for the second (init only)
+  int n0, n1;
+};
+
+int persistent_grid(int kind, int prec);   // resident blocks for a multi-item launch
+cudaError_t launch_conv_multi(int arith, const ConvItem* items, const long long* prefix,
+                              int nitems, long long total, cudaStream_t st);
+cudaError_t launch_timepass_multi(int prec, const TpItem* items, const long long* prefix,
+                                  int nitems, long long total, cudaStream_t st);
+cudaError_t launch_dst_multi(int prec, const DstItem* items, const long long* prefix, int nitems,
+                             long long total, cudaStream_t st);
+cudaError_t launch_w_update_multi(const VecItem* items, int nitems, cudaStream_t st);
+// which: 0 init, 1 delta, 2 gamma, 3 check
+cudaError_t launch_scalar_multi(int which, const ScalItem* items, int nitems, cudaStream_t st);
+cudaError_t launch_count_running(const ScalItem* items, int nitems, int* out, cudaStream_t st);
+
 }  // namespace bltt

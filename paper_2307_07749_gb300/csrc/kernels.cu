@@ -2,6 +2,8 @@
 // of the ABAC preconditioner, the BLTT matvec (2N circulant embedding or direct taps), the
 // preconditioner set-up and the MINRES vector/scalar kernels.
 #include <math.h>
+#include <algorithm>
+#include <type_traits>
 #include "common.cuh"
 #include "internal.h"
 
@@ -119,18 +121,19 @@ constexpr int kBatch = 4;   // independent global loads in flight per thread in 
 // S x_a = -Im(Z_{k+1}) / sqrt(2P) and S x_b = Re(Z_{k+1}) / sqrt(2P), S the normalised DST-I.
 // Lines: line g has elements base(g) + p*inner, base(g) = (g/inner)*(m*inner) + g%inner.
 template <class A, bool SWZ>
-__global__ void __launch_bounds__(kThreads)
-k_dst(long long nlines, int m, long long inner, int P, int log2L, int log2NC, Combine cb,
-      double* out, int flip, int N, long long M, const double* dot_with, double* partials,
-      const typename A::V* __restrict__ tw, const int* phase, int want) {
-  if (skip_phase(phase, want)) return;
+__device__ __forceinline__ void dst_tile(long long nlines, int m, long long inner, int P, int log2L,
+                                         int log2NC, const Combine& cb, double* out, int flip,
+                                         int N, long long M, const double* dot_with,
+                                         double* partials, const typename A::V* __restrict__ tw,
+                                         long long tile) {
   using V = typename A::V;
+  __syncthreads();   // the previous tile of a persistent block may still read shared memory
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* buf = reinterpret_cast<V*>(smem_raw);
   __shared__ double red[32];
   __shared__ long long s_in[kMaxCols], s_out[kMaxCols];
   const int L = 2 * P, NC = 1 << log2NC, W = 2 * NC;
-  const long long g0 = (long long)blockIdx.x * W;
+  const long long g0 = tile * W;
   for (int c = threadIdx.x; c < W; c += kThreads) {
     long long g = g0 + c;
     long long b = -1, o = -1;
@@ -197,8 +200,18 @@ k_dst(long long nlines, int m, long long inner, int P, int log2L, int log2NC, Co
   }
   if (partials) {
     double s = block_sum<kThreads>(acc, red);
-    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    if (threadIdx.x == 0) partials[tile] = s;
   }
+}
+
+template <class A, bool SWZ>
+__global__ void __launch_bounds__(kThreads)
+k_dst(long long nlines, int m, long long inner, int P, int log2L, int log2NC, Combine cb,
+      double* out, int flip, int N, long long M, const double* dot_with, double* partials,
+      const typename A::V* __restrict__ tw, const int* phase, int want) {
+  if (skip_phase(phase, want)) return;
+  dst_tile<A, SWZ>(nlines, m, inner, P, log2L, log2NC, cb, out, flip, N, M, dot_with, partials,
+                   tw, blockIdx.x);
 }
 
 // ============================================================================================
@@ -268,19 +281,20 @@ __device__ __forceinline__ void tp_freq_mul(typename A::V* buf, const OpTables& 
 }
 
 template <class A>
-__global__ void __launch_bounds__(kThreads)
-k_timepass(OpTables op, PrecTables pt, Combine cb, double* out, const double* dot_with,
-           double* partials, const int* phase, int want, int log2NC,
-           const typename A::V* __restrict__ tw) {
-  if (skip_phase(phase, want)) return;
+__device__ __forceinline__ void timepass_tile(const OpTables& op, const PrecTables& pt,
+                                              const Combine& cb, double* out,
+                                              const double* dot_with, double* partials,
+                                              int log2NC, const typename A::V* __restrict__ tw,
+                                              long long tile) {
   using V = typename A::V;
+  __syncthreads();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* buf = reinterpret_cast<V*>(smem_raw);
   __shared__ double red[32];
   __shared__ double s_mu[kMaxCols];
   const int N = op.N, NC = 1 << log2NC, W = 2 * NC, log2W = log2NC + 1;
   const long long M = op.M;
-  const long long g0 = (long long)blockIdx.x * W;
+  const long long g0 = tile * W;
   for (int c = threadIdx.x; c < W; c += kThreads) s_mu[c] = (g0 + c < M) ? mode_mu(op, g0 + c) : 0.0;
   double c0, c1, c2;
   load_coef(cb, c0, c1, c2);
@@ -327,8 +341,17 @@ k_timepass(OpTables op, PrecTables pt, Combine cb, double* out, const double* do
   }
   if (partials) {
     double s = block_sum<kThreads>(acc, red);
-    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    if (threadIdx.x == 0) partials[tile] = s;
   }
+}
+
+template <class A>
+__global__ void __launch_bounds__(kThreads)
+k_timepass(OpTables op, PrecTables pt, Combine cb, double* out, const double* dot_with,
+           double* partials, const int* phase, int want, int log2NC,
+           const typename A::V* __restrict__ tw) {
+  if (skip_phase(phase, want)) return;
+  timepass_tile<A>(op, pt, cb, out, dot_with, partials, log2NC, tw, blockIdx.x);
 }
 
 // identity preconditioner (MINRES-I): z = v, with the same fused load and dot
@@ -390,12 +413,13 @@ template <> struct MuT<ArithD> { using t = double; static __device__ __forceinli
 template <> struct MuT<ArithDF> { using t = dfl; static __device__ __forceinline__ dfl make(double v) { return df_from(v); } };
 
 template <class A>
-__global__ void __launch_bounds__(kThreads)
-k_conv(OpTables op, int spectral, int which, const double* x, const double* xscale, double* y,
-       int flip, int mode, const double* rhs, double* partials, const int* phase, int want,
-       const double* st_src, int log2NC) {
-  if (skip_phase(phase, want)) return;
+__device__ __forceinline__ void conv_tile(const OpTables& op, int spectral, int which,
+                                          const double* x, const double* xscale, double* y,
+                                          int flip, int mode, const double* rhs,
+                                          double* partials, const double* st_src, int log2NC,
+                                          long long tile) {
   using V = typename A::V;
+  __syncthreads();
   using MT = typename MuT<A>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* buf = reinterpret_cast<V*>(smem_raw);
@@ -404,7 +428,7 @@ k_conv(OpTables op, int spectral, int which, const double* x, const double* xsca
   __shared__ int s_nb[kMaxCols];
   const int N = op.N, L = 2 * N, NC = 1 << log2NC, W = 2 * NC, log2W = log2NC + 1;
   const long long M = op.M;
-  const long long g0 = (long long)blockIdx.x * W;
+  const long long g0 = tile * W;
   const double s = xscale ? *xscale : 1.0;
   const bool genb = (op.b_kind == 1);
   const bool extra_st = !spectral && which == 0 && st_src != nullptr;
@@ -527,8 +551,18 @@ k_conv(OpTables op, int spectral, int which, const double* x, const double* xsca
   }
   if (partials) {
     double sum = block_sum<kThreads>(acc, red);
-    if (threadIdx.x == 0) partials[blockIdx.x] = (mode == MV_STORE) ? sum * s : sum;
+    if (threadIdx.x == 0) partials[tile] = (mode == MV_STORE) ? sum * s : sum;
   }
+}
+
+template <class A>
+__global__ void __launch_bounds__(kThreads)
+k_conv(OpTables op, int spectral, int which, const double* x, const double* xscale, double* y,
+       int flip, int mode, const double* rhs, double* partials, const int* phase, int want,
+       const double* st_src, int log2NC) {
+  if (skip_phase(phase, want)) return;
+  conv_tile<A>(op, spectral, which, x, xscale, y, flip, mode, rhs, partials, st_src, log2NC,
+               blockIdx.x);
 }
 
 // Direct matvec for blocks that vanish beyond ntaps (heat BDF / CN): y_t = sum_{k<ntaps}
@@ -664,8 +698,8 @@ __device__ double reduce_partials(const double* p, int n, double* scratch) {
   return block_sum<256>(acc, scratch);
 }
 
-__global__ void __launch_bounds__(256) k_scalar_init(MinresDev* st, const double* pzv, int nzv,
-                                                     const double* pb, int nb) {
+__device__ __forceinline__ void scalar_init(MinresDev* st, const double* pzv, int nzv,
+                                            const double* pb, int nb) {
   __shared__ double red[32];
   double g2 = reduce_partials(pzv, nzv, red);
   __syncthreads();
@@ -689,7 +723,7 @@ __global__ void __launch_bounds__(256) k_scalar_init(MinresDev* st, const double
   else st->phase = PH_RUN;
 }
 
-__global__ void __launch_bounds__(256) k_scalar_delta(MinresDev* st, const double* p, int np) {
+__device__ __forceinline__ void scalar_delta(MinresDev* st, const double* p, int np) {
   if (st->phase != PH_RUN) return;
   __shared__ double red[32];
   double delta = reduce_partials(p, np, red);
@@ -701,7 +735,7 @@ __global__ void __launch_bounds__(256) k_scalar_delta(MinresDev* st, const doubl
   st->coef[2] = -st->gamma / st->gamma_prev;
 }
 
-__global__ void __launch_bounds__(256) k_scalar_gamma(MinresDev* st, const double* p, int np) {
+__device__ __forceinline__ void scalar_gamma(MinresDev* st, const double* p, int np) {
   if (st->phase != PH_RUN) return;
   __shared__ double red[32];
   double g2 = reduce_partials(p, np, red);
@@ -733,7 +767,7 @@ __global__ void __launch_bounds__(256) k_scalar_gamma(MinresDev* st, const doubl
   if (gn == 0.0 || st->relres_est <= st->tol || st->iter >= st->maxit) st->phase = PH_CHECK;
 }
 
-__global__ void __launch_bounds__(256) k_scalar_check(MinresDev* st, const double* p, int np) {
+__device__ __forceinline__ void scalar_check(MinresDev* st, const double* p, int np) {
   __shared__ double red[32];
   const bool check = (st->phase == PH_CHECK);
   double r2 = check ? reduce_partials(p, np, red) : 0.0;
@@ -750,6 +784,20 @@ __global__ void __launch_bounds__(256) k_scalar_check(MinresDev* st, const doubl
   } else {
     st->phase = PH_RUN;
   }
+}
+
+__global__ void __launch_bounds__(256) k_scalar_init(MinresDev* st, const double* pzv, int nzv,
+                                                     const double* pb, int nb) {
+  scalar_init(st, pzv, nzv, pb, nb);
+}
+__global__ void __launch_bounds__(256) k_scalar_delta(MinresDev* st, const double* p, int np) {
+  scalar_delta(st, p, np);
+}
+__global__ void __launch_bounds__(256) k_scalar_gamma(MinresDev* st, const double* p, int np) {
+  scalar_gamma(st, p, np);
+}
+__global__ void __launch_bounds__(256) k_scalar_check(MinresDev* st, const double* p, int np) {
+  scalar_check(st, p, np);
 }
 
 // w_{j+1} = (z_j - a3 w_{j-1} - a2 w_j)/a1 (written over w_{j-1}); x += c_{j+1} eta w_{j+1}
@@ -973,6 +1021,179 @@ cudaError_t launch_w_update(MinresDev* s, const double* z, double* w_prev, const
 }
 cudaError_t launch_sum_partials(const double* partials, int np, double* out, cudaStream_t st) {
   k_sum_partials<<<1, 256, 0, st>>>(partials, np, out);
+  return cudaGetLastError();
+}
+
+// ============================================================================================
+// Multi-item kernels (batched solves)
+__device__ __forceinline__ int find_item(const long long* prefix, int nitems, long long t) {
+  int lo = 0, hi = nitems - 1;           // largest i with prefix[i] <= t
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <class A>
+__global__ void __launch_bounds__(kThreads)
+k_conv_multi(const ConvItem* __restrict__ items, const long long* __restrict__ prefix, int nitems,
+             long long total) {
+  for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+    const int it = find_item(prefix, nitems, t);
+    const ConvItem& ci = items[it];
+    if (ci.phase && *ci.phase != ci.want) continue;
+    conv_tile<A>(ci.op, ci.spectral, 0, ci.x, ci.xscale, ci.y, ci.flip, ci.mode, ci.rhs,
+                 ci.partials, ci.spectral ? nullptr : ci.x, ci.log2NC, t - prefix[it]);
+  }
+}
+
+template <class A>
+__global__ void __launch_bounds__(kThreads)
+k_timepass_multi(const TpItem* __restrict__ items, const long long* __restrict__ prefix,
+                 int nitems, long long total) {
+  for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+    const int it = find_item(prefix, nitems, t);
+    const TpItem& ti = items[it];
+    if (ti.phase && *ti.phase != ti.want) continue;
+    const typename A::V* tw = reinterpret_cast<const typename A::V*>(
+        sizeof(typename A::V) == 16 ? (std::is_same<A, ArithDF>::value ? (const void*)ti.op.tw_N_df
+                                                                        : (const void*)ti.op.tw_N)
+                                    : (const void*)ti.op.tw_N32);
+    timepass_tile<A>(ti.op, ti.pt, ti.cb, ti.out, ti.dot_with, ti.partials, ti.log2NC, tw,
+                     t - prefix[it]);
+  }
+}
+
+template <class A>
+__global__ void __launch_bounds__(kThreads)
+k_dst_multi(const DstItem* __restrict__ items, const long long* __restrict__ prefix, int nitems,
+            long long total) {
+  for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+    const int it = find_item(prefix, nitems, t);
+    const DstItem& di = items[it];
+    const typename A::V* tw = reinterpret_cast<const typename A::V*>(di.tw);
+    if (di.inner == 1)
+      dst_tile<A, true>(di.nlines, di.m, di.inner, di.P, di.log2L, di.log2NC, di.cb, di.out,
+                        di.flip, (int)di.N, di.M, di.dot_with, di.partials, tw, t - prefix[it]);
+    else
+      dst_tile<A, false>(di.nlines, di.m, di.inner, di.P, di.log2L, di.log2NC, di.cb, di.out,
+                         di.flip, (int)di.N, di.M, di.dot_with, di.partials, tw, t - prefix[it]);
+  }
+}
+
+// one block row of items per blockIdx.y; elements grid-strided over blockIdx.x
+__global__ void __launch_bounds__(256) k_w_update_multi(const VecItem* __restrict__ items) {
+  const VecItem& vi = items[blockIdx.y];
+  if (!vi.st->wpending) return;
+  const MinresDev* st = vi.st;
+  const double ig = st->w_inv_gamma, a1i = st->w_a1inv, a2 = st->w_a2, a3 = st->w_a3,
+               ce = st->w_ceta;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < vi.n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double wn = (vi.z[e] * ig - a3 * vi.w_prev[e] - a2 * vi.w[e]) * a1i;
+    vi.w_prev[e] = wn;
+    vi.x[e] = fma(ce, wn, vi.x[e]);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_scalar_multi(int which, const ScalItem* __restrict__ items) {
+  const ScalItem& si = items[blockIdx.x];
+  switch (which) {
+    case 0: scalar_init(si.st, si.p0, si.n0, si.p1, si.n1); break;
+    case 1: scalar_delta(si.st, si.p0, si.n0); break;
+    case 2: scalar_gamma(si.st, si.p0, si.n0); break;
+    default: scalar_check(si.st, si.p0, si.n0); break;
+  }
+}
+
+__global__ void k_count_running(const ScalItem* __restrict__ items, int nitems, int* out) {
+  int c = 0;
+  for (int i = threadIdx.x; i < nitems; i += blockDim.x) {
+    const int ph = items[i].st->phase;
+    c += (ph == PH_RUN || ph == PH_CHECK) ? 1 : 0;
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if (threadIdx.x == 0) *out = c;
+}
+
+int persistent_grid(int kind, int prec) {
+  int dev = 0, sms = 152, per = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  size_t smem = (prec == PREC_F32 ? sizeof(float2) : sizeof(double2)) * kCap;
+  if (kind == 0) {
+    if (prec == PREC_DF) { set_smem(k_conv_multi<ArithDF>, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_conv_multi<ArithDF>, kThreads, smem); }
+    else { set_smem(k_conv_multi<ArithD>, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_conv_multi<ArithD>, kThreads, smem); }
+  } else if (kind == 1) {
+    if (prec == PREC_F32) { set_smem(k_timepass_multi<ArithF>, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_timepass_multi<ArithF>, kThreads, smem); }
+    else if (prec == PREC_DF) { set_smem(k_timepass_multi<ArithDF>, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_timepass_multi<ArithDF>, kThreads, smem); }
+    else { set_smem(k_timepass_multi<ArithD>, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_timepass_multi<ArithD>, kThreads, smem); }
+  } else {
+    if (prec == PREC_DF) { set_smem(k_dst_multi<ArithDF>, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dst_multi<ArithDF>, kThreads, smem); }
+    else { set_smem(k_dst_multi<ArithD>, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dst_multi<ArithD>, kThreads, smem); }
+  }
+  if (per < 1) per = 1;
+  return sms * per;
+}
+
+cudaError_t launch_conv_multi(int arith, const ConvItem* items, const long long* prefix,
+                              int nitems, long long total, cudaStream_t st) {
+  const int g = (int)std::min<long long>(persistent_grid(0, arith ? PREC_DF : PREC_F64), total);
+  if (g <= 0) return cudaSuccess;
+  if (arith)
+    k_conv_multi<ArithDF><<<g, kThreads, kCap * sizeof(float4), st>>>(items, prefix, nitems, total);
+  else
+    k_conv_multi<ArithD><<<g, kThreads, kCap * sizeof(double2), st>>>(items, prefix, nitems, total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_timepass_multi(int prec, const TpItem* items, const long long* prefix,
+                                  int nitems, long long total, cudaStream_t st) {
+  const int g = (int)std::min<long long>(persistent_grid(1, prec), total);
+  if (g <= 0) return cudaSuccess;
+  if (prec == PREC_F32)
+    k_timepass_multi<ArithF><<<g, kThreads, kCap * sizeof(float2), st>>>(items, prefix, nitems, total);
+  else if (prec == PREC_DF)
+    k_timepass_multi<ArithDF><<<g, kThreads, kCap * sizeof(float4), st>>>(items, prefix, nitems, total);
+  else
+    k_timepass_multi<ArithD><<<g, kThreads, kCap * sizeof(double2), st>>>(items, prefix, nitems, total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dst_multi(int prec, const DstItem* items, const long long* prefix, int nitems,
+                             long long total, cudaStream_t st) {
+  const int g = (int)std::min<long long>(persistent_grid(2, prec), total);
+  if (g <= 0) return cudaSuccess;
+  if (prec == PREC_DF)
+    k_dst_multi<ArithDF><<<g, kThreads, kCap * sizeof(float4), st>>>(items, prefix, nitems, total);
+  else
+    k_dst_multi<ArithD><<<g, kThreads, kCap * sizeof(double2), st>>>(items, prefix, nitems, total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_w_update_multi(const VecItem* items, int nitems, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  dim3 grid(std::max(1, 152 * 8 / std::max(1, nitems)), nitems);
+  k_w_update_multi<<<grid, 256, 0, st>>>(items);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scalar_multi(int which, const ScalItem* items, int nitems, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  k_scalar_multi<<<nitems, 256, 0, st>>>(which, items);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_running(const ScalItem* items, int nitems, int* out, cudaStream_t st) {
+  k_count_running<<<1, 32, 0, st>>>(items, nitems, out);
   return cudaGetLastError();
 }
 
