@@ -158,6 +158,28 @@ bltt_status bltt_minres_solve_ex(bltt_handle h, const double* f_dev, double alph
 bltt_status bltt_minres_solve(bltt_handle h, const double* f_dev, double alpha, double tol,
                               int maxit, int precision, double* u_dev, bltt_solve_info* info);
 
+/* Solve many BLTT systems with several right-hand sides each, together (batching: one launch per
+ * MINRES phase covers every (system, right-hand side) item of a wave; the phase sequence of two
+ * iterations is captured in a CUDA graph and replayed until every item has stopped).  Each item
+ * is the solve of bltt_minres_solve_ex in the DST basis (Sec. 2-3, Sec. 5) with its own MINRES
+ * state; the items of one system share its tables.  Waves are sized to 85% of the free device
+ * memory (or to the byte count in the environment variable BLTT_BATCH_MAX_BYTES, if smaller);
+ * tile widths come from a built-in autotuner (opts->sync_every < 0 disables it).
+ *   nsys systems sys[s] (host structs as for bltt_create; N and m[ax]+1 powers of two) with
+ *   nrhs[s] >= 1 right-hand sides each; f_dev / u_dev: host arrays of sum(nrhs) device pointers
+ *   (system-major), each a vector of that system's N*M doubles, u not aliasing f.
+ *   alpha: host array of nsys values in (0,1], or NULL for the default rule (1e-8; 1e-3 for the
+ *   FP32 preconditioner).  opts: precision and matvec_arith as for bltt_minres_solve_ex (basis
+ *   is always the DST basis); may be NULL.  info: host array of sum(nrhs) entries or NULL;
+ *   relres_true is the true residual of the DST-basis system (equal to the physical one up to
+ *   the rounding of the exit DST).
+ * Returns BLTT_OK when every item converged, else the first failing item's status.  Systems whose
+ * blocks have at most 4 nonzero coefficients (the direct matvec) give BLTT_ERR_UNSUPPORTED. */
+bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, const int* nrhs,
+                               const double* const* f_dev, double* const* u_dev,
+                               const double* alpha, double tol, int maxit,
+                               const bltt_solve_opts* opts, bltt_solve_info* info);
+
 /* Per-kernel device time, collected with CUDA events around every launch on the handle's
  * stream while profiling is enabled (tracing aid; adds two event records per launch). */
 typedef struct {

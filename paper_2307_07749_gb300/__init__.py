@@ -89,6 +89,12 @@ _SIGS = {
     "bltt_residual_noalloc": (ctypes.c_int, [ctypes.POINTER(bltt_blocks), ctypes.c_int,
                                              ctypes.c_longlong, _P, _P, _P, _P,
                                              ctypes.POINTER(ctypes.c_double)]),
+    "bltt_solve_batched": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(bltt_blocks),
+                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_P),
+                                          ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_double),
+                                          ctypes.c_double, ctypes.c_int,
+                                          ctypes.POINTER(bltt_solve_opts),
+                                          ctypes.POINTER(bltt_solve_info)]),
     "bltt_last_error": (ctypes.c_char_p, [_P]),
     "bltt_version": (ctypes.c_char_p, []),
 }
@@ -224,6 +230,35 @@ def bltt_residual_noalloc(a, b, N, ndim, m, h, u, f, r=None, stream=None):
     if st != BLTT_OK:
         raise BlttError(st, "bltt_residual_noalloc")
     return out.value
+
+
+def bltt_solve_batched(problems, fs, us, alpha=None, tol=1e-8, maxit=200, precision=PREC_F64,
+                       matvec_arith=ARITH_DEFAULT, autotune=True):
+    """Batched solve.  problems: list of objects with N, d, m, h, a, b; fs / us: list (per
+    problem) of lists of float64 CUDA tensors.  Returns (status, list of info dicts, system-major)."""
+    nsys = len(problems)
+    keep = []
+    blocks = (bltt_blocks * nsys)()
+    for s, p in enumerate(problems):
+        a = np.ascontiguousarray(p.a, dtype=np.float64)
+        b = np.ascontiguousarray(p.b, dtype=np.float64)
+        keep += [a, b]
+        m = list(p.m) + [1] * (3 - len(p.m))
+        h = list(p.h) + [1.0] * (3 - len(p.h))
+        blocks[s] = bltt_blocks(int(p.N), a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                bltt_space(int(p.d), (ctypes.c_int * 3)(*m), (ctypes.c_double * 3)(*h)))
+    nrhs = (ctypes.c_int * nsys)(*[len(f) for f in fs])
+    tot = sum(len(f) for f in fs)
+    fp = (_P * tot)(*[_ptr(t, "f").value for f in fs for t in f])
+    up = (_P * tot)(*[_ptr(t, "u").value for u in us for t in u])
+    al = None if alpha is None else (ctypes.c_double * nsys)(*[float(x) for x in alpha])
+    opts = bltt_solve_opts(precision, BASIS_SPECTRAL, PRECOND_ABAC, 0 if autotune else -1, 0,
+                           matvec_arith)
+    infos = (bltt_solve_info * tot)()
+    st = lib().bltt_solve_batched(nsys, blocks, nrhs, fp, up, al, float(tol), int(maxit),
+                                  ctypes.byref(opts), infos)
+    return st, [infos[i].as_dict() for i in range(tot)]
 
 
 def bltt_version():

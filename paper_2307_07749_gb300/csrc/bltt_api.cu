@@ -10,7 +10,6 @@
 #include <string>
 #include <vector>
 
-#include "../../include/bltt.h"
 #include "internal.h"
 
 using namespace bltt;
@@ -441,6 +440,13 @@ void prof_harvest(bltt_ctx* h) {
 }
 
 }  // namespace
+
+namespace bltt {
+const OpTables& ctx_op(bltt_handle h) { return h->op; }
+bltt_status ctx_prepare(bltt_handle h, double alpha, int prec) { return prepare_precond(h, alpha, prec); }
+PrecTables ctx_prec_tables(bltt_handle h) { return prec_tables(h, 0); }
+long long ctx_n(bltt_handle h) { return h->n; }
+}  // namespace bltt
 
 // =============================================================================================
 extern "C" {

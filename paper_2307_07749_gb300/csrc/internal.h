@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/bltt.h"
+
 namespace bltt {
 
 constexpr int kThreads = 512;      // threads of every FFT tile kernel
@@ -165,6 +167,12 @@ struct ScalItem {           // scalar recurrence of one item
 };
 
 int persistent_grid(int kind, int prec);   // resident blocks for a multi-item launch
+
+// handle internals used by the batched driver (defined in bltt_api.cu)
+const OpTables& ctx_op(bltt_handle h);
+bltt_status ctx_prepare(bltt_handle h, double alpha, int prec);
+PrecTables ctx_prec_tables(bltt_handle h);
+long long ctx_n(bltt_handle h);
 cudaError_t launch_conv_multi(int arith, const ConvItem* items, const long long* prefix,
                               int nitems, long long total, cudaStream_t st);
 cudaError_t launch_timepass_multi(int prec, const TpItem* items, const long long* prefix,

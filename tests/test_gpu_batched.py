@@ -1,0 +1,76 @@
+"""Batched solves: many systems of uneven N and M with several right-hand sides each, in one
+launch per MINRES phase under a CUDA graph.  Every item is compared with the oracle's own solve."""
+import numpy as np
+import pytest
+
+import oracle as O
+from workloads import fractional_problem, rhs_uniform
+from _gpu_helpers import rel, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2307_07749_gb300 import build
+    build.build()
+    import paper_2307_07749_gb300 as mod
+    return mod
+
+
+def small_batch(seed=7):
+    rng = np.random.default_rng(seed)
+    probs = []
+    for s in range(8):
+        d = int(rng.choice([1, 2]))
+        m = int(rng.choice([7, 15, 31] if d == 2 else [15, 31, 63, 127]))
+        N = int(rng.choice([16, 32, 64, 128]))
+        probs.append(fractional_problem(d, m, N, float(rng.uniform(0.2, 0.9))))
+    fs = [[rhs_uniform(p.n, 1000 * s + r) for r in range(2)] for s, p in enumerate(probs)]
+    return probs, fs
+
+
+@pytest.mark.parametrize("form", [
+    dict(precision=64, matvec_arith=1, alpha=1e-8),
+    dict(precision=32, matvec_arith=2, alpha=1e-3),
+    dict(precision=96, matvec_arith=2, alpha=1e-5),
+], ids=["f64", "f32_prec", "f32x2"])
+def test_batched_matches_oracle(B, form):
+    probs, fs = small_batch()
+    fd = [[to_dev(f) for f in row] for row in fs]
+    ud = [[to_dev(np.zeros_like(f)) for f in row] for row in fs]
+    st, infos = B.bltt_solve_batched(probs, fd, ud, alpha=[form["alpha"]] * len(probs), tol=1e-8,
+                                     maxit=100, precision=form["precision"],
+                                     matvec_arith=form["matvec_arith"])
+    assert st == 0, [i["status"] for i in infos]
+    k = 0
+    for s, p in enumerate(probs):
+        for r, f in enumerate(fs[s]):
+            info = infos[k]
+            k += 1
+            ref = O.solve(p, f, alpha=form["alpha"], tol=1e-8)
+            u = to_host(ud[s][r])
+            assert info["relres_true"] <= 1e-8
+            assert rel(O.bltt_matvec(p, u), f) <= 1e-8
+            slack = 1 if form["precision"] == 64 else 4
+            assert abs(info["iters"] - ref["iters"]) <= slack, (s, r, info["iters"], ref["iters"])
+            assert rel(u, ref["x"]) <= 1e-6
+
+
+def test_batched_equals_single_solves_and_splits_waves(B, monkeypatch):
+    probs, fs = small_batch(seed=8)
+    fd = [[to_dev(f) for f in row] for row in fs]
+    ud = [[to_dev(np.zeros_like(f)) for f in row] for row in fs]
+    # a workspace cap of ~3 items forces several waves
+    sizes = sorted((9 * p.n * 8 for p in probs), reverse=True)
+    monkeypatch.setenv("BLTT_BATCH_MAX_BYTES", str(int(sizes[0] * 2.5)))
+    st, infos = B.bltt_solve_batched(probs, fd, ud, tol=1e-8, maxit=100)
+    assert st == 0
+    k = 0
+    for s, p in enumerate(probs):
+        sol = B.Solver(p)
+        for r in range(2):
+            u1, inf1 = sol.solve(fd[s][r], alpha=1e-8, tol=1e-8, maxit=100, precision=64, basis=1)
+            assert infos[k]["iters"] == inf1["iters"]
+            assert rel(to_host(ud[s][r]), to_host(u1)) <= 1e-12
+            k += 1
