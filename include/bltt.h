@@ -180,6 +180,36 @@ bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, const int* nrhs
                                const double* alpha, double tol, int maxit,
                                const bltt_solve_opts* opts, bltt_solve_info* info);
 
+/* ---- learned alpha --------------------------------------------------------------------------
+ * A small MLP predicts the alpha that minimises the MINRES iterations of a problem from four
+ * features (log N, log M, gamma, log(tau/h^2)); the paper fixes alpha = 1e-8 (Sec. 5.2) and its
+ * Theorem 1 only bounds alpha from above, so the network is an addition of this library, trained
+ * on alpha sweeps run by this solver.  Network: 4 -> 32 -> 32 -> 1, tanh hidden layers, FP32.
+ * Model: a host array of BLTT_ALPHA_MODEL_FLOATS floats laid out as W1[32][4], b1[32], W2[32][32],
+ * b2[32], w3[32], b3 (the 1249 trainable parameters), then mean[4], std[4] of the features and
+ * y_mean, y_std of the label log10(alpha): the network maps (x - mean)/std to
+ * (log10(alpha) - y_mean)/y_std.  The caller initialises the parameters (no random draws inside).
+ * Loss: mean squared error over the n samples.  All three calls allocate device memory for their
+ * inputs and scratch and synchronise the legacy stream.  std and y_std must be > 0, else
+ * BLTT_ERR_INVALID_ARG. */
+#define BLTT_ALPHA_MODEL_FLOATS 1259
+#define BLTT_ALPHA_NPARAM 1249
+
+/* Gradient of the loss w.r.t. the 1249 parameters (grad_out, host) and the loss (loss_out, host,
+ * may be NULL), by one forward and one backward pass over the n samples (feats: [n][4] host,
+ * labels: n values of log10(alpha), host). */
+bltt_status bltt_alpha_grad(const float* model, const float* feats, const float* labels, int n,
+                            float* grad_out, float* loss_out);
+
+/* Train `model` in place: `epochs` full-batch Adam steps (learning rate lr, beta1 0.9, beta2
+ * 0.999, eps 1e-8) on the n samples.  loss_hist (host, may be NULL) receives the loss before each
+ * step.  One CUDA block runs the whole training; sums over samples run in a fixed order. */
+bltt_status bltt_alpha_train(float* model, const float* feats, const float* labels, int n,
+                             int epochs, float lr, float* loss_hist);
+
+/* alpha_out[s] = 10^(network(feats[s])) for n feature rows (host arrays). */
+bltt_status bltt_alpha_predict(const float* model, const float* feats, int n, float* alpha_out);
+
 /* Per-kernel device time, collected with CUDA events around every launch on the handle's
  * stream while profiling is enabled (tracing aid; adds two event records per launch). */
 typedef struct {

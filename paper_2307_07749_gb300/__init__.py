@@ -95,6 +95,9 @@ _SIGS = {
                                           ctypes.c_double, ctypes.c_int,
                                           ctypes.POINTER(bltt_solve_opts),
                                           ctypes.POINTER(bltt_solve_info)]),
+    "bltt_alpha_grad": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P]),
+    "bltt_alpha_train": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_float, _P]),
+    "bltt_alpha_predict": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
     "bltt_last_error": (ctypes.c_char_p, [_P]),
     "bltt_version": (ctypes.c_char_p, []),
 }
@@ -259,6 +262,45 @@ def bltt_solve_batched(problems, fs, us, alpha=None, tol=1e-8, maxit=200, precis
     st = lib().bltt_solve_batched(nsys, blocks, nrhs, fp, up, al, float(tol), int(maxit),
                                   ctypes.byref(opts), infos)
     return st, [infos[i].as_dict() for i in range(tot)]
+
+
+ALPHA_MODEL_FLOATS, ALPHA_NPARAM = 1259, 1249
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def bltt_alpha_grad(model, feats, labels):
+    """(gradient [1249], loss) of the MSE of the alpha network on (feats [n,4], labels [n])."""
+    model, feats, labels = _f32(model), _f32(feats), _f32(labels)
+    g = np.zeros(ALPHA_NPARAM, np.float32)
+    loss = np.zeros(1, np.float32)
+    st = lib().bltt_alpha_grad(model.ctypes.data, feats.ctypes.data, labels.ctypes.data,
+                               len(labels), g.ctypes.data, loss.ctypes.data)
+    if st != BLTT_OK:
+        raise BlttError(st, "bltt_alpha_grad")
+    return g, float(loss[0])
+
+
+def bltt_alpha_train(model, feats, labels, epochs, lr=1e-2):
+    """Return (trained model copy, loss history)."""
+    model, feats, labels = _f32(model).copy(), _f32(feats), _f32(labels)
+    hist = np.zeros(max(epochs, 1), np.float32)
+    st = lib().bltt_alpha_train(model.ctypes.data, feats.ctypes.data, labels.ctypes.data,
+                                len(labels), int(epochs), float(lr), hist.ctypes.data)
+    if st != BLTT_OK:
+        raise BlttError(st, "bltt_alpha_train")
+    return model, hist[:epochs]
+
+
+def bltt_alpha_predict(model, feats):
+    model, feats = _f32(model), _f32(feats)
+    out = np.zeros(len(feats), np.float32)
+    st = lib().bltt_alpha_predict(model.ctypes.data, feats.ctypes.data, len(feats), out.ctypes.data)
+    if st != BLTT_OK:
+        raise BlttError(st, "bltt_alpha_predict")
+    return out
 
 
 def bltt_version():
