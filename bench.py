@@ -296,6 +296,113 @@ def run_reference(args):
     return 0
 
 
+def run_batched(args):
+    """96 L1 fractional systems of uneven N and M with 4 right-hand sides each (8.75 G unknowns
+    in all), solved by one bltt_solve_batched call, against the same items solved one by one.
+    Right-hand sides: U[-1,1] from torch's CUDA generator seeded 4 + 1000 s + r (drawing 70 GB on
+    the host would dominate the run)."""
+    import torch
+    from paper_2307_07749_gb300 import build
+    build.build()
+    import paper_2307_07749_gb300 as B
+    from workloads import batched_systems
+    sysl = batched_systems(96, 4, seed=4)
+    probs = [p for p, _ in sysl]
+    fs, us = [], []
+    for s, p in enumerate(probs):
+        row_f, row_u = [], []
+        for r in range(4):
+            g = torch.Generator(device="cuda")
+            g.manual_seed(4 + 1000 * s + r)
+            row_f.append(torch.rand(p.n, generator=g, dtype=torch.float64, device="cuda") * 2 - 1)
+            row_u.append(torch.empty(p.n, dtype=torch.float64, device="cuda"))
+        fs.append(row_f)
+        us.append(row_u)
+    torch.cuda.synchronize()
+    total_n = sum(p.n * 4 for p in probs)
+    out = {"workload": "batched96x4", "systems": 96, "rhs_per_system": 4, "unknowns": total_n}
+    forms = {"chosen": dict(precision=32, matvec_arith=2, alpha=1e-3),
+             "plain_f64": dict(precision=64, matvec_arith=1, alpha=1e-8)}
+    for name, fm in forms.items():
+        t0 = time.perf_counter()
+        st, infos = B.bltt_solve_batched(probs, fs, us, alpha=[fm["alpha"]] * 96, tol=TOL,
+                                         maxit=100, precision=fm["precision"],
+                                         matvec_arith=fm["matvec_arith"])
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+        iters = [i["iters"] for i in infos]
+        units = sum(p.n * iters[4 * s + r] for s, p in enumerate(probs) for r in range(4))
+        # the same items one at a time through bltt_minres_solve_ex on a stream (graph replay)
+        stream = torch.cuda.Stream()
+        t0 = time.perf_counter()
+        seq_iters = []
+        with torch.cuda.stream(stream):
+            for s, p in enumerate(probs):
+                sol = B.Solver(p, stream=stream)
+                for r in range(4):
+                    _, inf = sol.solve(fs[s][r], alpha=fm["alpha"], tol=TOL, maxit=100,
+                                       precision=fm["precision"], basis=B.BASIS_SPECTRAL,
+                                       matvec_arith=fm["matvec_arith"], u=us[s][r])
+                    seq_iters.append(inf["iters"])
+                sol.close()
+        torch.cuda.synchronize()
+        t_seq = time.perf_counter() - t0
+        out[name] = {"status": st, "batched_s": t_batch, "sequential_s": t_seq,
+                     "value_batched": units / t_batch, "value_sequential":
+                     sum(p.n * seq_iters[4 * s + r] for s, p in enumerate(probs) for r in range(4)) / t_seq,
+                     "unit": "unknown-iter/s", "max_relres": max(i["relres_true"] for i in infos),
+                     "iters_per_system": [iters[4 * s] for s in range(96)],
+                     "iters_match_sequential": iters == seq_iters}
+    print(json.dumps(out))
+    return 0
+
+
+def run_alpha(args):
+    """Learned alpha (FP32-preconditioner form): sweeps, training, held-out evaluation."""
+    import torch
+    from paper_2307_07749_gb300 import build
+    build.build()
+    import paper_2307_07749_gb300 as B
+    from paper_2307_07749_gb300 import learned_alpha as LA
+    from workloads import alpha_training_problems
+    t0 = time.perf_counter()
+    train = alpha_training_problems(args.alpha_train, seed=5)
+    X, t, raw = LA.build_dataset(train, maxit=40)
+    t_sweep = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    model, hist = LA.train(X, t, epochs=4000, lr=3e-3, seed=0)
+    t_train = time.perf_counter() - t0
+    held = alpha_training_problems(args.alpha_heldout, seed=55)
+    alphas = LA.predict(model, [p for p, _ in held])
+
+    def evaluate(alpha_of, maxit=60):
+        its, secs, fails = [], [], 0
+        for (p, rf), a in zip(held, alpha_of):
+            s = B.Solver(p)
+            f = torch.from_numpy(rf()).cuda()
+            t1 = time.perf_counter()
+            _, info = s.solve(f, alpha=float(a), tol=TOL, maxit=maxit, precision=32, basis=1,
+                              matvec_arith=2, raise_on_error=False, rebuild=True)
+            torch.cuda.synchronize()
+            secs.append(time.perf_counter() - t1)
+            ok = info["status"] == 0
+            fails += 0 if ok else 1
+            its.append(info["iters"] if ok else maxit)
+            s.close()
+        return {"mean_iters": float(np.mean(its)), "mean_ms": 1e3 * float(np.mean(secs)),
+                "not_converged": fails}
+
+    res = {"workload": "alpha_learning", "train_problems": len(train), "labelled": int(len(t)),
+           "heldout": len(held), "sweep_s": t_sweep, "train_s": t_train,
+           "loss_first_last": [float(hist[0]), float(hist[-1])],
+           "learned": evaluate(alphas),
+           "paper_rule_1e-8": evaluate([1e-8] * len(held)),
+           "fixed_1e-3": evaluate([1e-3] * len(held)),
+           "form": "FP32 preconditioner, double-float matvec, DST basis, tol 1e-8"}
+    print(json.dumps(res))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -304,9 +411,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="frac2d", choices=["frac2d", "batched", "alpha"],
+                    help="frac2d: the headline line; batched / alpha: supplementary reports")
+    ap.add_argument("--alpha-train", type=int, default=2000)
+    ap.add_argument("--alpha-heldout", type=int, default=256)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "alpha":
+        return run_alpha(args)
     args.warmup = max(args.warmup, 3)
 
     rank, local, ws = dist_init()

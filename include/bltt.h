@@ -94,6 +94,9 @@ typedef struct {
   int sync_every;    /* iterations issued between host checks of the device state (0: 2)        */
   int rebuild;       /* 1: rebuild the per-alpha preconditioner tables even if cached            */
   int matvec_arith;  /* BLTT_ARITH_*                                                             */
+  int no_graph;      /* 1: launch every kernel directly; 0: capture sync_every (rounded up to even)
+                        iterations in a CUDA graph, cached per handle, and replay it (used when the
+                        handle's stream is not the legacy stream and profiling is off)            */
 } bltt_solve_opts;
 
 typedef struct {

@@ -48,7 +48,7 @@ class bltt_blocks(ctypes.Structure):
 class bltt_solve_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("basis", ctypes.c_int), ("precond", ctypes.c_int),
                 ("sync_every", ctypes.c_int), ("rebuild", ctypes.c_int),
-                ("matvec_arith", ctypes.c_int)]
+                ("matvec_arith", ctypes.c_int), ("no_graph", ctypes.c_int)]
 
 
 class bltt_solve_info(ctypes.Structure):
@@ -183,8 +183,8 @@ def bltt_precond_apply(handle, alpha, v, z, precision=PREC_F64):
 
 def bltt_minres_solve_ex(handle, f, alpha, tol, maxit, u, precision=PREC_F64, basis=BASIS_AUTO,
                          precond=PRECOND_ABAC, sync_every=0, raise_on_error=True, rebuild=0,
-                         matvec_arith=ARITH_DEFAULT):
-    opts = bltt_solve_opts(precision, basis, precond, sync_every, rebuild, matvec_arith)
+                         matvec_arith=ARITH_DEFAULT, no_graph=0):
+    opts = bltt_solve_opts(precision, basis, precond, sync_every, rebuild, matvec_arith, no_graph)
     info = bltt_solve_info()
     st = lib().bltt_minres_solve_ex(handle, _ptr(f, "f"), float(alpha), float(tol), int(maxit),
                                     ctypes.byref(opts), _ptr(u, "u"), ctypes.byref(info))
@@ -257,7 +257,7 @@ def bltt_solve_batched(problems, fs, us, alpha=None, tol=1e-8, maxit=200, precis
     up = (_P * tot)(*[_ptr(t, "u").value for u in us for t in u])
     al = None if alpha is None else (ctypes.c_double * nsys)(*[float(x) for x in alpha])
     opts = bltt_solve_opts(precision, BASIS_SPECTRAL, PRECOND_ABAC, 0 if autotune else -1, 0,
-                           matvec_arith)
+                           matvec_arith, 0)
     infos = (bltt_solve_info * tot)()
     st = lib().bltt_solve_batched(nsys, blocks, nrhs, fp, up, al, float(tol), int(maxit),
                                   ctypes.byref(opts), infos)
@@ -360,11 +360,11 @@ class Solver:
 
     def solve(self, f, alpha=1e-8, tol=1e-8, maxit=200, precision=PREC_F64, basis=BASIS_AUTO,
               precond=PRECOND_ABAC, u=None, sync_every=0, raise_on_error=True, rebuild=False,
-              matvec_arith=ARITH_DEFAULT):
+              matvec_arith=ARITH_DEFAULT, graph=True):
         import torch
         u = torch.empty_like(f) if u is None else u
         st, info = bltt_minres_solve_ex(self.handle, f, alpha, tol, maxit, u, precision, basis,
                                         precond, sync_every, raise_on_error, int(rebuild),
-                                        matvec_arith)
+                                        matvec_arith, 0 if graph else 1)
         info["status_name"] = STATUS_NAMES.get(st, st)
         return u, info

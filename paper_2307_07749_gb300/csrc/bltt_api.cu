@@ -5,6 +5,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <map>
 #include <string>
@@ -98,6 +99,9 @@ struct bltt_ctx {
   double2* pc_bhat64 = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   long long launches = 0;
+  // cached CUDA graph of the MINRES iterations and the key it was captured for
+  cudaGraphExec_t gexec = nullptr;
+  const void* gkey[12] = {nullptr};
   // per-launch profiling
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -114,6 +118,7 @@ struct bltt_ctx {
     if (scal_host) cudaFreeHost(scal_host);
     for (auto& e : ev) if (e) cudaEventDestroy(e);
     for (auto& e : ev_pool) cudaEventDestroy(e);
+    if (gexec) cudaGraphExecDestroy(gexec);
   }
   bool stream_sync_ok = true;
 
@@ -576,6 +581,7 @@ bltt_status bltt_create(const bltt_blocks* blocks, int N, long long M, bltt_hand
     }
   }
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&h->ev[i]);
+  if (e == cudaSuccess) e = prepare_kernel_attributes();
   if (e != cudaSuccess) {
     bltt_status s = (e == cudaErrorMemoryAllocation) ? BLTT_ERR_OOM : BLTT_ERR_CUDA;
     std::string msg = std::string("bltt_create: ") + cudaGetErrorString(e);
@@ -718,42 +724,86 @@ bltt_status bltt_minres_solve_ex(bltt_handle h, const double* f, double alpha, d
   PCK(h, "scalar", launch_scalar_init(h->state, h->partials[0], nzv, h->partials[1], nb, st), "scalar init");
   h->launches++;
 
-  int issued = 0;
-  for (;;) {
-    const int prv = 1 - cur;
+  // one MINRES iteration (A1..A4 of the hot loop); the caller rotates the buffers afterwards
+  const long long per_iter = 5 + ((op.b_kind == 1 && op.ntaps == 0 && !spectral) ? 4 : 2) +
+                             (spectral || none ? 0 : 2 * op.d);
+  auto issue_iteration = [&](int c0) -> bltt_status {
+    const long long saved = h->launches;   // counted per iteration by the caller (per_iter)
+    struct Restore { bltt_ctx* hh; long long v; ~Restore() { hh->launches = v; } } restore{h, saved};
+    const int prv = 1 - c0;
     // q = Y A z_j  (z_j = z_u / gamma_j), delta_j = <q, z_j>
-    PCK(h, mv_name(op), launch_matvec(op, spectral, zbuf[cur], &h->state->inv_gamma, q, 1, MV_STORE, nullptr,
-                        h->partials[0], &np, phase, tmp, st), "matvec");
-    h->launches += (op.b_kind == 1 && op.ntaps == 0 && !spectral) ? 2 : 1;
+    PCK(h, mv_name(op), launch_matvec(op, spectral, zbuf[c0], &h->state->inv_gamma, q, 1, MV_STORE,
+                                      nullptr, h->partials[0], &np, phase, tmp, st), "matvec");
     PCK(h, "scalar", launch_scalar_delta(h->state, h->partials[0], np, st), "scalar delta");
-    h->launches++;
     // v_{j+1} = q - (delta/gamma) v_j - (gamma/gamma_prev) v_{j-1} (over v_{j-1});
     // z_{j+1} = P^{-1} v_{j+1} (over z_{j-1}); <z_{j+1}, v_{j+1}>
-    {
-      Combine c{};
-      c.in0 = q; c.in1 = vbuf[cur]; c.in2 = vbuf[prv];
-      c.coef = h->state->coef; c.vout = vbuf[prv];
-      s = precond_chain(h, spectral, o.precision, pt, c, zbuf[prv], vbuf[prv], h->partials[1], &np, phase);
-      if (s != BLTT_OK) return s;
-    }
+    Combine c{};
+    c.in0 = q; c.in1 = vbuf[c0]; c.in2 = vbuf[prv];
+    c.coef = h->state->coef; c.vout = vbuf[prv];
+    bltt_status r = precond_chain(h, spectral, o.precision, pt, c, zbuf[prv], vbuf[prv],
+                                  h->partials[1], &np, phase);
+    if (r != BLTT_OK) return r;
     PCK(h, "scalar", launch_scalar_gamma(h->state, h->partials[1], np, st), "scalar gamma");
-    h->launches++;
-    PCK(h, "w_update", launch_w_update(h->state, zbuf[cur], wbuf[prv], wbuf[cur], x, n, st), "w update");
-    h->launches++;
+    PCK(h, "w_update", launch_w_update(h->state, zbuf[c0], wbuf[prv], wbuf[c0], x, n, st), "w update");
     // true residual when the estimate says so
-    PCK(h, mv_name(op), launch_matvec(op, spectral, x, nullptr, nullptr, 1, MV_RESID, bvec, h->partials[0], &np,
-                        phase, tmp, st), "residual");
-    h->launches += (op.b_kind == 1 && op.ntaps == 0 && !spectral) ? 2 : 1;
+    PCK(h, mv_name(op), launch_matvec(op, spectral, x, nullptr, nullptr, 1, MV_RESID, bvec,
+                                      h->partials[0], &np, phase, tmp, st), "residual");
     PCK(h, "scalar", launch_scalar_check(h->state, h->partials[0], np, st), "scalar check");
-    h->launches++;
+    return BLTT_OK;
+  };
+  auto rotate = [&]() {
     std::swap(vbuf[0], vbuf[1]);
     std::swap(zbuf[0], zbuf[1]);
     std::swap(wbuf[0], wbuf[1]);
-    ++issued;
-    if (issued % sync_every == 0 || issued >= maxit) {
+  };
+  // A5: blocks of G iterations captured once in a CUDA graph (G even, so that the buffers return
+  // to their roles) and replayed; the legacy stream cannot be captured, profiling needs the
+  // direct launches
+  const int G = (sync_every + 1) & ~1;
+  const bool graph_mode = (st != nullptr) && !h->prof && !o.no_graph;
+  int issued = 0;
+  if (graph_mode) {
+    const void* key[12] = {(const void*)(intptr_t)spectral, (const void*)(intptr_t)o.precision,
+                           (const void*)(intptr_t)op.mv_arith, (const void*)(intptr_t)none,
+                           (const void*)(intptr_t)G, x, pt.g64, pt.g32, pt.gdf, pt.dinv, st,
+                           (const void*)(intptr_t)op.ntaps};
+    if (!h->gexec || std::memcmp(key, h->gkey, sizeof key) != 0) {
+      if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+      cudaGraph_t g = nullptr;
+      CK(h, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+      bltt_status cap = BLTT_OK;
+      for (int i = 0; i < G && cap == BLTT_OK; ++i) {
+        cap = issue_iteration(cur);
+        rotate();
+      }
+      cudaError_t ce = cudaStreamEndCapture(st, &g);
+      if (cap != BLTT_OK) { if (g) cudaGraphDestroy(g); return cap; }
+      CK(h, ce, "end capture");
+      ce = cudaGraphInstantiate(&h->gexec, g, 0);
+      cudaGraphDestroy(g);
+      CK(h, ce, "graph instantiate");
+      std::memcpy(h->gkey, key, sizeof key);
+    }
+    for (;;) {
+      CK(h, cudaGraphLaunch(h->gexec, st), "graph launch");
+      h->launches += per_iter * G;
+      issued += G;
       CK(h, cudaMemcpyAsync(sh, h->state, sizeof *sh, cudaMemcpyDeviceToHost, st), "state download");
       CK(h, cudaStreamSynchronize(st), "sync");
       if (sh->phase != PH_RUN || issued >= maxit) break;
+    }
+  } else {
+    for (;;) {
+      s = issue_iteration(cur);
+      if (s != BLTT_OK) return s;
+      h->launches += per_iter;
+      rotate();
+      ++issued;
+      if (issued % sync_every == 0 || issued >= maxit) {
+        CK(h, cudaMemcpyAsync(sh, h->state, sizeof *sh, cudaMemcpyDeviceToHost, st), "state download");
+        CK(h, cudaStreamSynchronize(st), "sync");
+        if (sh->phase != PH_RUN || issued >= maxit) break;
+      }
     }
   }
   double relres_phys = sh->relres_true;

@@ -116,6 +116,7 @@ cudaError_t launch_copy_scaled_check(const double* src, double* dst, long long n
 cudaError_t launch_sum_partials(const double* partials, int np, double* out, cudaStream_t st);
 
 int tile_columns(long long nlines, int Lfft);   // complex columns per tile for a line batch
+cudaError_t prepare_kernel_attributes();         // shared-memory limits of every tile kernel
 
 // ---------------------------------------------------------------------------------------------
 // Multi-item ("wave") launches for batched solves: one launch covers the tiles of many items

@@ -868,6 +868,18 @@ template <class A> static cudaError_t ensure_smem_conv() {
   return e;
 }
 
+cudaError_t prepare_kernel_attributes() {
+  cudaError_t e = ensure_smem_dst<ArithD>();
+  if (e == cudaSuccess) e = ensure_smem_dst<ArithF>();
+  if (e == cudaSuccess) e = ensure_smem_dst<ArithDF>();
+  if (e == cudaSuccess) e = ensure_smem_tp<ArithD>();
+  if (e == cudaSuccess) e = ensure_smem_tp<ArithF>();
+  if (e == cudaSuccess) e = ensure_smem_tp<ArithDF>();
+  if (e == cudaSuccess) e = ensure_smem_conv<ArithD>();
+  if (e == cudaSuccess) e = ensure_smem_conv<ArithDF>();
+  return e;
+}
+
 cudaError_t launch_dst(const OpTables& op, int axis, int prec, const Combine& in, double* out,
                        int flip, const double* dot_with, double* partials, int* nparts,
                        const int* phase, cudaStream_t st) {

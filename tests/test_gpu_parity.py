@@ -174,6 +174,30 @@ def test_comparison_solvers(B, precond, alpha):
     assert info["relres_true"] <= 1e-8
 
 
+@pytest.mark.parametrize("form", [dict(precision=64, basis=1, matvec_arith=1, alpha=1e-8),
+                                  dict(precision=32, basis=2, matvec_arith=2, alpha=1e-3)],
+                         ids=["f64_spectral", "f32_physical"])
+def test_graph_replay_matches_direct_launches(B, form):
+    # A5: iterations captured in a CUDA graph on a non-default stream give the same result as
+    # direct launches (the legacy stream cannot be captured and always launches directly)
+    import torch
+    prob = fractional_problem(2, 31, 32, 0.7)
+    f = to_dev(rhs_uniform(prob.n, 37))
+    st = torch.cuda.Stream()
+    s = B.Solver(prob, stream=st)
+    with torch.cuda.stream(st):
+        u1, i1 = s.solve(f, tol=1e-8, maxit=50, graph=True, **form)
+        u1b, i1b = s.solve(f, tol=1e-8, maxit=50, graph=True, **form)   # cached graph
+        u2, i2 = s.solve(f, tol=1e-8, maxit=50, graph=False, **form)
+        u3, i3 = s.solve(f, tol=1e-8, maxit=50, graph=True, sync_every=4, **form)
+    torch.cuda.synchronize()
+    assert i1["status"] == i2["status"] == i3["status"] == 0
+    assert i1["iters"] == i2["iters"] == i1b["iters"]
+    assert torch.equal(u1, u2) and torch.equal(u1, u1b)
+    assert abs(i3["iters"] - i1["iters"]) <= 3     # overshoot is skipped on the device
+    assert rel(to_host(u3), to_host(u1)) <= 1e-12
+
+
 def test_errors(B):
     prob = fractional_problem(1, 15, 16, 0.5)
     s = B.Solver(prob)
