@@ -24,8 +24,9 @@
  *  - Errors: every call returns a bltt_status; nothing aborts, exits or traps.  A failed call
  *    leaves outputs unspecified; bltt_last_error(h) returns a message for the last failure on h.
  *  - Threads: a handle is not thread-safe; distinct handles may be used from distinct threads.
- *  - Sizes: N and every m[ax]+1 must be powers of two with 2 <= N <= 4096 and
- *    2 <= m[ax]+1 <= 4096; other sizes return BLTT_ERR_UNSUPPORTED.
+ *  - Sizes: N and every m[ax]+1 must be powers of two with 2 <= N <= 2048 and
+ *    2 <= m[ax]+1 <= 2048 (each FFT, of length 2N or 2(m+1), must fit one 4096-point tile);
+ *    other sizes return BLTT_ERR_UNSUPPORTED.
  */
 #ifndef BLTT_H
 #define BLTT_H

@@ -246,15 +246,28 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
   cudaMalloc(&run_count, sizeof(int));
   cudaMallocHost(&run_count_h, sizeof(int));
 
+  // one arena sized for the largest wave, reused by every wave
+  size_t arena_bytes = 0;
+  int max_ni = 0;
   for (const auto& wave : waves) {
-    const int ni = (int)wave.size();
-    // arena
     size_t bytes = 0;
     for (int i : wave) bytes += item_bytes(items[i]);
-    unsigned char* arena = nullptr;
-    if (cudaMalloc(&arena, bytes) != cudaSuccess) { result = BLTT_ERR_OOM; break; }
-    MinresDev* states = nullptr;
-    if (cudaMalloc(&states, sizeof(MinresDev) * ni) != cudaSuccess) { cudaFree(arena); result = BLTT_ERR_OOM; break; }
+    arena_bytes = std::max(arena_bytes, bytes);
+    max_ni = std::max(max_ni, (int)wave.size());
+  }
+  unsigned char* arena = nullptr;
+  MinresDev* states = nullptr;
+  if (cudaMalloc(&arena, arena_bytes) != cudaSuccess ||
+      cudaMalloc(&states, sizeof(MinresDev) * max_ni) != cudaSuccess) {
+    if (arena) cudaFree(arena);
+    cudaFree(run_count);
+    cudaFreeHost(run_count_h);
+    cleanup();
+    return BLTT_ERR_OOM;
+  }
+
+  for (const auto& wave : waves) {
+    const int ni = (int)wave.size();
     size_t off = 0;
     auto carve = [&](size_t nbytes) {
       unsigned char* p = arena + off;
@@ -451,8 +464,6 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
     for (void* p : dev_allocs) cudaFree(p);
-    cudaFree(states);
-    cudaFree(arena);
     if (e != cudaSuccess) { result = BLTT_ERR_CUDA; break; }
     for (int j = 0; j < ni; ++j) {
       const Item& it = items[wave[j]];
@@ -482,6 +493,8 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
   cudaEventElapsedTime(&ms, ev0, ev1);
   if (info)
     for (int i = 0; i < total_items; ++i) info[i].t_solve_ms = ms;
+  cudaFree(states);
+  cudaFree(arena);
   cudaFree(run_count);
   cudaFreeHost(run_count_h);
   cleanup();

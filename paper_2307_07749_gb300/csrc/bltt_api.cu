@@ -61,6 +61,7 @@ int ilog2i(long long v) { int l = 0; while ((1LL << l) < v) ++l; return l; }
 
 // ---------------------------------------------------------------------------------------------
 struct bltt_ctx {
+  struct Pending { const char* name; cudaEvent_t a, b; };
   int N = 0, d = 0, m[3] = {1, 1, 1};
   long long M = 0, n = 0;
   double h[3] = {1, 1, 1};
@@ -99,14 +100,16 @@ struct bltt_ctx {
   double2* pc_bhat64 = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   long long launches = 0;
-  // cached CUDA graph of the MINRES iterations and the key it was captured for
+  // cached CUDA graph of the MINRES iterations and the key it was captured for; when captured
+  // with profiling on, its event-record nodes (graph_prof) are read after every replay
   cudaGraphExec_t gexec = nullptr;
-  const void* gkey[12] = {nullptr};
+  const void* gkey[13] = {nullptr};
+  std::vector<Pending> graph_prof;
+  bool capturing = false;
   // per-launch profiling
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
-  struct Pending { const char* name; cudaEvent_t a, b; };
   std::vector<Pending> pending;
   struct Stat { long long launches = 0; double ms = 0; long long act = 0; double act_ms = 0; double max_ms = 0; };
   std::map<std::string, Stat> stats;
@@ -119,6 +122,7 @@ struct bltt_ctx {
     for (auto& e : ev) if (e) cudaEventDestroy(e);
     for (auto& e : ev_pool) cudaEventDestroy(e);
     if (gexec) cudaGraphExecDestroy(gexec);
+    for (auto& p : graph_prof) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   }
   bool stream_sync_ok = true;
 
@@ -395,6 +399,10 @@ const char* mv_name(const OpTables& op) {
 }
 
 cudaEvent_t prof_event(bltt_ctx* h) {
+  if (h->capturing) {
+    cudaEvent_t e;
+    return cudaEventCreate(&e) == cudaSuccess ? e : nullptr;
+  }
   if (h->ev_used == h->ev_pool.size()) {
     cudaEvent_t e;
     if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
@@ -404,19 +412,41 @@ cudaEvent_t prof_event(bltt_ctx* h) {
 }
 
 // record an event before a launch when profiling (returns null otherwise)
+// during stream capture an event must be recorded as an external node to be timed at replay
+void prof_record(bltt_ctx* h, cudaEvent_t e) {
+  if (h->capturing) cudaEventRecordWithFlags(e, h->stream, cudaEventRecordExternal);
+  else cudaEventRecord(e, h->stream);
+}
 cudaEvent_t prof_begin(bltt_ctx* h) {
   if (!h->prof) return nullptr;
   cudaEvent_t a = prof_event(h);
-  if (a) cudaEventRecord(a, h->stream);
+  if (a) prof_record(h, a);
   return a;
 }
 void prof_end(bltt_ctx* h, const char* name, cudaEvent_t a) {
   if (!h->prof || !a) return;
   cudaEvent_t b = prof_event(h);
   if (!b) return;
-  cudaEventRecord(b, h->stream);
+  prof_record(h, b);
   h->pending.push_back({name, a, b});
 }
+// accumulate the event pairs of the last graph replay (the caller has synchronised)
+void prof_harvest_graph(bltt_ctx* h) {
+  std::map<std::string, float> mx;
+  std::vector<float> ms(h->graph_prof.size(), -1.f);
+  for (size_t i = 0; i < h->graph_prof.size(); ++i)
+    if (cudaEventElapsedTime(&ms[i], h->graph_prof[i].a, h->graph_prof[i].b) != cudaSuccess) ms[i] = -1.f;
+  for (size_t i = 0; i < h->graph_prof.size(); ++i) {
+    if (ms[i] < 0.f) continue;
+    auto& st = h->stats[h->graph_prof[i].name];
+    st.launches += 1;
+    st.ms += ms[i];
+    st.max_ms = std::max(st.max_ms, (double)ms[i]);
+    if (ms[i] > 0.25 * st.max_ms) { st.act += 1; st.act_ms += ms[i]; }
+  }
+  (void)cudaGetLastError();   // a failed timing query must not surface at the next launch check
+}
+
 void prof_harvest(bltt_ctx* h) {
   if (h->pending.empty()) { h->ev_used = 0; return; }
   cudaStreamSynchronize(h->stream);
@@ -442,6 +472,7 @@ void prof_harvest(bltt_ctx* h) {
   }
   h->pending.clear();
   h->ev_used = 0;
+  (void)cudaGetLastError();
 }
 
 }  // namespace
@@ -477,10 +508,11 @@ bltt_status bltt_create(const bltt_blocks* blocks, int N, long long M, bltt_hand
     prodm *= sp.m[ax];
   }
   if (prodm != M) return fail(nullptr, BLTT_ERR_INVALID_ARG, "M != prod(m)");
-  if (!is_pow2(N) || N > 4096) return fail(nullptr, BLTT_ERR_UNSUPPORTED, "N must be a power of two <= 4096");
+  // every FFT must fit one tile: 2N (matvec) and 2(m+1) (DST) <= kCap points
+  if (!is_pow2(N) || 2 * N > kCap) return fail(nullptr, BLTT_ERR_UNSUPPORTED, "N must be a power of two <= 2048");
   for (int ax = 0; ax < sp.ndim; ++ax)
-    if (!is_pow2(sp.m[ax] + 1) || sp.m[ax] + 1 > 4096)
-      return fail(nullptr, BLTT_ERR_UNSUPPORTED, "m+1 must be a power of two <= 4096");
+    if (!is_pow2(sp.m[ax] + 1) || 2 * (sp.m[ax] + 1) > kCap)
+      return fail(nullptr, BLTT_ERR_UNSUPPORTED, "m+1 must be a power of two <= 2048");
   for (int k = 0; k < N; ++k)
     if (!std::isfinite(blocks->a[k]) || !std::isfinite(blocks->b[k]))
       return fail(nullptr, BLTT_ERR_NUMERIC, "non-finite block coefficient");
@@ -760,22 +792,29 @@ bltt_status bltt_minres_solve_ex(bltt_handle h, const double* f, double alpha, d
   // to their roles) and replayed; the legacy stream cannot be captured, profiling needs the
   // direct launches
   const int G = (sync_every + 1) & ~1;
-  const bool graph_mode = (st != nullptr) && !h->prof && !o.no_graph;
+  const bool graph_mode = (st != nullptr) && !o.no_graph;
   int issued = 0;
   if (graph_mode) {
-    const void* key[12] = {(const void*)(intptr_t)spectral, (const void*)(intptr_t)o.precision,
+    const void* key[13] = {(const void*)(intptr_t)spectral, (const void*)(intptr_t)o.precision,
                            (const void*)(intptr_t)op.mv_arith, (const void*)(intptr_t)none,
                            (const void*)(intptr_t)G, x, pt.g64, pt.g32, pt.gdf, pt.dinv, st,
-                           (const void*)(intptr_t)op.ntaps};
+                           (const void*)(intptr_t)op.ntaps, (const void*)(intptr_t)h->prof};
     if (!h->gexec || std::memcmp(key, h->gkey, sizeof key) != 0) {
       if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+      for (auto& p : h->graph_prof) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+      h->graph_prof.clear();
+      prof_harvest(h);                     // nothing of the capture may mix with earlier events
       cudaGraph_t g = nullptr;
       CK(h, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+      h->capturing = true;
       bltt_status cap = BLTT_OK;
       for (int i = 0; i < G && cap == BLTT_OK; ++i) {
         cap = issue_iteration(cur);
         rotate();
       }
+      h->capturing = false;
+      h->graph_prof.swap(h->pending);      // the event-record nodes of this graph
+      h->pending.clear();
       cudaError_t ce = cudaStreamEndCapture(st, &g);
       if (cap != BLTT_OK) { if (g) cudaGraphDestroy(g); return cap; }
       CK(h, ce, "end capture");
@@ -790,6 +829,7 @@ bltt_status bltt_minres_solve_ex(bltt_handle h, const double* f, double alpha, d
       issued += G;
       CK(h, cudaMemcpyAsync(sh, h->state, sizeof *sh, cudaMemcpyDeviceToHost, st), "state download");
       CK(h, cudaStreamSynchronize(st), "sync");
+      if (h->prof) prof_harvest_graph(h);
       if (sh->phase != PH_RUN || issued >= maxit) break;
     }
   } else {

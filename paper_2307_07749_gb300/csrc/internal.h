@@ -7,8 +7,8 @@
 
 namespace bltt {
 
-constexpr int kThreads = 512;      // threads of every FFT tile kernel
-constexpr int kCap = 8192;         // complex points per FFT tile (128 KB of FP64 smem)
+constexpr int kThreads = 256;      // threads of every FFT tile kernel
+constexpr int kCap = 4096;         // complex points per FFT tile (64 KB of FP64 smem)
 constexpr int kMaxPartials = 1 << 20;
 constexpr int kMaxCols = 256;     // real lines per FFT tile (column info kept in shared memory)
 

@@ -115,6 +115,11 @@ __device__ __forceinline__ int fast_div(int e, int m, float inv_m) {
 
 constexpr int kBatch = 4;   // independent global loads in flight per thread in the tile loaders
 
+// threads per tile block and complex points per tile, per arithmetic: 256 threads and 4096 points
+// (32 KB of FP32, 64 KB of FP64 / double-float shared memory) let two to four independent blocks
+// share an SM, so that one block's loads, stores and barriers overlap another block's arithmetic
+template <class A> struct TileCfg { static constexpr int NT = kThreads, CAP = kCap; };
+
 // ============================================================================================
 // DST-I along one spatial axis (Steps 1 and 3 of Sec. 5.1).  Two real lines x_a, x_b share one
 // complex FFT of length 2P (P = m+1) of their odd extensions [0, x, 0, -rev(x)]; then
@@ -126,6 +131,7 @@ __device__ __forceinline__ void dst_tile(long long nlines, int m, long long inne
                                          int N, long long M, const double* dot_with,
                                          double* partials, const typename A::V* __restrict__ tw,
                                          long long tile) {
+  constexpr int NT = TileCfg<A>::NT, CAP = TileCfg<A>::CAP;
   using V = typename A::V;
   __syncthreads();   // the previous tile of a persistent block may still read shared memory
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -134,7 +140,7 @@ __device__ __forceinline__ void dst_tile(long long nlines, int m, long long inne
   __shared__ long long s_in[kMaxCols], s_out[kMaxCols];
   const int L = 2 * P, NC = 1 << log2NC, W = 2 * NC;
   const long long g0 = tile * W;
-  for (int c = threadIdx.x; c < W; c += kThreads) {
+  for (int c = threadIdx.x; c < W; c += NT) {
     long long g = g0 + c;
     long long b = -1, o = -1;
     if (g < nlines) {
@@ -147,7 +153,7 @@ __device__ __forceinline__ void dst_tile(long long nlines, int m, long long inne
   }
   const int cmask = NC - 1;
   auto at = [&](int p, int cc) { return p * NC + (SWZ ? (cc ^ (p & cmask)) : cc); };
-  for (int e = threadIdx.x; e < 2 * NC; e += kThreads)
+  for (int e = threadIdx.x; e < 2 * NC; e += NT)
     buf[at((e & 1) ? P : 0, e >> 1)] = A::zero();
   __syncthreads();
   double c0, c1, c2;
@@ -155,12 +161,12 @@ __device__ __forceinline__ void dst_tile(long long nlines, int m, long long inne
   const bool contiguous = (inner == 1);
   const float inv_m = 1.0f / (float)m;
   const int total = m * W, log2W = log2NC + 1;
-  for (int e0 = threadIdx.x; e0 < total; e0 += kBatch * kThreads) {
+  for (int e0 = threadIdx.x; e0 < total; e0 += kBatch * NT) {
     double v[kBatch];
     int cs[kBatch], ps[kBatch];
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
-      const int e = e0 + u * kThreads;
+      const int e = e0 + u * NT;
       int c = 0, p = 0;
       if (contiguous) { c = fast_div(e, m, inv_m); p = e - c * m; }
       else { p = e >> log2W; c = e & (W - 1); }
@@ -173,7 +179,7 @@ __device__ __forceinline__ void dst_tile(long long nlines, int m, long long inne
     }
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
-      const int e = e0 + u * kThreads;
+      const int e = e0 + u * NT;
       if (e < total) {
         const int cc = cs[u] >> 1, comp = cs[u] & 1;
         A::put_pm(buf, at(ps[u] + 1, cc), at(L - 1 - ps[u], cc), comp, v[u]);
@@ -181,11 +187,11 @@ __device__ __forceinline__ void dst_tile(long long nlines, int m, long long inne
     }
   }
   __syncthreads();
-  fft_columns<A, kThreads, kCap, false, SWZ>(buf, L, log2L, log2NC, tw);
+  fft_columns<A, NT, CAP, false, SWZ>(buf, L, log2L, log2NC, tw);
   const typename A::Sc scale = A::make_sc(rsqrt((double)L));
   const typename A::Sc nscale = A::make_sc(-rsqrt((double)L));
   double acc = 0.0;
-  for (int e = threadIdx.x; e < total; e += kThreads) {
+  for (int e = threadIdx.x; e < total; e += NT) {
     int c, k;
     if (contiguous) { c = fast_div(e, m, inv_m); k = e - c * m; }
     else { k = e >> log2W; c = e & (W - 1); }
@@ -199,13 +205,13 @@ __device__ __forceinline__ void dst_tile(long long nlines, int m, long long inne
     }
   }
   if (partials) {
-    double s = block_sum<kThreads>(acc, red);
+    double s = block_sum<NT>(acc, red);
     if (threadIdx.x == 0) partials[tile] = s;
   }
 }
 
 template <class A, bool SWZ>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(TileCfg<A>::NT)
 k_dst(long long nlines, int m, long long inner, int P, int log2L, int log2NC, Combine cb,
       double* out, int flip, int N, long long M, const double* dot_with, double* partials,
       const typename A::V* __restrict__ tw, const int* phase, int want) {
@@ -261,10 +267,11 @@ template <class A, bool CONJ>
 __device__ __forceinline__ void tp_freq_mul(typename A::V* buf, const OpTables& op,
                                             const PrecTables& pt, int log2NC, long long g0,
                                             const double* s_mu) {
+  constexpr int NT = TileCfg<A>::NT, CAP = TileCfg<A>::CAP;
   using V = typename A::V;
   const int N = op.N, half = N >> 1, NC = 1 << log2NC;
   const int items = (half + 1) << log2NC;
-  for (int it = threadIdx.x; it < items; it += kThreads) {
+  for (int it = threadIdx.x; it < items; it += NT) {
     const int cc = it & (NC - 1), k = it >> log2NC;
     const long long ia = g0 + 2 * cc, ib = ia + 1;
     V Ga = A::zero(), Gb = A::zero();
@@ -286,6 +293,7 @@ __device__ __forceinline__ void timepass_tile(const OpTables& op, const PrecTabl
                                               const double* dot_with, double* partials,
                                               int log2NC, const typename A::V* __restrict__ tw,
                                               long long tile) {
+  constexpr int NT = TileCfg<A>::NT, CAP = TileCfg<A>::CAP;
   using V = typename A::V;
   __syncthreads();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -295,22 +303,22 @@ __device__ __forceinline__ void timepass_tile(const OpTables& op, const PrecTabl
   const int N = op.N, NC = 1 << log2NC, W = 2 * NC, log2W = log2NC + 1;
   const long long M = op.M;
   const long long g0 = tile * W;
-  for (int c = threadIdx.x; c < W; c += kThreads) s_mu[c] = (g0 + c < M) ? mode_mu(op, g0 + c) : 0.0;
+  for (int c = threadIdx.x; c < W; c += NT) s_mu[c] = (g0 + c < M) ? mode_mu(op, g0 + c) : 0.0;
   double c0, c1, c2;
   load_coef(cb, c0, c1, c2);
   const int total = N * W;
-  for (int e0 = threadIdx.x; e0 < total; e0 += kBatch * kThreads) {
+  for (int e0 = threadIdx.x; e0 < total; e0 += kBatch * NT) {
     double v[kBatch];
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
-      const int e = e0 + u * kThreads;
+      const int e = e0 + u * NT;
       const int p = e >> log2W, c = e & (W - 1);
       v[u] = 0.0;
       if (e < total && g0 + c < M) v[u] = combine_at(cb, (long long)p * M + g0 + c, c0, c1, c2);
     }
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
-      const int e = e0 + u * kThreads;
+      const int e = e0 + u * NT;
       if (e < total) {
         const int p = e >> log2W, c = e & (W - 1);
         A::put_sc(buf, p * NC + (c >> 1), c & 1, v[u], RowSc<A>::dinv(pt, p));
@@ -318,19 +326,19 @@ __device__ __forceinline__ void timepass_tile(const OpTables& op, const PrecTabl
     }
   }
   __syncthreads();
-  fft_columns<A, kThreads, kCap, false>(buf, N, op.log2N, log2NC, tw);
+  fft_columns<A, NT, CAP, false>(buf, N, op.log2N, log2NC, tw);
   tp_freq_mul<A, true>(buf, op, pt, log2NC, g0, s_mu);
   __syncthreads();
-  fft_columns<A, kThreads, kCap, true>(buf, N, op.log2N, log2NC, tw);
-  for (int e = threadIdx.x; e < N * NC; e += kThreads)
+  fft_columns<A, NT, CAP, true>(buf, N, op.log2N, log2NC, tw);
+  for (int e = threadIdx.x; e < N * NC; e += NT)
     buf[e] = A::scale_sc(buf[e], RowSc<A>::d2(pt, e >> log2NC));
   __syncthreads();
-  fft_columns<A, kThreads, kCap, false>(buf, N, op.log2N, log2NC, tw);
+  fft_columns<A, NT, CAP, false>(buf, N, op.log2N, log2NC, tw);
   tp_freq_mul<A, false>(buf, op, pt, log2NC, g0, s_mu);
   __syncthreads();
-  fft_columns<A, kThreads, kCap, true>(buf, N, op.log2N, log2NC, tw);
+  fft_columns<A, NT, CAP, true>(buf, N, op.log2N, log2NC, tw);
   double acc = 0.0;
-  for (int e = threadIdx.x; e < total; e += kThreads) {
+  for (int e = threadIdx.x; e < total; e += NT) {
     const int p = e >> log2W, c = e & (W - 1);
     if (g0 + c < M) {
       const long long idx = (long long)p * M + g0 + c;
@@ -340,13 +348,13 @@ __device__ __forceinline__ void timepass_tile(const OpTables& op, const PrecTabl
     }
   }
   if (partials) {
-    double s = block_sum<kThreads>(acc, red);
+    double s = block_sum<NT>(acc, red);
     if (threadIdx.x == 0) partials[tile] = s;
   }
 }
 
 template <class A>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(TileCfg<A>::NT)
 k_timepass(OpTables op, PrecTables pt, Combine cb, double* out, const double* dot_with,
            double* partials, const int* phase, int want, int log2NC,
            const typename A::V* __restrict__ tw) {
@@ -418,6 +426,7 @@ __device__ __forceinline__ void conv_tile(const OpTables& op, int spectral, int 
                                           int flip, int mode, const double* rhs,
                                           double* partials, const double* st_src, int log2NC,
                                           long long tile) {
+  constexpr int NT = TileCfg<A>::NT, CAP = TileCfg<A>::CAP;
   using V = typename A::V;
   __syncthreads();
   using MT = typename MuT<A>::t;
@@ -432,7 +441,7 @@ __device__ __forceinline__ void conv_tile(const OpTables& op, int spectral, int 
   const double s = xscale ? *xscale : 1.0;
   const bool genb = (op.b_kind == 1);
   const bool extra_st = !spectral && which == 0 && st_src != nullptr;
-  for (int c = threadIdx.x; c < W; c += kThreads) {
+  for (int c = threadIdx.x; c < W; c += NT) {
     const long long i = g0 + c;
     double mu = 0.0;
     int nb = 0;
@@ -453,17 +462,17 @@ __device__ __forceinline__ void conv_tile(const OpTables& op, int spectral, int 
   const typename A::Sc ssc = A::make_sc(s);
   const bool odd = ((op.log2N + 1) & 1) != 0;
   const int total = N * W;
-  for (int e0 = threadIdx.x; e0 < total; e0 += kBatch * kThreads) {
+  for (int e0 = threadIdx.x; e0 < total; e0 += kBatch * NT) {
     double v[kBatch];
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
-      const int e = e0 + u * kThreads;
+      const int e = e0 + u * NT;
       const int p = e >> log2W, c = e & (W - 1);
       v[u] = (e < total && g0 + c < M) ? x[(long long)p * M + g0 + c] : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
-      const int e = e0 + u * kThreads;
+      const int e = e0 + u * NT;
       if (e < total) {
         const int p = e >> log2W, c = e & (W - 1);
         if (odd) {
@@ -477,13 +486,13 @@ __device__ __forceinline__ void conv_tile(const OpTables& op, int spectral, int 
     }
   }
   if (!odd)
-    for (int e = threadIdx.x; e < N * NC; e += kThreads) buf[N * NC + e] = A::zero();
+    for (int e = threadIdx.x; e < N * NC; e += NT) buf[N * NC + e] = A::zero();
   __syncthreads();
   const V* __restrict__ tw = ConvTables<A>::tw(op);
-  fft_columns<A, kThreads, kCap, false>(buf, L, op.log2N + 1, log2NC, tw, odd);
+  fft_columns<A, NT, CAP, false>(buf, L, op.log2N + 1, log2NC, tw, odd);
   if (!spectral) {
     const V* __restrict__ H = ConvTables<A>::H(op, which);
-    for (int e = threadIdx.x; e < L * NC; e += kThreads) {
+    for (int e = threadIdx.x; e < L * NC; e += NT) {
       const int k = e >> log2NC;
       const V h = (k <= N) ? H[k] : A::conj(H[L - k]);
       buf[e] = A::mul(buf[e], h);
@@ -493,7 +502,7 @@ __device__ __forceinline__ void conv_tile(const OpTables& op, int spectral, int 
     const V* __restrict__ HA = ConvTables<A>::H(op, 0);
     const V* __restrict__ HB = ConvTables<A>::H(op, 1);
     const int items = (N + 1) << log2NC;
-    for (int it = threadIdx.x; it < items; it += kThreads) {
+    for (int it = threadIdx.x; it < items; it += NT) {
       const int cc = it & (NC - 1), k = it >> log2NC;
       const V a_ = HA[k], b_ = HB[k];
       const V Ha = ConvTables<A>::Hmode(a_, b_, s_mu[2 * cc], genb);
@@ -507,11 +516,11 @@ __device__ __forceinline__ void conv_tile(const OpTables& op, int spectral, int 
     }
   }
   __syncthreads();
-  fft_columns<A, kThreads, kCap, true>(buf, L, op.log2N + 1, log2NC, tw);
+  fft_columns<A, NT, CAP, true>(buf, L, op.log2N + 1, log2NC, tw);
   double acc = 0.0;
   const double st_coef = (op.b_kind == 0) ? op.b0 * s : 1.0;
   const long long s1 = op.m[0], s2 = (long long)op.m[0] * op.m[1];
-  for (int e = threadIdx.x; e < total; e += kThreads) {
+  for (int e = threadIdx.x; e < total; e += NT) {
     const int t = e >> log2W, c = e & (W - 1);
     const long long i = g0 + c;
     if (i >= M) continue;
@@ -550,13 +559,13 @@ __device__ __forceinline__ void conv_tile(const OpTables& op, int spectral, int 
     }
   }
   if (partials) {
-    double sum = block_sum<kThreads>(acc, red);
+    double sum = block_sum<NT>(acc, red);
     if (threadIdx.x == 0) partials[tile] = (mode == MV_STORE) ? sum * s : sum;
   }
 }
 
 template <class A>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(TileCfg<A>::NT)
 k_conv(OpTables op, int spectral, int which, const double* x, const double* xscale, double* y,
        int flip, int mode, const double* rhs, double* partials, const int* phase, int want,
        const double* st_src, int log2NC) {
@@ -834,8 +843,8 @@ static int grid_stream(long long n, int threads) {
 template <class A> static cudaError_t ensure_smem_dst() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = set_smem(k_dst<A, false>, kCap * sizeof(typename A::V));
-  if (e == cudaSuccess) e = set_smem(k_dst<A, true>, kCap * sizeof(typename A::V));
+  cudaError_t e = set_smem(k_dst<A, false>, TileCfg<A>::CAP * sizeof(typename A::V));
+  if (e == cudaSuccess) e = set_smem(k_dst<A, true>, TileCfg<A>::CAP * sizeof(typename A::V));
   if (e == cudaSuccess) done = true;
   return e;
 }
@@ -845,25 +854,25 @@ static void run_dst(const OpTables& op, long long grid, long long nlines, int m,
                     int P, int L, int log2NC, const Combine& in, double* out, int flip,
                     const double* dot_with, double* partials, const typename A::V* tw,
                     const int* phase, cudaStream_t st) {
-  const size_t smem = kCap * sizeof(typename A::V);
+  const size_t smem = TileCfg<A>::CAP * sizeof(typename A::V);
   if (inner == 1)
-    k_dst<A, true><<<(unsigned)grid, kThreads, smem, st>>>(nlines, m, inner, P, ilog2(L), log2NC,
+    k_dst<A, true><<<(unsigned)grid, TileCfg<A>::NT, smem, st>>>(nlines, m, inner, P, ilog2(L), log2NC,
         in, out, flip, op.N, op.M, dot_with, partials, tw, phase, PH_RUN);
   else
-    k_dst<A, false><<<(unsigned)grid, kThreads, smem, st>>>(nlines, m, inner, P, ilog2(L), log2NC,
+    k_dst<A, false><<<(unsigned)grid, TileCfg<A>::NT, smem, st>>>(nlines, m, inner, P, ilog2(L), log2NC,
         in, out, flip, op.N, op.M, dot_with, partials, tw, phase, PH_RUN);
 }
 template <class A> static cudaError_t ensure_smem_tp() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = set_smem(k_timepass<A>, kCap * sizeof(typename A::V));
+  cudaError_t e = set_smem(k_timepass<A>, TileCfg<A>::CAP * sizeof(typename A::V));
   if (e == cudaSuccess) done = true;
   return e;
 }
 template <class A> static cudaError_t ensure_smem_conv() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = set_smem(k_conv<A>, kCap * sizeof(typename A::V));
+  cudaError_t e = set_smem(k_conv<A>, TileCfg<A>::CAP * sizeof(typename A::V));
   if (e == cudaSuccess) done = true;
   return e;
 }
@@ -888,6 +897,7 @@ cudaError_t launch_dst(const OpTables& op, int axis, int prec, const Combine& in
   for (int a = 0; a < axis; ++a) inner *= op.m[a];
   const long long nlines = (long long)op.N * op.M / m;
   const int P = m + 1, L = 2 * P;
+  if (L > kCap) return cudaErrorInvalidValue;      // the FFT must fit one tile
   const int NC = tile_columns(nlines, L);
   const int log2NC = ilog2(NC);
   const long long grid = (nlines + 2 * NC - 1) / (2 * NC);
@@ -919,6 +929,7 @@ cudaError_t launch_timepass(const OpTables& op, const PrecTables& pt, int prec, 
     k_precond_identity<<<g, 256, 0, st>>>(in, out, n, dot_with, partials, phase, PH_RUN);
     return cudaGetLastError();
   }
+  if (op.N > kCap) return cudaErrorInvalidValue;   // the FFT must fit one tile
   const int NC = tile_columns(op.M, op.N);
   const int log2NC = ilog2(NC);
   const long long grid = (op.M + 2 * NC - 1) / (2 * NC);
@@ -947,6 +958,7 @@ static cudaError_t launch_conv_t(const OpTables& op, int spectral, const double*
                                  const double* xscale, double* y, int flip, int mode,
                                  const double* rhs, double* partials, int* nparts,
                                  const int* phase, int want, double* tmp, cudaStream_t st) {
+  if (2 * op.N > kCap) return cudaErrorInvalidValue;   // the FFT must fit one tile
   cudaError_t e = ensure_smem_conv<A>();
   if (e != cudaSuccess) return e;
   const int NC = tile_columns(op.M, 2 * op.N);
@@ -1048,7 +1060,7 @@ __device__ __forceinline__ int find_item(const long long* prefix, int nitems, lo
 }
 
 template <class A>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(TileCfg<A>::NT)
 k_conv_multi(const ConvItem* __restrict__ items, const long long* __restrict__ prefix, int nitems,
              long long total) {
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
@@ -1061,7 +1073,7 @@ k_conv_multi(const ConvItem* __restrict__ items, const long long* __restrict__ p
 }
 
 template <class A>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(TileCfg<A>::NT)
 k_timepass_multi(const TpItem* __restrict__ items, const long long* __restrict__ prefix,
                  int nitems, long long total) {
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
@@ -1078,7 +1090,7 @@ k_timepass_multi(const TpItem* __restrict__ items, const long long* __restrict__
 }
 
 template <class A>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(TileCfg<A>::NT)
 k_dst_multi(const DstItem* __restrict__ items, const long long* __restrict__ prefix, int nitems,
             long long total) {
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {

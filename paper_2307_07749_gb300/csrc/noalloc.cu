@@ -123,9 +123,7 @@ extern "C" bltt_status bltt_residual_noalloc(const bltt_blocks* blocks, int N, l
     prodm *= sp.m[ax];
   }
   if (prodm != M) return na_fail(BLTT_ERR_INVALID_ARG, "M != prod(m)");
-  if (!pow2(N) || N > 4096) return na_fail(BLTT_ERR_UNSUPPORTED, "N must be a power of two <= 4096");
-  for (int ax = 0; ax < sp.ndim; ++ax)
-    if (sp.m[ax] + 1 > 4096) return na_fail(BLTT_ERR_UNSUPPORTED, "m+1 must be <= 4096");
+  if (!pow2(N) || 2 * N > kCap) return na_fail(BLTT_ERR_UNSUPPORTED, "N must be a power of two <= 2048");
   if (r_dev && (r_dev == u_dev || r_dev == f_dev))
     return na_fail(BLTT_ERR_INVALID_ARG, "r must not alias u or f");
 

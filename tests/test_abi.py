@@ -60,6 +60,9 @@ def test_host_validation(lib):
     b = p.b.copy()
     b[1] = -2.0
     assert _create(p.a, b, 8, 1, (7,), (0.125,)) == 2
+    # beyond the largest FFT a tile holds (N = 4096, m + 1 = 4096)
+    assert _create(np.r_[1.0, np.zeros(4095)], np.r_[1.0, np.zeros(4095)], 4096, 1, (7,), (0.125,)) == 8
+    assert _create(p.a, p.b, 8, 1, (4095,), (1 / 4096,)) == 8
     # non-finite coefficient
     a = p.a.copy()
     a[3] = np.nan
