@@ -296,6 +296,33 @@ def run_reference(args):
     return 0
 
 
+FORMS = {
+    "chosen": dict(alpha=ALPHA_F32, precision=32, basis=1, arith=2),
+    "plain_f64": dict(alpha=ALPHA_F64, precision=64, basis=1, arith=1),
+    "f32x2_all": dict(alpha=ALPHA_F64, precision=96, basis=1, arith=2),
+    "f32_physical": dict(alpha=ALPHA_F32, precision=32, basis=2, arith=2),
+}
+
+
+def run_once(args):
+    """One solve of the headline workload in one form, direct launches (for ncu captures)."""
+    import torch
+    from paper_2307_07749_gb300 import build
+    build.build()
+    import paper_2307_07749_gb300 as B
+    from workloads import workload, rhs_uniform
+    prob, _ = workload(WORKLOAD)
+    s = B.Solver(prob)
+    fd = torch.from_numpy(rhs_uniform(prob.n, 2)).cuda()
+    fm = FORMS[args.form]
+    u, info = s.solve(fd, alpha=fm["alpha"], tol=TOL, maxit=100, precision=fm["precision"],
+                      basis=fm["basis"], matvec_arith=fm["arith"], graph=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": WORKLOAD, "form": args.form, "iters": info["iters"],
+                      "status": info["status"], "relres_true": info["relres_true"]}))
+    return 0 if info["status"] == 0 else 1
+
+
 def run_batched(args):
     """96 L1 fractional systems of uneven N and M with 4 right-hand sides each (8.75 G unknowns
     in all), solved by one bltt_solve_batched call, against the same items solved one by one.
@@ -415,8 +442,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="frac2d", choices=["frac2d", "batched", "alpha"],
-                    help="frac2d: the headline line; batched / alpha: supplementary reports")
+    ap.add_argument("--workload", default="frac2d", choices=["frac2d", "batched", "alpha", "once"],
+                    help="frac2d: the headline line; batched / alpha: supplementary reports; "
+                         "once: a single solve of the headline workload (for ncu captures)")
+    ap.add_argument("--form", default="chosen", choices=["chosen", "plain_f64", "f32x2_all", "f32_physical"])
     ap.add_argument("--alpha-train", type=int, default=2000)
     ap.add_argument("--alpha-heldout", type=int, default=256)
     args = ap.parse_args()
@@ -426,6 +455,8 @@ def main():
         return run_batched(args)
     if args.workload == "alpha":
         return run_alpha(args)
+    if args.workload == "once":
+        return run_once(args)
     args.warmup = max(args.warmup, 3)
 
     rank, local, ws = dist_init()
