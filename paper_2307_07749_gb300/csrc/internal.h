@@ -22,6 +22,7 @@ struct MinresDev {
   double coef[3];        // v_{j+1} = coef0 q + coef1 v_j + coef2 v_{j-1}
   double w_inv_gamma;    // 1/gamma_j for the w update of iteration j
   double w_a1inv, w_a2, w_a3, w_ceta;
+  double w_cz, w_cwp, w_cw;   // w_{j+1} = w_cz z_j + w_cwp w_{j-1} + w_cw w_j (folded coefficients)
   double normb, relres_est, relres_true, tol;
   double gamma_new;
   int iter, maxit, phase, status, wpending, pad;

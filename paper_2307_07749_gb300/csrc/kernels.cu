@@ -22,13 +22,21 @@ __device__ __forceinline__ void load_coef(const Combine& cb, double& c0, double&
 }
 
 // v = in0[e] + c1 in1[e] + c2 in2[e] (FP64); optionally stored to vout[e] (vout may alias
-// in1/in2: the same thread reads before it writes).
+// in1/in2: the same thread reads before it writes).  When v is stored, the inputs are streamed
+// (evict-first) so that v itself is more likely to stay in L2 for the dot product at the end of
+// the tile.
 __device__ __forceinline__ double combine_at(const Combine& cb, long long e, double, double c1,
                                              double c2) {
-  double v = cb.in0[e];
-  if (cb.in1) v = fma(c1, cb.in1[e], v);
-  if (cb.in2) v = fma(c2, cb.in2[e], v);
-  if (cb.vout) cb.vout[e] = v;
+  if (!cb.vout) {
+    double v = cb.in0[e];
+    if (cb.in1) v = fma(c1, cb.in1[e], v);
+    if (cb.in2) v = fma(c2, cb.in2[e], v);
+    return v;
+  }
+  double v = __ldcs(cb.in0 + e);
+  if (cb.in1) v = fma(c1, __ldcs(cb.in1 + e), v);
+  if (cb.in2) v = fma(c2, __ldcs(cb.in2 + e), v);
+  cb.vout[e] = v;
   return v;
 }
 
@@ -113,7 +121,7 @@ __device__ __forceinline__ int fast_div(int e, int m, float inv_m) {
   return c;
 }
 
-constexpr int kBatch = 4;   // independent global loads in flight per thread in the tile loaders
+constexpr int kBatch = 8;   // independent global loads in flight per thread in the tile loaders
 
 // threads per tile block and complex points per tile, per arithmetic: 256 threads and 4096 points
 // (32 KB of FP32, 64 KB of FP64 / double-float shared memory) let two to four independent blocks
@@ -763,6 +771,9 @@ __device__ __forceinline__ void scalar_gamma(MinresDev* st, const double* p, int
   st->w_a2 = a2;
   st->w_a3 = a3;
   st->w_ceta = cn * st->eta;
+  st->w_cz = st->inv_gamma / a1;
+  st->w_cwp = -a3 / a1;
+  st->w_cw = -a2 / a1;
   st->eta = -sn * st->eta;
   st->gamma_prev = gamma;
   st->gamma = gn;
@@ -809,19 +820,29 @@ __global__ void __launch_bounds__(256) k_scalar_check(MinresDev* st, const doubl
   scalar_check(st, p, np);
 }
 
-// w_{j+1} = (z_j - a3 w_{j-1} - a2 w_j)/a1 (written over w_{j-1}); x += c_{j+1} eta w_{j+1}
+// w_{j+1} = (z_j - a3 w_{j-1} - a2 w_j)/a1 (written over w_{j-1}); x += c_{j+1} eta w_{j+1}.
+// The coefficients are folded (w_cz = 1/(gamma_j a1), ...) so that each element costs four FP64
+// operations: GB300 runs FP64 at 1/64 of its FP32 rate and this kernel is bound by that pipe.
+__device__ __forceinline__ void w_update_elem(const double* __restrict__ z, double* w_prev,
+                                              const double* __restrict__ w, double* x, long long e,
+                                              double cz, double cwp, double cw, double ce) {
+  const double wn = fma(cz, __ldcs(z + e), fma(cwp, __ldcs(w_prev + e), cw * __ldcs(w + e)));
+  __stcs(w_prev + e, wn);
+  __stcs(x + e, fma(ce, wn, __ldcs(x + e)));
+}
+
 __global__ void __launch_bounds__(256) k_w_update(const MinresDev* st, const double* z,
                                                   double* w_prev, const double* w, double* x,
                                                   long long n) {
   if (!st->wpending) return;
-  const double ig = st->w_inv_gamma, a1i = st->w_a1inv, a2 = st->w_a2, a3 = st->w_a3,
-               ce = st->w_ceta;
+  const double cz = st->w_cz, cwp = st->w_cwp, cw = st->w_cw, ce = st->w_ceta;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += stride) {
-    const double wn = (z[e] * ig - a3 * w_prev[e] - a2 * w[e]) * a1i;
-    w_prev[e] = wn;
-    x[e] = fma(ce, wn, x[e]);
+  long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; e + 3 * stride < n; e += 4 * stride) {          // four independent elements in flight
+#pragma unroll
+    for (int u = 0; u < 4; ++u) w_update_elem(z, w_prev, w, x, e + u * stride, cz, cwp, cw, ce);
   }
+  for (; e < n; e += stride) w_update_elem(z, w_prev, w, x, e, cz, cwp, cw, ce);
 }
 
 __global__ void __launch_bounds__(256) k_sum_partials(const double* p, int np, double* out) {
@@ -1111,14 +1132,10 @@ __global__ void __launch_bounds__(256) k_w_update_multi(const VecItem* __restric
   const VecItem& vi = items[blockIdx.y];
   if (!vi.st->wpending) return;
   const MinresDev* st = vi.st;
-  const double ig = st->w_inv_gamma, a1i = st->w_a1inv, a2 = st->w_a2, a3 = st->w_a3,
-               ce = st->w_ceta;
+  const double cz = st->w_cz, cwp = st->w_cwp, cw = st->w_cw, ce = st->w_ceta;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < vi.n;
-       e += (long long)gridDim.x * blockDim.x) {
-    const double wn = (vi.z[e] * ig - a3 * vi.w_prev[e] - a2 * vi.w[e]) * a1i;
-    vi.w_prev[e] = wn;
-    vi.x[e] = fma(ce, wn, vi.x[e]);
-  }
+       e += (long long)gridDim.x * blockDim.x)
+    w_update_elem(vi.z, vi.w_prev, vi.w, vi.x, e, cz, cwp, cw, ce);
 }
 
 __global__ void __launch_bounds__(256) k_scalar_multi(int which, const ScalItem* __restrict__ items) {
