@@ -89,7 +89,6 @@ struct bltt_ctx {
   float2* pc_dinv_df = nullptr;
   float2* pc_d2_df = nullptr;
   float4* pc_gdf = nullptr;
-  float2* pc_g32 = nullptr;
   float4* pc_ahatdf = nullptr;
   float4* pc_bhatdf = nullptr;
   bool pc_hasdf = false;
@@ -288,15 +287,8 @@ bltt_status prepare_precond(bltt_ctx* h, double alpha, int prec) {
     CK(h, cudaStreamSynchronize(h->stream), "sync after table upload");
     h->pc_alpha = alpha;
   }
-  if (prec == PREC_F32 && !h->pc_has32) {
-    if (!h->pc_g32) CK(h, h->alloc(&h->pc_g32, (size_t)(N / 2 + 1) * h->M), "alloc g32 table");
-    cudaEvent_t pa = prof_begin(h);
-    CK(h, launch_setup_g32(h->op, h->pc_ahat32, h->pc_bhat32, nullptr, nullptr, h->pc_g32, nullptr,
-                           h->stream), "setup g32");
-    prof_end(h, "setup_g", pa);
-    h->launches++;
-    h->pc_has32 = true;
-  }
+  // the FP32 time pass evaluates lambda^{-1/2} from ahat32 and bhat32 where it needs it: no table
+  if (prec == PREC_F32) h->pc_has32 = true;
   if (prec == PREC_F64 && !h->pc_has64) {
     if (!h->pc_g64) CK(h, h->alloc(&h->pc_g64, (size_t)(N / 2 + 1) * h->M), "alloc g64 table");
     cudaEvent_t pa = prof_begin(h);
@@ -308,7 +300,7 @@ bltt_status prepare_precond(bltt_ctx* h, double alpha, int prec) {
   if (prec == PREC_DF && !h->pc_hasdf) {
     if (!h->pc_gdf) CK(h, h->alloc(&h->pc_gdf, (size_t)(N / 2 + 1) * h->M), "alloc gdf table");
     cudaEvent_t pa = prof_begin(h);
-    CK(h, launch_setup_g32(h->op, h->pc_ahat32, h->pc_bhat32, h->pc_ahatdf, h->pc_bhatdf, nullptr,
+    CK(h, launch_setup_gdf(h->op, h->pc_ahat32, h->pc_bhat32, h->pc_ahatdf, h->pc_bhatdf,
                            h->pc_gdf, h->stream), "setup gdf");
     prof_end(h, "setup_g", pa);
     h->launches++;
@@ -327,7 +319,6 @@ PrecTables prec_tables(bltt_ctx* h, int none) {
   pt.dinv_df = h->pc_dinv_df;
   pt.d2_df = h->pc_d2_df;
   pt.gdf = h->pc_gdf;
-  pt.g32 = h->pc_g32;
   pt.g64 = h->pc_g64;
   pt.ahat32 = h->pc_ahat32;
   pt.bhat32 = h->pc_bhat32;
@@ -797,7 +788,7 @@ bltt_status bltt_minres_solve_ex(bltt_handle h, const double* f, double alpha, d
   if (graph_mode) {
     const void* key[13] = {(const void*)(intptr_t)spectral, (const void*)(intptr_t)o.precision,
                            (const void*)(intptr_t)op.mv_arith, (const void*)(intptr_t)none,
-                           (const void*)(intptr_t)G, x, pt.g64, pt.g32, pt.gdf, pt.dinv, st,
+                           (const void*)(intptr_t)G, x, pt.g64, pt.ahat32, pt.gdf, pt.dinv, st,
                            (const void*)(intptr_t)op.ntaps, (const void*)(intptr_t)h->prof};
     if (!h->gexec || std::memcmp(key, h->gkey, sizeof key) != 0) {
       if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }

@@ -100,6 +100,10 @@ struct ArithD {
   static __device__ __forceinline__ V scale(V a, double s) { return make_double2(a.x * s, a.y * s); }
   static __device__ __forceinline__ V zero() { return make_double2(0.0, 0.0); }
   static __device__ __forceinline__ V from(double re, double im) { return make_double2(re, im); }
+  // a compile-time constant given in FP64 and as FP32 leading + trailing parts
+  static __device__ __forceinline__ V cst(double re, double im, float, float, float, float) {
+    return make_double2(re, im);
+  }
   static __device__ __forceinline__ double part(V a, int comp) { return comp ? a.y : a.x; }
   static __device__ __forceinline__ void put(V* buf, int idx, int comp, double x) {
     reinterpret_cast<double*>(buf)[2 * idx + comp] = x;
@@ -139,6 +143,9 @@ struct ArithF {
   }
   static __device__ __forceinline__ V zero() { return make_float2(0.f, 0.f); }
   static __device__ __forceinline__ V from(double re, double im) { return make_float2((float)re, (float)im); }
+  static __device__ __forceinline__ V cst(double, double, float rh, float, float ih, float) {
+    return make_float2(rh, ih);
+  }
   static __device__ __forceinline__ double part(V a, int comp) { return f2d_bits(comp ? a.y : a.x); }
   static __device__ __forceinline__ void put(V* buf, int idx, int comp, double x) {
     reinterpret_cast<float*>(buf)[2 * idx + comp] = d2f_bits(x);
@@ -187,6 +194,9 @@ struct ArithDF {
     return pack(df_mul(re(a), f), df_mul(im(a), f));
   }
   static __device__ __forceinline__ V zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  static __device__ __forceinline__ V cst(double, double, float rh, float rl, float ih, float il) {
+    return make_float4(rh, rl, ih, il);
+  }
   static __device__ __forceinline__ V from(double r, double i) { return pack(df_from(r), df_from(i)); }
   static __device__ __forceinline__ double part(V a, int comp) {
     return comp ? df_to(im(a)) : df_to(re(a));
@@ -203,63 +213,128 @@ struct ArithDF {
 };
 
 // ------------------------------------------------------------------------------------------
-// Shared-memory Stockham FFT (self-sorting; radix 4 with one radix-2 pass when log2 L is odd).
+// Radix-16 butterfly.  With r = b + 4c and q = c' + 4d (b, c, c', d < 4),
+//   X_q = sum_b w4^{b d} w16^{b c'} sum_c w4^{c c'} x_{b+4c},
+// i.e. four length-4 DFTs over c, the constant twiddles w16^{b c'}, and four length-4 DFTs over
+// b.  w16 = exp(-2 pi i / 16) (forward) or its conjugate (INV).
+
+// cos(pi/8), sin(pi/8) and sqrt(1/2): FP64 values and FP32 leading + trailing parts
+struct K16 {
+  static constexpr double C = 0.92387953251128674, S = 0.38268343236508978,
+                          Q = 0.70710678118654752;
+  static constexpr float Ch = 0x1.d906bcp-1f, Cl = 0x1.e651a8p-26f;
+  static constexpr float Sh = 0x1.87de2ap-2f, Sl = 0x1.abaa58p-28f;
+  static constexpr float Qh = 0x1.6a09e6p-1f, Ql = 0x1.9fcef4p-27f;
+};
+
+// w16^E for the exponents E in {1, 2, 3, 6, 9} that the butterfly needs (E = 4 is a rotation)
+template <class A, int E, bool INV>
+__device__ __forceinline__ typename A::V w16() {
+  constexpr float g = INV ? -1.f : 1.f;   // sign of -Im
+  using K = K16;
+  if constexpr (E == 1) return A::cst(K::C, -g * K::S, K::Ch, K::Cl, -g * K::Sh, -g * K::Sl);
+  else if constexpr (E == 2) return A::cst(K::Q, -g * K::Q, K::Qh, K::Ql, -g * K::Qh, -g * K::Ql);
+  else if constexpr (E == 3) return A::cst(K::S, -g * K::C, K::Sh, K::Sl, -g * K::Ch, -g * K::Cl);
+  else if constexpr (E == 6) return A::cst(-K::Q, -g * K::Q, -K::Qh, -K::Ql, -g * K::Qh, -g * K::Ql);
+  else return A::cst(-K::C, g * K::S, -K::Ch, -K::Cl, g * K::Sh, g * K::Sl);   // E == 9
+}
+
+template <class A, bool INV>
+__device__ __forceinline__ void dft4(typename A::V& x0, typename A::V& x1, typename A::V& x2,
+                                     typename A::V& x3) {
+  using V = typename A::V;
+  const V t0 = A::add(x0, x2), t1 = A::sub(x0, x2), t2 = A::add(x1, x3);
+  const V t3 = A::template rot<INV>(A::sub(x1, x3));
+  x0 = A::add(t0, t2);
+  x1 = A::add(t1, t3);
+  x2 = A::sub(t0, t2);
+  x3 = A::sub(t1, t3);
+}
+
+// in place; on return X_{c' + 4d} is in v[4c' + d]
+template <class A, bool INV>
+__device__ __forceinline__ void dft16(typename A::V (&v)[16]) {
+#pragma unroll
+  for (int b = 0; b < 4; ++b) dft4<A, INV>(v[b], v[b + 4], v[b + 8], v[b + 12]);
+  v[5] = A::mul(v[5], w16<A, 1, INV>());
+  v[6] = A::mul(v[6], w16<A, 2, INV>());
+  v[7] = A::mul(v[7], w16<A, 3, INV>());
+  v[9] = A::mul(v[9], w16<A, 2, INV>());
+  v[10] = A::template rot<INV>(v[10]);
+  v[11] = A::mul(v[11], w16<A, 6, INV>());
+  v[13] = A::mul(v[13], w16<A, 3, INV>());
+  v[14] = A::mul(v[14], w16<A, 6, INV>());
+  v[15] = A::mul(v[15], w16<A, 9, INV>());
+#pragma unroll
+  for (int c = 0; c < 4; ++c) dft4<A, INV>(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+}
+
+// ------------------------------------------------------------------------------------------
+// Shared-memory Stockham FFT (self-sorting, mixed radix).  The passes are: radix 2 when log2 L
+// is odd, radix 4 when the remaining exponent is 2 mod 4, then radix 16.  Running the short
+// passes first keeps every radix-16 pass at Ns >= 4, where its stores stay bank-conflict-free.
 //
 // buf holds NC = 2^log2NC independent complex columns of length L, element (p, c) at
 // buf[p * NC + c] (or at buf[p * NC + (c ^ (p mod NC))] with SWZ).  tw holds
 // w_L^k = exp(-2 pi i k / L), k < L.  skip_radix2: the caller has already applied the first
-// radix-2 pass (used when the upper half of the input is zero: the pass only duplicates).  Forward: X_k = sum_j x_j w^{jk};
-// inverse (INV): conjugate twiddles, no 1/L scaling.  Every pass loads all of its butterfly
-// inputs into registers, synchronises, then writes, so the transform runs in place.
-// CAP bounds NC * L; the block has NT threads.
+// radix-2 pass (used when the upper half of the input is zero: the pass only duplicates).
+// Forward: X_k = sum_j x_j w^{jk}; inverse (INV): conjugate twiddles, no 1/L scaling.  Every
+// pass loads all of its butterfly inputs into registers, synchronises, then writes, so the
+// transform runs in place.  CAP bounds NC * L; the block has NT threads.
+//
+// A pass of radix R with Ns outputs already combined: butterfly j (of L/R) reads x_{j + r L/R},
+// multiplies input r by w_L^{r k L/(R Ns)} (k = j mod Ns), transforms, and writes output q at
+// (j - k) R + k + q Ns.
 template <class A, int NT, int CAP, bool INV, bool SWZ = false>
-__device__ void fft_columns(typename A::V* buf, int L, int log2L, int log2NC,
+__device__ __forceinline__ void fft_columns(typename A::V* buf, int L, int log2L, int log2NC,
                             const typename A::V* __restrict__ tw, bool skip_radix2 = false) {
   using V = typename A::V;
-  constexpr int IPT4 = (CAP / 4 + NT - 1) / NT;   // radix-4 butterflies per thread
+  constexpr int IPT2 = (CAP / 2 + NT - 1) / NT;
+  constexpr int IPT4 = (CAP / 4 + NT - 1) / NT;
+  constexpr int IPT16 = (CAP / 16 + NT - 1) / NT;
   const int tid = threadIdx.x;
   const int NC = 1 << log2NC, cmask = NC - 1;
-  // element (p, c) lives at p * NC + (c ^ (p & cmask)) when SWZ (bank-conflict-free column walks)
   auto at = [&](int p, int c) { return (p << log2NC) + (SWZ ? (c ^ (p & cmask)) : c); };
-  int Ns = 1;
+  int log2Ns = 0;
   if (log2L & 1) {
     if (!skip_radix2) {
       const int half = L >> 1;
       const int total = half << log2NC;
-      V v[2 * IPT4][2];
+      V v[IPT2][2];
 #pragma unroll
-      for (int s = 0; s < 2 * IPT4; ++s) {
-        int it = tid + s * NT;
+      for (int s = 0; s < IPT2; ++s) {
+        const int it = tid + s * NT;
         if (it < total) {
-          int c = it & cmask, j = it >> log2NC;
+          const int c = it & cmask, j = it >> log2NC;
           v[s][0] = buf[at(j, c)];
           v[s][1] = buf[at(j + half, c)];
         }
       }
       __syncthreads();
 #pragma unroll
-      for (int s = 0; s < 2 * IPT4; ++s) {
-        int it = tid + s * NT;
+      for (int s = 0; s < IPT2; ++s) {
+        const int it = tid + s * NT;
         if (it < total) {
-          int c = it & cmask, j = it >> log2NC;
+          const int c = it & cmask, j = it >> log2NC;
           buf[at(2 * j, c)] = A::add(v[s][0], v[s][1]);
           buf[at(2 * j + 1, c)] = A::sub(v[s][0], v[s][1]);
         }
       }
       __syncthreads();
     }
-    Ns = 2;
+    log2Ns = 1;
   }
-  const int quarter = L >> 2;
-  const int total = quarter << log2NC;
-  for (; Ns < L; Ns <<= 2) {
-    const int tstep = L / (4 * Ns);
+  if ((log2L - log2Ns) & 2) {
+    const int Ns = 1 << log2Ns;
+    const int quarter = L >> 2;
+    const int total = quarter << log2NC;
+    const int tstep_log = log2L - 2 - log2Ns;
     V v[IPT4][4];
 #pragma unroll
     for (int s = 0; s < IPT4; ++s) {
-      int it = tid + s * NT;
+      const int it = tid + s * NT;
       if (it < total) {
-        int c = it & cmask, j = it >> log2NC;
+        const int c = it & cmask, j = it >> log2NC;
 #pragma unroll
         for (int r = 0; r < 4; ++r) v[s][r] = buf[at(j + r * quarter, c)];
       }
@@ -267,27 +342,61 @@ __device__ void fft_columns(typename A::V* buf, int L, int log2L, int log2NC,
     __syncthreads();
 #pragma unroll
     for (int s = 0; s < IPT4; ++s) {
-      int it = tid + s * NT;
+      const int it = tid + s * NT;
       if (it < total) {
-        int c = it & cmask, j = it >> log2NC;
-        int k = j & (Ns - 1);
+        const int c = it & cmask, j = it >> log2NC;
+        const int k = j & (Ns - 1);
         if (k != 0) {
-          int e = k * tstep;
+          const int e = k << tstep_log;
 #pragma unroll
           for (int r = 1; r < 4; ++r) {
-            V w = tw[r * e];
+            const V w = tw[r * e];
             v[s][r] = INV ? A::mulc(v[s][r], w) : A::mul(v[s][r], w);
           }
         }
-        V t0 = A::add(v[s][0], v[s][2]);
-        V t1 = A::sub(v[s][0], v[s][2]);
-        V t2 = A::add(v[s][1], v[s][3]);
-        V t3 = A::template rot<INV>(A::sub(v[s][1], v[s][3]));
-        int o = (j - k) * 4 + k;
-        buf[at(o, c)] = A::add(t0, t2);
-        buf[at(o + Ns, c)] = A::add(t1, t3);
-        buf[at(o + 2 * Ns, c)] = A::sub(t0, t2);
-        buf[at(o + 3 * Ns, c)] = A::sub(t1, t3);
+        dft4<A, INV>(v[s][0], v[s][1], v[s][2], v[s][3]);
+        const int o = (j - k) * 4 + k;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) buf[at(o + q * Ns, c)] = v[s][q];
+      }
+    }
+    __syncthreads();
+    log2Ns += 2;
+  }
+  const int sixteenth = L >> 4;
+  const int total16 = sixteenth << log2NC;
+  for (; log2Ns < log2L; log2Ns += 4) {
+    const int Ns = 1 << log2Ns;
+    const int tstep_log = log2L - 4 - log2Ns;
+    V v[IPT16][16];
+#pragma unroll
+    for (int s = 0; s < IPT16; ++s) {
+      const int it = tid + s * NT;
+      if (it < total16) {
+        const int c = it & cmask, j = it >> log2NC;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[s][r] = buf[at(j + r * sixteenth, c)];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < IPT16; ++s) {
+      const int it = tid + s * NT;
+      if (it < total16) {
+        const int c = it & cmask, j = it >> log2NC;
+        const int k = j & (Ns - 1);
+        if (k != 0) {
+          const int e = k << tstep_log;
+#pragma unroll
+          for (int r = 1; r < 16; ++r) {
+            const V w = tw[r * e];
+            v[s][r] = INV ? A::mulc(v[s][r], w) : A::mul(v[s][r], w);
+          }
+        }
+        dft16<A, INV>(v[s]);
+        const int o = (j - k) * 16 + k;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) buf[at(o + q * Ns, c)] = v[s][4 * (q & 3) + (q >> 2)];
       }
     }
     __syncthreads();

@@ -67,10 +67,9 @@ struct PrecTables {
   const float2* dinv_df; // the same as double-float (hi, lo)
   const float2* d2_df;
   const float4* gdf;     // [(N/2+1)][M]: the g64 table as double-float, f32x2 form
-  const float2* g32;     // [(N/2+1)][M]: the same in FP32, FP32 form
   const double2* g64;    // [(N/2+1)][M]: lambda^{-1/2}/(2N), FP64 form
-  const float2* ahat32;  // [N/2+1]: FFT_N(D a), FP32 form
-  const float2* bhat32;
+  const float2* ahat32;  // [N/2+1]: FFT_N(D a); the FP32 form evaluates lambda^{-1/2}/(2N) from
+  const float2* bhat32;  // these two where it uses it
   int none;              // 1: identity preconditioner (MINRES-I)
 };
 
@@ -101,8 +100,8 @@ cudaError_t launch_matvec(const OpTables& op, int spectral, const double* x, con
                           int* nparts, const int* phase, double* tmp, cudaStream_t st);
 cudaError_t launch_setup_g64(const OpTables& op, const double2* ahat, const double2* bhat,
                              double2* g64, float4* gdf, cudaStream_t st);
-cudaError_t launch_setup_g32(const OpTables& op, const float2* ahat32, const float2* bhat32,
-                             const float4* ahatdf, const float4* bhatdf, float2* g32, float4* gdf,
+cudaError_t launch_setup_gdf(const OpTables& op, const float2* ahat32, const float2* bhat32,
+                             const float4* ahatdf, const float4* bhatdf, float4* gdf,
                              cudaStream_t st);
 cudaError_t launch_flip_copy(const double* f, double* b, int N, long long M, double* partials,
                              int* nparts, cudaStream_t st);

@@ -94,6 +94,18 @@ __device__ __forceinline__ C<T> inv_sqrt_principal(T x, T y) {
   return mk<T>(s * ir, -t * ir);
 }
 
+// the same in FP32 with the hardware reciprocal square root (a few ulp): |z|^2 = x^2 + y^2 must
+// stay inside the normal FP32 range, else the accurate form above is taken
+__device__ __forceinline__ float2 inv_sqrt_principal_fast(float x, float y) {
+  const float rr = fmaf(x, x, y * y);
+  if (!(rr > 1e-36f && rr < 1e36f)) return inv_sqrt_principal<float>(x, y);
+  const float ir = rsqrtf(rr);        // 1/|z|
+  const float h = 0.5f * fmaf(rr, ir, x);   // s^2 = (|z| + x)/2
+  const float is = rsqrtf(h);         // 1/s
+  const float t = 0.5f * y * is;      // y/(2s)
+  return make_float2(h * is * ir, -t * ir);
+}
+
 template <typename K>
 static cudaError_t set_smem(K kern, size_t bytes) {
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -126,7 +138,12 @@ constexpr int kBatch = 8;   // independent global loads in flight per thread in 
 // threads per tile block and complex points per tile, per arithmetic: 256 threads and 4096 points
 // (32 KB of FP32, 64 KB of FP64 / double-float shared memory) let two to four independent blocks
 // share an SM, so that one block's loads, stores and barriers overlap another block's arithmetic
-template <class A> struct TileCfg { static constexpr int NT = kThreads, CAP = kCap; };
+template <class A> struct TileCfg {
+  static constexpr int NT = kThreads, CAP = kCap;
+  // resident blocks per SM the register budget is held to: 128 registers per thread for FP64 and
+  // double-float, 64 for FP32
+  static constexpr int MINB = sizeof(typename A::V) == 8 ? 4 : 2;
+};
 
 // ============================================================================================
 // DST-I along one spatial axis (Steps 1 and 3 of Sec. 5.1).  Two real lines x_a, x_b share one
@@ -198,18 +215,41 @@ __device__ __forceinline__ void dst_tile(long long nlines, int m, long long inne
   fft_columns<A, NT, CAP, false, SWZ>(buf, L, log2L, log2NC, tw);
   const typename A::Sc scale = A::make_sc(rsqrt((double)L));
   const typename A::Sc nscale = A::make_sc(-rsqrt((double)L));
+  // read-out in batches: the global loads of a batch (the dot-product partner) are all issued
+  // before the first use, so that their latencies overlap.  dot_with == out asks for ||out||^2.
+  const bool self_dot = (dot_with == out);
+  const double* dwsrc = self_dot ? nullptr : dot_with;
   double acc = 0.0;
-  for (int e = threadIdx.x; e < total; e += NT) {
-    int c, k;
-    if (contiguous) { c = fast_div(e, m, inv_m); k = e - c * m; }
-    else { k = e >> log2W; c = e & (W - 1); }
-    const long long o = s_out[c];
-    if (o >= 0) {
-      const V z = buf[at(k + 1, c >> 1)];
-      const double val = (c & 1) ? A::part_sc(z, 0, scale) : A::part_sc(z, 1, nscale);
-      const long long idx = o + (long long)k * inner;
-      out[idx] = val;
-      if (dot_with) acc = fma(val, dot_with[idx], acc);
+  for (int e0 = threadIdx.x; e0 < total; e0 += kBatch * NT) {
+    double dw[kBatch];
+    long long ix[kBatch];
+    int cs[kBatch], ks[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int e = e0 + u * NT;
+      int c = 0, k = 0;
+      if (contiguous) { c = fast_div(e, m, inv_m); k = e - c * m; }
+      else { k = e >> log2W; c = e & (W - 1); }
+      cs[u] = c; ks[u] = k;
+      ix[u] = -1;
+      dw[u] = 0.0;
+      if (e < total) {
+        const long long o = s_out[c];
+        if (o >= 0) {
+          ix[u] = o + (long long)k * inner;
+          if (dwsrc) dw[u] = dwsrc[ix[u]];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      if (ix[u] >= 0) {
+        const int c = cs[u];
+        const V z = buf[at(ks[u] + 1, c >> 1)];
+        const double val = (c & 1) ? A::part_sc(z, 0, scale) : A::part_sc(z, 1, nscale);
+        out[ix[u]] = val;
+        acc = fma(val, self_dot ? val : dw[u], acc);
+      }
     }
   }
   if (partials) {
@@ -219,7 +259,7 @@ __device__ __forceinline__ void dst_tile(long long nlines, int m, long long inne
 }
 
 template <class A, bool SWZ>
-__global__ void __launch_bounds__(TileCfg<A>::NT)
+__global__ void __launch_bounds__(TileCfg<A>::NT, TileCfg<A>::MINB)
 k_dst(long long nlines, int m, long long inner, int P, int log2L, int log2NC, Combine cb,
       double* out, int flip, int N, long long M, const double* dot_with, double* partials,
       const typename A::V* __restrict__ tw, const int* phase, int want) {
@@ -250,31 +290,37 @@ template <> struct RowSc<ArithDF> {
   static __device__ __forceinline__ dfl d2(const PrecTables& pt, int p) { return ArithDF::row_sc(pt.d2_df, p); }
 };
 
-// G for mode i at frequency k: lambda^{-1/2}/(2N), lambda = ahat_k + bhat_k mu_i
+// G for mode i at frequency k: lambda^{-1/2}/(2N), lambda = ahat_k + bhat_k mu_i.  FP64 and
+// double-float read the per-(frequency, mode) table built at set-up; FP32 evaluates it where it is
+// used, from the N/2+1 entries of ahat and bhat (two reciprocal square roots), which spares a
+// table's 8 bytes per unknown of DRAM reads and their latency
 template <class A> struct GSrc;
 template <> struct GSrc<ArithDF> {
   static __device__ __forceinline__ float4 get(const OpTables& op, const PrecTables& pt, int k,
-                                              long long i, double) {
+                                              long long i, float) {
     return pt.gdf[(long long)k * op.M + i];
   }
 };
 template <> struct GSrc<ArithD> {
   static __device__ __forceinline__ double2 get(const OpTables& op, const PrecTables& pt, int k,
-                                               long long i, double) {
+                                               long long i, float) {
     return pt.g64[(long long)k * op.M + i];
   }
 };
 template <> struct GSrc<ArithF> {
   static __device__ __forceinline__ float2 get(const OpTables& op, const PrecTables& pt, int k,
-                                              long long i, double) {
-    return pt.g32[(long long)k * op.M + i];
+                                              long long, float mu32) {
+    const float2 a = pt.ahat32[k], b = pt.bhat32[k];
+    const float2 g = inv_sqrt_principal_fast(fmaf(b.x, mu32, a.x), fmaf(b.y, mu32, a.y));
+    const float sc = 0.5f / (float)op.N;
+    return make_float2(g.x * sc, g.y * sc);
   }
 };
 
 template <class A, bool CONJ>
 __device__ __forceinline__ void tp_freq_mul(typename A::V* buf, const OpTables& op,
                                             const PrecTables& pt, int log2NC, long long g0,
-                                            const double* s_mu) {
+                                            const float* s_mu) {
   constexpr int NT = TileCfg<A>::NT, CAP = TileCfg<A>::CAP;
   using V = typename A::V;
   const int N = op.N, half = N >> 1, NC = 1 << log2NC;
@@ -307,11 +353,12 @@ __device__ __forceinline__ void timepass_tile(const OpTables& op, const PrecTabl
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* buf = reinterpret_cast<V*>(smem_raw);
   __shared__ double red[32];
-  __shared__ double s_mu[kMaxCols];
+  __shared__ float s_mu[kMaxCols];   // FP32 mode eigenvalues, used by the FP32 G
   const int N = op.N, NC = 1 << log2NC, W = 2 * NC, log2W = log2NC + 1;
   const long long M = op.M;
   const long long g0 = tile * W;
-  for (int c = threadIdx.x; c < W; c += NT) s_mu[c] = (g0 + c < M) ? mode_mu(op, g0 + c) : 0.0;
+  if (std::is_same<A, ArithF>::value)
+    for (int c = threadIdx.x; c < W; c += NT) s_mu[c] = (g0 + c < M) ? mode_mu32(op, g0 + c) : 0.f;
   double c0, c1, c2;
   load_coef(cb, c0, c1, c2);
   const int total = N * W;
@@ -345,14 +392,30 @@ __device__ __forceinline__ void timepass_tile(const OpTables& op, const PrecTabl
   tp_freq_mul<A, false>(buf, op, pt, log2NC, g0, s_mu);
   __syncthreads();
   fft_columns<A, NT, CAP, true>(buf, N, op.log2N, log2NC, tw);
+  // read-out in batches: the dot-product partner of a whole batch is loaded before its first use;
+  // dot_with == out asks for ||out||^2
+  const bool self_dot = (dot_with == out);
+  const double* dwsrc = self_dot ? nullptr : dot_with;
   double acc = 0.0;
-  for (int e = threadIdx.x; e < total; e += NT) {
-    const int p = e >> log2W, c = e & (W - 1);
-    if (g0 + c < M) {
-      const long long idx = (long long)p * M + g0 + c;
-      const double z = A::part_sc(buf[p * NC + (c >> 1)], c & 1, RowSc<A>::dinv(pt, p));
-      out[idx] = z;
-      if (dot_with) acc = fma(z, dot_with[idx], acc);
+  for (int e0 = threadIdx.x; e0 < total; e0 += kBatch * NT) {
+    double dw[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int e = e0 + u * NT;
+      const int p = e >> log2W, c = e & (W - 1);
+      dw[u] = 0.0;
+      if (dwsrc && e < total && g0 + c < M) dw[u] = dwsrc[(long long)p * M + g0 + c];
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int e = e0 + u * NT;
+      const int p = e >> log2W, c = e & (W - 1);
+      if (e < total && g0 + c < M) {
+        const long long idx = (long long)p * M + g0 + c;
+        const double z = A::part_sc(buf[p * NC + (c >> 1)], c & 1, RowSc<A>::dinv(pt, p));
+        out[idx] = z;
+        acc = fma(z, self_dot ? z : dw[u], acc);
+      }
     }
   }
   if (partials) {
@@ -362,7 +425,7 @@ __device__ __forceinline__ void timepass_tile(const OpTables& op, const PrecTabl
 }
 
 template <class A>
-__global__ void __launch_bounds__(TileCfg<A>::NT)
+__global__ void __launch_bounds__(TileCfg<A>::NT, TileCfg<A>::MINB)
 k_timepass(OpTables op, PrecTables pt, Combine cb, double* out, const double* dot_with,
            double* partials, const int* phase, int want, int log2NC,
            const typename A::V* __restrict__ tw) {
@@ -528,42 +591,61 @@ __device__ __forceinline__ void conv_tile(const OpTables& op, int spectral, int 
   double acc = 0.0;
   const double st_coef = (op.b_kind == 0) ? op.b0 * s : 1.0;
   const long long s1 = op.m[0], s2 = (long long)op.m[0] * op.m[1];
-  for (int e = threadIdx.x; e < total; e += NT) {
-    const int t = e >> log2W, c = e & (W - 1);
-    const long long i = g0 + c;
-    if (i >= M) continue;
-    double val = A::part(buf[t * NC + (c >> 1)], c & 1);
-    if (extra_st) {
-      const double* xt = st_src + (long long)t * M;
-      const int nb = s_nb[c];
-      const double xi2 = 2.0 * xt[i];
-      double sx = xi2;
-      if (nb & 1) sx -= xt[i - 1];
-      if (nb & 2) sx -= xt[i + 1];
-      double lap = sx * op.h2inv[0];
-      if (op.d > 1) {
-        double sy = xi2;
-        if (nb & 4) sy -= xt[i - s1];
-        if (nb & 8) sy -= xt[i + s1];
-        lap = fma(sy, op.h2inv[1], lap);
-        if (op.d > 2) {
-          double sz = xi2;
-          if (nb & 16) sz -= xt[i - s2];
-          if (nb & 32) sz -= xt[i + s2];
-          lap = fma(sz, op.h2inv[2], lap);
-        }
+  // read-out in batches: the global operand of each output (x for the dot product, or the
+  // right-hand side) is loaded for a whole batch before its first use
+  for (int e0 = threadIdx.x; e0 < total; e0 += kBatch * NT) {
+    double pre[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int e = e0 + u * NT;
+      const int t = e >> log2W, c = e & (W - 1);
+      pre[u] = 0.0;
+      if (e < total && g0 + c < M) {
+        const int to = flip ? (N - 1 - t) : t;
+        const long long idx = (long long)to * M + g0 + c;
+        if (mode != MV_STORE) pre[u] = rhs[idx];
+        else if (partials) pre[u] = x[idx];
       }
-      val = fma(st_coef, lap, val);
     }
-    const int to = flip ? (N - 1 - t) : t;
-    const long long idx = (long long)to * M + i;
-    if (mode == MV_STORE) {
-      y[idx] = val;
-      if (partials) acc = fma(val, x[idx], acc);     // times s once per block below
-    } else {
-      const double r = rhs[idx] - val;
-      if (y) y[idx] = r;
-      acc = fma(r, r, acc);
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int e = e0 + u * NT;
+      const int t = e >> log2W, c = e & (W - 1);
+      const long long i = g0 + c;
+      if (e >= total || i >= M) continue;
+      double val = A::part(buf[t * NC + (c >> 1)], c & 1);
+      if (extra_st) {
+        const double* xt = st_src + (long long)t * M;
+        const int nb = s_nb[c];
+        const double xi2 = 2.0 * xt[i];
+        double sx = xi2;
+        if (nb & 1) sx -= xt[i - 1];
+        if (nb & 2) sx -= xt[i + 1];
+        double lap = sx * op.h2inv[0];
+        if (op.d > 1) {
+          double sy = xi2;
+          if (nb & 4) sy -= xt[i - s1];
+          if (nb & 8) sy -= xt[i + s1];
+          lap = fma(sy, op.h2inv[1], lap);
+          if (op.d > 2) {
+            double sz = xi2;
+            if (nb & 16) sz -= xt[i - s2];
+            if (nb & 32) sz -= xt[i + s2];
+            lap = fma(sz, op.h2inv[2], lap);
+          }
+        }
+        val = fma(st_coef, lap, val);
+      }
+      const int to = flip ? (N - 1 - t) : t;
+      const long long idx = (long long)to * M + i;
+      if (mode == MV_STORE) {
+        y[idx] = val;
+        acc = fma(val, pre[u], acc);     // times s once per block below
+      } else {
+        const double r = pre[u] - val;
+        if (y) y[idx] = r;
+        acc = fma(r, r, acc);
+      }
     }
   }
   if (partials) {
@@ -573,7 +655,7 @@ __device__ __forceinline__ void conv_tile(const OpTables& op, int spectral, int 
 }
 
 template <class A>
-__global__ void __launch_bounds__(TileCfg<A>::NT)
+__global__ void __launch_bounds__(TileCfg<A>::NT, TileCfg<A>::MINB)
 k_conv(OpTables op, int spectral, int which, const double* x, const double* xscale, double* y,
        int flip, int mode, const double* rhs, double* partials, const int* phase, int want,
        const double* st_src, int log2NC) {
@@ -655,11 +737,10 @@ __global__ void k_setup_g64(OpTables op, const double2* ahat, const double2* bha
 // principal lambda^{-1/2} in FP32 (half-angle form); the double-float value takes one Newton
 // step for z^{-1/2}, g1 = g0 (3 - lambda g0^2) / 2, in double-float (the error squares: 2^-24 ->
 // about 2^-47), with lambda = ahat_k + bhat_k mu_i formed in double-float.
-__global__ void k_setup_g32(OpTables op, const float2* ahat32, const float2* bhat32,
-                            const float4* ahatdf, const float4* bhatdf, float2* g32, float4* gdf) {
+__global__ void k_setup_gdf(OpTables op, const float2* ahat32, const float2* bhat32,
+                            const float4* ahatdf, const float4* bhatdf, float4* gdf) {
   const int half = op.N / 2;
   const long long total = (long long)(half + 1) * op.M;
-  const float sc = 0.5f / (float)op.N;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const int k = (int)(e / op.M);
@@ -667,26 +748,23 @@ __global__ void k_setup_g32(OpTables op, const float2* ahat32, const float2* bha
     const float mu = mode_mu32(op, i);
     const float2 a = ahat32[k], b = bhat32[k];
     const float2 g0 = inv_sqrt_principal<float>(fmaf(b.x, mu, a.x), fmaf(b.y, mu, a.y));
-    if (g32) g32[e] = make_float2(g0.x * sc, g0.y * sc);
-    if (gdf) {
-      const float4 A4 = ahatdf[k], B4 = bhatdf[k];
-      // mu_i as double-float: sum of the per-axis FP64 eigenvalues
-      long long r = i / op.m[0];
-      dfl m_ = df_from(op.mu_axis[0][i - r * op.m[0]]);
-      if (op.d > 1) {
-        long long r2 = r / op.m[1];
-        m_ = df_add(m_, df_from(op.mu_axis[1][r - r2 * op.m[1]]));
-        if (op.d > 2) m_ = df_add(m_, df_from(op.mu_axis[2][r2]));
-      }
-      const float4 lam = ArithDF::pack(df_add(dfl{A4.x, A4.y}, df_mul(m_, dfl{B4.x, B4.y})),
-                                       df_add(dfl{A4.z, A4.w}, df_mul(m_, dfl{B4.z, B4.w})));
-      const float4 g = make_float4(g0.x, 0.f, g0.y, 0.f);
-      const float4 t = ArithDF::mul(lam, ArithDF::mul(g, g));          // lambda g0^2 ~ 1
-      const float4 three_m = ArithDF::sub(make_float4(3.f, 0.f, 0.f, 0.f), t);
-      const float4 g1 = ArithDF::mul(g, three_m);                        // 2 g1
-      const dfl s2 = {0.25f / (float)op.N, 0.f};                         // (1/2) (1/(2N)), exact
-      gdf[e] = ArithDF::pack(df_mul(dfl{g1.x, g1.y}, s2), df_mul(dfl{g1.z, g1.w}, s2));
+    const float4 A4 = ahatdf[k], B4 = bhatdf[k];
+    // mu_i as double-float: sum of the per-axis FP64 eigenvalues
+    long long r = i / op.m[0];
+    dfl m_ = df_from(op.mu_axis[0][i - r * op.m[0]]);
+    if (op.d > 1) {
+      long long r2 = r / op.m[1];
+      m_ = df_add(m_, df_from(op.mu_axis[1][r - r2 * op.m[1]]));
+      if (op.d > 2) m_ = df_add(m_, df_from(op.mu_axis[2][r2]));
     }
+    const float4 lam = ArithDF::pack(df_add(dfl{A4.x, A4.y}, df_mul(m_, dfl{B4.x, B4.y})),
+                                     df_add(dfl{A4.z, A4.w}, df_mul(m_, dfl{B4.z, B4.w})));
+    const float4 g = make_float4(g0.x, 0.f, g0.y, 0.f);
+    const float4 t = ArithDF::mul(lam, ArithDF::mul(g, g));          // lambda g0^2 ~ 1
+    const float4 three_m = ArithDF::sub(make_float4(3.f, 0.f, 0.f, 0.f), t);
+    const float4 g1 = ArithDF::mul(g, three_m);                        // 2 g1
+    const dfl s2 = {0.25f / (float)op.N, 0.f};                         // (1/2) (1/(2N)), exact
+    gdf[e] = ArithDF::pack(df_mul(dfl{g1.x, g1.y}, s2), df_mul(dfl{g1.z, g1.w}, s2));
   }
 }
 
@@ -1025,11 +1103,11 @@ cudaError_t launch_setup_g64(const OpTables& op, const double2* ahat, const doub
   return cudaGetLastError();
 }
 
-cudaError_t launch_setup_g32(const OpTables& op, const float2* ahat32, const float2* bhat32,
-                             const float4* ahatdf, const float4* bhatdf, float2* g32, float4* gdf,
+cudaError_t launch_setup_gdf(const OpTables& op, const float2* ahat32, const float2* bhat32,
+                             const float4* ahatdf, const float4* bhatdf, float4* gdf,
                              cudaStream_t st) {
   long long total = (long long)(op.N / 2 + 1) * op.M;
-  k_setup_g32<<<grid_stream(total, 256), 256, 0, st>>>(op, ahat32, bhat32, ahatdf, bhatdf, g32, gdf);
+  k_setup_gdf<<<grid_stream(total, 256), 256, 0, st>>>(op, ahat32, bhat32, ahatdf, bhatdf, gdf);
   return cudaGetLastError();
 }
 
@@ -1070,7 +1148,8 @@ cudaError_t launch_sum_partials(const double* partials, int np, double* out, cud
 }
 
 // ============================================================================================
-// Multi-item kernels (batched solves)
+// Multi-item kernels (batched solves).  They keep the full register budget: their tile bodies
+// read the item tables through memory rather than from kernel parameters and need more registers.
 __device__ __forceinline__ int find_item(const long long* prefix, int nitems, long long t) {
   int lo = 0, hi = nitems - 1;           // largest i with prefix[i] <= t
   while (lo < hi) {

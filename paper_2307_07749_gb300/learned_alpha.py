@@ -2,9 +2,9 @@
 
 The paper fixes alpha = 1e-8 (Sec. 5.2); its Theorem 1 bounds alpha from above only.  With an
 FP32 preconditioner that alpha fails (rounding grows like alpha^{-(N-1)/N}), so the best alpha
-depends on the problem.  This module labels each training problem with the alpha of a 16-point
-sweep (10^{-j/2}, j = 1..16) that needs the fewest MINRES iterations to reach the tolerance
-(ties go to the larger alpha), and fits the library's MLP (bltt_alpha_train) to
+depends on the problem.  This module labels each training problem from a 16-point sweep
+(10^{-j/2}, j = 1..16) by the alphas that need the fewest MINRES iterations to reach the
+tolerance (the centre of the widest run of them, see label), and fits the library's MLP (bltt_alpha_train) to
 (log N, log M, gamma, log(tau/h^2)) -> log10(alpha).  Every solve and every network pass runs in
 the library's CUDA kernels; this file only arranges inputs.
 """
@@ -47,15 +47,27 @@ def sweep(solver, f_dev, alphas=SWEEP, tol=1e-8, maxit=40, precision=PREC_F32,
 
 
 def label(results):
-    """log10 of the alpha with the fewest iterations (ties: the larger alpha); None if none
-    converged."""
-    best = None
+    """log10 alpha label of one sweep: the fewest iterations decide; among the alphas that reach
+    that count, the label is the centre (in log10 alpha) of the longest run of consecutive sweep
+    points that all reach it (equal runs: the run of larger alpha).  The centre keeps the largest
+    margin to the points where the count rises, on the small-alpha side often sharply (rounding of
+    the FP32 form).  None if no alpha converged."""
+    its = [it for _, it, _ in results if it is not None]
+    if not its:
+        return None
+    best = min(its)
+    runs, cur = [], []
     for a, it, _ in results:
-        if it is None:
-            continue
-        if best is None or it < best[1] or (it == best[1] and a > best[0]):
-            best = (a, it)
-    return None if best is None else math.log10(best[0])
+        if it == best:
+            cur.append(math.log10(a))
+        elif cur:
+            runs.append(cur)
+            cur = []
+    if cur:
+        runs.append(cur)
+    # longest run; among equally long runs the one of largest alpha
+    run = max(runs, key=lambda r: (len(r), max(r)))
+    return 0.5 * (min(run) + max(run))
 
 
 def init_model(feats, labels, seed=0) -> np.ndarray:

@@ -76,3 +76,21 @@ def test_null_handle_calls(lib):
     assert L.bltt_matvec(None, None, None, 1) == 1
     assert L.bltt_precond_apply(None, 0.5, None, None, 64) == 1
     assert L.bltt_set_stream(None, None) == 1
+
+
+def test_alpha_label_rule(lib):
+    """Sweep labels: the fewest iterations decide; the label is the centre (log10) of the longest
+    run of consecutive sweep points reaching that count, equal runs going to larger alpha."""
+    from paper_2307_07749_gb300 import learned_alpha as LA
+    a = [10.0 ** (-j / 2.0) for j in range(1, 9)]          # 10^-0.5 .. 10^-4
+
+    def res(its):
+        return [(x, it, 0.0) for x, it in zip(a, its)]
+
+    # plateau of 5s over 10^-1.5 .. 10^-2.5, a cliff below it
+    assert LA.label(res([9, 7, 5, 5, 5, None, None, None])) == pytest.approx(-2.0)
+    # a single minimum beats a longer plateau of higher counts
+    assert LA.label(res([6, 6, 6, 6, 5, 6, 12, None])) == pytest.approx(-2.5)
+    # two equally long runs: the one of larger alpha
+    assert LA.label(res([4, 4, 6, 4, 4, 7, None, None])) == pytest.approx(-0.75)
+    assert LA.label(res([None] * 8)) is None
