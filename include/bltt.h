@@ -163,12 +163,15 @@ bltt_status bltt_minres_solve(bltt_handle h, const double* f_dev, double alpha, 
                               int maxit, int precision, double* u_dev, bltt_solve_info* info);
 
 /* Solve many BLTT systems with several right-hand sides each, together (batching: one launch per
- * MINRES phase covers every (system, right-hand side) item of a wave; the phase sequence of two
- * iterations is captured in a CUDA graph and replayed until every item has stopped).  Each item
+ * MINRES phase covers every (system, right-hand side) item of a wave below 2^21 unknowns, and each
+ * larger item, which fills the GPU by itself, gets its own launch of that phase; the phase
+ * sequence of two iterations is captured in a CUDA graph and replayed until every item has
+ * stopped).  Each item
  * is the solve of bltt_minres_solve_ex in the DST basis (Sec. 2-3, Sec. 5) with its own MINRES
  * state; the items of one system share its tables.  Waves are sized to 85% of the free device
  * memory (or to the byte count in the environment variable BLTT_BATCH_MAX_BYTES, if smaller);
- * tile widths come from a built-in autotuner (opts->sync_every < 0 disables it).
+ * the tile widths of the shared launches come from a built-in autotuner (opts->sync_every < 0
+ * disables it).
  *   nsys systems sys[s] (host structs as for bltt_create; N and m[ax]+1 powers of two) with
  *   nrhs[s] >= 1 right-hand sides each; f_dev / u_dev: host arrays of sum(nrhs) device pointers
  *   (system-major), each a vector of that system's N*M doubles, u not aliasing f.

@@ -7,8 +7,11 @@
 // concatenated tile list; items that have converged skip their tiles).  The phase sequence of two
 // MINRES iterations is captured once per wave in a CUDA graph and replayed until every item has
 // stopped.  Waves are sized so that their workspace fits the device memory that is free.
-// The tile width of each (kernel, N, M, d) shape is chosen by a small autotuner that times the
-// candidate widths on the first batch that meets the shape and caches the choice.
+// Items of at least kBigItem unknowns fill the GPU on their own: their FFT phases use the
+// single-item kernels (operator tables as kernel parameters, two blocks per SM) inside the same
+// graph, and only the smaller items share the multi-item launches, whose tile width for each
+// (kernel, N, M, d) shape is chosen by a small autotuner that times the candidate widths on the
+// first batch that meets the shape and caches the choice.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -25,7 +28,11 @@ using namespace bltt;
 
 namespace {
 
+// unknowns from which an item runs its FFT phases as single-item launches (at least 512 tiles)
+constexpr long long kBigItem = 1LL << 21;
+
 struct Item {
+  bool big;
   int sys, rhs;
   long long n, M;
   int N, d, m[3];
@@ -182,6 +189,7 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
     for (int r = 0; r < nrhs[s]; ++r, ++k) {
       Item it{};
       it.sys = s; it.rhs = r; it.N = op.N; it.M = op.M; it.n = (long long)op.N * op.M; it.d = op.d;
+      it.big = it.n >= kBigItem;
       for (int ax = 0; ax < 3; ++ax) it.m[ax] = op.m[ax];
       it.f = f_dev[k]; it.u = u_dev[k];
       if (!it.f || !it.u || it.f == it.u) { cleanup(); return BLTT_ERR_INVALID_ARG; }
@@ -299,6 +307,7 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
       const OpTables& op = ctx_op(H[it.sys]);
       PrecTables pt = ctx_prec_tables(H[it.sys]);
       const bool en = (o.sync_every >= 0);
+      if (it.big) continue;   // single-item launches keep the default widths
       it.l2nc_conv = tune(0, it, op, pt, prec, arith, en, st, it.f, it.q);
       it.l2nc_tp = tune(1, it, op, pt, prec, arith, en, st, it.f, it.z[0]);
       it.tiles_conv = (it.M + (2LL << it.l2nc_conv) - 1) / (2LL << it.l2nc_conv);
@@ -314,11 +323,15 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
     std::vector<VecItem> w_loop[2];
     std::vector<ScalItem> sc_init, sc_delta, sc_gamma, sc_check;
     long long tot_conv = 0, tot_tp = 0, tot_dst[3] = {0, 0, 0};
+    std::vector<int> bigs;   // wave positions of the items with single-item launches
+    int ns = 0;              // items in the multi-item descriptors
     for (int j = 0; j < ni; ++j) {
       Item& it = items[wave[j]];
       const OpTables& op = ctx_op(H[it.sys]);
       PrecTables pt = ctx_prec_tables(H[it.sys]);
       const int dprec = arith ? PREC_DF : PREC_F64;
+      if (it.big) bigs.push_back(j);
+      else ++ns;
       // entry (f -> b = Y (I x U) f, ||b||^2 in the last pass) and exit (x -> u) DSTs
       long long inner = 1;
       for (int ax = 0; ax < 3; ++ax) {
@@ -340,20 +353,24 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
         dq.cb.in0 = (ax == 0) ? it.x : it.u;
         dq.out = it.u;
         dq.flip = 0;
-        pre_dst[ax].push_back(tot_dst[ax]);
-        tot_dst[ax] += it.tiles_dst[ax];
-        dst_in[ax].push_back(di);
-        dst_out[ax].push_back(dq);
+        if (!it.big) {
+          pre_dst[ax].push_back(tot_dst[ax]);
+          tot_dst[ax] += it.tiles_dst[ax];
+          dst_in[ax].push_back(di);
+          dst_out[ax].push_back(dq);
+        }
       }
-      pre_conv.push_back(tot_conv);
-      tot_conv += it.tiles_conv;
-      pre_tp.push_back(tot_tp);
-      tot_tp += it.tiles_tp;
+      if (!it.big) {
+        pre_conv.push_back(tot_conv);
+        tot_conv += it.tiles_conv;
+        pre_tp.push_back(tot_tp);
+        tot_tp += it.tiles_tp;
+      }
       TpItem ti{};
       ti.op = op; ti.pt = pt; ti.log2NC = it.l2nc_tp;
       ti.cb.in0 = it.b; ti.cb.vout = it.v[0];
       ti.out = it.z[0]; ti.dot_with = it.v[0]; ti.partials = it.p0;
-      tp_init.push_back(ti);
+      if (!it.big) tp_init.push_back(ti);
       ScalItem si{};
       si.st = it.st; si.p0 = it.p0; si.n0 = (int)it.tiles_tp; si.p1 = it.p1;
       si.n1 = (int)it.tiles_dst[it.d - 1];
@@ -364,13 +381,13 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
         ci.op = op; ci.x = it.z[cur]; ci.xscale = &it.st->inv_gamma; ci.y = it.q; ci.flip = 1;
         ci.mode = MV_STORE; ci.spectral = 1; ci.log2NC = it.l2nc_conv; ci.partials = it.p0;
         ci.phase = &it.st->phase; ci.want = PH_RUN;
-        cv_loop[e].push_back(ci);
+        if (!it.big) cv_loop[e].push_back(ci);
         TpItem tl{};
         tl.op = op; tl.pt = pt; tl.log2NC = it.l2nc_tp;
         tl.cb.in0 = it.q; tl.cb.in1 = it.v[cur]; tl.cb.in2 = it.v[prv]; tl.cb.coef = it.st->coef;
         tl.cb.vout = it.v[prv]; tl.out = it.z[prv]; tl.dot_with = it.v[prv]; tl.partials = it.p1;
         tl.phase = &it.st->phase; tl.want = PH_RUN;
-        tp_loop[e].push_back(tl);
+        if (!it.big) tp_loop[e].push_back(tl);
         VecItem vi{};
         vi.st = it.st; vi.z = it.z[cur]; vi.w_prev = it.w[prv]; vi.w = it.w[cur]; vi.x = it.x;
         vi.n = it.n;
@@ -380,7 +397,7 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
       cr.op = op; cr.x = it.x; cr.y = nullptr; cr.rhs = it.b; cr.flip = 1; cr.mode = MV_RESID;
       cr.spectral = 1; cr.log2NC = it.l2nc_conv; cr.partials = it.p0; cr.phase = &it.st->phase;
       cr.want = PH_CHECK;
-      cv_res.push_back(cr);
+      if (!it.big) cv_res.push_back(cr);
       ScalItem sd{};
       sd.st = it.st; sd.p0 = it.p0; sd.n0 = (int)it.tiles_conv;
       sc_delta.push_back(sd);
@@ -413,10 +430,69 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
     ScalItem* d_sc_gamma = up(sc_gamma);
     ScalItem* d_sc_check = up(sc_check);
     const int dprec = arith ? PREC_DF : PREC_F64;
+    // single-item launches of the big items (same operands as their descriptors above)
+    auto big_dst = [&](bool entry) {
+      cudaError_t r = cudaSuccess;
+      for (int j : bigs) {
+        const Item& it = items[wave[j]];
+        const OpTables& op = ctx_op(H[it.sys]);
+        for (int ax = 0; ax < it.d && r == cudaSuccess; ++ax) {
+          Combine c{};
+          const bool last = (ax == it.d - 1);
+          if (entry) {
+            c.in0 = (ax == 0) ? it.f : it.b;
+            r = launch_dst(op, ax, dprec, c, it.b, ax == 0 ? 1 : 0, last ? it.b : nullptr,
+                           last ? it.p1 : nullptr, nullptr, nullptr, st);
+          } else {
+            c.in0 = (ax == 0) ? it.x : it.u;
+            r = launch_dst(op, ax, dprec, c, it.u, 0, nullptr, nullptr, nullptr, nullptr, st);
+          }
+        }
+      }
+      return r;
+    };
+    auto big_tp = [&](int par, bool init) {
+      cudaError_t r = cudaSuccess;
+      for (int j : bigs) {
+        if (r != cudaSuccess) break;
+        const Item& it = items[wave[j]];
+        const OpTables& op = ctx_op(H[it.sys]);
+        PrecTables pt = ctx_prec_tables(H[it.sys]);
+        Combine c{};
+        if (init) {
+          c.in0 = it.b; c.vout = it.v[0];
+          r = launch_timepass(op, pt, prec, c, it.z[0], it.v[0], it.p0, nullptr, nullptr, st);
+        } else {
+          const int cur = par, prv = 1 - par;
+          c.in0 = it.q; c.in1 = it.v[cur]; c.in2 = it.v[prv]; c.coef = it.st->coef;
+          c.vout = it.v[prv];
+          r = launch_timepass(op, pt, prec, c, it.z[prv], it.v[prv], it.p1, nullptr,
+                              &it.st->phase, st);
+        }
+      }
+      return r;
+    };
+    auto big_conv = [&](int par, bool resid) {
+      cudaError_t r = cudaSuccess;
+      for (int j : bigs) {
+        if (r != cudaSuccess) break;
+        const Item& it = items[wave[j]];
+        const OpTables& op = ctx_op(H[it.sys]);
+        if (resid)
+          r = launch_matvec(op, 1, it.x, nullptr, nullptr, 1, MV_RESID, it.b, it.p0, nullptr,
+                            &it.st->phase, nullptr, st);
+        else
+          r = launch_matvec(op, 1, it.z[par], &it.st->inv_gamma, it.q, 1, MV_STORE, nullptr,
+                            it.p0, nullptr, &it.st->phase, nullptr, st);
+      }
+      return r;
+    };
     // entry: DSTs, first preconditioner apply, zero vectors, scalar init
-    for (int ax = 0; ax < 3 && e == cudaSuccess; ++ax)
-      e = launch_dst_multi(dprec, d_dst_in[ax], d_pre_dst[ax], ni, tot_dst[ax], st);
-    if (e == cudaSuccess) e = launch_timepass_multi(prec, d_tp_init, d_pre_tp, ni, tot_tp, st);
+    if (e == cudaSuccess) e = big_dst(true);
+    for (int ax = 0; ax < 3 && e == cudaSuccess && ns > 0; ++ax)
+      e = launch_dst_multi(dprec, d_dst_in[ax], d_pre_dst[ax], ns, tot_dst[ax], st);
+    if (e == cudaSuccess) e = big_tp(0, true);
+    if (e == cudaSuccess && ns > 0) e = launch_timepass_multi(prec, d_tp_init, d_pre_tp, ns, tot_tp, st);
     for (int j = 0; j < ni && e == cudaSuccess; ++j) {
       Item& it = items[wave[j]];
       e = cudaMemsetAsync(it.x, 0, it.n * 8, st);
@@ -434,12 +510,15 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
     if (e == cudaSuccess) {
       cudaError_t ce = cudaSuccess;
       for (int par = 0; par < 2 && ce == cudaSuccess; ++par) {
-        ce = launch_conv_multi(arith, d_cv_loop[par], d_pre_conv, ni, tot_conv, st);
+        ce = big_conv(par, false);
+        if (ce == cudaSuccess && ns > 0) ce = launch_conv_multi(arith, d_cv_loop[par], d_pre_conv, ns, tot_conv, st);
         if (ce == cudaSuccess) ce = launch_scalar_multi(1, d_sc_delta, ni, st);
-        if (ce == cudaSuccess) ce = launch_timepass_multi(prec, d_tp_loop[par], d_pre_tp, ni, tot_tp, st);
+        if (ce == cudaSuccess) ce = big_tp(par, false);
+        if (ce == cudaSuccess && ns > 0) ce = launch_timepass_multi(prec, d_tp_loop[par], d_pre_tp, ns, tot_tp, st);
         if (ce == cudaSuccess) ce = launch_scalar_multi(2, d_sc_gamma, ni, st);
         if (ce == cudaSuccess) ce = launch_w_update_multi(d_w_loop[par], ni, st);
-        if (ce == cudaSuccess) ce = launch_conv_multi(arith, d_cv_res, d_pre_conv, ni, tot_conv, st);
+        if (ce == cudaSuccess) ce = big_conv(par, true);
+        if (ce == cudaSuccess && ns > 0) ce = launch_conv_multi(arith, d_cv_res, d_pre_conv, ns, tot_conv, st);
         if (ce == cudaSuccess) ce = launch_scalar_multi(3, d_sc_check, ni, st);
       }
       e = cudaStreamEndCapture(st, &graph);
@@ -456,8 +535,9 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
       if (e != cudaSuccess || *run_count_h == 0 || issued >= maxit) break;
     }
     // exit DSTs: u = (I x U) x_hat
-    for (int ax = 0; ax < 3 && e == cudaSuccess; ++ax)
-      e = launch_dst_multi(dprec, d_dst_out[ax], d_pre_dst[ax], ni, tot_dst[ax], st);
+    if (e == cudaSuccess) e = big_dst(false);
+    for (int ax = 0; ax < 3 && e == cudaSuccess && ns > 0; ++ax)
+      e = launch_dst_multi(dprec, d_dst_out[ax], d_pre_dst[ax], ns, tot_dst[ax], st);
     std::vector<MinresDev> sh(ni);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sh.data(), states, sizeof(MinresDev) * ni, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -74,3 +74,34 @@ def test_batched_equals_single_solves_and_splits_waves(B, monkeypatch):
             assert infos[k]["iters"] == inf1["iters"]
             assert rel(to_host(ud[s][r]), to_host(u1)) <= 1e-12
             k += 1
+
+
+@pytest.mark.parametrize("form", [
+    dict(precision=64, matvec_arith=1, alpha=1e-8),
+    dict(precision=32, matvec_arith=2, alpha=1e-3),
+], ids=["f64", "f32_prec"])
+def test_batched_big_and_small_items_equal_single_solves(B, form):
+    """Items of at least 2^21 unknowns run their FFT phases as single-item launches inside the
+    batched graph, the smaller ones share the multi-item launches: both kinds reproduce the single
+    solves (same iterations, same solution)."""
+    probs = [fractional_problem(2, 127, 256, 0.6), fractional_problem(1, 63, 64, 0.4),
+             fractional_problem(2, 31, 128, 0.8)]
+    assert probs[0].n >= 1 << 21 and probs[1].n < 1 << 21 and probs[2].n < 1 << 21
+    fs = [[rhs_uniform(p.n, 50 + 10 * s + r) for r in range(2)] for s, p in enumerate(probs)]
+    fd = [[to_dev(f) for f in row] for row in fs]
+    ud = [[to_dev(np.zeros_like(f)) for f in row] for row in fs]
+    st, infos = B.bltt_solve_batched(probs, fd, ud, alpha=[form["alpha"]] * len(probs), tol=1e-8,
+                                     maxit=100, precision=form["precision"],
+                                     matvec_arith=form["matvec_arith"])
+    assert st == 0, [i["status"] for i in infos]
+    k = 0
+    for s, p in enumerate(probs):
+        sol = B.Solver(p)
+        for r in range(2):
+            u1, inf1 = sol.solve(fd[s][r], alpha=form["alpha"], tol=1e-8, maxit=100,
+                                 precision=form["precision"], basis=1,
+                                 matvec_arith=form["matvec_arith"])
+            assert infos[k]["relres_true"] <= 1e-8
+            assert infos[k]["iters"] == inf1["iters"], (s, r, infos[k]["iters"], inf1["iters"])
+            assert rel(to_host(ud[s][r]), to_host(u1)) <= 1e-10
+            k += 1
