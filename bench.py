@@ -308,20 +308,27 @@ FORMS = {
 
 
 def run_once(args):
-    """One solve of the headline workload in one form, direct launches (for ncu captures)."""
+    """One solve of the headline workload in one form, direct launches (for ncu captures).
+    --m 127 keeps the kernels and FFT lengths of the 2-D N = 1024 workload on a quarter of its
+    modes (132 MB per vector, still above L2), for captures that replay each kernel many times."""
     import torch
     from paper_2307_07749_gb300 import build
     build.build()
     import paper_2307_07749_gb300 as B
-    from workloads import workload, rhs_uniform
-    prob, _ = workload(WORKLOAD)
+    from workloads import workload, rhs_uniform, fractional_problem
+    if args.m == 255:
+        prob, _ = workload(WORKLOAD)
+        name = WORKLOAD
+    else:
+        prob = fractional_problem(2, args.m, 1024, 0.7)
+        name = f"frac2d_N1024_m{args.m}_g0.7"
     s = B.Solver(prob)
     fd = torch.from_numpy(rhs_uniform(prob.n, 2)).cuda()
     fm = FORMS[args.form]
     u, info = s.solve(fd, alpha=fm["alpha"], tol=TOL, maxit=100, precision=fm["precision"],
                       basis=fm["basis"], matvec_arith=fm["arith"], graph=False)
     torch.cuda.synchronize()
-    print(json.dumps({"workload": WORKLOAD, "form": args.form, "iters": info["iters"],
+    print(json.dumps({"workload": name, "form": args.form, "iters": info["iters"],
                       "status": info["status"], "relres_true": info["relres_true"]}))
     return 0 if info["status"] == 0 else 1
 
@@ -449,6 +456,8 @@ def main():
                     help="frac2d: the headline line; batched / alpha: supplementary reports; "
                          "once: a single solve of the headline workload (for ncu captures)")
     ap.add_argument("--form", default="chosen", choices=["chosen", "plain_f64", "f32x2_all", "f32_physical"])
+    ap.add_argument("--m", type=int, default=255, choices=[63, 127, 255],
+                    help="--workload once: interior points per axis (255: the headline workload)")
     ap.add_argument("--alpha-train", type=int, default=2000)
     ap.add_argument("--alpha-heldout", type=int, default=256)
     args = ap.parse_args()
