@@ -44,6 +44,18 @@ __device__ __forceinline__ dfl df_add(dfl a, dfl b) {
 }
 __device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
 
+// a + b without the final renormalisation: (s, e) with s = fl(a.hi + b.hi) and e its exact error
+// plus the trailing parts.  The pair still represents the sum to the same accuracy; |e| may reach
+// a few ulp(s), which costs about one bit in the next operation.  For intermediate sums whose
+// next use is another addition or multiplication.
+__device__ __forceinline__ dfl df_add_nr(dfl a, dfl b) {
+  float s = __fadd_rn(a.hi, b.hi);
+  float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  return {s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
+}
+__device__ __forceinline__ dfl df_sub_nr(dfl a, dfl b) { return df_add_nr(a, df_neg(b)); }
+
 // a * b: exact product of the leading parts by FMA, cross terms folded into the error
 __device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
   float p = __fmul_rn(a.hi, b.hi);
@@ -72,6 +84,23 @@ __device__ __forceinline__ dfl df_dot2(dfl a, dfl b, dfl c, dfl d) {
   return {h, __fsub_rn(err, __fsub_rn(h, s))};
 }
 
+// a * b + c * d without the final renormalisation (see df_add_nr)
+__device__ __forceinline__ dfl df_dot2_nr(dfl a, dfl b, dfl c, dfl d) {
+  float p1 = __fmul_rn(a.hi, b.hi);
+  float e1 = __fmaf_rn(a.hi, b.hi, -p1);
+  float p2 = __fmul_rn(c.hi, d.hi);
+  float e2 = __fmaf_rn(c.hi, d.hi, -p2);
+  float s = __fadd_rn(p1, p2);
+  float bb = __fsub_rn(s, p1);
+  float es = __fadd_rn(__fsub_rn(p1, __fsub_rn(s, bb)), __fsub_rn(p2, bb));
+  float err = __fadd_rn(__fadd_rn(e1, e2), es);
+  err = __fmaf_rn(a.hi, b.lo, err);
+  err = __fmaf_rn(a.lo, b.hi, err);
+  err = __fmaf_rn(c.hi, d.lo, err);
+  err = __fmaf_rn(c.lo, d.hi, err);
+  return {s, err};
+}
+
 // ------------------------------------------------------------------------------------------
 // Arithmetic traits of the FFT engine.  V: a complex value; R: its real scalar.
 struct ArithD {
@@ -87,6 +116,8 @@ struct ArithD {
   }
   static __device__ __forceinline__ V add(V a, V b) { return make_double2(a.x + b.x, a.y + b.y); }
   static __device__ __forceinline__ V sub(V a, V b) { return make_double2(a.x - b.x, a.y - b.y); }
+  static __device__ __forceinline__ V add_nr(V a, V b) { return add(a, b); }
+  static __device__ __forceinline__ V sub_nr(V a, V b) { return sub(a, b); }
   static __device__ __forceinline__ V conj(V a) { return make_double2(a.x, -a.y); }
   static __device__ __forceinline__ V mul(V a, V b) {
     return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
@@ -94,6 +125,8 @@ struct ArithD {
   static __device__ __forceinline__ V mulc(V a, V b) {   // a * conj(b)
     return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
   }
+  static __device__ __forceinline__ V mul_nr(V a, V b) { return mul(a, b); }
+  static __device__ __forceinline__ V mulc_nr(V a, V b) { return mulc(a, b); }
   template <bool INV> static __device__ __forceinline__ V rot(V a) {   // * -i (fwd), * i (inv)
     return INV ? make_double2(-a.y, a.x) : make_double2(a.y, -a.x);
   }
@@ -127,6 +160,8 @@ struct ArithF {
   }
   static __device__ __forceinline__ V add(V a, V b) { return make_float2(a.x + b.x, a.y + b.y); }
   static __device__ __forceinline__ V sub(V a, V b) { return make_float2(a.x - b.x, a.y - b.y); }
+  static __device__ __forceinline__ V add_nr(V a, V b) { return add(a, b); }
+  static __device__ __forceinline__ V sub_nr(V a, V b) { return sub(a, b); }
   static __device__ __forceinline__ V conj(V a) { return make_float2(a.x, -a.y); }
   static __device__ __forceinline__ V mul(V a, V b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -134,6 +169,8 @@ struct ArithF {
   static __device__ __forceinline__ V mulc(V a, V b) {
     return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
   }
+  static __device__ __forceinline__ V mul_nr(V a, V b) { return mul(a, b); }
+  static __device__ __forceinline__ V mulc_nr(V a, V b) { return mulc(a, b); }
   template <bool INV> static __device__ __forceinline__ V rot(V a) {
     return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
   }
@@ -179,12 +216,22 @@ struct ArithDF {
   static __device__ __forceinline__ V pack(dfl r, dfl i) { return make_float4(r.hi, r.lo, i.hi, i.lo); }
   static __device__ __forceinline__ V add(V a, V b) { return pack(df_add(re(a), re(b)), df_add(im(a), im(b))); }
   static __device__ __forceinline__ V sub(V a, V b) { return pack(df_sub(re(a), re(b)), df_sub(im(a), im(b))); }
+  // without the final renormalisation (intermediate sums of a butterfly)
+  static __device__ __forceinline__ V add_nr(V a, V b) { return pack(df_add_nr(re(a), re(b)), df_add_nr(im(a), im(b))); }
+  static __device__ __forceinline__ V sub_nr(V a, V b) { return pack(df_sub_nr(re(a), re(b)), df_sub_nr(im(a), im(b))); }
   static __device__ __forceinline__ V conj(V a) { return make_float4(a.x, a.y, -a.z, -a.w); }
   static __device__ __forceinline__ V mul(V a, V b) {
     return pack(df_dot2(re(a), re(b), df_neg(im(a)), im(b)), df_dot2(re(a), im(b), im(a), re(b)));
   }
   static __device__ __forceinline__ V mulc(V a, V b) {
     return pack(df_dot2(re(a), re(b), im(a), im(b)), df_dot2(im(a), re(b), df_neg(re(a)), im(b)));
+  }
+  // products that only feed the first (non-renormalising) level of a butterfly
+  static __device__ __forceinline__ V mul_nr(V a, V b) {
+    return pack(df_dot2_nr(re(a), re(b), df_neg(im(a)), im(b)), df_dot2_nr(re(a), im(b), im(a), re(b)));
+  }
+  static __device__ __forceinline__ V mulc_nr(V a, V b) {
+    return pack(df_dot2_nr(re(a), re(b), im(a), im(b)), df_dot2_nr(im(a), re(b), df_neg(re(a)), im(b)));
   }
   template <bool INV> static __device__ __forceinline__ V rot(V a) {
     return INV ? make_float4(-a.z, -a.w, a.x, a.y) : make_float4(a.z, a.w, -a.x, -a.y);
@@ -243,8 +290,9 @@ template <class A, bool INV>
 __device__ __forceinline__ void dft4(typename A::V& x0, typename A::V& x1, typename A::V& x2,
                                      typename A::V& x3) {
   using V = typename A::V;
-  const V t0 = A::add(x0, x2), t1 = A::sub(x0, x2), t2 = A::add(x1, x3);
-  const V t3 = A::template rot<INV>(A::sub(x1, x3));
+  // the first level's sums are not renormalised: they only feed the second level
+  const V t0 = A::add_nr(x0, x2), t1 = A::sub_nr(x0, x2), t2 = A::add_nr(x1, x3);
+  const V t3 = A::template rot<INV>(A::sub_nr(x1, x3));
   x0 = A::add(t0, t2);
   x1 = A::add(t1, t3);
   x2 = A::sub(t0, t2);
@@ -256,15 +304,15 @@ template <class A, bool INV>
 __device__ __forceinline__ void dft16(typename A::V (&v)[16]) {
 #pragma unroll
   for (int b = 0; b < 4; ++b) dft4<A, INV>(v[b], v[b + 4], v[b + 8], v[b + 12]);
-  v[5] = A::mul(v[5], w16<A, 1, INV>());
-  v[6] = A::mul(v[6], w16<A, 2, INV>());
-  v[7] = A::mul(v[7], w16<A, 3, INV>());
-  v[9] = A::mul(v[9], w16<A, 2, INV>());
+  v[5] = A::mul_nr(v[5], w16<A, 1, INV>());
+  v[6] = A::mul_nr(v[6], w16<A, 2, INV>());
+  v[7] = A::mul_nr(v[7], w16<A, 3, INV>());
+  v[9] = A::mul_nr(v[9], w16<A, 2, INV>());
   v[10] = A::template rot<INV>(v[10]);
-  v[11] = A::mul(v[11], w16<A, 6, INV>());
-  v[13] = A::mul(v[13], w16<A, 3, INV>());
-  v[14] = A::mul(v[14], w16<A, 6, INV>());
-  v[15] = A::mul(v[15], w16<A, 9, INV>());
+  v[11] = A::mul_nr(v[11], w16<A, 6, INV>());
+  v[13] = A::mul_nr(v[13], w16<A, 3, INV>());
+  v[14] = A::mul_nr(v[14], w16<A, 6, INV>());
+  v[15] = A::mul_nr(v[15], w16<A, 9, INV>());
 #pragma unroll
   for (int c = 0; c < 4; ++c) dft4<A, INV>(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
 }
@@ -351,7 +399,7 @@ __device__ __forceinline__ void fft_columns(typename A::V* buf, int L, int log2L
 #pragma unroll
           for (int r = 1; r < 4; ++r) {
             const V w = tw[r * e];
-            v[s][r] = INV ? A::mulc(v[s][r], w) : A::mul(v[s][r], w);
+            v[s][r] = INV ? A::mulc_nr(v[s][r], w) : A::mul_nr(v[s][r], w);
           }
         }
         dft4<A, INV>(v[s][0], v[s][1], v[s][2], v[s][3]);
@@ -390,7 +438,7 @@ __device__ __forceinline__ void fft_columns(typename A::V* buf, int L, int log2L
 #pragma unroll
           for (int r = 1; r < 16; ++r) {
             const V w = tw[r * e];
-            v[s][r] = INV ? A::mulc(v[s][r], w) : A::mul(v[s][r], w);
+            v[s][r] = INV ? A::mulc_nr(v[s][r], w) : A::mul_nr(v[s][r], w);
           }
         }
         dft16<A, INV>(v[s]);
