@@ -22,15 +22,15 @@ __device__ __forceinline__ void load_coef(const Combine& cb, double& c0, double&
 }
 
 // v = in0[e] + c1 in1[e] + c2 in2[e] (FP64); optionally stored to vout[e] (vout may alias
-// in1/in2: the same thread reads before it writes).  When v is stored, the inputs are streamed
-// (evict-first) so that v itself is more likely to stay in L2 for the dot product at the end of
-// the tile.
+// in1/in2: the same thread reads before it writes).  The vector loads bypass L1 (which keeps the
+// tables: twiddles, spectra, row scales); when v is stored, the inputs are streamed (evict-first)
+// so that v itself is more likely to stay in L2 for the dot product at the end of the tile.
 __device__ __forceinline__ double combine_at(const Combine& cb, long long e, double, double c1,
                                              double c2) {
   if (!cb.vout) {
-    double v = cb.in0[e];
-    if (cb.in1) v = fma(c1, cb.in1[e], v);
-    if (cb.in2) v = fma(c2, cb.in2[e], v);
+    double v = __ldcg(cb.in0 + e);
+    if (cb.in1) v = fma(c1, __ldcg(cb.in1 + e), v);
+    if (cb.in2) v = fma(c2, __ldcg(cb.in2 + e), v);
     return v;
   }
   double v = __ldcs(cb.in0 + e);
@@ -237,7 +237,7 @@ __device__ __forceinline__ void dst_tile(long long nlines, int m, long long inne
         const long long o = s_out[c];
         if (o >= 0) {
           ix[u] = o + (long long)k * inner;
-          if (dwsrc) dw[u] = dwsrc[ix[u]];
+          if (dwsrc) dw[u] = __ldcs(dwsrc + ix[u]);
         }
       }
     }
@@ -404,7 +404,7 @@ __device__ __forceinline__ void timepass_tile(const OpTables& op, const PrecTabl
       const int e = e0 + u * NT;
       const int p = e >> log2W, c = e & (W - 1);
       dw[u] = 0.0;
-      if (dwsrc && e < total && g0 + c < M) dw[u] = dwsrc[(long long)p * M + g0 + c];
+      if (dwsrc && e < total && g0 + c < M) dw[u] = __ldcs(dwsrc + (long long)p * M + g0 + c);
     }
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
@@ -539,7 +539,7 @@ __device__ __forceinline__ void conv_tile(const OpTables& op, int spectral, int 
     for (int u = 0; u < kBatch; ++u) {
       const int e = e0 + u * NT;
       const int p = e >> log2W, c = e & (W - 1);
-      v[u] = (e < total && g0 + c < M) ? x[(long long)p * M + g0 + c] : 0.0;
+      v[u] = (e < total && g0 + c < M) ? __ldcg(x + (long long)p * M + g0 + c) : 0.0;   // L2 only
     }
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
@@ -603,8 +603,8 @@ __device__ __forceinline__ void conv_tile(const OpTables& op, int spectral, int 
       if (e < total && g0 + c < M) {
         const int to = flip ? (N - 1 - t) : t;
         const long long idx = (long long)to * M + g0 + c;
-        if (mode != MV_STORE) pre[u] = rhs[idx];
-        else if (partials) pre[u] = x[idx];
+        if (mode != MV_STORE) pre[u] = __ldcs(rhs + idx);
+        else if (partials) pre[u] = __ldcs(x + idx);
       }
     }
 #pragma unroll
