@@ -204,7 +204,7 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
       for (int ax = 0; ax < 3; ++ax) {
         if (ax < it.d) {
           const long long nl = it.n / it.m[ax];
-          const int nc = tile_columns(nl, 2 * (it.m[ax] + 1));
+          const int nc = tile_columns(nl, it.m[ax] + 1);
           it.l2nc_dst[ax] = ilog2ll(nc);
           it.tiles_dst[ax] = (nl + 2 * nc - 1) / (2 * nc);
           it.maxtiles = std::max(it.maxtiles, it.tiles_dst[ax]);
@@ -338,12 +338,12 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
         DstItem di{}, dq{};
         di.N = it.N; di.M = it.M;
         if (ax < it.d) {
-          di.m = it.m[ax]; di.P = it.m[ax] + 1; di.log2L = ilog2ll(2 * di.P);
+          di.m = it.m[ax]; di.P = it.m[ax] + 1; di.log2P = ilog2ll(di.P);
           di.nlines = it.n / it.m[ax]; di.inner = inner; di.log2NC = it.l2nc_dst[ax];
           di.tw = dprec == PREC_DF ? (const void*)op.tw_dst_df[ax] : (const void*)op.tw_dst[ax];
           inner *= it.m[ax];
         } else {
-          di.nlines = 0; di.inner = 1; di.m = 1; di.P = 2; di.log2L = 2;
+          di.nlines = 0; di.inner = 1; di.m = 1; di.P = 2; di.log2P = 1;
         }
         dq = di;
         di.cb.in0 = (ax == 0) ? it.f : it.b;

@@ -110,6 +110,7 @@ struct ArithD {
   static __device__ __forceinline__ Sc make_sc(double s) { return s; }
   static __device__ __forceinline__ Sc row_sc(const double* t64, const float*, int p) { return t64[p]; }
   static __device__ __forceinline__ V scale_sc(V a, Sc s) { return make_double2(a.x * s, a.y * s); }
+  static __device__ __forceinline__ Sc neg_imag_sc(V a) { return -a.y; }   // -Im a as a scale
   static __device__ __forceinline__ double part_sc(V a, int comp, Sc s) { return (comp ? a.y : a.x) * s; }
   static __device__ __forceinline__ void put_sc(V* buf, int idx, int comp, double x, Sc s) {
     reinterpret_cast<double*>(buf)[2 * idx + comp] = x * s;
@@ -154,6 +155,7 @@ struct ArithF {
   static __device__ __forceinline__ Sc make_sc(double s) { return (float)s; }
   static __device__ __forceinline__ Sc row_sc(const double*, const float* t32, int p) { return t32[p]; }
   static __device__ __forceinline__ V scale_sc(V a, Sc s) { return make_float2(a.x * s, a.y * s); }
+  static __device__ __forceinline__ Sc neg_imag_sc(V a) { return -a.y; }
   static __device__ __forceinline__ double part_sc(V a, int comp, Sc s) { return f2d_bits((comp ? a.y : a.x) * s); }
   static __device__ __forceinline__ void put_sc(V* buf, int idx, int comp, double x, Sc s) {
     reinterpret_cast<float*>(buf)[2 * idx + comp] = d2f_bits(x) * s;
@@ -204,6 +206,7 @@ struct ArithDF {
   static __device__ __forceinline__ V scale_sc(V a, Sc s) {
     return pack(df_mul(dfl{a.x, a.y}, s), df_mul(dfl{a.z, a.w}, s));
   }
+  static __device__ __forceinline__ Sc neg_imag_sc(V a) { return {-a.z, -a.w}; }
   static __device__ __forceinline__ double part_sc(V a, int comp, Sc s) {
     return df_to(df_mul(comp ? dfl{a.z, a.w} : dfl{a.x, a.y}, s));
   }
@@ -324,7 +327,8 @@ __device__ __forceinline__ void dft16(typename A::V (&v)[16]) {
 //
 // buf holds NC = 2^log2NC independent complex columns of length L, element (p, c) at
 // buf[p * NC + c] (or at buf[p * NC + (c ^ (p mod NC))] with SWZ).  tw holds
-// w_L^k = exp(-2 pi i k / L), k < L.  skip_radix2: the caller has already applied the first
+// w_L^k = exp(-2 pi i k / L), k < L, at tw[k << tw_shift] (a table of a 2^tw_shift times longer
+// transform serves at that stride).  skip_radix2: the caller has already applied the first
 // radix-2 pass (used when the upper half of the input is zero: the pass only duplicates).
 // Forward: X_k = sum_j x_j w^{jk}; inverse (INV): conjugate twiddles, no 1/L scaling.  Every
 // pass loads all of its butterfly inputs into registers, synchronises, then writes, so the
@@ -335,7 +339,8 @@ __device__ __forceinline__ void dft16(typename A::V (&v)[16]) {
 // (j - k) R + k + q Ns.
 template <class A, int NT, int CAP, bool INV, bool SWZ = false>
 __device__ __forceinline__ void fft_columns(typename A::V* buf, int L, int log2L, int log2NC,
-                            const typename A::V* __restrict__ tw, bool skip_radix2 = false) {
+                            const typename A::V* __restrict__ tw, bool skip_radix2 = false,
+                            int tw_shift = 0) {
   using V = typename A::V;
   constexpr int IPT2 = (CAP / 2 + NT - 1) / NT;
   constexpr int IPT4 = (CAP / 4 + NT - 1) / NT;
@@ -395,7 +400,7 @@ __device__ __forceinline__ void fft_columns(typename A::V* buf, int L, int log2L
         const int c = it & cmask, j = it >> log2NC;
         const int k = j & (Ns - 1);
         if (k != 0) {
-          const int e = k << tstep_log;
+          const int e = k << (tstep_log + tw_shift);
 #pragma unroll
           for (int r = 1; r < 4; ++r) {
             const V w = tw[r * e];
@@ -434,7 +439,7 @@ __device__ __forceinline__ void fft_columns(typename A::V* buf, int L, int log2L
         const int c = it & cmask, j = it >> log2NC;
         const int k = j & (Ns - 1);
         if (k != 0) {
-          const int e = k << tstep_log;
+          const int e = k << (tstep_log + tw_shift);
 #pragma unroll
           for (int r = 1; r < 16; ++r) {
             const V w = tw[r * e];

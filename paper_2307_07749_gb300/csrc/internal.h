@@ -145,7 +145,7 @@ struct TpItem {
 };
 struct DstItem {
   long long nlines, inner, N, M;
-  int m, P, log2L, log2NC, flip, pad;
+  int m, P, log2P, log2NC, flip, pad;   // DST-I length m, FFT length P = m + 1
   Combine cb;
   double* out;
   const double* dot_with;

@@ -146,24 +146,35 @@ template <class A> struct TileCfg {
 };
 
 // ============================================================================================
-// DST-I along one spatial axis (Steps 1 and 3 of Sec. 5.1).  Two real lines x_a, x_b share one
-// complex FFT of length 2P (P = m+1) of their odd extensions [0, x, 0, -rev(x)]; then
-// S x_a = -Im(Z_{k+1}) / sqrt(2P) and S x_b = Re(Z_{k+1}) / sqrt(2P), S the normalised DST-I.
+// DST-I along one spatial axis (Steps 1 and 3 of Sec. 5.1), by one real FFT of length P = m+1 per
+// line.  With S_k = sum_{j=1}^{m} x_j sin(pi j k/P), y_j = sin(pi j/P)(x_j + x_{P-j}) +
+// (x_j - x_{P-j})/2 (x_0 = x_P = 0) and Y = FFT_P(y):
+//   S_{2k} = -Im Y_k,   S_{2k+1} - S_{2k-1} = Re Y_k   (S_{-1} = -S_1, so S_1 = Re Y_0 / 2),
+// because sin(a+b) - sin(a-b) = 2 cos(a) sin(b), and in each sum over j the part that is odd under
+// j -> P-j cancels.  The orthonormal DST-I is sqrt(2/P) S.  Two lines share one complex FFT of
+// x_a + i x_b: R_k = (F_k + F_{P-k})/2 carries (Re Ya_k, Re Yb_k) and E_k = i (F_k - F_{P-k})/2
+// carries (-Im Ya_k, -Im Yb_k); the odd outputs are prefix sums of R along k, per column, taken
+// in shared memory.  The FFT reads the length-2P twiddle table at stride 2, and sin(pi j/P) is
+// -Im w_{2P}^j from the same table.
 // Lines: line g has elements base(g) + p*inner, base(g) = (g/inner)*(m*inner) + g%inner.
 template <class A, bool SWZ>
-__device__ __forceinline__ void dst_tile(long long nlines, int m, long long inner, int P, int log2L,
+__device__ __forceinline__ void dst_tile(long long nlines, int m, long long inner, int P, int log2P,
                                          int log2NC, const Combine& cb, double* out, int flip,
                                          int N, long long M, const double* dot_with,
                                          double* partials, const typename A::V* __restrict__ tw,
                                          long long tile) {
   constexpr int NT = TileCfg<A>::NT, CAP = TileCfg<A>::CAP;
+  constexpr int CH = 8;                           // rows per prefix-sum chunk
+  constexpr int IPT = (CAP / 2 + NT - 1) / NT;    // (k, column) items per thread, k < P/2
   using V = typename A::V;
+  using Sc = typename A::Sc;
   __syncthreads();   // the previous tile of a persistent block may still read shared memory
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* buf = reinterpret_cast<V*>(smem_raw);
   __shared__ double red[32];
   __shared__ long long s_in[kMaxCols], s_out[kMaxCols];
-  const int L = 2 * P, NC = 1 << log2NC, W = 2 * NC;
+  __shared__ V s_tot[NT];                         // prefix-sum chunk totals
+  const int NC = 1 << log2NC, W = 2 * NC, half = P >> 1;
   const long long g0 = tile * W;
   for (int c = threadIdx.x; c < W; c += NT) {
     long long g = g0 + c;
@@ -178,14 +189,14 @@ __device__ __forceinline__ void dst_tile(long long nlines, int m, long long inne
   }
   const int cmask = NC - 1;
   auto at = [&](int p, int cc) { return p * NC + (SWZ ? (cc ^ (p & cmask)) : cc); };
-  for (int e = threadIdx.x; e < 2 * NC; e += NT)
-    buf[at((e & 1) ? P : 0, e >> 1)] = A::zero();
+  for (int cc = threadIdx.x; cc < NC; cc += NT) buf[at(0, cc)] = A::zero();   // x_0 = 0
   __syncthreads();
   double c0, c1, c2;
   load_coef(cb, c0, c1, c2);
   const bool contiguous = (inner == 1);
   const float inv_m = 1.0f / (float)m;
   const int total = m * W, log2W = log2NC + 1;
+  // x_j (j = p + 1) of line c into row j, column c/2, component c%2
   for (int e0 = threadIdx.x; e0 < total; e0 += kBatch * NT) {
     double v[kBatch];
     int cs[kBatch], ps[kBatch];
@@ -205,18 +216,87 @@ __device__ __forceinline__ void dst_tile(long long nlines, int m, long long inne
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
       const int e = e0 + u * NT;
-      if (e < total) {
-        const int cc = cs[u] >> 1, comp = cs[u] & 1;
-        A::put_pm(buf, at(ps[u] + 1, cc), at(L - 1 - ps[u], cc), comp, v[u]);
+      if (e < total) A::put(buf, at(ps[u] + 1, cs[u] >> 1), cs[u] & 1, v[u]);
+    }
+  }
+  __syncthreads();
+  // y_j and y_{P-j} from x_j and x_{P-j}, in place (each item owns both rows)
+  const Sc halfsc = A::make_sc(0.5);
+  for (int it = threadIdx.x; it < (half << log2NC); it += NT) {
+    const int cc = it & cmask, j = 1 + (it >> log2NC), jm = P - j;
+    const V xa = buf[at(j, cc)], xb = buf[at(jm, cc)];
+    const V sm = A::scale_sc(A::add(xa, xb), A::neg_imag_sc(tw[j]));   // sin(pi j/P) (x_j + x_{P-j})
+    const V df = A::scale_sc(A::sub(xa, xb), halfsc);
+    buf[at(j, cc)] = A::add(sm, df);
+    if (jm != j) buf[at(jm, cc)] = A::sub(sm, df);
+  }
+  __syncthreads();
+  fft_columns<A, NT, CAP, false, SWZ>(buf, P, log2P, log2NC, tw, false, 1);   // w_P = w_{2P}^2
+  // R_k into rows k < P/2 (R_0 = F_0/2: the halved first term of the odd outputs), E_k into
+  // rows P/2 + k; all reads before the barrier, all writes after
+  {
+    V rr[IPT], ee[IPT];
+#pragma unroll
+    for (int s = 0; s < IPT; ++s) {
+      const int it = threadIdx.x + s * NT;
+      if (it < (half << log2NC)) {
+        const int cc = it & cmask, k = it >> log2NC;
+        const V fk = buf[at(k, cc)], fm = buf[at((P - k) & (P - 1), cc)];
+        rr[s] = A::scale_sc(k == 0 ? fk : A::add(fk, fm), halfsc);
+        ee[s] = A::template rot<true>(A::scale_sc(A::sub(fk, fm), halfsc));
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < IPT; ++s) {
+      const int it = threadIdx.x + s * NT;
+      if (it < (half << log2NC)) {
+        const int cc = it & cmask, k = it >> log2NC;
+        buf[at(k, cc)] = rr[s];
+        buf[at(half + k, cc)] = ee[s];
       }
     }
   }
   __syncthreads();
-  fft_columns<A, NT, CAP, false, SWZ>(buf, L, log2L, log2NC, tw);
-  const typename A::Sc scale = A::make_sc(rsqrt((double)L));
-  const typename A::Sc nscale = A::make_sc(-rsqrt((double)L));
+  // inclusive prefix sums of R along k in every column: chunks of ch rows (one per thread), the
+  // chunk totals scanned per column in order, then added back
+  const int ch = half < CH ? half : CH;
+  const int cpc = half / ch;                      // chunks per column
+  const int nchunks = cpc << log2NC;              // <= NT: P NC <= CAP
+  const int t = threadIdx.x;
+  const int tcc = t & cmask, tq = t >> log2NC;
+  if (t < nchunks) {
+    V run = A::zero();
+    for (int i = 0; i < ch; ++i) {
+      const int k = tq * ch + i;
+      run = A::add(run, buf[at(k, tcc)]);
+      buf[at(k, tcc)] = run;
+    }
+    s_tot[t] = run;
+  }
+  __syncthreads();
+  if (t < NC) {
+    V off = A::zero();
+    for (int q = 0; q < cpc; ++q) {
+      const int idx = (q << log2NC) + t;
+      const V tv = s_tot[idx];
+      s_tot[idx] = off;
+      off = A::add(off, tv);
+    }
+  }
+  __syncthreads();
+  if (t < nchunks && tq > 0) {
+    const V off = s_tot[t];
+    for (int i = 0; i < ch; ++i) {
+      const int k = tq * ch + i;
+      buf[at(k, tcc)] = A::add(buf[at(k, tcc)], off);
+    }
+  }
+  __syncthreads();
+  const Sc scale = A::make_sc(sqrt(2.0 / (double)P));
   // read-out in batches: the global loads of a batch (the dot-product partner) are all issued
   // before the first use, so that their latencies overlap.  dot_with == out asks for ||out||^2.
+  // Output j = p + 1: S_j from row j/2 (j odd: the prefix sums) or row P/2 + j/2 (j even).
   const bool self_dot = (dot_with == out);
   const double* dwsrc = self_dot ? nullptr : dot_with;
   double acc = 0.0;
@@ -244,9 +324,9 @@ __device__ __forceinline__ void dst_tile(long long nlines, int m, long long inne
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
       if (ix[u] >= 0) {
-        const int c = cs[u];
-        const V z = buf[at(ks[u] + 1, c >> 1)];
-        const double val = (c & 1) ? A::part_sc(z, 0, scale) : A::part_sc(z, 1, nscale);
+        const int c = cs[u], j = ks[u] + 1;
+        const V z = buf[at((j & 1) ? (j >> 1) : half + (j >> 1), c >> 1)];
+        const double val = A::part_sc(z, c & 1, scale);
         out[ix[u]] = val;
         acc = fma(val, self_dot ? val : dw[u], acc);
       }
@@ -260,11 +340,11 @@ __device__ __forceinline__ void dst_tile(long long nlines, int m, long long inne
 
 template <class A, bool SWZ>
 __global__ void __launch_bounds__(TileCfg<A>::NT, TileCfg<A>::MINB)
-k_dst(long long nlines, int m, long long inner, int P, int log2L, int log2NC, Combine cb,
+k_dst(long long nlines, int m, long long inner, int P, int log2P, int log2NC, Combine cb,
       double* out, int flip, int N, long long M, const double* dot_with, double* partials,
       const typename A::V* __restrict__ tw, const int* phase, int want) {
   if (skip_phase(phase, want)) return;
-  dst_tile<A, SWZ>(nlines, m, inner, P, log2L, log2NC, cb, out, flip, N, M, dot_with, partials,
+  dst_tile<A, SWZ>(nlines, m, inner, P, log2P, log2NC, cb, out, flip, N, M, dot_with, partials,
                    tw, blockIdx.x);
 }
 
@@ -950,15 +1030,15 @@ template <class A> static cudaError_t ensure_smem_dst() {
 
 template <class A>
 static void run_dst(const OpTables& op, long long grid, long long nlines, int m, long long inner,
-                    int P, int L, int log2NC, const Combine& in, double* out, int flip,
+                    int P, int log2NC, const Combine& in, double* out, int flip,
                     const double* dot_with, double* partials, const typename A::V* tw,
                     const int* phase, cudaStream_t st) {
   const size_t smem = TileCfg<A>::CAP * sizeof(typename A::V);
   if (inner == 1)
-    k_dst<A, true><<<(unsigned)grid, TileCfg<A>::NT, smem, st>>>(nlines, m, inner, P, ilog2(L), log2NC,
+    k_dst<A, true><<<(unsigned)grid, TileCfg<A>::NT, smem, st>>>(nlines, m, inner, P, ilog2(P), log2NC,
         in, out, flip, op.N, op.M, dot_with, partials, tw, phase, PH_RUN);
   else
-    k_dst<A, false><<<(unsigned)grid, TileCfg<A>::NT, smem, st>>>(nlines, m, inner, P, ilog2(L), log2NC,
+    k_dst<A, false><<<(unsigned)grid, TileCfg<A>::NT, smem, st>>>(nlines, m, inner, P, ilog2(P), log2NC,
         in, out, flip, op.N, op.M, dot_with, partials, tw, phase, PH_RUN);
 }
 template <class A> static cudaError_t ensure_smem_tp() {
@@ -995,24 +1075,24 @@ cudaError_t launch_dst(const OpTables& op, int axis, int prec, const Combine& in
   long long inner = 1;
   for (int a = 0; a < axis; ++a) inner *= op.m[a];
   const long long nlines = (long long)op.N * op.M / m;
-  const int P = m + 1, L = 2 * P;
-  if (L > kCap) return cudaErrorInvalidValue;      // the FFT must fit one tile
-  const int NC = tile_columns(nlines, L);
+  const int P = m + 1;
+  if (P > kCap) return cudaErrorInvalidValue;      // the FFT (length P) must fit one tile
+  const int NC = tile_columns(nlines, P);
   const int log2NC = ilog2(NC);
   const long long grid = (nlines + 2 * NC - 1) / (2 * NC);
   if (nparts) *nparts = (int)grid;
   cudaError_t e;
   if (prec == PREC_F64) {
     if ((e = ensure_smem_dst<ArithD>()) != cudaSuccess) return e;
-    run_dst<ArithD>(op, grid, nlines, m, inner, P, L, log2NC, in, out, flip, dot_with, partials,
+    run_dst<ArithD>(op, grid, nlines, m, inner, P, log2NC, in, out, flip, dot_with, partials,
                     op.tw_dst[axis], phase, st);
   } else if (prec == PREC_DF) {
     if ((e = ensure_smem_dst<ArithDF>()) != cudaSuccess) return e;
-    run_dst<ArithDF>(op, grid, nlines, m, inner, P, L, log2NC, in, out, flip, dot_with, partials,
+    run_dst<ArithDF>(op, grid, nlines, m, inner, P, log2NC, in, out, flip, dot_with, partials,
                      op.tw_dst_df[axis], phase, st);
   } else {
     if ((e = ensure_smem_dst<ArithF>()) != cudaSuccess) return e;
-    run_dst<ArithF>(op, grid, nlines, m, inner, P, L, log2NC, in, out, flip, dot_with, partials,
+    run_dst<ArithF>(op, grid, nlines, m, inner, P, log2NC, in, out, flip, dot_with, partials,
                     op.tw_dst32[axis], phase, st);
   }
   return cudaGetLastError();
@@ -1198,10 +1278,10 @@ k_dst_multi(const DstItem* __restrict__ items, const long long* __restrict__ pre
     const DstItem& di = items[it];
     const typename A::V* tw = reinterpret_cast<const typename A::V*>(di.tw);
     if (di.inner == 1)
-      dst_tile<A, true>(di.nlines, di.m, di.inner, di.P, di.log2L, di.log2NC, di.cb, di.out,
+      dst_tile<A, true>(di.nlines, di.m, di.inner, di.P, di.log2P, di.log2NC, di.cb, di.out,
                         di.flip, (int)di.N, di.M, di.dot_with, di.partials, tw, t - prefix[it]);
     else
-      dst_tile<A, false>(di.nlines, di.m, di.inner, di.P, di.log2L, di.log2NC, di.cb, di.out,
+      dst_tile<A, false>(di.nlines, di.m, di.inner, di.P, di.log2P, di.log2NC, di.cb, di.out,
                          di.flip, (int)di.N, di.M, di.dot_with, di.partials, tw, t - prefix[it]);
   }
 }
