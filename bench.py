@@ -41,6 +41,12 @@ TOL = 1e-8
 ALPHA_F64 = 1e-8          # the paper's alpha rule (Sec. 5.2)
 ALPHA_F32 = 1e-3          # FP32 preconditioner: alpha raised so that FP32 rounding stays below tol
 ALPHA_F32X2 = 1e-6        # double-float preconditioner: the sweep's fastest alpha on this workload
+# DRAM bytes (read + write) per unknown of one launch, from one ncu capture of the current kernel
+# (profiles/ncu_chosen_form_frac2d_N1024_m127.md: the m = 127 case, scaled by the unknowns)
+NCU_TRAFFIC_PER_UNKNOWN = {
+    "conv_df": (13.03, "ncu dram__bytes_read.sum + dram__bytes_write.sum, m = 127 case, 13.03 B "
+                       "per unknown scaled to the launch's unknowns"),
+}
 FP64_PEAK_TFLOPS = 1.259  # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (measured 1.20 at 1995 MHz)
 FP32_PEAK_TFLOPS = 80.6   # 128 FFMA/clk/SM x 152 SMs x 2.07 GHz (measured 69.8 at 1995 MHz)
 FP32_PEAK_TOPS = 40.28    # FP32 pipe: 128 instructions/clk/SM x 152 SMs x 2.07 GHz
@@ -556,7 +562,9 @@ def main():
     if dom:
         roof = {"kernel": dom["name"], "bound": dom["bound"], "achieved": round(dom["achieved"], 4),
                 "peak": dom["peak"], "unit": dom["unit"], "frac": round(dom["frac"], 4),
-                "traffic": None,
+                "traffic": NCU_TRAFFIC_PER_UNKNOWN.get(dom["name"], (None, ""))[0] and
+                           NCU_TRAFFIC_PER_UNKNOWN[dom["name"]][0] * prob.n,
+                "traffic_source": NCU_TRAFFIC_PER_UNKNOWN.get(dom["name"], (None, None))[1],
                 "peak_source": (("derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz, confirmed by a "
                                  "measured 1.20 TFLOP/s FP64 FMA loop") if dom["unit"].endswith("(FP64)")
                                 else ("derived: 128 FP32 ops/clk/SM x 152 SMs x 2.07 GHz, confirmed "
