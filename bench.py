@@ -98,10 +98,13 @@ def kernel_cost(name, N, m, d):
     if name in ("timepass64", "timepass32"):   # 4 real FFTs of N, 2 spectral products, 3 scalings
         b = 40.0 + (8.0 if name == "timepass64" else 0.0)
         return ("alu64" if name == "timepass64" else "hbm"), b, 10.0 * lN + 15.0
-    if name in ("dst64", "dst32"):   # one complex FFT of 2(m+1) per two lines
-        return ("alu64" if name == "dst64" else "hbm"), 16.0, 5.0 * np.log2(2 * (m + 1)) * (m + 1) / m
+    # DST-I: one complex FFT of length P = m+1 per two lines, the y_j pre-pass, the split of the
+    # two spectra and the prefix sum of the odd outputs
+    P = m + 1
+    if name in ("dst64", "dst32"):
+        return ("alu64" if name == "dst64" else "hbm"), 16.0, 5.0 * P * np.log2(P) / (2 * m) + 6.0
     if name == "dst_df":
-        return "alu32", 16.0, df_fft_ops(2 * (m + 1)) * (m + 1) / m
+        return "alu32", 16.0, P * df_fft_ops(P) / (2 * m) + 61.0
     if name == "timepass_df":
         return "alu32", 48.0, 4 * df_fft_ops(N) / 2 + 2 * 82.0 / 2 + 3 * 14.0
     if name == "w_update":
