@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -31,6 +32,21 @@ void twiddle_table(int L, std::vector<double2>& out) {
   }
 }
 
+// the table of one length, computed once per process (long double is a software format on some
+// hosts, so the per-alpha set-up must not recompute it)
+const std::vector<double2>& twiddles(int L) {
+  static std::mutex mu;
+  static std::map<int, std::vector<double2>> cache;   // nodes do not move: references stay valid
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(L);
+  if (it == cache.end()) {
+    std::vector<double2> t;
+    twiddle_table(L, t);
+    it = cache.emplace(L, std::move(t)).first;
+  }
+  return it->second;
+}
+
 // forward DFT X_k = sum_j x_j exp(-2 pi i jk/L), L a power of two (iterative radix 2)
 void host_fft(std::vector<cd>& a) {
   const int n = (int)a.size();
@@ -40,14 +56,14 @@ void host_fft(std::vector<cd>& a) {
     j ^= bit;
     if (i < j) std::swap(a[i], a[j]);
   }
-  std::vector<double2> tw;
-  twiddle_table(n, tw);
+  const std::vector<double2>& tw = twiddles(n);
   for (int len = 2; len <= n; len <<= 1) {
     const int step = n / len;
     for (int i = 0; i < n; i += len)
       for (int k = 0; k < len / 2; ++k) {
-        cd w(tw[k * step].x, tw[k * step].y);
-        cd u = a[i + k], v = a[i + k + len / 2] * w;
+        const double wr = tw[k * step].x, wi = tw[k * step].y;
+        const cd u = a[i + k], b = a[i + k + len / 2];
+        const cd v(b.real() * wr - b.imag() * wi, b.real() * wi + b.imag() * wr);   // b * w
         a[i + k] = u + v;
         a[i + k + len / 2] = u - v;
       }
@@ -189,8 +205,7 @@ cudaError_t upload_df(bltt_ctx* h, const std::vector<double2>& src, const float4
 }
 
 cudaError_t upload_twiddles(bltt_ctx* h, int L, const double2** d64, const float2** d32) {
-  std::vector<double2> tw;
-  twiddle_table(L, tw);
+  const std::vector<double2>& tw = twiddles(L);
   std::vector<float2> tw32(L);
   for (int k = 0; k < L; ++k) tw32[k] = make_float2((float)tw[k].x, (float)tw[k].y);
   double2* p64;
@@ -584,23 +599,19 @@ bltt_status bltt_create(const bltt_blocks* blocks, int N, long long M, bltt_hand
   if (e == cudaSuccess) e = upload_df(h, Ah, &op.Ahat_df);
   if (e == cudaSuccess) e = upload_df(h, Bh, &op.Bhat_df);
   if (e == cudaSuccess) {
-    std::vector<double2> tw;
-    twiddle_table(2 * N, tw);
+    const std::vector<double2>& tw = twiddles(2 * N);
     e = upload_df(h, tw, &op.tw_2N_df);
   }
   op.mv_arith = 0;
   if (e == cudaSuccess) e = upload_twiddles(h, N, &op.tw_N, &op.tw_N32);
   if (e == cudaSuccess) {
-    std::vector<double2> tw;
-    twiddle_table(N, tw);
+    const std::vector<double2>& tw = twiddles(N);
     e = upload_df(h, tw, &op.tw_N_df);
   }
   for (int ax = 0; ax < h->d && e == cudaSuccess; ++ax) {
     e = upload_twiddles(h, 2 * (h->m[ax] + 1), &op.tw_dst[ax], &op.tw_dst32[ax]);
     if (e == cudaSuccess) {
-      std::vector<double2> tw;
-      twiddle_table(2 * (h->m[ax] + 1), tw);
-      e = upload_df(h, tw, &op.tw_dst_df[ax]);
+      e = upload_df(h, twiddles(2 * (h->m[ax] + 1)), &op.tw_dst_df[ax]);
     }
   }
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&h->ev[i]);
