@@ -115,6 +115,11 @@ struct ArithD {
   static __device__ __forceinline__ void put_sc(V* buf, int idx, int comp, double x, Sc s) {
     reinterpret_cast<double*>(buf)[2 * idx + comp] = x * s;
   }
+  static __device__ __forceinline__ void put_sc2(V* buf, int i1, int i2, int comp, double x, Sc s) {
+    const double v = x * s;
+    reinterpret_cast<double*>(buf)[2 * i1 + comp] = v;
+    reinterpret_cast<double*>(buf)[2 * i2 + comp] = v;
+  }
   static __device__ __forceinline__ V add(V a, V b) { return make_double2(a.x + b.x, a.y + b.y); }
   static __device__ __forceinline__ V sub(V a, V b) { return make_double2(a.x - b.x, a.y - b.y); }
   static __device__ __forceinline__ V add_nr(V a, V b) { return add(a, b); }
@@ -159,6 +164,11 @@ struct ArithF {
   static __device__ __forceinline__ double part_sc(V a, int comp, Sc s) { return f2d_bits((comp ? a.y : a.x) * s); }
   static __device__ __forceinline__ void put_sc(V* buf, int idx, int comp, double x, Sc s) {
     reinterpret_cast<float*>(buf)[2 * idx + comp] = d2f_bits(x) * s;
+  }
+  static __device__ __forceinline__ void put_sc2(V* buf, int i1, int i2, int comp, double x, Sc s) {
+    const float v = d2f_bits(x) * s;
+    reinterpret_cast<float*>(buf)[2 * i1 + comp] = v;
+    reinterpret_cast<float*>(buf)[2 * i2 + comp] = v;
   }
   static __device__ __forceinline__ V add(V a, V b) { return make_float2(a.x + b.x, a.y + b.y); }
   static __device__ __forceinline__ V sub(V a, V b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -213,6 +223,12 @@ struct ArithDF {
   static __device__ __forceinline__ void put_sc(V* buf, int idx, int comp, double x, Sc s) {
     dfl v = df_mul(df_from(x), s);
     reinterpret_cast<float2*>(buf)[2 * idx + comp] = make_float2(v.hi, v.lo);
+  }
+  // the same value into two slots, converted and scaled once
+  static __device__ __forceinline__ void put_sc2(V* buf, int i1, int i2, int comp, double x, Sc s) {
+    const dfl v = df_mul(df_from(x), s);
+    reinterpret_cast<float2*>(buf)[2 * i1 + comp] = make_float2(v.hi, v.lo);
+    reinterpret_cast<float2*>(buf)[2 * i2 + comp] = make_float2(v.hi, v.lo);
   }
   static __device__ __forceinline__ dfl re(V a) { return {a.x, a.y}; }
   static __device__ __forceinline__ dfl im(V a) { return {a.z, a.w}; }
@@ -320,10 +336,31 @@ __device__ __forceinline__ void dft16(typename A::V (&v)[16]) {
   for (int c = 0; c < 4; ++c) dft4<A, INV>(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
 }
 
+// Radix-8 butterfly.  With r = b + 2c and q = c' + 4d (b, d < 2; c, c' < 4),
+//   X_q = sum_b w2^{b d} w8^{b c'} sum_c w4^{c c'} x_{b+2c}:
+// two length-4 DFTs over c, the twiddles w8^{c'} on the b = 1 half, four length-2 DFTs over b.
+// In place; on return X_{c' + 4d} is in v[2c' + d].
+template <class A, bool INV>
+__device__ __forceinline__ void dft8(typename A::V (&v)[8]) {
+  dft4<A, INV>(v[0], v[2], v[4], v[6]);
+  dft4<A, INV>(v[1], v[3], v[5], v[7]);
+  v[3] = A::mul_nr(v[3], w16<A, 2, INV>());   // w8^1 = w16^2
+  v[5] = A::template rot<INV>(v[5]);          // w8^2 = -i (forward)
+  v[7] = A::mul_nr(v[7], w16<A, 6, INV>());   // w8^3 = w16^6
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const typename A::V a = v[2 * c], b = v[2 * c + 1];
+    v[2 * c] = A::add(a, b);
+    v[2 * c + 1] = A::sub(a, b);
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // Shared-memory Stockham FFT (self-sorting, mixed radix).  The passes are: radix 2 when log2 L
-// is odd, radix 4 when the remaining exponent is 2 mod 4, then radix 16.  Running the short
-// passes first keeps every radix-16 pass at Ns >= 4, where its stores stay bank-conflict-free.
+// is odd, then, with 16 points per thread (CAP = 16 NT), radix 4 when the remaining exponent is
+// 2 mod 4 and radix 16 for the rest; with at most 8 points per thread, one or two radix-4 passes
+// (remaining exponent 2 or 1 mod 3) and radix 8 for the rest.  Running the short passes first
+// keeps the long ones at Ns >= 4, where their stores stay bank-conflict-free.
 //
 // buf holds NC = 2^log2NC independent complex columns of length L, element (p, c) at
 // buf[p * NC + c] (or at buf[p * NC + (c ^ (p mod NC))] with SWZ).  tw holds
@@ -377,7 +414,10 @@ __device__ __forceinline__ void fft_columns(typename A::V* buf, int L, int log2L
     }
     log2Ns = 1;
   }
-  if ((log2L - log2Ns) & 2) {
+  constexpr bool R8 = (CAP / NT) <= 8;   // radix-8 plan (at most 8 points per thread)
+  const int rem = log2L - log2Ns;
+  const int n4 = R8 ? (rem % 3 == 2 ? 1 : (rem % 3 == 1 ? 2 : 0)) : ((rem & 2) ? 1 : 0);
+  for (int i4 = 0; i4 < n4; ++i4) {
     const int Ns = 1 << log2Ns;
     const int quarter = L >> 2;
     const int total = quarter << log2NC;
@@ -415,6 +455,48 @@ __device__ __forceinline__ void fft_columns(typename A::V* buf, int L, int log2L
     }
     __syncthreads();
     log2Ns += 2;
+  }
+  if constexpr (R8) {
+    constexpr int IPT8 = (CAP / 8 + NT - 1) / NT;
+    const int eighth = L >> 3;
+    const int total8 = eighth << log2NC;
+    for (; log2Ns < log2L; log2Ns += 3) {
+      const int Ns = 1 << log2Ns;
+      const int tstep_log = log2L - 3 - log2Ns;
+      V v[IPT8][8];
+#pragma unroll
+      for (int s = 0; s < IPT8; ++s) {
+        const int it = tid + s * NT;
+        if (it < total8) {
+          const int c = it & cmask, j = it >> log2NC;
+#pragma unroll
+          for (int r = 0; r < 8; ++r) v[s][r] = buf[at(j + r * eighth, c)];
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int s = 0; s < IPT8; ++s) {
+        const int it = tid + s * NT;
+        if (it < total8) {
+          const int c = it & cmask, j = it >> log2NC;
+          const int k = j & (Ns - 1);
+          if (k != 0) {
+            const int e = k << (tstep_log + tw_shift);
+#pragma unroll
+            for (int r = 1; r < 8; ++r) {
+              const V w = tw[r * e];
+              v[s][r] = INV ? A::mulc_nr(v[s][r], w) : A::mul_nr(v[s][r], w);
+            }
+          }
+          dft8<A, INV>(v[s]);
+          const int o = (j - k) * 8 + k;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) buf[at(o + q * Ns, c)] = v[s][2 * (q & 3) + (q >> 2)];
+        }
+      }
+      __syncthreads();
+    }
+    return;
   }
   const int sixteenth = L >> 4;
   const int total16 = sixteenth << log2NC;

@@ -7,7 +7,7 @@
 
 namespace bltt {
 
-constexpr int kThreads = 256;      // threads of every FFT tile kernel
+constexpr int kThreads = 256;      // threads of an FFT tile kernel (double-float: twice as many)
 constexpr int kCap = 4096;         // complex points per FFT tile (64 KB of FP64 smem)
 constexpr int kMaxPartials = 1 << 20;
 constexpr int kMaxCols = 256;     // real lines per FFT tile (column info kept in shared memory)

@@ -140,9 +140,15 @@ constexpr int kBatch = 8;   // independent global loads in flight per thread in 
 // share an SM, so that one block's loads, stores and barriers overlap another block's arithmetic
 template <class A> struct TileCfg {
   static constexpr int NT = kThreads, CAP = kCap;
-  // resident blocks per SM the register budget is held to: 128 registers per thread for FP64 and
-  // double-float, 64 for FP32
+  // resident blocks per SM the register budget is held to: 128 registers per thread for FP64, 64
+  // for FP32
   static constexpr int MINB = sizeof(typename A::V) == 8 ? 4 : 2;
+};
+// double-float: 512 threads on the 4096 points (8 per thread, radix-8 passes) at 64 registers,
+// two blocks per SM: twice the warps of the FP64 tile and about a third of its transform code
+template <> struct TileCfg<ArithDF> {
+  static constexpr int NT = 2 * kThreads, CAP = kCap;
+  static constexpr int MINB = 2;
 };
 
 // ============================================================================================
@@ -628,8 +634,7 @@ __device__ __forceinline__ void conv_tile(const OpTables& op, int spectral, int 
         const int p = e >> log2W, c = e & (W - 1);
         if (odd) {
           // the first radix-2 pass pairs x_p with the zero x_{p+N}: both outputs equal x_p
-          A::put_sc(buf, (2 * p) * NC + (c >> 1), c & 1, v[u], ssc);
-          A::put_sc(buf, (2 * p + 1) * NC + (c >> 1), c & 1, v[u], ssc);
+          A::put_sc2(buf, (2 * p) * NC + (c >> 1), (2 * p + 1) * NC + (c >> 1), c & 1, v[u], ssc);
         } else {
           A::put_sc(buf, p * NC + (c >> 1), c & 1, v[u], ssc);
         }
@@ -1116,17 +1121,17 @@ cudaError_t launch_timepass(const OpTables& op, const PrecTables& pt, int prec, 
   if (prec == PREC_F64) {
     cudaError_t e = ensure_smem_tp<ArithD>();
     if (e != cudaSuccess) return e;
-    k_timepass<ArithD><<<(unsigned)grid, kThreads, kCap * sizeof(double2), st>>>(
+    k_timepass<ArithD><<<(unsigned)grid, TileCfg<ArithD>::NT, kCap * sizeof(double2), st>>>(
         op, pt, in, out, dot_with, partials, phase, PH_RUN, log2NC, op.tw_N);
   } else if (prec == PREC_DF) {
     cudaError_t e = ensure_smem_tp<ArithDF>();
     if (e != cudaSuccess) return e;
-    k_timepass<ArithDF><<<(unsigned)grid, kThreads, kCap * sizeof(float4), st>>>(
+    k_timepass<ArithDF><<<(unsigned)grid, TileCfg<ArithDF>::NT, kCap * sizeof(float4), st>>>(
         op, pt, in, out, dot_with, partials, phase, PH_RUN, log2NC, op.tw_N_df);
   } else {
     cudaError_t e = ensure_smem_tp<ArithF>();
     if (e != cudaSuccess) return e;
-    k_timepass<ArithF><<<(unsigned)grid, kThreads, kCap * sizeof(float2), st>>>(
+    k_timepass<ArithF><<<(unsigned)grid, TileCfg<ArithF>::NT, kCap * sizeof(float2), st>>>(
         op, pt, in, out, dot_with, partials, phase, PH_RUN, log2NC, op.tw_N32);
   }
   return cudaGetLastError();
@@ -1148,11 +1153,11 @@ static cudaError_t launch_conv_t(const OpTables& op, int spectral, const double*
   const double* st_src = x;
   if (!spectral && op.b_kind == 1) {
     // conv_b(x) first (scaled like x), then y = conv_a(x) + L conv_b(x)
-    k_conv<A><<<(unsigned)grid, kThreads, smem, st>>>(op, 0, 1, x, xscale, tmp, 0, MV_STORE,
+    k_conv<A><<<(unsigned)grid, TileCfg<A>::NT, smem, st>>>(op, 0, 1, x, xscale, tmp, 0, MV_STORE,
                                                      nullptr, nullptr, phase, want, nullptr, log2NC);
     st_src = tmp;
   }
-  k_conv<A><<<(unsigned)grid, kThreads, smem, st>>>(op, spectral, 0, x, xscale, y, flip, mode, rhs,
+  k_conv<A><<<(unsigned)grid, TileCfg<A>::NT, smem, st>>>(op, spectral, 0, x, xscale, y, flip, mode, rhs,
                                                    partials, phase, want, st_src, log2NC);
   return cudaGetLastError();
 }
@@ -1324,21 +1329,21 @@ int persistent_grid(int kind, int prec) {
   size_t smem = (prec == PREC_F32 ? sizeof(float2) : sizeof(double2)) * kCap;
   if (kind == 0) {
     if (prec == PREC_DF) { set_smem(k_conv_multi<ArithDF>, smem);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_conv_multi<ArithDF>, kThreads, smem); }
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_conv_multi<ArithDF>, TileCfg<ArithDF>::NT, smem); }
     else { set_smem(k_conv_multi<ArithD>, smem);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_conv_multi<ArithD>, kThreads, smem); }
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_conv_multi<ArithD>, TileCfg<ArithD>::NT, smem); }
   } else if (kind == 1) {
     if (prec == PREC_F32) { set_smem(k_timepass_multi<ArithF>, smem);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_timepass_multi<ArithF>, kThreads, smem); }
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_timepass_multi<ArithF>, TileCfg<ArithF>::NT, smem); }
     else if (prec == PREC_DF) { set_smem(k_timepass_multi<ArithDF>, smem);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_timepass_multi<ArithDF>, kThreads, smem); }
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_timepass_multi<ArithDF>, TileCfg<ArithDF>::NT, smem); }
     else { set_smem(k_timepass_multi<ArithD>, smem);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_timepass_multi<ArithD>, kThreads, smem); }
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_timepass_multi<ArithD>, TileCfg<ArithD>::NT, smem); }
   } else {
     if (prec == PREC_DF) { set_smem(k_dst_multi<ArithDF>, smem);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dst_multi<ArithDF>, kThreads, smem); }
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dst_multi<ArithDF>, TileCfg<ArithDF>::NT, smem); }
     else { set_smem(k_dst_multi<ArithD>, smem);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dst_multi<ArithD>, kThreads, smem); }
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dst_multi<ArithD>, TileCfg<ArithD>::NT, smem); }
   }
   if (per < 1) per = 1;
   return sms * per;
@@ -1349,9 +1354,9 @@ cudaError_t launch_conv_multi(int arith, const ConvItem* items, const long long*
   const int g = (int)std::min<long long>(persistent_grid(0, arith ? PREC_DF : PREC_F64), total);
   if (g <= 0) return cudaSuccess;
   if (arith)
-    k_conv_multi<ArithDF><<<g, kThreads, kCap * sizeof(float4), st>>>(items, prefix, nitems, total);
+    k_conv_multi<ArithDF><<<g, TileCfg<ArithDF>::NT, kCap * sizeof(float4), st>>>(items, prefix, nitems, total);
   else
-    k_conv_multi<ArithD><<<g, kThreads, kCap * sizeof(double2), st>>>(items, prefix, nitems, total);
+    k_conv_multi<ArithD><<<g, TileCfg<ArithD>::NT, kCap * sizeof(double2), st>>>(items, prefix, nitems, total);
   return cudaGetLastError();
 }
 
@@ -1360,11 +1365,11 @@ cudaError_t launch_timepass_multi(int prec, const TpItem* items, const long long
   const int g = (int)std::min<long long>(persistent_grid(1, prec), total);
   if (g <= 0) return cudaSuccess;
   if (prec == PREC_F32)
-    k_timepass_multi<ArithF><<<g, kThreads, kCap * sizeof(float2), st>>>(items, prefix, nitems, total);
+    k_timepass_multi<ArithF><<<g, TileCfg<ArithF>::NT, kCap * sizeof(float2), st>>>(items, prefix, nitems, total);
   else if (prec == PREC_DF)
-    k_timepass_multi<ArithDF><<<g, kThreads, kCap * sizeof(float4), st>>>(items, prefix, nitems, total);
+    k_timepass_multi<ArithDF><<<g, TileCfg<ArithDF>::NT, kCap * sizeof(float4), st>>>(items, prefix, nitems, total);
   else
-    k_timepass_multi<ArithD><<<g, kThreads, kCap * sizeof(double2), st>>>(items, prefix, nitems, total);
+    k_timepass_multi<ArithD><<<g, TileCfg<ArithD>::NT, kCap * sizeof(double2), st>>>(items, prefix, nitems, total);
   return cudaGetLastError();
 }
 
@@ -1373,9 +1378,9 @@ cudaError_t launch_dst_multi(int prec, const DstItem* items, const long long* pr
   const int g = (int)std::min<long long>(persistent_grid(2, prec), total);
   if (g <= 0) return cudaSuccess;
   if (prec == PREC_DF)
-    k_dst_multi<ArithDF><<<g, kThreads, kCap * sizeof(float4), st>>>(items, prefix, nitems, total);
+    k_dst_multi<ArithDF><<<g, TileCfg<ArithDF>::NT, kCap * sizeof(float4), st>>>(items, prefix, nitems, total);
   else
-    k_dst_multi<ArithD><<<g, kThreads, kCap * sizeof(double2), st>>>(items, prefix, nitems, total);
+    k_dst_multi<ArithD><<<g, TileCfg<ArithD>::NT, kCap * sizeof(double2), st>>>(items, prefix, nitems, total);
   return cudaGetLastError();
 }
 
