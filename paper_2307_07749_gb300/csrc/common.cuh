@@ -356,11 +356,12 @@ __device__ __forceinline__ void dft8(typename A::V (&v)[8]) {
 }
 
 // ------------------------------------------------------------------------------------------
-// Shared-memory Stockham FFT (self-sorting, mixed radix).  The passes are: radix 2 when log2 L
-// is odd, then, with 16 points per thread (CAP = 16 NT), radix 4 when the remaining exponent is
-// 2 mod 4 and radix 16 for the rest; with at most 8 points per thread, one or two radix-4 passes
-// (remaining exponent 2 or 1 mod 3) and radix 8 for the rest.  Running the short passes first
-// keeps the long ones at Ns >= 4, where their stores stay bank-conflict-free.
+// Shared-memory Stockham FFT (self-sorting, mixed radix).  With 16 points per thread (CAP = 16 NT)
+// the passes are radix 2 when log2 L is odd, radix 4 when the remaining exponent is 2 mod 4, and
+// radix 16 for the rest.  With at most 8 points per thread they are one or two radix-4 passes
+// (exponent 2 or 1 mod 3) and radix 8 for the rest, with a radix-2 pass first only when the
+// caller has applied it (skip_radix2) or L = 2.  Running the short passes first keeps the long
+// ones at Ns >= 4, where their stores stay bank-conflict-free.
 //
 // buf holds NC = 2^log2NC independent complex columns of length L, element (p, c) at
 // buf[p * NC + c] (or at buf[p * NC + (c ^ (p mod NC))] with SWZ).  tw holds
@@ -385,8 +386,11 @@ __device__ __forceinline__ void fft_columns(typename A::V* buf, int L, int log2L
   const int tid = threadIdx.x;
   const int NC = 1 << log2NC, cmask = NC - 1;
   auto at = [&](int p, int c) { return (p << log2NC) + (SWZ ? (c ^ (p & cmask)) : c); };
+  constexpr bool R8 = (CAP / NT) <= 8;   // radix-8 plan (at most 8 points per thread)
   int log2Ns = 0;
-  if (log2L & 1) {
+  // radix 2 first when log2 L is odd; the radix-8 plan needs it only when the caller has applied
+  // it (skip_radix2) or for L = 2, and otherwise absorbs the odd level into its radix-4/8 passes
+  if ((log2L & 1) && (!R8 || skip_radix2 || log2L == 1)) {
     if (!skip_radix2) {
       const int half = L >> 1;
       const int total = half << log2NC;
@@ -414,7 +418,6 @@ __device__ __forceinline__ void fft_columns(typename A::V* buf, int L, int log2L
     }
     log2Ns = 1;
   }
-  constexpr bool R8 = (CAP / NT) <= 8;   // radix-8 plan (at most 8 points per thread)
   const int rem = log2L - log2Ns;
   const int n4 = R8 ? (rem % 3 == 2 ? 1 : (rem % 3 == 1 ? 2 : 0)) : ((rem & 2) ? 1 : 0);
   for (int i4 = 0; i4 < n4; ++i4) {
