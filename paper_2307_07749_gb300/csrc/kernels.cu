@@ -1001,6 +1001,41 @@ __global__ void __launch_bounds__(256) k_w_update(const MinresDev* st, const dou
   const double cz = st->w_cz, cwp = st->w_cwp, cw = st->w_cw, ce = st->w_ceta;
   const long long stride = (long long)gridDim.x * blockDim.x;
   long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const bool vec = ((n & 1) == 0) &&
+                   ((((uintptr_t)z | (uintptr_t)w_prev | (uintptr_t)w | (uintptr_t)x) & 15) == 0);
+  if (vec) {
+    // pairs of elements as 16-byte accesses; all loads of four pairs are issued before the first
+    // store (the stores may alias nothing the loads read, but the compiler cannot know that)
+    const double2* z2 = reinterpret_cast<const double2*>(z);
+    double2* wp2 = reinterpret_cast<double2*>(w_prev);
+    const double2* w2 = reinterpret_cast<const double2*>(w);
+    double2* x2 = reinterpret_cast<double2*>(x);
+    const long long n2 = n >> 1;
+    for (; e + 3 * stride < n2; e += 4 * stride) {
+      double2 a[4], b[4], c[4], d[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long i = e + u * stride;
+        a[u] = __ldcs(z2 + i); b[u] = __ldcs(wp2 + i); c[u] = __ldcs(w2 + i); d[u] = __ldcs(x2 + i);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long i = e + u * stride;
+        double2 wn, xn;
+        wn.x = fma(cz, a[u].x, fma(cwp, b[u].x, cw * c[u].x));
+        wn.y = fma(cz, a[u].y, fma(cwp, b[u].y, cw * c[u].y));
+        xn.x = fma(ce, wn.x, d[u].x);
+        xn.y = fma(ce, wn.y, d[u].y);
+        __stcs(wp2 + i, wn);
+        __stcs(x2 + i, xn);
+      }
+    }
+    for (; e < n2; e += stride) {
+      w_update_elem(z, w_prev, w, x, 2 * e, cz, cwp, cw, ce);
+      w_update_elem(z, w_prev, w, x, 2 * e + 1, cz, cwp, cw, ce);
+    }
+    return;
+  }
   for (; e + 3 * stride < n; e += 4 * stride) {          // four independent elements in flight
 #pragma unroll
     for (int u = 0; u < 4; ++u) w_update_elem(z, w_prev, w, x, e + u * stride, cz, cwp, cw, ce);
