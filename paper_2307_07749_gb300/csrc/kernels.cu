@@ -994,18 +994,16 @@ __device__ __forceinline__ void w_update_elem(const double* __restrict__ z, doub
   __stcs(x + e, fma(ce, wn, __ldcs(x + e)));
 }
 
-__global__ void __launch_bounds__(256) k_w_update(const MinresDev* st, const double* z,
-                                                  double* w_prev, const double* w, double* x,
-                                                  long long n) {
-  if (!st->wpending) return;
-  const double cz = st->w_cz, cwp = st->w_cwp, cw = st->w_cw, ce = st->w_ceta;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+// elements e0, e0 + stride, ... < n of one update; pairs of elements as 16-byte accesses when
+// every vector is 16-byte aligned, with all loads of four pairs issued before the first store (the
+// stores alias nothing that the loads read, but the compiler cannot know that)
+__device__ __forceinline__ void w_update_range(const double* z, double* w_prev, const double* w,
+                                               double* x, long long n, long long e,
+                                               long long stride, double cz, double cwp,
+                                               double cw, double ce) {
   const bool vec = ((n & 1) == 0) &&
                    ((((uintptr_t)z | (uintptr_t)w_prev | (uintptr_t)w | (uintptr_t)x) & 15) == 0);
   if (vec) {
-    // pairs of elements as 16-byte accesses; all loads of four pairs are issued before the first
-    // store (the stores may alias nothing the loads read, but the compiler cannot know that)
     const double2* z2 = reinterpret_cast<const double2*>(z);
     double2* wp2 = reinterpret_cast<double2*>(w_prev);
     const double2* w2 = reinterpret_cast<const double2*>(w);
@@ -1041,6 +1039,14 @@ __global__ void __launch_bounds__(256) k_w_update(const MinresDev* st, const dou
     for (int u = 0; u < 4; ++u) w_update_elem(z, w_prev, w, x, e + u * stride, cz, cwp, cw, ce);
   }
   for (; e < n; e += stride) w_update_elem(z, w_prev, w, x, e, cz, cwp, cw, ce);
+}
+
+__global__ void __launch_bounds__(256) k_w_update(const MinresDev* st, const double* z,
+                                                  double* w_prev, const double* w, double* x,
+                                                  long long n) {
+  if (!st->wpending) return;
+  w_update_range(z, w_prev, w, x, n, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                 (long long)gridDim.x * blockDim.x, st->w_cz, st->w_cwp, st->w_cw, st->w_ceta);
 }
 
 __global__ void __launch_bounds__(256) k_sum_partials(const double* p, int np, double* out) {
@@ -1331,10 +1337,8 @@ __global__ void __launch_bounds__(256) k_w_update_multi(const VecItem* __restric
   const VecItem& vi = items[blockIdx.y];
   if (!vi.st->wpending) return;
   const MinresDev* st = vi.st;
-  const double cz = st->w_cz, cwp = st->w_cwp, cw = st->w_cw, ce = st->w_ceta;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < vi.n;
-       e += (long long)gridDim.x * blockDim.x)
-    w_update_elem(vi.z, vi.w_prev, vi.w, vi.x, e, cz, cwp, cw, ce);
+  w_update_range(vi.z, vi.w_prev, vi.w, vi.x, vi.n, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                 (long long)gridDim.x * blockDim.x, st->w_cz, st->w_cwp, st->w_cw, st->w_ceta);
 }
 
 __global__ void __launch_bounds__(256) k_scalar_multi(int which, const ScalItem* __restrict__ items) {
