@@ -448,20 +448,38 @@ __device__ __forceinline__ void timepass_tile(const OpTables& op, const PrecTabl
   double c0, c1, c2;
   load_coef(cb, c0, c1, c2);
   const int total = N * W;
-  for (int e0 = threadIdx.x; e0 < total; e0 += kBatch * NT) {
-    double v[kBatch];
+  // the Lanczos combine v = in0 + c1 in1 + c2 in2 (stored to vout) for a batch of elements: all
+  // loads of the batch first, then the combines and stores (vout may alias in1 or in2, element by
+  // element, so the compiler could not move one element's loads above another's store)
+  constexpr int kCB = 4;   // elements per batch: 12 loads in flight per thread
+  for (int e0 = threadIdx.x; e0 < total; e0 += kCB * NT) {
+    double v[kCB], a1[kCB], a2[kCB];
 #pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
+    for (int u = 0; u < kCB; ++u) {
       const int e = e0 + u * NT;
       const int p = e >> log2W, c = e & (W - 1);
-      v[u] = 0.0;
-      if (e < total && g0 + c < M) v[u] = combine_at(cb, (long long)p * M + g0 + c, c0, c1, c2);
+      v[u] = 0.0; a1[u] = 0.0; a2[u] = 0.0;
+      if (e < total && g0 + c < M) {
+        const long long idx = (long long)p * M + g0 + c;
+        if (cb.vout) {
+          v[u] = __ldcs(cb.in0 + idx);
+          if (cb.in1) a1[u] = __ldcs(cb.in1 + idx);
+          if (cb.in2) a2[u] = __ldcs(cb.in2 + idx);
+        } else {
+          v[u] = __ldcg(cb.in0 + idx);
+          if (cb.in1) a1[u] = __ldcg(cb.in1 + idx);
+          if (cb.in2) a2[u] = __ldcg(cb.in2 + idx);
+        }
+      }
     }
 #pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
+    for (int u = 0; u < kCB; ++u) {
       const int e = e0 + u * NT;
       if (e < total) {
         const int p = e >> log2W, c = e & (W - 1);
+        if (cb.in1) v[u] = fma(c1, a1[u], v[u]);
+        if (cb.in2) v[u] = fma(c2, a2[u], v[u]);
+        if (cb.vout && g0 + c < M) cb.vout[(long long)p * M + g0 + c] = v[u];
         A::put_sc(buf, p * NC + (c >> 1), c & 1, v[u], RowSc<A>::dinv(pt, p));
       }
     }
