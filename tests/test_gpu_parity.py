@@ -89,6 +89,36 @@ def test_precond_parity_f32(B, prob, alpha):
     assert rel(z, ref) <= precond_tol(prob.N, alpha, 32)
 
 
+LONG_LINES = [fractional_problem(1, m, 16, 0.6) for m in (511, 1023, 2047)]
+
+
+@pytest.mark.parametrize("prob", LONG_LINES, ids=[p.name for p in LONG_LINES])
+@pytest.mark.parametrize("precision", [64, 96, 32], ids=["f64", "f32x2", "f32"])
+def test_precond_parity_long_dst_lines(B, prob, precision):
+    """DST-I lines of 511, 1023 and 2047 points (real FFTs of 512 to 2048 points, the prefix
+    sums over 256 to 1024 rows): the preconditioner in the physical basis against the oracle."""
+    s = B.Solver(prob)
+    v = np.random.default_rng(25).standard_normal(prob.n)
+    z = to_host(s.precond_apply(1e-2, to_dev(v), precision=precision))
+    ref = O.precond_apply(prob, 1e-2, v)
+    assert rel(z, ref) <= precond_tol(prob.N, 1e-2, precision)
+
+
+@pytest.mark.parametrize("arith", [1, 2], ids=["f64", "f32x2"])
+def test_solve_long_dst_lines(B, arith):
+    """DST basis with lines of 2047 points: the entry and exit DSTs of a solve against the
+    oracle's physical-basis solve."""
+    prob = LONG_LINES[-1]
+    f = rhs_uniform(prob.n, 37)
+    ref = O.solve(prob, f, alpha=1e-8, tol=1e-8)
+    u, info = B.Solver(prob).solve(to_dev(f), alpha=1e-8, tol=1e-8, maxit=100, precision=64,
+                                   basis=1, matvec_arith=arith)
+    assert info["status"] == 0, info
+    assert abs(info["iters"] - ref["iters"]) <= 1, (info["iters"], ref["iters"])
+    assert rel(O.bltt_matvec(prob, to_host(u)), f) <= 1e-8
+    assert rel(to_host(u), ref["x"]) <= 1e-6
+
+
 def test_precond_in_place(B):
     prob = fractional_problem(2, 31, 32, 0.7)
     s = B.Solver(prob)
