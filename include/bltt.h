@@ -162,6 +162,18 @@ bltt_status bltt_minres_solve_ex(bltt_handle h, const double* f_dev, double alph
 bltt_status bltt_minres_solve(bltt_handle h, const double* f_dev, double alpha, double tol,
                               int maxit, int precision, double* u_dev, bltt_solve_info* info);
 
+/* The solve of bltt_minres_solve_ex (Sec. 2-3, Sec. 5) with f and u in HOST memory: f_host (N*M
+ * doubles) is copied into a device staging buffer on the handle's stream, and u goes back into
+ * u_host on a second stream of the handle as soon as it is final, overlapping the physical-basis
+ * residual check that ends the solve.  Pinned host buffers (cudaHostAlloc / cudaHostRegister)
+ * make both copies asynchronous DMA; pageable ones work but are staged by the driver.  The first
+ * call allocates the two staging vectors and the copy stream; they live until bltt_destroy.
+ * Returns when u_host holds the result (same statuses as bltt_minres_solve_ex; u_host may not
+ * alias f_host; a status raised before the iterations end leaves u_host untouched).  The paper has no host-memory variant: it is the end-to-end form of its solve. */
+bltt_status bltt_minres_solve_host(bltt_handle h, const double* f_host, double alpha, double tol,
+                                   int maxit, const bltt_solve_opts* opts, double* u_host,
+                                   bltt_solve_info* info);
+
 /* Solve many BLTT systems with several right-hand sides each, together (batching: one launch per
  * MINRES phase covers every (system, right-hand side) item of a wave below 2^21 unknowns, and each
  * larger item, which fills the GPU by itself, gets its own launch of that phase; the phase

@@ -84,6 +84,9 @@ _SIGS = {
                                             ctypes.POINTER(bltt_solve_info)]),
     "bltt_minres_solve": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                          ctypes.c_int, _P, ctypes.POINTER(bltt_solve_info)]),
+    "bltt_minres_solve_host": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_int, ctypes.POINTER(bltt_solve_opts), _P,
+                                              ctypes.POINTER(bltt_solve_info)]),
     "bltt_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "bltt_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(bltt_kernel_stat), ctypes.c_int]),
     "bltt_residual_noalloc": (ctypes.c_int, [ctypes.POINTER(bltt_blocks), ctypes.c_int,
@@ -140,6 +143,20 @@ def _ptr(t, name="tensor"):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _host_ptr(t, name="array"):
+    """Address of a contiguous float64 host array (CPU torch tensor or numpy array)."""
+    import torch
+    if isinstance(t, torch.Tensor):
+        if t.dtype != torch.float64 or t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float64 CPU tensor")
+        return ctypes.c_void_p(t.data_ptr())
+    if isinstance(t, np.ndarray):
+        if t.dtype != np.float64 or not t.flags.c_contiguous:
+            raise ValueError(f"{name} must be a C-contiguous float64 array")
+        return ctypes.c_void_p(t.ctypes.data)
+    raise TypeError(f"{name} must be a CPU torch.Tensor or a numpy array")
+
+
 # --------------------------------------------------------------------------------------------
 # functions with the C names
 
@@ -188,6 +205,22 @@ def bltt_minres_solve_ex(handle, f, alpha, tol, maxit, u, precision=PREC_F64, ba
     info = bltt_solve_info()
     st = lib().bltt_minres_solve_ex(handle, _ptr(f, "f"), float(alpha), float(tol), int(maxit),
                                     ctypes.byref(opts), _ptr(u, "u"), ctypes.byref(info))
+    if raise_on_error and st not in (BLTT_OK, 6):
+        _check(st, handle)
+    return st, info.as_dict()
+
+
+def bltt_minres_solve_host(handle, f_host, alpha, tol, maxit, u_host, precision=PREC_F64,
+                           basis=BASIS_AUTO, precond=PRECOND_ABAC, sync_every=0,
+                           raise_on_error=True, rebuild=0, matvec_arith=ARITH_DEFAULT, no_graph=0):
+    """bltt_minres_solve_ex with f and u in host memory (pinned for asynchronous copies)."""
+    if f_host is u_host:
+        raise ValueError("u must not alias f")
+    opts = bltt_solve_opts(precision, basis, precond, sync_every, rebuild, matvec_arith, no_graph)
+    info = bltt_solve_info()
+    st = lib().bltt_minres_solve_host(handle, _host_ptr(f_host, "f"), float(alpha), float(tol),
+                                      int(maxit), ctypes.byref(opts), _host_ptr(u_host, "u"),
+                                      ctypes.byref(info))
     if raise_on_error and st not in (BLTT_OK, 6):
         _check(st, handle)
     return st, info.as_dict()
@@ -368,3 +401,16 @@ class Solver:
                                         matvec_arith, 0 if graph else 1)
         info["status_name"] = STATUS_NAMES.get(st, st)
         return u, info
+
+    def solve_host(self, f_host, alpha=1e-8, tol=1e-8, maxit=200, precision=PREC_F64,
+                   basis=BASIS_AUTO, precond=PRECOND_ABAC, u_host=None, sync_every=0,
+                   raise_on_error=True, rebuild=False, matvec_arith=ARITH_DEFAULT, graph=True):
+        """solve() with f and u in host memory; u_host defaults to a pinned tensor."""
+        import torch
+        if u_host is None:
+            u_host = torch.empty(f_host.shape, dtype=torch.float64, pin_memory=True)
+        st, info = bltt_minres_solve_host(self.handle, f_host, alpha, tol, maxit, u_host,
+                                          precision, basis, precond, sync_every, raise_on_error,
+                                          int(rebuild), matvec_arith, 0 if graph else 1)
+        info["status_name"] = STATUS_NAMES.get(st, st)
+        return u_host, info

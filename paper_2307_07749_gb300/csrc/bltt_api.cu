@@ -128,9 +128,16 @@ struct bltt_ctx {
   std::vector<Pending> pending;
   struct Stat { long long launches = 0; double ms = 0; long long act = 0; double act_ms = 0; double max_ms = 0; };
   std::map<std::string, Stat> stats;
+  // host-buffer solves: device staging of f and u, a copy stream and its event
+  double* io_f = nullptr;
+  double* io_u = nullptr;
+  cudaStream_t io_stream = nullptr;
+  cudaEvent_t io_ev = nullptr;
 
   ~bltt_ctx() {
     if (stream_sync_ok) cudaStreamSynchronize(stream);
+    if (io_stream) { cudaStreamSynchronize(io_stream); cudaStreamDestroy(io_stream); }
+    if (io_ev) cudaEventDestroy(io_ev);
     for (void* p : allocs) cudaFree(p);
     if (state_host) cudaFreeHost(state_host);
     if (scal_host) cudaFreeHost(scal_host);
@@ -676,9 +683,34 @@ bltt_status bltt_precond_apply(bltt_handle h, double alpha, const double* v, dou
   return precond_chain(h, 0, precision, pt, c, z, nullptr, nullptr, nullptr, nullptr);
 }
 
+}  // extern "C"
+
+namespace {
+// where a host-buffer solve copies u back: on h->io_stream, as soon as u is final, so that the
+// copy overlaps the rest of the solve (the physical-basis residual check)
+struct HostOut {
+  double* u_host;
+};
+
+bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol, int maxit,
+                       const bltt_solve_opts* opts, double* u, bltt_solve_info* info,
+                       const HostOut* hout);
+}  // namespace
+
+extern "C" {
+
 bltt_status bltt_minres_solve_ex(bltt_handle h, const double* f, double alpha, double tol,
                                  int maxit, const bltt_solve_opts* opts, double* u,
                                  bltt_solve_info* info) {
+  return solve_impl(h, f, alpha, tol, maxit, opts, u, info, nullptr);
+}
+
+}  // extern "C"
+
+namespace {
+bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol, int maxit,
+                       const bltt_solve_opts* opts, double* u, bltt_solve_info* info,
+                       const HostOut* hout) {
   if (!h) return BLTT_ERR_INVALID_ARG;
   if (info) { std::memset(info, 0, sizeof *info); info->status = BLTT_ERR_INVALID_ARG; }
   if (!f || !u) return fail(h, BLTT_ERR_INVALID_ARG, "null vector");
@@ -849,9 +881,24 @@ bltt_status bltt_minres_solve_ex(bltt_handle h, const double* f, double alpha, d
     }
   }
   double relres_phys = sh->relres_true;
+  // host-buffer solve: u goes back on the copy stream once final
+  auto copy_out = [&]() -> bltt_status {
+    if (!hout) return BLTT_OK;
+    CK(h, cudaEventRecord(h->io_ev, st), "event");
+    CK(h, cudaStreamWaitEvent(h->io_stream, h->io_ev, 0), "wait");
+    CK(h, cudaMemcpyAsync(hout->u_host, u, (size_t)h->n * sizeof(double), cudaMemcpyDeviceToHost,
+                          h->io_stream), "copy u to the host");
+    return BLTT_OK;
+  };
+  if (!spectral) {
+    s = copy_out();
+    if (s != BLTT_OK) return s;
+  }
   if (spectral) {
-    // u = (I (x) U) x_hat, then ||f - A u|| / ||f|| in the physical basis
+    // u = (I (x) U) x_hat, then ||f - A u|| / ||f|| in the physical basis (while u is copied out)
     s = dst_all(h, op, x, u, 0, nullptr, nullptr);
+    if (s != BLTT_OK) return s;
+    s = copy_out();
     if (s != BLTT_OK) return s;
     int nr = 0;
     PCK(h, mv_name(op), launch_matvec(op, 0, u, nullptr, nullptr, 0, MV_RESID, f, h->partials[0], &nr, nullptr,
@@ -888,6 +935,32 @@ bltt_status bltt_minres_solve_ex(bltt_handle h, const double* f, double alpha, d
   if (result == BLTT_ERR_NUMERIC) h->err = "MINRES breakdown: <z, v> negative or non-finite";
   else if (result == BLTT_ERR_NOT_CONVERGED) h->err = "maxit reached before the stopping rule held";
   return result;
+}
+}  // namespace
+
+extern "C" {
+
+bltt_status bltt_minres_solve_host(bltt_handle h, const double* f_host, double alpha, double tol,
+                                   int maxit, const bltt_solve_opts* opts, double* u_host,
+                                   bltt_solve_info* info) {
+  if (!h) return BLTT_ERR_INVALID_ARG;
+  if (info) { std::memset(info, 0, sizeof *info); info->status = BLTT_ERR_INVALID_ARG; }
+  if (!f_host || !u_host) return fail(h, BLTT_ERR_INVALID_ARG, "null vector");
+  if (f_host == u_host) return fail(h, BLTT_ERR_INVALID_ARG, "u must not alias f");
+  if (!h->io_f) {
+    CK(h, h->alloc(&h->io_f, (size_t)h->n), "staging of f");
+    CK(h, h->alloc(&h->io_u, (size_t)h->n), "staging of u");
+    CK(h, cudaStreamCreateWithFlags(&h->io_stream, cudaStreamNonBlocking), "copy stream");
+    CK(h, cudaEventCreateWithFlags(&h->io_ev, cudaEventDisableTiming), "copy event");
+  }
+  CK(h, cudaMemcpyAsync(h->io_f, f_host, (size_t)h->n * sizeof(double), cudaMemcpyHostToDevice,
+                        h->stream), "copy f to the device");
+  const HostOut hout{u_host};
+  const bltt_status st = solve_impl(h, h->io_f, alpha, tol, maxit, opts, h->io_u, info, &hout);
+  // whatever the status, no copy into u_host is still in flight when the call returns
+  const cudaError_t ce = cudaStreamSynchronize(h->io_stream);
+  if (st == BLTT_OK && ce != cudaSuccess) return fail(h, BLTT_ERR_CUDA, cudaGetErrorString(ce));
+  return st;
 }
 
 bltt_status bltt_profile_enable(bltt_handle h, int enable) {

@@ -266,3 +266,36 @@ def test_solve_matches_time_stepping(B):
     u, info = s.solve(to_dev(f), alpha=1e-8, tol=1e-10, maxit=50)
     ustar = O.timestep_solve(prob, f)
     assert rel(to_host(u), ustar) <= 1e-8
+
+
+@pytest.mark.parametrize("form", [dict(precision=64, basis=1, matvec_arith=1, alpha=1e-8),
+                                  dict(precision=32, basis=2, matvec_arith=2, alpha=1e-3),
+                                  dict(precision=32, basis=1, matvec_arith=2, alpha=1e-3)],
+                         ids=["f64_spectral", "f32_physical", "f32_spectral"])
+def test_solve_host_buffers(B, form):
+    # the host-buffer solve: f from host memory, u back into host memory on a copy stream that
+    # overlaps the final residual check; same kernels, so the same bits as the device solve
+    import torch
+    prob = fractional_problem(2, 31, 32, 0.7)
+    f = rhs_uniform(prob.n, 38)
+    st = torch.cuda.Stream()
+    s = B.Solver(prob, stream=st)
+    with torch.cuda.stream(st):
+        ud, idev = s.solve(to_dev(f), tol=1e-8, maxit=50, **form)
+    torch.cuda.synchronize()
+    fp = torch.from_numpy(f).pin_memory()
+    uh, ih = s.solve_host(fp, tol=1e-8, maxit=50, **form)             # pinned, staging allocated
+    uh2, ih2 = s.solve_host(fp, tol=1e-8, maxit=50, **form)           # staging reused
+    upg = np.full(prob.n, np.nan)
+    _, ipg = s.solve_host(f, tol=1e-8, maxit=50, u_host=upg, **form)  # pageable numpy arrays
+    for i in (ih, ih2, ipg):
+        assert i["status"] == 0 and i["iters"] == idev["iters"]
+        assert i["relres_true"] == idev["relres_true"]
+    ref = to_host(ud)
+    assert np.array_equal(uh.numpy(), ref) and np.array_equal(uh2.numpy(), ref)
+    assert np.array_equal(upg, ref)
+    assert rel(O.bltt_matvec(prob, upg), f) <= 1e-8
+    with pytest.raises(ValueError):
+        s.solve_host(fp, u_host=fp)
+    with pytest.raises(ValueError):
+        s.solve_host(to_dev(f))
