@@ -85,8 +85,16 @@ enum { BLTT_PRECOND_ABAC = 0, BLTT_PRECOND_NONE = 1 };
  * F32X2: every value carried as an unevaluated sum of two FP32 numbers (double-float, about 48
  * significant bits) and computed on the FP32 pipes, which GB300 runs at 58x its FP64 rate; the
  * product stays FP64 in memory and agrees with the FP64 result to about 1e-14 relative.
+ * TC: the time convolution of the in-loop products y = Y A z (not the residual checks, which stay
+ * F32X2) runs on the tensor cores as a dense product with the time-flipped Toeplitz (Hankel)
+ * matrix of a: x and a are split into four balanced 8-bit digits relative to a power-of-two
+ * bound of each spatial line (of a), the digit products are exact bf16 x bf16 -> FP32 tensor-core
+ * sums, and the b_0 term and the scale are double-float.  Relative error about 2^-30 of
+ * sum_k |a_k| |x_k| per element.  Requires b = b_0 e_0, an FFT-class a (more than 4 nonzeros)
+ * and N in {128, 256, 512, 1024}; elsewhere it is BLTT_ERR_UNSUPPORTED.  Uses a workspace of
+ * N * 128 * ceil(M/128) * 8 bytes, allocated on first use.
  * DEFAULT: the handle's setting (F64 unless bltt_set_matvec_arith changed it). */
-enum { BLTT_ARITH_DEFAULT = 0, BLTT_ARITH_F64 = 1, BLTT_ARITH_F32X2 = 2 };
+enum { BLTT_ARITH_DEFAULT = 0, BLTT_ARITH_F64 = 1, BLTT_ARITH_F32X2 = 2, BLTT_ARITH_TC = 3 };
 
 typedef struct {
   int precision;     /* BLTT_PREC_F64 (default when 0) or BLTT_PREC_F32                        */
@@ -128,7 +136,7 @@ bltt_status bltt_destroy(bltt_handle h);
 /* Issue all later work of h on `cuda_stream` (a cudaStream_t; NULL = legacy default stream). */
 bltt_status bltt_set_stream(bltt_handle h, void* cuda_stream);
 
-/* Set the handle's matvec arithmetic (BLTT_ARITH_F64 or BLTT_ARITH_F32X2); used by bltt_matvec
+/* Set the handle's matvec arithmetic (BLTT_ARITH_F64, _F32X2 or _TC); used by bltt_matvec
  * and by solves whose opts leave matvec_arith at DEFAULT.  Blocks with at most 4 nonzero
  * coefficients use the direct shifted sum in FP64 whatever this setting. */
 bltt_status bltt_set_matvec_arith(bltt_handle h, int arith);

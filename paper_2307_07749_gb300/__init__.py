@@ -27,7 +27,7 @@ STATUS_NAMES = {
 PREC_F64, PREC_F32, PREC_F32X2 = 64, 32, 96
 BASIS_AUTO, BASIS_SPECTRAL, BASIS_PHYSICAL = 0, 1, 2
 PRECOND_ABAC, PRECOND_NONE = 0, 1
-ARITH_DEFAULT, ARITH_F64, ARITH_F32X2 = 0, 1, 2
+ARITH_DEFAULT, ARITH_F64, ARITH_F32X2, ARITH_TC = 0, 1, 2, 3
 
 
 class BlttError(RuntimeError):

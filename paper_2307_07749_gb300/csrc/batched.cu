@@ -142,7 +142,8 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
   if (o.precision == 0) o.precision = 64;
   if (o.precision != 64 && o.precision != 32 && o.precision != 96) return BLTT_ERR_INVALID_ARG;
   const int prec = o.precision;
-  const int arith = (o.matvec_arith == BLTT_ARITH_F32X2) ? 1 : 0;
+  // the batched driver has no tensor-core product: BLTT_ARITH_TC runs as double-float
+  const int arith = (o.matvec_arith == BLTT_ARITH_F32X2 || o.matvec_arith == BLTT_ARITH_TC) ? 1 : 0;
   int total_items = 0;
   for (int s = 0; s < nsys; ++s) {
     if (nrhs[s] < 1) return BLTT_ERR_INVALID_ARG;

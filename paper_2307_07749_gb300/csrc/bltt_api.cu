@@ -226,6 +226,25 @@ cudaError_t upload_twiddles(bltt_ctx* h, int L, const double2** d64, const float
   return cudaSuccess;
 }
 
+// ensure the tensor-core matvec workspace: digit planes, column exponents, the error flag
+bltt_status ensure_tc(bltt_ctx* h) {
+  if (!tc_eligible(h->op) || !h->op.tc_hank)
+    return fail(h, BLTT_ERR_UNSUPPORTED,
+                "the tensor-core matvec needs b = b0 e_0, more than 4 nonzeros in a and N in "
+                "{128, 256, 512, 1024}");
+  if (h->op.tc_xd) return BLTT_OK;
+  uint16_t* xd = nullptr;
+  int *xe = nullptr, *err = nullptr;
+  CK(h, h->alloc(&xd, tc_workspace_bytes(h->N, h->M) / sizeof(uint16_t)), "digit planes");
+  CK(h, h->alloc(&xe, (size_t)tc_strips(h->M) * 128), "column exponents");
+  CK(h, h->alloc(&err, 1), "error flag");
+  CK(h, cudaMemset(err, 0, sizeof(int)), "error flag");
+  h->op.tc_xd = xd;
+  h->op.tc_xe = xe;
+  h->op.tc_err = err;
+  return BLTT_OK;
+}
+
 // ensure the solve workspace: 10 vectors of n doubles, partial sums, device scalar state
 bltt_status ensure_workspace(bltt_ctx* h) {
   if (h->ws) return BLTT_OK;
@@ -407,8 +426,10 @@ bltt_status dst_all(bltt_ctx* h, const OpTables& op, const double* in, double* o
   return BLTT_OK;
 }
 
-const char* mv_name(const OpTables& op) {
-  return op.ntaps > 0 ? "direct" : (op.mv_arith ? "conv_df" : "conv");
+const char* mv_name(const OpTables& op, int mode = MV_STORE) {
+  if (op.ntaps > 0) return "direct";
+  if (op.mv_arith == 2 && mode == MV_STORE) return "conv_tc";
+  return op.mv_arith ? "conv_df" : "conv";
 }
 
 cudaEvent_t prof_event(bltt_ctx* h) {
@@ -610,6 +631,19 @@ bltt_status bltt_create(const bltt_blocks* blocks, int N, long long M, bltt_hand
     e = upload_df(h, tw, &op.tw_2N_df);
   }
   op.mv_arith = 0;
+  // tensor-core time product: digit planes of the time-flipped a (when the problem qualifies)
+  if (e == cudaSuccess && tc_eligible(op)) {
+    int eT = 0, nc = 0;
+    std::vector<uint16_t> hank((size_t)kTcDigits * (16 * (N / 128) + 15) * 64);
+    tc_hankel_digits(h->a.data(), N, hank.data(), &eT, &nc);
+    if (eT >= -60 && eT <= 60) {
+      uint16_t* ph = nullptr;
+      e = upload(h, &ph, hank.data(), hank.size());
+      op.tc_hank = ph;
+      op.tc_eT = eT;
+      op.tc_ncores = nc;
+    }
+  }
   if (e == cudaSuccess) e = upload_twiddles(h, N, &op.tw_N, &op.tw_N32);
   if (e == cudaSuccess) {
     const std::vector<double2>& tw = twiddles(N);
@@ -648,9 +682,13 @@ bltt_status bltt_set_stream(bltt_handle h, void* s) {
 
 bltt_status bltt_set_matvec_arith(bltt_handle h, int arith) {
   if (!h) return BLTT_ERR_INVALID_ARG;
-  if (arith != BLTT_ARITH_F64 && arith != BLTT_ARITH_F32X2)
-    return fail(h, BLTT_ERR_INVALID_ARG, "arith must be BLTT_ARITH_F64 or BLTT_ARITH_F32X2");
-  h->op.mv_arith = (arith == BLTT_ARITH_F32X2) ? 1 : 0;
+  if (arith != BLTT_ARITH_F64 && arith != BLTT_ARITH_F32X2 && arith != BLTT_ARITH_TC)
+    return fail(h, BLTT_ERR_INVALID_ARG, "arith must be BLTT_ARITH_F64, _F32X2 or _TC");
+  if (arith == BLTT_ARITH_TC) {
+    bltt_status s = ensure_tc(h);
+    if (s != BLTT_OK) return s;
+  }
+  h->op.mv_arith = (arith == BLTT_ARITH_TC) ? 2 : (arith == BLTT_ARITH_F32X2) ? 1 : 0;
   return BLTT_OK;
 }
 
@@ -729,13 +767,19 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
   const int spectral = (basis == BLTT_BASIS_SPECTRAL) ? 1 : 0;
   const int sync_every = o.sync_every > 0 ? o.sync_every : 2;
 
-  if (o.matvec_arith < 0 || o.matvec_arith > 2) return fail(h, BLTT_ERR_INVALID_ARG, "bad matvec_arith");
+  if (o.matvec_arith < 0 || o.matvec_arith > 3) return fail(h, BLTT_ERR_INVALID_ARG, "bad matvec_arith");
   bltt_status s = ensure_workspace(h);
   if (s != BLTT_OK) return s;
+  if (o.matvec_arith == BLTT_ARITH_TC) {
+    s = ensure_tc(h);
+    if (s != BLTT_OK) return s;
+  }
   h->launches = 0;
   OpTables op = h->op;
   if (o.matvec_arith == BLTT_ARITH_F64) op.mv_arith = 0;
   if (o.matvec_arith == BLTT_ARITH_F32X2) op.mv_arith = 1;
+  if (o.matvec_arith == BLTT_ARITH_TC) op.mv_arith = 2;
+  const bool tc = (op.mv_arith == 2);
   cudaStream_t st = h->stream;
   CK(h, cudaEventRecord(h->ev[0], st), "event");
   if (o.rebuild) h->pc_alpha = -1.0;
@@ -792,7 +836,7 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
 
   // one MINRES iteration (A1..A4 of the hot loop); the caller rotates the buffers afterwards
   const long long per_iter = 5 + ((op.b_kind == 1 && op.ntaps == 0 && !spectral) ? 4 : 2) +
-                             (spectral || none ? 0 : 2 * op.d);
+                             (spectral || none ? 0 : 2 * op.d) + (tc ? 1 : 0);
   auto issue_iteration = [&](int c0) -> bltt_status {
     const long long saved = h->launches;   // counted per iteration by the caller (per_iter)
     struct Restore { bltt_ctx* hh; long long v; ~Restore() { hh->launches = v; } } restore{h, saved};
@@ -812,7 +856,7 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
     PCK(h, "scalar", launch_scalar_gamma(h->state, h->partials[1], np, st), "scalar gamma");
     PCK(h, "w_update", launch_w_update(h->state, zbuf[c0], wbuf[prv], wbuf[c0], x, n, st), "w update");
     // true residual when the estimate says so
-    PCK(h, mv_name(op), launch_matvec(op, spectral, x, nullptr, nullptr, 1, MV_RESID, bvec,
+    PCK(h, mv_name(op, MV_RESID), launch_matvec(op, spectral, x, nullptr, nullptr, 1, MV_RESID, bvec,
                                       h->partials[0], &np, phase, tmp, st), "residual");
     PCK(h, "scalar", launch_scalar_check(h->state, h->partials[0], np, st), "scalar check");
     return BLTT_OK;
@@ -901,7 +945,7 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
     s = copy_out();
     if (s != BLTT_OK) return s;
     int nr = 0;
-    PCK(h, mv_name(op), launch_matvec(op, 0, u, nullptr, nullptr, 0, MV_RESID, f, h->partials[0], &nr, nullptr,
+    PCK(h, mv_name(op, MV_RESID), launch_matvec(op, 0, u, nullptr, nullptr, 0, MV_RESID, f, h->partials[0], &nr, nullptr,
                         tmp, st), "final residual");
     h->launches += (op.b_kind == 1 && op.ntaps == 0) ? 2 : 1;
     PCK(h, "scalar", launch_sum_partials(h->partials[0], nr, h->scal, st), "sum");
@@ -931,6 +975,16 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
     info->t_solve_ms = t_all;
     info->kernel_launches = h->launches;
     info->status = result;
+  }
+  if (tc) {
+    // a bounded wait of the tensor-core kernel that gave up shows as NaN partials; name it
+    int flag = 0;
+    CK(h, cudaMemcpy(&flag, op.tc_err, sizeof(int), cudaMemcpyDeviceToHost), "error flag");
+    if (flag) {
+      CK(h, cudaMemset(op.tc_err, 0, sizeof(int)), "error flag");
+      if (info) info->status = BLTT_ERR_TIMEOUT;
+      return fail(h, BLTT_ERR_TIMEOUT, "a bounded wait of the tensor-core matvec gave up");
+    }
   }
   if (result == BLTT_ERR_NUMERIC) h->err = "MINRES breakdown: <z, v> negative or non-finite";
   else if (result == BLTT_ERR_NOT_CONVERGED) h->err = "maxit reached before the stopping rule held";

@@ -54,7 +54,16 @@ struct OpTables {
   const float4* tw_2N_df;
   const float4* tw_dst_df[3];
   const float4* tw_N_df;
-  int mv_arith;               // 0: FP64, 1: double-float (matvec and the FP64-accurate DSTs)
+  int mv_arith;               // 0: FP64, 1: double-float (matvec and the FP64-accurate DSTs),
+                              // 2: tensor-core time product in MV_STORE matvecs, else as 1
+  // tensor-core time product (kernels in tcmv.cu): bf16 digit planes of the time-flipped
+  // coefficients as 8x8 Hankel core matrices, their power-of-two scale, and the workspace that
+  // receives the digit planes and column exponents of each matvec input
+  const uint16_t* tc_hank;    // [kTcDigits][tc_ncores][64] bf16 bit patterns (device)
+  int tc_ncores, tc_eT;
+  uint16_t* tc_xd;            // [strips][N/16][kTcDigits][2048] bf16 bit patterns (device)
+  int* tc_xe;                 // [strips * 128] column exponents (device)
+  int* tc_err;                // device flag: a bounded wait of the tensor-core kernel gave up
 };
 
 // Per-alpha preconditioner data.
@@ -98,6 +107,18 @@ enum MvMode { MV_STORE = 0, MV_RESID = 1 };
 cudaError_t launch_matvec(const OpTables& op, int spectral, const double* x, const double* xscale,
                           double* y, int flip, int mode, const double* rhs, double* partials,
                           int* nparts, const int* phase, double* tmp, cudaStream_t st);
+// tensor-core time product (tcmv.cu)
+constexpr int kTcDigits = 5;          // bf16 digit planes per operand
+bool tc_eligible(const OpTables& op); // b = b0 e_0, FFT-class a, N in {128, 256, 512, 1024}
+int tc_strips(long long M);           // 128-line strips of the spatial index
+size_t tc_workspace_bytes(int N, long long M);
+// digit planes of the time-flipped a (host), eT with max|a| < 2^eT, ncores = 16 N/128 + 15
+void tc_hankel_digits(const double* a, int N, uint16_t* out, int* eT, int* ncores);
+// y = Y A (s x) or A (s x) (flip 0) with the time product on the tensor cores; partials (if not
+// null) receive <y, s x> per block, *nparts their count
+cudaError_t launch_tc_matvec(const OpTables& op, int spectral, const double* x,
+                             const double* xscale, double* y, int flip, double* partials,
+                             int* nparts, const int* phase, cudaStream_t st);
 cudaError_t launch_setup_g64(const OpTables& op, const double2* ahat, const double2* bhat,
                              double2* g64, float4* gdf, cudaStream_t st);
 cudaError_t launch_setup_gdf(const OpTables& op, const float2* ahat32, const float2* bhat32,

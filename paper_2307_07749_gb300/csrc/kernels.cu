@@ -6,15 +6,12 @@
 #include <type_traits>
 #include "common.cuh"
 #include "internal.h"
+#include "opdev.cuh"
 
 namespace bltt {
 
 // ============================================================================================
 // helpers
-__device__ __forceinline__ bool skip_phase(const int* phase, int want) {
-  return phase != nullptr && *phase != want;
-}
-
 __device__ __forceinline__ void load_coef(const Combine& cb, double& c0, double& c1, double& c2) {
   c0 = 1.0;
   if (cb.coef) { c1 = cb.coef[1]; c2 = cb.coef[2]; }
@@ -38,49 +35,6 @@ __device__ __forceinline__ double combine_at(const Combine& cb, long long e, dou
   if (cb.in2) v = fma(c2, __ldcs(cb.in2 + e), v);
   cb.vout[e] = v;
   return v;
-}
-
-// eigenvalue of L for spatial mode i (x fastest): sum over axes of the 1-D eigenvalues
-__device__ __forceinline__ double mode_mu(const OpTables& op, long long i) {
-  long long r = i / op.m[0];
-  double mu = op.mu_axis[0][i - r * op.m[0]];
-  if (op.d > 1) {
-    long long r2 = r / op.m[1];
-    mu += op.mu_axis[1][r - r2 * op.m[1]];
-    if (op.d > 2) mu += op.mu_axis[2][r2];
-  }
-  return mu;
-}
-__device__ __forceinline__ float mode_mu32(const OpTables& op, long long i) {
-  long long r = i / op.m[0];
-  float mu = op.mu_axis32[0][i - r * op.m[0]];
-  if (op.d > 1) {
-    long long r2 = r / op.m[1];
-    mu += op.mu_axis32[1][r - r2 * op.m[1]];
-    if (op.d > 2) mu += op.mu_axis32[2][r2];
-  }
-  return mu;
-}
-
-// (L x)[i] on the time slice starting at x_t: the 2d+1 point Dirichlet stencil (Sec. 5.2)
-__device__ __forceinline__ double stencil_at(const OpTables& op, const double* __restrict__ x_t,
-                                             long long i) {
-  const double xi = x_t[i];
-  double acc = 0.0;
-  long long r = i, stride = 1;
-#pragma unroll 1
-  for (int ax = 0; ax < op.d; ++ax) {
-    const int mm = op.m[ax];
-    long long q = r / mm;
-    int c = (int)(r - q * mm);
-    r = q;
-    double s = 2.0 * xi;
-    if (c > 0) s -= x_t[i - stride];
-    if (c < mm - 1) s -= x_t[i + stride];
-    acc = fma(s, op.h2inv[ax], acc);
-    stride *= mm;
-  }
-  return acc;
 }
 
 // principal (x + i y)^{-1/2} for x > 0, by the half-angle form of the square root:
@@ -1233,7 +1187,9 @@ cudaError_t launch_matvec(const OpTables& op, int spectral, const double* x, con
                                 want);
     return cudaGetLastError();
   }
-  if (op.mv_arith == 1)
+  if (op.mv_arith == 2 && mode == MV_STORE)
+    return launch_tc_matvec(op, spectral, x, xscale, y, flip, partials, nparts, phase, st);
+  if (op.mv_arith >= 1)
     return launch_conv_t<ArithDF>(op, spectral, x, xscale, y, flip, mode, rhs, partials, nparts,
                                   phase, want, tmp, st);
   return launch_conv_t<ArithD>(op, spectral, x, xscale, y, flip, mode, rhs, partials, nparts,
