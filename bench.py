@@ -70,14 +70,15 @@ def df_conv_ops(N):
 
 
 def peaks():
-    p = {"hbm_gbs": 6695.5, "source": "fallback"}
+    p = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             j = json.load(fh)
         p["hbm_gbs"] = float(j["hbm_gbs"])
+        p["bf16_tflops"] = float(j["bf16_tflops"])
         p["source"] = "measured"
     except Exception:
-        p["hbm_gbs"] = 6800.0
+        pass
     return p
 
 
@@ -93,6 +94,13 @@ def kernel_cost(name, N, m, d):
         return "alu32", 16.0, df_conv_ops(N)
     if name == "direct":
         return "hbm", 16.0, 6.0
+    # tensor-core product: 15 digit-pair MMAs over the input times that reach each output block
+    # of 128 times (128 (NB - rb) for row block rb of NB = N/128), 2 flops per multiply-add
+    if name == "conv_tc":
+        NB = N // 128
+        return "tensor", 24.0, 2.0 * 15 * 128 * (NB + 1) / 2
+    if name == "tc_digits":   # read x, write five bf16 digit planes
+        return "hbm", 18.0, 0.0
     # the time pass inside the loop fuses the Lanczos combine: q, v_j, v_{j-1} read, v_{j+1} and z
     # written (40 B); the FP64 and double-float forms also read the lambda^{-1/2} table (8 B once)
     if name in ("timepass64", "timepass32"):   # 4 real FFTs of N, 2 spectral products, 3 scalings
@@ -310,6 +318,7 @@ FORMS = {
     "plain_f64": dict(alpha=ALPHA_F64, precision=64, basis=1, arith=1),
     "f32x2_all": dict(alpha=ALPHA_F32X2, precision=96, basis=1, arith=2),
     "f32_physical": dict(alpha=ALPHA_F32, precision=32, basis=2, arith=2),
+    "tc": dict(alpha=ALPHA_F32, precision=32, basis=1, arith=3),
 }
 
 
@@ -461,7 +470,7 @@ def main():
     ap.add_argument("--workload", default="frac2d", choices=["frac2d", "batched", "alpha", "once"],
                     help="frac2d: the headline line; batched / alpha: supplementary reports; "
                          "once: a single solve of the headline workload (for ncu captures)")
-    ap.add_argument("--form", default="chosen", choices=["chosen", "plain_f64", "f32x2_all", "f32_physical"])
+    ap.add_argument("--form", default="chosen", choices=list(FORMS))
     ap.add_argument("--m", type=int, default=255, choices=[63, 127, 255],
                     help="--workload once: interior points per axis (255: the headline workload)")
     ap.add_argument("--alpha-train", type=int, default=2000)
@@ -501,6 +510,7 @@ def main():
                           arith=B.ARITH_F32X2),
         "f32_physical": dict(alpha=ALPHA_F32, precision=32, basis=B.BASIS_PHYSICAL,
                              arith=B.ARITH_F32X2),
+        "tc": dict(alpha=ALPHA_F32, precision=32, basis=B.BASIS_SPECTRAL, arith=B.ARITH_TC),
     }
     res = {}
     with torch.cuda.stream(stream):
@@ -531,7 +541,7 @@ def main():
 
     ch = summarise(res["chosen"])
     pl = summarise(res["plain_f64"])
-    others = {k: summarise(res[k]) for k in ("f32x2_all", "f32_physical")}
+    others = {k: summarise(res[k]) for k in ("f32x2_all", "f32_physical", "tc")}
 
     # roofline of the dominant kernel of the chosen form (live CUDA-event durations)
     pk = peaks()
@@ -551,6 +561,11 @@ def main():
             kern.append(dict(name=name, launches=launches, total_ms=tot_ms, bound="alu",
                              achieved=ach, peak=FP32_PEAK_TOPS, unit="Tops/s (FP32 pipe)",
                              frac=ach / FP32_PEAK_TOPS, bytes_per_unit=bpu, flops_per_unit=fpu))
+        elif bound == "tensor":
+            ach = fpu * units / (avg_ms / 1e3) / 1e12
+            kern.append(dict(name=name, launches=launches, total_ms=tot_ms, bound="tensor",
+                             achieved=ach, peak=pk["bf16_tflops"], unit="TFLOP/s (bf16 tensor)",
+                             frac=ach / pk["bf16_tflops"], bytes_per_unit=bpu, flops_per_unit=fpu))
         elif bpu > 0:
             ach = bpu * units / (avg_ms / 1e3) / 1e9
             kern.append(dict(name=name, launches=launches, total_ms=tot_ms, bound="hbm",
@@ -627,6 +642,7 @@ def main():
             "kernels": [{k: (round(v, 5) if isinstance(v, float) else v) for k, v in kk.items()}
                         for kk in kern],
             "kernels_plain_f64": {k: [int(v[2]), round(v[3], 4)] for k, v in res["plain_f64"]["profile"].items()},
+            "kernels_tc": {k: [int(v[2]), round(v[3], 4)] for k, v in res["tc"]["profile"].items()},
             "e2e": e2e,
             "gpu_launches": ch["launches"],
             "clocks": res["chosen"]["clocks"],

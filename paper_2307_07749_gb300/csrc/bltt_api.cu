@@ -842,8 +842,16 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
     struct Restore { bltt_ctx* hh; long long v; ~Restore() { hh->launches = v; } } restore{h, saved};
     const int prv = 1 - c0;
     // q = Y A z_j  (z_j = z_u / gamma_j), delta_j = <q, z_j>
-    PCK(h, mv_name(op), launch_matvec(op, spectral, zbuf[c0], &h->state->inv_gamma, q, 1, MV_STORE,
-                                      nullptr, h->partials[0], &np, phase, tmp, st), "matvec");
+    if (tc) {
+      // the two kernels of the tensor-core product, profiled apart
+      PCK(h, "tc_digits", launch_tc_digits(op, zbuf[c0], phase, st), "digit planes");
+      PCK(h, "conv_tc", launch_tc_product(op, spectral, zbuf[c0], &h->state->inv_gamma, q, 1,
+                                          h->partials[0], &np, phase, st), "matvec");
+    } else {
+      PCK(h, mv_name(op), launch_matvec(op, spectral, zbuf[c0], &h->state->inv_gamma, q, 1,
+                                        MV_STORE, nullptr, h->partials[0], &np, phase, tmp, st),
+          "matvec");
+    }
     PCK(h, "scalar", launch_scalar_delta(h->state, h->partials[0], np, st), "scalar delta");
     // v_{j+1} = q - (delta/gamma) v_j - (gamma/gamma_prev) v_{j-1} (over v_{j-1});
     // z_{j+1} = P^{-1} v_{j+1} (over z_{j-1}); <z_{j+1}, v_{j+1}>

@@ -408,7 +408,9 @@ __global__ void __launch_bounds__(kThreadsMv, 1) k_tc_mv(const MvParams p) {
       if (!mbar_wait(done_bar, 0)) *err = 1;
     }
   } else {
-    // epilogue: warp w reads TMEM lanes 32 (w % 4) ..: line jj; 32 output times per warp
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) ..: line jj, 32 output times per warp.  The
+    // three accumulators are folded into a double-float value per output and TMEM is released
+    // at once, so that the next unit's MMAs run while this unit's outputs are finished.
     const int q = warp & 3, chunk = (warp - 2) >> 2;
     const int jj = 32 * q + lane;
     const double s = p.xscale ? *p.xscale : 1.0;
@@ -417,58 +419,65 @@ __global__ void __launch_bounds__(kThreadsMv, 1) k_tc_mv(const MvParams p) {
     for (int u = blockIdx.x; u < p.nunits; u += gridDim.x, ++ui) {
       if (*err || !mbar_wait(tfull, ui & 1u)) { *err = 1; break; }
       tc_after_sync();
-      int strip, rb;
-      unit_of(u, p.nstrips, NB, strip, rb);
-      const long long j = (long long)strip * kRows + jj;
-      const bool valid = j < M;
-      const int e = valid ? op.tc_xe[j] : 0;
-      const int kx = op.tc_eT + e - 14;          // time product = accumulators x 2^kx
-      dfl cdf = {0.0f, 0.0f};
-      if (valid && p.spectral) cdf = df_from(op.b0 * mode_mu(op, j) * s);
-      dfl dot_df = {0.0f, 0.0f};
-      double dot_u = 0.0;
-#pragma unroll 1
+      float hh[32], ll[32];
+#pragma unroll
       for (int half = 0; half < 2; ++half) {
-        const int col = 32 * chunk + 16 * half;
-        const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col;
+        const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * chunk + 16 * half);
         float a0[16], a1[16], a2[16];
         __syncwarp();
         tmem_ld16(ta, a0);
         tmem_ld16(ta + 128u, a1);
         tmem_ld16(ta + 256u, a2);
-        if (!valid) continue;
 #pragma unroll
         for (int cc = 0; cc < 16; ++cc) {
-          const int n = kCols * rb + col + cc;       // flipped time of the Hankel row
-          const int t = N - 1 - n;
-          const int srow = p.flip ? n : t;
           // (h, l) = a0 + a1 + a2: two-sum of the exact parts, the rounded part folded in
           const float h = __fadd_rn(a0[cc], a1[cc]);
           const float bb = __fsub_rn(h, a0[cc]);
-          float l = __fadd_rn(__fsub_rn(a0[cc], __fsub_rn(h, bb)), __fsub_rn(a1[cc], bb));
-          l = __fadd_rn(l, a2[cc]);
-          double val;
-          const long long oi = (long long)srow * M + j;
-          if (p.spectral) {
-            const dfl xt = d2df_shift(__ldcg(p.x + (long long)t * M + j), -kx);
-            const dfl w = df_dot2(sdf, dfl{h, l}, cdf, xt);
-            val = f2d_shift(w.hi, kx) + f2d_shift(w.lo, kx);
-            p.y[oi] = val;
-            if (p.partials) dot_df = df_add(dot_df, df_mul(w, d2df_shift(__ldcg(p.x + oi), -kx)));
-          } else {
-            const double tp = f2d_shift(h, kx) + f2d_shift(l, kx);
-            const double lap = stencil_at(op, p.x + (long long)t * M, j);
-            val = s * fma(op.b0, lap, tp);
-            p.y[oi] = val;
-            if (p.partials) dot_u = fma(val, __ldcg(p.x + oi), dot_u);
-          }
+          const float l = __fadd_rn(__fsub_rn(a0[cc], __fsub_rn(h, bb)), __fsub_rn(a1[cc], bb));
+          hh[16 * half + cc] = h;
+          ll[16 * half + cc] = __fadd_rn(l, a2[cc]);
         }
       }
-      if (p.spectral) dot_u = ldexp(df_to(dot_df), 2 * kx);
-      dot += dot_u;
       tc_before_sync();
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty);
+      int strip, rb;
+      unit_of(u, p.nstrips, NB, strip, rb);
+      const long long j = (long long)strip * kRows + jj;
+      if (j >= M) continue;
+      const int e = op.tc_xe[j];
+      const int kx = op.tc_eT + e - 14;          // time product = accumulators x 2^kx
+      const dfl cdf = p.spectral ? df_from(op.b0 * mode_mu(op, j) * s) : dfl{0.0f, 0.0f};
+      const int n0 = kCols * rb + 32 * chunk;    // flipped time of the first Hankel row
+      double dot_u = 0.0;
+      // batches of four outputs: every load of a batch is issued before its first store
+#pragma unroll
+      for (int b0 = 0; b0 < 32; b0 += 4) {
+        double xt[4], xs[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int n = n0 + b0 + i, t = N - 1 - n;
+          const int srow = p.flip ? n : t;
+          xt[i] = p.spectral ? __ldcg(p.x + (long long)t * M + j) : 0.0;
+          xs[i] = p.partials ? __ldcg(p.x + (long long)srow * M + j) : 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int n = n0 + b0 + i, t = N - 1 - n;
+          const int srow = p.flip ? n : t;
+          double val;
+          if (p.spectral) {
+            const dfl w = df_dot2(sdf, dfl{hh[b0 + i], ll[b0 + i]}, cdf, d2df_shift(xt[i], -kx));
+            val = f2d_shift(w.hi, kx) + f2d_shift(w.lo, kx);
+          } else {
+            const double tp = f2d_shift(hh[b0 + i], kx) + f2d_shift(ll[b0 + i], kx);
+            val = s * fma(op.b0, stencil_at(op, p.x + (long long)t * M, j), tp);
+          }
+          p.y[(long long)srow * M + j] = val;
+          dot_u = fma(val, xs[i], dot_u);
+        }
+      }
+      dot += dot_u;
     }
   }
   __syncthreads();
@@ -527,9 +536,18 @@ void tc_hankel_digits(const double* a, int N, uint16_t* out, int* eT, int* ncore
   *ncores = nc;
 }
 
-cudaError_t launch_tc_matvec(const OpTables& op, int spectral, const double* x,
-                             const double* xscale, double* y, int flip, double* partials,
-                             int* nparts, const int* phase, cudaStream_t st) {
+cudaError_t launch_tc_digits(const OpTables& op, const double* x, const int* phase,
+                             cudaStream_t st) {
+  if (!tc_eligible(op) || !op.tc_xd || !op.tc_xe) return cudaErrorInvalidValue;
+  const int nstrips = tc_strips(op.M);
+  k_tc_digits<<<(unsigned)(nstrips * (kRows / 32)), 256, 0, st>>>(x, op.N, op.M, op.tc_xd,
+                                                                    op.tc_xe, phase);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_product(const OpTables& op, int spectral, const double* x,
+                              const double* xscale, double* y, int flip, double* partials,
+                              int* nparts, const int* phase, cudaStream_t st) {
   if (!tc_eligible(op) || !op.tc_hank || !op.tc_xd || !op.tc_xe || !op.tc_err)
     return cudaErrorInvalidValue;
   if (g_num_sms == 0) {
@@ -542,8 +560,6 @@ cudaError_t launch_tc_matvec(const OpTables& op, int spectral, const double* x,
     g_num_sms = n;
   }
   const int nstrips = tc_strips(op.M);
-  k_tc_digits<<<(unsigned)(nstrips * (kRows / 32)), 256, 0, st>>>(x, op.N, op.M, op.tc_xd,
-                                                                    op.tc_xe, phase);
   MvParams prm;
   prm.op = op;
   prm.x = x;
@@ -560,6 +576,14 @@ cudaError_t launch_tc_matvec(const OpTables& op, int spectral, const double* x,
   if (nparts) *nparts = grid;
   k_tc_mv<<<grid, kThreadsMv, kSmemMv, st>>>(prm);
   return cudaGetLastError();
+}
+
+cudaError_t launch_tc_matvec(const OpTables& op, int spectral, const double* x,
+                             const double* xscale, double* y, int flip, double* partials,
+                             int* nparts, const int* phase, cudaStream_t st) {
+  cudaError_t e = launch_tc_digits(op, x, phase, st);
+  if (e != cudaSuccess) return e;
+  return launch_tc_product(op, spectral, x, xscale, y, flip, partials, nparts, phase, st);
 }
 
 }  // namespace bltt
