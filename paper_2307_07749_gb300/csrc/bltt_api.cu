@@ -844,7 +844,8 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
     // q = Y A z_j  (z_j = z_u / gamma_j), delta_j = <q, z_j>
     if (tc) {
       // the two kernels of the tensor-core product, profiled apart
-      PCK(h, "tc_digits", launch_tc_digits(op, zbuf[c0], phase, st), "digit planes");
+      PCK(h, "tc_digits", launch_tc_digits(op, zbuf[c0], &h->state->inv_gamma, phase, st),
+          "digit planes");
       PCK(h, "conv_tc", launch_tc_product(op, spectral, zbuf[c0], &h->state->inv_gamma, q, 1,
                                           h->partials[0], &np, phase, st), "matvec");
     } else {

@@ -116,9 +116,9 @@ size_t tc_workspace_bytes(int N, long long M);
 void tc_hankel_digits(const double* a, int N, uint16_t* out, int* eT, int* ncores);
 // y = Y A (s x) or A (s x) (flip 0) with the time product on the tensor cores; partials (if not
 // null) receive <y, s x> per block, *nparts their count.  launch_tc_matvec = launch_tc_digits
-// (digit planes and line exponents of x into the workspace) then launch_tc_product.
-cudaError_t launch_tc_digits(const OpTables& op, const double* x, const int* phase,
-                             cudaStream_t st);
+// (digit planes and line exponents of s x into the workspace) then launch_tc_product.
+cudaError_t launch_tc_digits(const OpTables& op, const double* x, const double* xscale,
+                             const int* phase, cudaStream_t st);
 cudaError_t launch_tc_product(const OpTables& op, int spectral, const double* x,
                               const double* xscale, double* y, int flip, double* partials,
                               int* nparts, const int* phase, cudaStream_t st);

@@ -190,29 +190,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 }
 
 // ------------------------------------------------------------------------------------------
-// double <-> double-float with a power-of-two scale, on the integer pipes
+// float -> double with a power-of-two scale, on the integer pipes
 
-// x 2^k as (hi, lo): hi = x 2^k rounded to FP32, lo the next ~22 bits; 0 when x 2^k leaves the
-// normal FP32 range downwards (the caller's scale keeps |x 2^k| < 2^24)
-__device__ __forceinline__ dfl d2df_shift(double x, int k) {
-  const uint64_t b = bits_d(x);
-  const uint32_t hw = (uint32_t)(b >> 32), lw = (uint32_t)b;
-  const int E = (int)((hw >> 20) & 0x7FFu);
-  const int ef = E - 1023 + 127 + k;
-  if (E == 0 || ef <= 0) return {0.0f, 0.0f};
-  const uint32_t sign = hw & 0x80000000u;
-  const uint32_t m = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
-  const uint32_t rest = lw & 0x1FFFFFFFu;
-  const uint32_t up = (rest > 0x10000000u) | ((rest == 0x10000000u) & (m & 1u));
-  const float hi = __uint_as_float((((uint32_t)ef << 23) + m + up) | sign);
-  // remainder (rest - up 2^29) in units of 2^(E-1075+k), kept to 22 bits
-  const int r = ((int)rest - (int)(up << 29)) >> 7;
-  const float rf = __int_as_float(0x4B400000 + r) - 12582912.0f;
-  const int el = ef - 23 - 29 + 7;                // exponent field of 2^(E-1075+k+7)
-  float lo = 0.0f;
-  if (el > 0) lo = rf * __uint_as_float((uint32_t)el << 23);
-  return {hi, sign ? -lo : lo};
-}
 // f 2^k as a double (exact); k moves the exponent field, zero stays zero
 __device__ __forceinline__ double f2d_shift(float f, int k) {
   const double d = f2d_bits(f);
@@ -221,14 +200,18 @@ __device__ __forceinline__ double f2d_shift(float f, int k) {
 }
 
 // ------------------------------------------------------------------------------------------
-// digit planes of x: block = 32 lines (a quarter strip) x all N times, 256 threads.  Pass 1
-// takes the largest exponent of each line, pass 2 writes the digits in the A-operand image:
+// digit planes of s x (s = *xscale, 1 when null): block = 32 lines (a quarter strip) x all N
+// times, 256 threads.  Pass 1 takes the largest exponent of each line of x, which with that of s
+// bounds the line of s x (one bit loose at most); pass 2 writes the digits in the A-operand image:
 // per (strip, K step, plane) 128 lines x 16 times, core matrix (line/8, time/8) at byte
 // (line/8) 128 + (time/8) 2048, row line%8 at 16 bytes, time%8 at 2 bytes.
-__global__ void __launch_bounds__(256) k_tc_digits(const double* __restrict__ x, int N,
+__global__ void __launch_bounds__(256) k_tc_digits(const double* __restrict__ x,
+                                                   const double* __restrict__ xscale, int N,
                                                    long long M, uint16_t* __restrict__ xd,
                                                    int* __restrict__ xe, const int* phase) {
   if (skip_phase(phase, PH_RUN)) return;
+  const double sc = xscale ? *xscale : 1.0;
+  const int es = tc_exp_bound((int)((bits_d(sc) >> 52) & 0x7FF));   // |s| < 2^es
   __shared__ int s_e[8][32];
   const int c = threadIdx.x & 31, r0 = threadIdx.x >> 5;
   const long long j = (long long)blockIdx.x * 32 + c;
@@ -244,10 +227,10 @@ __global__ void __launch_bounds__(256) k_tc_digits(const double* __restrict__ x,
   if (r0 == 0) {
     for (int r = 1; r < 8; ++r) emax = max(emax, s_e[r][c]);
     s_e[0][c] = emax;
-    xe[j] = tc_exp_bound(emax);
+    xe[j] = (emax == 0) ? 0 : tc_exp_bound(emax) + es;
   }
   __syncthreads();
-  const int e = tc_exp_bound(s_e[0][c]);
+  const int e = (s_e[0][c] == 0) ? 0 : tc_exp_bound(s_e[0][c]) + es;
   const long long strip = j >> 7;
   const int jj = (int)(j & 127);
   const int NKS = N / kKs;
@@ -255,7 +238,7 @@ __global__ void __launch_bounds__(256) k_tc_digits(const double* __restrict__ x,
   for (int kg = r0; kg < N / 8; kg += 8) {
     double v[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = valid ? __ldcs(x + (long long)(8 * kg + i) * M + j) : 0.0;
+    for (int i = 0; i < 8; ++i) v[i] = valid ? sc * __ldcs(x + (long long)(8 * kg + i) * M + j) : 0.0;
     uint32_t w[kTcDigits][4];
 #pragma unroll
     for (int i = 0; i < 8; i += 2) {
@@ -297,11 +280,16 @@ __device__ __forceinline__ void unit_of(int u, int nstrips, int NB, int& strip, 
 
 // the fifteen digit pairs (i of a', j of x) with i + j <= 4, their accumulator and whether they
 // open it (first product into the accumulator in a unit's first K step)
+// (pairs in order of weight g = i + j, i rising inside a weight)
 constexpr int kPairs = 15;
-__constant__ int c_pair_i[kPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4};
-__constant__ int c_pair_j[kPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0};
-__constant__ int c_pair_acc[kPairs] = {0, 1, 1, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2};
-__constant__ int c_pair_open[kPairs] = {1, 1, 0, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+struct Pair {
+  int i, j, acc, open;
+};
+__host__ __device__ constexpr Pair pair_of(int q) {
+  const int g = q < 1 ? 0 : q < 3 ? 1 : q < 6 ? 2 : q < 10 ? 3 : 4;
+  const int i = q - g * (g + 1) / 2;
+  return Pair{i, g - i, g < 2 ? g : 2, (i == 0 && g <= 2) ? 1 : 0};
+}
 
 __global__ void __launch_bounds__(kThreadsMv, 1) k_tc_mv(const MvParams p) {
   if (skip_phase(p.phase, PH_RUN)) return;
@@ -377,7 +365,12 @@ __global__ void __launch_bounds__(kThreadsMv, 1) k_tc_mv(const MvParams p) {
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // MMA issuer
+      // MMA issuer.  Descriptors are built once; a start address moves by adding its offset
+      // (in 16-byte units) to the low field, which stays below 2^14 inside shared memory.
+      const uint64_t adesc0 = sdesc(stage0, 2048, 128), bdesc0 = sdesc(hank0, 128, 128);
+      uint64_t bplane[kTcDigits];
+#pragma unroll
+      for (int i = 0; i < kTcDigits; ++i) bplane[i] = (uint64_t)(i * ncores * 8);
       uint32_t it = 0, ui = 0;
       for (int u = blockIdx.x; u < p.nunits && !*err; u += gridDim.x, ++ui) {
         if (ui > 0 && !mbar_wait(tempty, (ui - 1) & 1u)) { *err = 1; break; }
@@ -390,13 +383,14 @@ __global__ void __launch_bounds__(kThreadsMv, 1) k_tc_mv(const MvParams p) {
           const int s = (int)(it % kStages);
           if (!mbar_wait(full_bar(s), (it / kStages) & 1u)) { ok = false; break; }
           tc_after_sync();
-          const uint32_t a_base = stage0 + s * kStageBytes;
-          const uint32_t b_base = hank0 + (uint32_t)(16 * rb + 2 * ks) * 128u;
+          const uint64_t ad = adesc0 + (uint64_t)(s * (kStageBytes / 16));
+          const uint64_t bd = bdesc0 + (uint64_t)((16 * rb + 2 * ks) * 8);
+          const uint32_t keep = ks > 0 ? 1u : 0u;
 #pragma unroll
           for (int q = 0; q < kPairs; ++q) {
-            const uint64_t ad = sdesc(a_base + c_pair_j[q] * kPlaneBytes, 2048, 128);
-            const uint64_t bd = sdesc(b_base + (uint32_t)(c_pair_i[q] * ncores * 128), 128, 128);
-            mma_bf16(tmem + 128u * c_pair_acc[q], ad, bd, (ks > 0 || !c_pair_open[q]) ? 1u : 0u);
+            const Pair pq = pair_of(q);
+            mma_bf16(tmem + 128u * pq.acc, ad + (uint64_t)(pq.j * (kPlaneBytes / 16)),
+                     bd + bplane[pq.i], pq.open ? keep : 1u);
           }
           mma_commit(empty_bar(s));
         }
@@ -414,7 +408,6 @@ __global__ void __launch_bounds__(kThreadsMv, 1) k_tc_mv(const MvParams p) {
     const int q = warp & 3, chunk = (warp - 2) >> 2;
     const int jj = 32 * q + lane;
     const double s = p.xscale ? *p.xscale : 1.0;
-    const dfl sdf = df_from(s);
     uint32_t ui = 0;
     for (int u = blockIdx.x; u < p.nunits; u += gridDim.x, ++ui) {
       if (*err || !mbar_wait(tfull, ui & 1u)) { *err = 1; break; }
@@ -445,9 +438,8 @@ __global__ void __launch_bounds__(kThreadsMv, 1) k_tc_mv(const MvParams p) {
       unit_of(u, p.nstrips, NB, strip, rb);
       const long long j = (long long)strip * kRows + jj;
       if (j >= M) continue;
-      const int e = op.tc_xe[j];
-      const int kx = op.tc_eT + e - 14;          // time product = accumulators x 2^kx
-      const dfl cdf = p.spectral ? df_from(op.b0 * mode_mu(op, j) * s) : dfl{0.0f, 0.0f};
+      const int kx = op.tc_eT + op.tc_xe[j] - 14;  // s x (T) x = accumulators x 2^kx
+      const double c = p.spectral ? op.b0 * mode_mu(op, j) * s : op.b0 * s;
       const int n0 = kCols * rb + 32 * chunk;    // flipped time of the first Hankel row
       double dot_u = 0.0;
       // batches of four outputs: every load of a batch is issued before its first store
@@ -458,21 +450,17 @@ __global__ void __launch_bounds__(kThreadsMv, 1) k_tc_mv(const MvParams p) {
         for (int i = 0; i < 4; ++i) {
           const int n = n0 + b0 + i, t = N - 1 - n;
           const int srow = p.flip ? n : t;
-          xt[i] = p.spectral ? __ldcg(p.x + (long long)t * M + j) : 0.0;
-          xs[i] = p.partials ? __ldcg(p.x + (long long)srow * M + j) : 0.0;
+          xt[i] = p.spectral ? __ldg(p.x + (long long)t * M + j) : 0.0;
+          xs[i] = p.partials ? __ldg(p.x + (long long)srow * M + j) : 0.0;
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int n = n0 + b0 + i, t = N - 1 - n;
           const int srow = p.flip ? n : t;
-          double val;
-          if (p.spectral) {
-            const dfl w = df_dot2(sdf, dfl{hh[b0 + i], ll[b0 + i]}, cdf, d2df_shift(xt[i], -kx));
-            val = f2d_shift(w.hi, kx) + f2d_shift(w.lo, kx);
-          } else {
-            const double tp = f2d_shift(hh[b0 + i], kx) + f2d_shift(ll[b0 + i], kx);
-            val = s * fma(op.b0, stencil_at(op, p.x + (long long)t * M, j), tp);
-          }
+          // time product in FP64 (exact sum of the two parts), then the b_0 term
+          const double tp = f2d_shift(hh[b0 + i], kx) + f2d_shift(ll[b0 + i], kx);
+          const double lx = p.spectral ? xt[i] : stencil_at(op, p.x + (long long)t * M, j);
+          const double val = fma(c, lx, tp);
           p.y[(long long)srow * M + j] = val;
           dot_u = fma(val, xs[i], dot_u);
         }
@@ -536,12 +524,12 @@ void tc_hankel_digits(const double* a, int N, uint16_t* out, int* eT, int* ncore
   *ncores = nc;
 }
 
-cudaError_t launch_tc_digits(const OpTables& op, const double* x, const int* phase,
-                             cudaStream_t st) {
+cudaError_t launch_tc_digits(const OpTables& op, const double* x, const double* xscale,
+                             const int* phase, cudaStream_t st) {
   if (!tc_eligible(op) || !op.tc_xd || !op.tc_xe) return cudaErrorInvalidValue;
   const int nstrips = tc_strips(op.M);
-  k_tc_digits<<<(unsigned)(nstrips * (kRows / 32)), 256, 0, st>>>(x, op.N, op.M, op.tc_xd,
-                                                                    op.tc_xe, phase);
+  k_tc_digits<<<(unsigned)(nstrips * (kRows / 32)), 256, 0, st>>>(x, xscale, op.N, op.M,
+                                                                    op.tc_xd, op.tc_xe, phase);
   return cudaGetLastError();
 }
 
@@ -581,7 +569,7 @@ cudaError_t launch_tc_product(const OpTables& op, int spectral, const double* x,
 cudaError_t launch_tc_matvec(const OpTables& op, int spectral, const double* x,
                              const double* xscale, double* y, int flip, double* partials,
                              int* nparts, const int* phase, cudaStream_t st) {
-  cudaError_t e = launch_tc_digits(op, x, phase, st);
+  cudaError_t e = launch_tc_digits(op, x, xscale, phase, st);
   if (e != cudaSuccess) return e;
   return launch_tc_product(op, spectral, x, xscale, y, flip, partials, nparts, phase, st);
 }
