@@ -173,7 +173,8 @@ bltt_status bltt_minres_solve(bltt_handle h, const double* f_dev, double alpha, 
 /* The solve of bltt_minres_solve_ex (Sec. 2-3, Sec. 5) with f and u in HOST memory: f_host (N*M
  * doubles) is copied into a device staging buffer on the handle's stream, and u goes back into
  * u_host on a second stream of the handle as soon as it is final, overlapping the physical-basis
- * residual check that ends the solve.  Pinned host buffers (cudaHostAlloc / cudaHostRegister)
+ * residual check that ends the solve; above 2^22 unknowns in the DST basis, f arrives in four
+ * chunks of time slices whose entry transforms start as each lands.  Pinned host buffers (cudaHostAlloc / cudaHostRegister)
  * make both copies asynchronous DMA; pageable ones work but are staged by the driver.  The first
  * call allocates the two staging vectors and the copy stream; they live until bltt_destroy.
  * Returns when u_host holds the result (same statuses as bltt_minres_solve_ex; u_host may not

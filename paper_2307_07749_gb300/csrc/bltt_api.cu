@@ -133,11 +133,14 @@ struct bltt_ctx {
   double* io_u = nullptr;
   cudaStream_t io_stream = nullptr;
   cudaEvent_t io_ev = nullptr;
+  cudaEvent_t io_chunk_ev[4] = {nullptr, nullptr, nullptr, nullptr};
 
   ~bltt_ctx() {
     if (stream_sync_ok) cudaStreamSynchronize(stream);
     if (io_stream) { cudaStreamSynchronize(io_stream); cudaStreamDestroy(io_stream); }
     if (io_ev) cudaEventDestroy(io_ev);
+    for (cudaEvent_t e : io_chunk_ev)
+      if (e) cudaEventDestroy(e);
     for (void* p : allocs) cudaFree(p);
     if (state_host) cudaFreeHost(state_host);
     if (scal_host) cudaFreeHost(scal_host);
@@ -729,10 +732,15 @@ namespace {
 struct HostOut {
   double* u_host;
 };
+// a host-buffer solve's right-hand side: copied into the staging vector f in chunks of time
+// slices on the copy stream, each chunk's entry DST starting as soon as it has landed
+struct HostIn {
+  const double* f_host;
+};
 
 bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol, int maxit,
                        const bltt_solve_opts* opts, double* u, bltt_solve_info* info,
-                       const HostOut* hout);
+                       const HostOut* hout, const HostIn* hin = nullptr);
 }  // namespace
 
 extern "C" {
@@ -746,9 +754,51 @@ bltt_status bltt_minres_solve_ex(bltt_handle h, const double* f, double alpha, d
 }  // extern "C"
 
 namespace {
+// entry transform b = Y (I (x) U) f of a host-buffer solve: f arrives in C chunks of N/C time
+// slices (copy stream); the DSTs of a chunk run on the compute stream once it has landed.  Lines
+// of every axis stay inside a time slice, so a chunk is transformed as a problem of N/C slices
+// whose output (flipped inside the chunk) is placed at the mirrored chunk of b.
+bltt_status dst_entry_chunked(bltt_ctx* h, const OpTables& op, const double* f_host, double* f,
+                              double* b, double* partials, int* nparts) {
+  const int N = h->N;
+  const long long M = h->M;
+  const int C = (N >= 8 && h->n >= (1LL << 22)) ? 4 : 1;
+  const int cN = N / C;
+  const int arith = op.mv_arith ? PREC_DF : PREC_F64;
+  cudaStream_t st = h->stream;
+  int total = 0;
+  for (int c = 0; c < C; ++c) {
+    if (!h->io_chunk_ev[c])
+      CK(h, cudaEventCreateWithFlags(&h->io_chunk_ev[c], cudaEventDisableTiming), "chunk event");
+    const long long t0 = (long long)c * cN;
+    CK(h, cudaMemcpyAsync(f + t0 * M, f_host + t0 * M, (size_t)cN * M * sizeof(double),
+                          cudaMemcpyHostToDevice, h->io_stream), "copy f to the device");
+    CK(h, cudaEventRecord(h->io_chunk_ev[c], h->io_stream), "event");
+    CK(h, cudaStreamWaitEvent(st, h->io_chunk_ev[c], 0), "wait");
+    OpTables oc = op;
+    oc.N = cN;
+    double* bc = b + (N - t0 - cN) * M;
+    for (int ax = 0; ax < op.d; ++ax) {
+      Combine cb{};
+      cb.in0 = (ax == 0) ? f + t0 * M : bc;
+      const bool last = (ax == op.d - 1);
+      int np = 0;
+      cudaEvent_t pa = prof_begin(h);
+      CK(h, launch_dst(oc, ax, arith, cb, bc, ax == 0 ? 1 : 0, last ? bc : nullptr,
+                       last ? partials + total : nullptr, last ? &np : nullptr, nullptr, st),
+         "dst");
+      prof_end(h, arith == PREC_DF ? "dst_df" : "dst64", pa);
+      h->launches++;
+      if (last) total += np;
+    }
+  }
+  *nparts = total;
+  return BLTT_OK;
+}
+
 bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol, int maxit,
                        const bltt_solve_opts* opts, double* u, bltt_solve_info* info,
-                       const HostOut* hout) {
+                       const HostOut* hout, const HostIn* hin) {
   if (!h) return BLTT_ERR_INVALID_ARG;
   if (info) { std::memset(info, 0, sizeof *info); info->status = BLTT_ERR_INVALID_ARG; }
   if (!f || !u) return fail(h, BLTT_ERR_INVALID_ARG, "null vector");
@@ -810,10 +860,16 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
 
   // b = Y f (spectral: Y (I (x) U) f) with ||b||^2
   int nb = 0, nzv = 0, np = 0;
-  if (spectral) {
+  if (spectral && hin) {
+    s = dst_entry_chunked(h, op, hin->f_host, const_cast<double*>(f), bvec, h->partials[1], &nb);
+    if (s != BLTT_OK) return s;
+  } else if (spectral) {
     s = dst_all(h, op, f, bvec, 1, h->partials[1], &nb);
     if (s != BLTT_OK) return s;
   } else {
+    if (hin)
+      CK(h, cudaMemcpyAsync(const_cast<double*>(f), hin->f_host, (size_t)h->n * sizeof(double),
+                            cudaMemcpyHostToDevice, st), "copy f to the device");
     PCK(h, "flip", launch_flip_copy(f, bvec, h->N, h->M, h->partials[1], &nb, st), "flip");
     h->launches++;
   }
@@ -1016,10 +1072,10 @@ bltt_status bltt_minres_solve_host(bltt_handle h, const double* f_host, double a
     CK(h, cudaStreamCreateWithFlags(&h->io_stream, cudaStreamNonBlocking), "copy stream");
     CK(h, cudaEventCreateWithFlags(&h->io_ev, cudaEventDisableTiming), "copy event");
   }
-  CK(h, cudaMemcpyAsync(h->io_f, f_host, (size_t)h->n * sizeof(double), cudaMemcpyHostToDevice,
-                        h->stream), "copy f to the device");
   const HostOut hout{u_host};
-  const bltt_status st = solve_impl(h, h->io_f, alpha, tol, maxit, opts, h->io_u, info, &hout);
+  const HostIn hin{f_host};
+  const bltt_status st = solve_impl(h, h->io_f, alpha, tol, maxit, opts, h->io_u, info, &hout,
+                                    &hin);
   // whatever the status, no copy into u_host is still in flight when the call returns
   const cudaError_t ce = cudaStreamSynchronize(h->io_stream);
   if (st == BLTT_OK && ce != cudaSuccess) return fail(h, BLTT_ERR_CUDA, cudaGetErrorString(ce));

@@ -299,3 +299,18 @@ def test_solve_host_buffers(B, form):
         s.solve_host(fp, u_host=fp)
     with pytest.raises(ValueError):
         s.solve_host(to_dev(f))
+
+
+def test_solve_host_buffers_chunked_entry(B):
+    # above 2^22 unknowns the host-buffer solve copies f in four chunks of time slices, each
+    # chunk's entry DST starting when it has landed; the result matches the device solve
+    import torch
+    prob = fractional_problem(2, 127, 512, 0.7)        # 8.3 M unknowns
+    f = rhs_uniform(prob.n, 39)
+    s = B.Solver(prob)
+    form = dict(precision=32, basis=1, matvec_arith=2, alpha=1e-3)
+    ud, idev = s.solve(to_dev(f), tol=1e-8, maxit=50, **form)
+    uh, ih = s.solve_host(torch.from_numpy(f).pin_memory(), tol=1e-8, maxit=50, **form)
+    assert ih["status"] == 0 and ih["iters"] == idev["iters"]
+    assert rel(uh.numpy(), to_host(ud)) <= 1e-13
+    assert ih["relres_true"] <= 1e-8
