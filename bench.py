@@ -459,6 +459,57 @@ def run_alpha(args):
     return 0
 
 
+def run_heat3d(args):
+    """The 3-D backward-Euler heat workload (N = 256, m = 127, 524 M unknowns, 4.2 GB per vector):
+    whole solves in the FP32-preconditioner form and the plain FP64 form, each kernel's live
+    duration against its algorithmic bytes (the memory-bound roofline run)."""
+    import torch
+    from paper_2307_07749_gb300 import build
+    build.build()
+    import paper_2307_07749_gb300 as B
+    from workloads import workload
+    prob, rf = workload("heat3d_bdf_N256_m127")
+    f = rf()
+    stream = torch.cuda.Stream()
+    solver = B.Solver(prob, stream=stream)
+    fd = torch.from_numpy(f).to("cuda")
+    del f
+    torch.cuda.synchronize()
+    pk = peaks()
+    forms = {"f32_precond": dict(alpha=ALPHA_F32, precision=32, basis=B.BASIS_SPECTRAL,
+                                 arith=B.ARITH_F32X2),
+             "plain_f64": dict(alpha=ALPHA_F64, precision=64, basis=B.BASIS_SPECTRAL,
+                               arith=B.ARITH_F64)}
+    out = {"workload": "heat3d_bdf_N256_m127", "unknowns": prob.n, "N": prob.N, "m": prob.m[0],
+           "d": prob.d, "tol": TOL, "steps": args.steps, "warmup": max(args.warmup, 1),
+           "l2": "inputs larger than L2 (4.2 GB per vector), no flush"}
+    with torch.cuda.stream(stream):
+        for key, fm in forms.items():
+            r = time_form(B, solver, fd, args.steps, max(args.warmup, 1), fm["alpha"],
+                          fm["precision"], fm["basis"], fm["arith"], 1, stream, profile=True)
+            iters = [i["iters"] for i in r["infos"]]
+            kern = []
+            for name, (_, _, launches, tot_ms) in r["profile"].items():
+                bound, bpu, fpu = kernel_cost(name, prob.N, prob.m[0], prob.d)
+                if launches == 0 or bpu == 0:
+                    continue
+                avg = tot_ms / launches
+                gbs = bpu * prob.n / (avg / 1e3) / 1e9
+                kern.append({"name": name, "launches": launches, "ms_per_launch": round(avg, 4),
+                             "bytes_per_unit": bpu, "GB/s": round(gbs, 1),
+                             "frac_hbm": round(gbs / pk["hbm_gbs"], 4), "bound": bound})
+            kern.sort(key=lambda k: -k["ms_per_launch"] * k["launches"])
+            ms = r["ms_total"] / args.steps
+            out[key] = {"value": prob.n * sum(iters) / (r["ms_total"] / 1e3),
+                        "unit": "unknown-iter/s", "iters": iters[-1], "ms_per_solve": ms,
+                        "relres_true": max(i["relres_true"] for i in r["infos"]),
+                        "status": max(i["status"] for i in r["infos"]), "form": fm,
+                        "kernels": kern}
+    out["hbm_peak_gbs"] = pk["hbm_gbs"]
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -467,9 +518,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="frac2d", choices=["frac2d", "batched", "alpha", "once"],
-                    help="frac2d: the headline line; batched / alpha: supplementary reports; "
-                         "once: a single solve of the headline workload (for ncu captures)")
+    ap.add_argument("--workload", default="frac2d",
+                    choices=["frac2d", "batched", "alpha", "once", "heat3d"],
+                    help="frac2d: the headline line; batched / alpha / heat3d: supplementary "
+                         "reports; once: a single solve of the headline workload (for ncu "
+                         "captures)")
     ap.add_argument("--form", default="chosen", choices=list(FORMS))
     ap.add_argument("--m", type=int, default=255, choices=[63, 127, 255],
                     help="--workload once: interior points per axis (255: the headline workload)")
@@ -484,6 +537,8 @@ def main():
         return run_alpha(args)
     if args.workload == "once":
         return run_once(args)
+    if args.workload == "heat3d":
+        return run_heat3d(args)
     args.warmup = max(args.warmup, 3)
 
     rank, local, ws = dist_init()

@@ -24,11 +24,28 @@ struct dfl {
   float hi, lo;
 };
 
-// double <-> double-float: the FP32 parts are converted on the integer pipes, which leaves one
-// FP64 subtraction (or addition) per value on the FP64 pipe
+// double <-> double-float: the FP32 parts are converted on the integer pipes.  double -> pair:
+// hi = x rounded to FP32; lo = x - hi rounded to FP32.  x - hi is the mantissa remainder below
+// hi's 24 bits, an integer r (|r| <= 2^28) times 2^(E-1075), so lo is the rounded integer times
+// that power of two, which equals the rounded FP64 difference whenever the power of two and lo
+// are normal FP32 numbers (949 <= E <= 1149); other exponents take the FP64 subtraction.
+// pair -> double leaves one FP64 addition.
 __device__ __forceinline__ dfl df_from(double x) {
-  float h = d2f_bits(x);
-  return {h, d2f_bits(x - f2d_bits(h))};
+  const uint64_t b = bits_d(x);
+  const uint32_t hw = (uint32_t)(b >> 32), lw = (uint32_t)b;
+  const int E = (int)((hw >> 20) & 0x7FFu);
+  if (E < 949 || E > 1149) {
+    const float h = d2f_bits(x);
+    return {h, d2f_bits(x - f2d_bits(h))};
+  }
+  const uint32_t sign = hw & 0x80000000u;
+  const uint32_t m = ((hw & 0xFFFFFu) << 3) | (lw >> 29);       // top 23 mantissa bits
+  const uint32_t rest = lw & 0x1FFFFFFFu;                        // 29 dropped bits
+  const uint32_t up = (rest > 0x10000000u) | ((rest == 0x10000000u) & (m & 1u));
+  const float h = __uint_as_float(((((uint32_t)(E - 1023 + 127)) << 23) + m + up) | sign);
+  const int r = (int)rest - (int)(up << 29);                     // x - h in units of 2^(E-1075)
+  const float lm = __int2float_rn(r) * __uint_as_float((uint32_t)(E - 1075 + 127) << 23);
+  return {h, __uint_as_float(__float_as_uint(lm) ^ (r != 0 ? sign : 0u))};
 }
 __device__ __forceinline__ double df_to(dfl a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
 __device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }

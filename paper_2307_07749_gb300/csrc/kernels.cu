@@ -722,43 +722,122 @@ k_conv(OpTables op, int spectral, int which, const double* x, const double* xsca
 }
 
 // Direct matvec for blocks that vanish beyond ntaps (heat BDF / CN): y_t = sum_{k<ntaps}
-// (a_k x_{t-k} + b_k [mu_i | L] x_{t-k}), same fused epilogues as k_conv.
-__global__ void __launch_bounds__(256)
-k_direct(OpTables op, int spectral, const double* x, const double* xscale, double* y, int flip,
+// (a_k x_{t-k} + b_k [mu_i | L] x_{t-k}), same fused epilogues as k_conv.  A thread owns one
+// spatial point and walks it through all N time steps: its coefficients s (a_k + b_k mu_i) are
+// formed once, the K-1 earlier x (and, in the physical basis, L x) stay in registers, and each
+// output costs K FP64 multiply-adds plus the fused dot product (GB300 runs FP64 at 2 FMA per
+// clock per SM, so the FP64 operation count, not the bytes, bounds this kernel).
+__device__ __forceinline__ double stencil_xyz(const OpTables& op, const double* __restrict__ x_t,
+                                              long long i, int ix, int iy, int iz) {
+  const double xi2 = 2.0 * x_t[i];
+  double sx = xi2;
+  if (ix > 0) sx -= x_t[i - 1];
+  if (ix < op.m[0] - 1) sx -= x_t[i + 1];
+  double lap = sx * op.h2inv[0];
+  if (op.d > 1) {
+    const long long s1 = op.m[0];
+    double sy = xi2;
+    if (iy > 0) sy -= x_t[i - s1];
+    if (iy < op.m[1] - 1) sy -= x_t[i + s1];
+    lap = fma(sy, op.h2inv[1], lap);
+    if (op.d > 2) {
+      const long long s2 = s1 * op.m[1];
+      double sz = xi2;
+      if (iz > 0) sz -= x_t[i - s2];
+      if (iz < op.m[2] - 1) sz -= x_t[i + s2];
+      lap = fma(sz, op.h2inv[2], lap);
+    }
+  }
+  return lap;
+}
+
+constexpr int kDirectThreads = 256;
+constexpr int kDirectPts = 4;      // points per thread, kDirectThreads apart: 8 KB rows per block
+
+template <int K, bool SPECTRAL>
+__global__ void __launch_bounds__(kDirectThreads)
+k_direct(OpTables op, const double* __restrict__ x, const double* xscale, double* y, int flip,
          int mode, const double* rhs, double* partials, const int* phase, int want) {
   if (skip_phase(phase, want)) return;
+  constexpr bool spectral = SPECTRAL;
+  constexpr int P = kDirectPts;
   __shared__ double red[32];
-  const int N = op.N, K = op.ntaps;
-  const long long M = op.M, n = (long long)N * M;
+  const int N = op.N;
+  const long long M = op.M;
   const double s = xscale ? *xscale : 1.0;
+  bool any_b = false;
+#pragma unroll
+  for (int k = 0; k < K; ++k) any_b |= (op.b_dev[k] != 0.0);
+  const bool lap = !spectral && any_b;
   double acc = 0.0;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int t = (int)(e / M);
-    const long long i = e - (long long)t * M;
-    const double mu = spectral ? mode_mu(op, i) : 0.0;
-    double val = 0.0;
-    for (int k = 0; k < K && k <= t; ++k) {
-      const double ak = op.a_dev[k], bk = op.b_dev[k];
-      const long long base = (long long)(t - k) * M;
-      if (ak != 0.0) val = fma(ak, x[base + i], val);
-      if (bk != 0.0) val = fma(bk, spectral ? mu * x[base + i] : stencil_at(op, x + base, i), val);
+  for (long long c0 = (long long)blockIdx.x * (P * kDirectThreads); c0 < M;
+       c0 += (long long)gridDim.x * (P * kDirectThreads)) {
+    long long ip[P];
+    int cx[P], cy[P], cz[P];
+    double ca[P][K], cb[P][K], xp[P][K], lp[P][K];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      ip[q] = c0 + q * kDirectThreads + threadIdx.x;
+      const long long i = ip[q] < M ? ip[q] : M - 1;     // tail points compute, never store
+      const long long r1 = i / op.m[0];
+      cx[q] = (int)(i - r1 * op.m[0]);
+      cy[q] = 0;
+      cz[q] = 0;
+      if (op.d > 1) {
+        const long long r2 = r1 / op.m[1];
+        cy[q] = (int)(r1 - r2 * op.m[1]);
+        cz[q] = (int)r2;
+      }
+      // per-point coefficients: spectral s (a_k + b_k mu_i); physical s a_k and s b_k
+      const double mu = spectral ? mode_mu(op, i) : 0.0;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const double ak = op.a_dev[k], bk = op.b_dev[k];
+        ca[q][k] = spectral ? s * fma(bk, mu, ak) : s * ak;
+        cb[q][k] = spectral ? 0.0 : s * bk;
+        xp[q][k] = 0.0;
+        lp[q][k] = 0.0;
+      }
     }
-    val *= s;
-    const int to = flip ? (N - 1 - t) : t;
-    const long long idx = (long long)to * M + i;
-    if (mode == MV_STORE) {
-      y[idx] = val;
-      if (partials) acc = fma(val, x[idx] * s, acc);
-    } else {
-      const double r = rhs[idx] - val;
-      if (y) y[idx] = r;
-      acc = fma(r, r, acc);
+    for (int t = 0; t < N; ++t) {
+      const long long row = (long long)t * M;
+      const long long orow = (long long)(flip ? (N - 1 - t) : t) * M;
+      double xs[P], pr[P];
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        const long long i = ip[q] < M ? ip[q] : M - 1;
+        xs[q] = x[row + i];
+        pr[q] = (mode != MV_STORE) ? rhs[orow + i] : (partials ? x[orow + i] : 0.0);
+      }
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        const long long i = ip[q] < M ? ip[q] : M - 1;
+#pragma unroll
+        for (int k = K - 1; k > 0; --k) { xp[q][k] = xp[q][k - 1]; lp[q][k] = lp[q][k - 1]; }
+        xp[q][0] = xs[q];
+        if (lap) lp[q][0] = stencil_xyz(op, x + row, i, cx[q], cy[q], cz[q]);
+        double val = 0.0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          val = fma(ca[q][k], xp[q][k], val);
+          if (!spectral) val = fma(cb[q][k], lp[q][k], val);
+        }
+        if (ip[q] < M) {
+          if (mode == MV_STORE) {
+            y[orow + i] = val;
+            acc = fma(val, pr[q], acc);               // times s once per block below
+          } else {
+            const double r = pr[q] - val;
+            if (y) y[orow + i] = r;
+            acc = fma(r, r, acc);
+          }
+        }
+      }
     }
   }
   if (partials) {
-    double sum = block_sum<256>(acc, red);
-    if (threadIdx.x == 0) partials[blockIdx.x] = sum;
+    double sum = block_sum<kDirectThreads>(acc, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = (mode == MV_STORE) ? sum * s : sum;
   }
 }
 
@@ -1180,11 +1259,22 @@ cudaError_t launch_matvec(const OpTables& op, int spectral, const double* x, con
                           int* nparts, const int* phase, double* tmp, cudaStream_t st) {
   const int want = (mode == MV_RESID) ? PH_CHECK : PH_RUN;
   if (op.ntaps > 0) {
-    long long n = (long long)op.N * op.M;
-    int g = grid_stream(n, 256);
-    if (nparts) *nparts = g;
-    k_direct<<<g, 256, 0, st>>>(op, spectral, x, xscale, y, flip, mode, rhs, partials, phase,
-                                want);
+    const long long per = (long long)kDirectPts * kDirectThreads;
+    long long g = (op.M + per - 1) / per;
+    if (g > 152LL * 8) g = 152LL * 8;
+    if (nparts) *nparts = (int)g;
+#define BLTT_DIRECT(K_)                                                                         \
+  (spectral ? k_direct<K_, true><<<(unsigned)g, kDirectThreads, 0, st>>>(                      \
+                  op, x, xscale, y, flip, mode, rhs, partials, phase, want)                     \
+            : k_direct<K_, false><<<(unsigned)g, kDirectThreads, 0, st>>>(                     \
+                  op, x, xscale, y, flip, mode, rhs, partials, phase, want))
+    switch (op.ntaps) {
+      case 1: BLTT_DIRECT(1); break;
+      case 2: BLTT_DIRECT(2); break;
+      case 3: BLTT_DIRECT(3); break;
+      default: BLTT_DIRECT(4); break;
+    }
+#undef BLTT_DIRECT
     return cudaGetLastError();
   }
   if (op.mv_arith == 2 && mode == MV_STORE)
