@@ -92,7 +92,7 @@ def kernel_cost(name, N, m, d):
         return "alu64", 16.0, 10.0 * l2N + 10.0
     if name == "conv_df":   # same algorithm in double-float on the FP32 pipes (FP32 operations)
         return "alu32", 16.0, df_conv_ops(N)
-    if name == "direct":
+    if name in ("direct", "direct_resid"):
         return "hbm", 16.0, 6.0
     # tensor-core product: 15 digit-pair MMAs over the input times that reach each output block
     # of 128 times (128 (NB - rb) for row block rb of NB = N/128), 2 flops per multiply-add
@@ -489,7 +489,7 @@ def run_heat3d(args):
                           fm["precision"], fm["basis"], fm["arith"], 1, stream, profile=True)
             iters = [i["iters"] for i in r["infos"]]
             kern = []
-            for name, (_, _, launches, tot_ms) in r["profile"].items():
+            for name, (all_l, all_ms, launches, tot_ms) in r["profile"].items():
                 bound, bpu, fpu = kernel_cost(name, prob.N, prob.m[0], prob.d)
                 if launches == 0 or bpu == 0:
                     continue
@@ -497,7 +497,8 @@ def run_heat3d(args):
                 gbs = bpu * prob.n / (avg / 1e3) / 1e9
                 kern.append({"name": name, "launches": launches, "ms_per_launch": round(avg, 4),
                              "bytes_per_unit": bpu, "GB/s": round(gbs, 1),
-                             "frac_hbm": round(gbs / pk["hbm_gbs"], 4), "bound": bound})
+                             "frac_hbm": round(gbs / pk["hbm_gbs"], 4), "bound": bound,
+                             "all_launches": all_l, "all_ms": round(all_ms, 3)})
             kern.sort(key=lambda k: -k["ms_per_launch"] * k["launches"])
             ms = r["ms_total"] / args.steps
             out[key] = {"value": prob.n * sum(iters) / (r["ms_total"] / 1e3),

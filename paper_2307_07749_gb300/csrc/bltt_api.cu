@@ -430,7 +430,7 @@ bltt_status dst_all(bltt_ctx* h, const OpTables& op, const double* in, double* o
 }
 
 const char* mv_name(const OpTables& op, int mode = MV_STORE) {
-  if (op.ntaps > 0) return "direct";
+  if (op.ntaps > 0) return mode == MV_RESID ? "direct_resid" : "direct";
   if (op.mv_arith == 2 && mode == MV_STORE) return "conv_tc";
   return op.mv_arith ? "conv_df" : "conv";
 }
