@@ -142,7 +142,8 @@ cudaError_t launch_w_update(MinresDev* s, const double* z, double* w_prev, const
 cudaError_t launch_copy_scaled_check(const double* src, double* dst, long long n, cudaStream_t st);
 cudaError_t launch_sum_partials(const double* partials, int np, double* out, cudaStream_t st);
 
-int tile_columns(long long nlines, int Lfft);   // complex columns per tile for a line batch
+// complex columns per tile for a line batch (tiles of `cap` complex points)
+int tile_columns(long long nlines, int Lfft, int cap = kCap);
 cudaError_t prepare_kernel_attributes();         // shared-memory limits of every tile kernel
 
 // ---------------------------------------------------------------------------------------------

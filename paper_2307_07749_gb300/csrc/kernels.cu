@@ -69,8 +69,8 @@ static int ilog2(long long v) { int l = 0; while ((1LL << l) < v) ++l; return l;
 
 // complex columns per FFT tile: fill the tile (kCap points) but keep at most kMaxCols real lines
 // and, when the batch is small, at least two tiles per SM
-int tile_columns(long long nlines, int Lfft) {
-  int nc = kCap / Lfft;
+int tile_columns(long long nlines, int Lfft, int cap) {
+  int nc = cap / Lfft;
   if (nc < 1) nc = 1;
   if (nc > kMaxCols / 2) nc = kMaxCols / 2;
   long long pairs = (nlines + 1) / 2;
@@ -102,6 +102,13 @@ template <class A> struct TileCfg {
 // two blocks per SM: twice the warps of the FP64 tile and about a third of its transform code
 template <> struct TileCfg<ArithDF> {
   static constexpr int NT = 2 * kThreads, CAP = kCap;
+  static constexpr int MINB = 2;
+};
+// a wide FP32 tile for the single-item time pass at long N: 8192 points and 512 threads (16 points
+// each, two blocks per SM), so that a tile spans twice the lines and every row of a vector is read
+// and written in runs twice as long (at N = 1024: 16 lines, 128 B, against 8 lines, 64 B)
+struct WideTileF {
+  static constexpr int NT = 2 * kThreads, CAP = 2 * kCap;
   static constexpr int MINB = 2;
 };
 
@@ -357,11 +364,11 @@ template <> struct GSrc<ArithF> {
   }
 };
 
-template <class A, bool CONJ>
+template <class A, bool CONJ, class Cfg>
 __device__ __forceinline__ void tp_freq_mul(typename A::V* buf, const OpTables& op,
                                             const PrecTables& pt, int log2NC, long long g0,
                                             const float* s_mu) {
-  constexpr int NT = TileCfg<A>::NT, CAP = TileCfg<A>::CAP;
+  constexpr int NT = Cfg::NT;
   using V = typename A::V;
   const int N = op.N, half = N >> 1, NC = 1 << log2NC;
   const int items = (half + 1) << log2NC;
@@ -381,13 +388,13 @@ __device__ __forceinline__ void tp_freq_mul(typename A::V* buf, const OpTables& 
   }
 }
 
-template <class A>
+template <class A, class Cfg = TileCfg<A>>
 __device__ __forceinline__ void timepass_tile(const OpTables& op, const PrecTables& pt,
                                               const Combine& cb, double* out,
                                               const double* dot_with, double* partials,
                                               int log2NC, const typename A::V* __restrict__ tw,
                                               long long tile) {
-  constexpr int NT = TileCfg<A>::NT, CAP = TileCfg<A>::CAP;
+  constexpr int NT = Cfg::NT, CAP = Cfg::CAP;
   using V = typename A::V;
   __syncthreads();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -440,14 +447,14 @@ __device__ __forceinline__ void timepass_tile(const OpTables& op, const PrecTabl
   }
   __syncthreads();
   fft_columns<A, NT, CAP, false>(buf, N, op.log2N, log2NC, tw);
-  tp_freq_mul<A, true>(buf, op, pt, log2NC, g0, s_mu);
+  tp_freq_mul<A, true, Cfg>(buf, op, pt, log2NC, g0, s_mu);
   __syncthreads();
   fft_columns<A, NT, CAP, true>(buf, N, op.log2N, log2NC, tw);
   for (int e = threadIdx.x; e < N * NC; e += NT)
     buf[e] = A::scale_sc(buf[e], RowSc<A>::d2(pt, e >> log2NC));
   __syncthreads();
   fft_columns<A, NT, CAP, false>(buf, N, op.log2N, log2NC, tw);
-  tp_freq_mul<A, false>(buf, op, pt, log2NC, g0, s_mu);
+  tp_freq_mul<A, false, Cfg>(buf, op, pt, log2NC, g0, s_mu);
   __syncthreads();
   fft_columns<A, NT, CAP, true>(buf, N, op.log2N, log2NC, tw);
   // read-out in batches: the dot-product partner of a whole batch is loaded before its first use;
@@ -482,13 +489,13 @@ __device__ __forceinline__ void timepass_tile(const OpTables& op, const PrecTabl
   }
 }
 
-template <class A>
-__global__ void __launch_bounds__(TileCfg<A>::NT, TileCfg<A>::MINB)
+template <class A, class Cfg = TileCfg<A>>
+__global__ void __launch_bounds__(Cfg::NT, Cfg::MINB)
 k_timepass(OpTables op, PrecTables pt, Combine cb, double* out, const double* dot_with,
            double* partials, const int* phase, int want, int log2NC,
            const typename A::V* __restrict__ tw) {
   if (skip_phase(phase, want)) return;
-  timepass_tile<A>(op, pt, cb, out, dot_with, partials, log2NC, tw, blockIdx.x);
+  timepass_tile<A, Cfg>(op, pt, cb, out, dot_with, partials, log2NC, tw, blockIdx.x);
 }
 
 // identity preconditioner (MINRES-I): z = v, with the same fused load and dot
@@ -1138,10 +1145,10 @@ static void run_dst(const OpTables& op, long long grid, long long nlines, int m,
     k_dst<A, false><<<(unsigned)grid, TileCfg<A>::NT, smem, st>>>(nlines, m, inner, P, ilog2(P), log2NC,
         in, out, flip, op.N, op.M, dot_with, partials, tw, phase, PH_RUN);
 }
-template <class A> static cudaError_t ensure_smem_tp() {
+template <class A, class Cfg = TileCfg<A>> static cudaError_t ensure_smem_tp() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = set_smem(k_timepass<A>, TileCfg<A>::CAP * sizeof(typename A::V));
+  cudaError_t e = set_smem(k_timepass<A, Cfg>, Cfg::CAP * sizeof(typename A::V));
   if (e == cudaSuccess) done = true;
   return e;
 }
@@ -1159,6 +1166,7 @@ cudaError_t prepare_kernel_attributes() {
   if (e == cudaSuccess) e = ensure_smem_dst<ArithDF>();
   if (e == cudaSuccess) e = ensure_smem_tp<ArithD>();
   if (e == cudaSuccess) e = ensure_smem_tp<ArithF>();
+  if (e == cudaSuccess) e = ensure_smem_tp<ArithF, WideTileF>();
   if (e == cudaSuccess) e = ensure_smem_tp<ArithDF>();
   if (e == cudaSuccess) e = ensure_smem_conv<ArithD>();
   if (e == cudaSuccess) e = ensure_smem_conv<ArithDF>();
@@ -1206,27 +1214,25 @@ cudaError_t launch_timepass(const OpTables& op, const PrecTables& pt, int prec, 
     return cudaGetLastError();
   }
   if (op.N > kCap) return cudaErrorInvalidValue;   // the FFT must fit one tile
-  const int NC = tile_columns(op.M, op.N);
-  const int log2NC = ilog2(NC);
-  const long long grid = (op.M + 2 * NC - 1) / (2 * NC);
-  if (nparts) *nparts = (int)grid;
-  if (prec == PREC_F64) {
-    cudaError_t e = ensure_smem_tp<ArithD>();
+  auto run = [&](auto arith, auto cfg, const auto* tw) -> cudaError_t {
+    using A = decltype(arith);
+    using Cfg = decltype(cfg);
+    cudaError_t e = ensure_smem_tp<A, Cfg>();
     if (e != cudaSuccess) return e;
-    k_timepass<ArithD><<<(unsigned)grid, TileCfg<ArithD>::NT, kCap * sizeof(double2), st>>>(
-        op, pt, in, out, dot_with, partials, phase, PH_RUN, log2NC, op.tw_N);
-  } else if (prec == PREC_DF) {
-    cudaError_t e = ensure_smem_tp<ArithDF>();
-    if (e != cudaSuccess) return e;
-    k_timepass<ArithDF><<<(unsigned)grid, TileCfg<ArithDF>::NT, kCap * sizeof(float4), st>>>(
-        op, pt, in, out, dot_with, partials, phase, PH_RUN, log2NC, op.tw_N_df);
-  } else {
-    cudaError_t e = ensure_smem_tp<ArithF>();
-    if (e != cudaSuccess) return e;
-    k_timepass<ArithF><<<(unsigned)grid, TileCfg<ArithF>::NT, kCap * sizeof(float2), st>>>(
-        op, pt, in, out, dot_with, partials, phase, PH_RUN, log2NC, op.tw_N32);
-  }
-  return cudaGetLastError();
+    const int NC = tile_columns(op.M, op.N, Cfg::CAP);
+    const int log2NC = ilog2(NC);
+    const long long grid = (op.M + 2 * NC - 1) / (2 * NC);
+    if (nparts) *nparts = (int)grid;
+    k_timepass<A, Cfg><<<(unsigned)grid, Cfg::NT, Cfg::CAP * sizeof(typename A::V), st>>>(
+        op, pt, in, out, dot_with, partials, phase, PH_RUN, log2NC, tw);
+    return cudaGetLastError();
+  };
+  if (prec == PREC_F64) return run(ArithD{}, TileCfg<ArithD>{}, op.tw_N);
+  if (prec == PREC_DF) return run(ArithDF{}, TileCfg<ArithDF>{}, op.tw_N_df);
+  // FP32: the wide tile where the common one would span fewer than 16 lines (N >= 1024)
+  if (2 * (kCap / op.N) < 16 && op.N <= WideTileF::CAP)
+    return run(ArithF{}, WideTileF{}, op.tw_N32);
+  return run(ArithF{}, TileCfg<ArithF>{}, op.tw_N32);
 }
 
 template <class A>
