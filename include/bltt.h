@@ -158,7 +158,9 @@ bltt_status bltt_precond_apply(bltt_handle h, double alpha, const double* v_dev,
 
 /* Solve A u = f through MINRES on Y A u = Y f with P_alpha (Sec. 2-3, Sec. 5).  Zero initial
  * guess (Sec. 5.2).  Stops when the recurrence estimate |eta_j|/eta_0 <= tol and then the true
- * relative residual ||Yf - YAu||/||Yf|| <= tol (both FP64); otherwise iterates on, up to maxit.
+ * relative residual ||Yf - YAu||/||Yf|| <= tol (both FP64-accurate); otherwise iterates on, up
+ * to maxit.  In the DST basis the true residual is the physical-basis one of the returned u,
+ * computed after the exit transform (the iterations resume if it misses tol).
  * f_dev: the unflipped right-hand side; u_dev: the solution (may not alias f_dev).
  * opts may be NULL (FP64, AUTO basis, ABAC).  info (host, may be NULL) receives the statistics.
  * Returns BLTT_OK, BLTT_ERR_NOT_CONVERGED (u holds the last iterate), BLTT_ERR_NUMERIC, ... */

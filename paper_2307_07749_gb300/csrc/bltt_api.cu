@@ -891,8 +891,12 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
   h->launches++;
 
   // one MINRES iteration (A1..A4 of the hot loop); the caller rotates the buffers afterwards
+  // DST basis: the true residual is checked by the host in the physical basis once the estimate
+  // has met the stopping rule (the iterations halt in PH_VERIFY and resume if the check fails),
+  // so the iterations carry no residual product of their own
+  const bool defer = (spectral != 0);
   const long long per_iter = 5 + ((op.b_kind == 1 && op.ntaps == 0 && !spectral) ? 4 : 2) +
-                             (spectral || none ? 0 : 2 * op.d) + (tc ? 1 : 0);
+                             (spectral || none ? 0 : 2 * op.d) + (tc ? 1 : 0) - (defer ? 1 : 0);
   auto issue_iteration = [&](int c0) -> bltt_status {
     const long long saved = h->launches;   // counted per iteration by the caller (per_iter)
     struct Restore { bltt_ctx* hh; long long v; ~Restore() { hh->launches = v; } } restore{h, saved};
@@ -920,6 +924,10 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
     if (r != BLTT_OK) return r;
     PCK(h, "scalar", launch_scalar_gamma(h->state, h->partials[1], np, st), "scalar gamma");
     PCK(h, "w_update", launch_w_update(h->state, zbuf[c0], wbuf[prv], wbuf[c0], x, n, st), "w update");
+    if (defer) {
+      PCK(h, "scalar", launch_scalar_defer(h->state, st), "scalar check");
+      return BLTT_OK;
+    }
     // true residual when the estimate says so
     PCK(h, mv_name(op, MV_RESID), launch_matvec(op, spectral, x, nullptr, nullptr, 1, MV_RESID, bvec,
                                       h->partials[0], &np, phase, tmp, st), "residual");
@@ -937,59 +945,12 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
   const int G = (sync_every + 1) & ~1;
   const bool graph_mode = (st != nullptr) && !o.no_graph;
   int issued = 0;
-  if (graph_mode) {
-    const void* key[13] = {(const void*)(intptr_t)spectral, (const void*)(intptr_t)o.precision,
-                           (const void*)(intptr_t)op.mv_arith, (const void*)(intptr_t)none,
-                           (const void*)(intptr_t)G, x, pt.g64, pt.ahat32, pt.gdf, pt.dinv, st,
-                           (const void*)(intptr_t)op.ntaps, (const void*)(intptr_t)h->prof};
-    if (!h->gexec || std::memcmp(key, h->gkey, sizeof key) != 0) {
-      if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
-      for (auto& p : h->graph_prof) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
-      h->graph_prof.clear();
-      prof_harvest(h);                     // nothing of the capture may mix with earlier events
-      cudaGraph_t g = nullptr;
-      CK(h, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
-      h->capturing = true;
-      bltt_status cap = BLTT_OK;
-      for (int i = 0; i < G && cap == BLTT_OK; ++i) {
-        cap = issue_iteration(cur);
-        rotate();
-      }
-      h->capturing = false;
-      h->graph_prof.swap(h->pending);      // the event-record nodes of this graph
-      h->pending.clear();
-      cudaError_t ce = cudaStreamEndCapture(st, &g);
-      if (cap != BLTT_OK) { if (g) cudaGraphDestroy(g); return cap; }
-      CK(h, ce, "end capture");
-      ce = cudaGraphInstantiate(&h->gexec, g, 0);
-      cudaGraphDestroy(g);
-      CK(h, ce, "graph instantiate");
-      std::memcpy(h->gkey, key, sizeof key);
-    }
-    for (;;) {
-      CK(h, cudaGraphLaunch(h->gexec, st), "graph launch");
-      h->launches += per_iter * G;
-      issued += G;
-      CK(h, cudaMemcpyAsync(sh, h->state, sizeof *sh, cudaMemcpyDeviceToHost, st), "state download");
-      CK(h, cudaStreamSynchronize(st), "sync");
-      if (h->prof) prof_harvest_graph(h);
-      if (sh->phase != PH_RUN || issued >= maxit) break;
-    }
-  } else {
-    for (;;) {
-      s = issue_iteration(cur);
-      if (s != BLTT_OK) return s;
-      h->launches += per_iter;
-      rotate();
-      ++issued;
-      if (issued % sync_every == 0 || issued >= maxit) {
-        CK(h, cudaMemcpyAsync(sh, h->state, sizeof *sh, cudaMemcpyDeviceToHost, st), "state download");
-        CK(h, cudaStreamSynchronize(st), "sync");
-        if (sh->phase != PH_RUN || issued >= maxit) break;
-      }
-    }
-  }
-  double relres_phys = sh->relres_true;
+  // buffer roles of the first iteration; iteration j uses them rotated j times
+  double* const vbuf0[2] = {vbuf[0], vbuf[1]};
+  double* const zbuf0[2] = {zbuf[0], zbuf[1]};
+  double* const wbuf0[2] = {wbuf[0], wbuf[1]};
+  bool resumed = false;
+  double relres_phys = 0.0;
   // host-buffer solve: u goes back on the copy stream once final
   auto copy_out = [&]() -> bltt_status {
     if (!hout) return BLTT_OK;
@@ -999,11 +960,65 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
                           h->io_stream), "copy u to the host");
     return BLTT_OK;
   };
-  if (!spectral) {
-    s = copy_out();
-    if (s != BLTT_OK) return s;
-  }
-  if (spectral) {
+  for (;;) {
+    if (graph_mode && !resumed) {
+      const void* key[13] = {(const void*)(intptr_t)spectral, (const void*)(intptr_t)o.precision,
+                             (const void*)(intptr_t)op.mv_arith, (const void*)(intptr_t)none,
+                             (const void*)(intptr_t)G, x, pt.g64, pt.ahat32, pt.gdf, pt.dinv, st,
+                             (const void*)(intptr_t)op.ntaps, (const void*)(intptr_t)h->prof};
+      if (!h->gexec || std::memcmp(key, h->gkey, sizeof key) != 0) {
+        if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+        for (auto& p : h->graph_prof) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+        h->graph_prof.clear();
+        prof_harvest(h);                     // nothing of the capture may mix with earlier events
+        cudaGraph_t g = nullptr;
+        CK(h, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+        h->capturing = true;
+        bltt_status cap = BLTT_OK;
+        for (int i = 0; i < G && cap == BLTT_OK; ++i) {
+          cap = issue_iteration(cur);
+          rotate();
+        }
+        h->capturing = false;
+        h->graph_prof.swap(h->pending);      // the event-record nodes of this graph
+        h->pending.clear();
+        cudaError_t ce = cudaStreamEndCapture(st, &g);
+        if (cap != BLTT_OK) { if (g) cudaGraphDestroy(g); return cap; }
+        CK(h, ce, "end capture");
+        ce = cudaGraphInstantiate(&h->gexec, g, 0);
+        cudaGraphDestroy(g);
+        CK(h, ce, "graph instantiate");
+        std::memcpy(h->gkey, key, sizeof key);
+      }
+      for (;;) {
+        CK(h, cudaGraphLaunch(h->gexec, st), "graph launch");
+        h->launches += per_iter * G;
+        issued += G;
+        CK(h, cudaMemcpyAsync(sh, h->state, sizeof *sh, cudaMemcpyDeviceToHost, st), "state download");
+        CK(h, cudaStreamSynchronize(st), "sync");
+        if (h->prof) prof_harvest_graph(h);
+        if (sh->phase != PH_RUN || issued >= maxit) break;
+      }
+    } else {
+      for (;;) {
+        s = issue_iteration(cur);
+        if (s != BLTT_OK) return s;
+        h->launches += per_iter;
+        rotate();
+        ++issued;
+        if (issued % sync_every == 0 || issued >= maxit) {
+          CK(h, cudaMemcpyAsync(sh, h->state, sizeof *sh, cudaMemcpyDeviceToHost, st), "state download");
+          CK(h, cudaStreamSynchronize(st), "sync");
+          if (sh->phase != PH_RUN || issued >= maxit) break;
+        }
+      }
+    }
+    relres_phys = sh->relres_true;
+    if (!spectral) {
+      s = copy_out();
+      if (s != BLTT_OK) return s;
+      break;
+    }
     // u = (I (x) U) x_hat, then ||f - A u|| / ||f|| in the physical basis (while u is copied out)
     s = dst_all(h, op, x, u, 0, nullptr, nullptr);
     if (s != BLTT_OK) return s;
@@ -1016,10 +1031,30 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
     PCK(h, "scalar", launch_sum_partials(h->partials[0], nr, h->scal, st), "sum");
     h->launches++;
     CK(h, cudaMemcpyAsync(h->scal_host, h->scal, sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
+    CK(h, cudaStreamSynchronize(st), "sync");
+    if (sh->normb > 0) relres_phys = std::sqrt(h->scal_host[0]) / sh->normb;
+    if (sh->phase != PH_VERIFY) break;
+    // the check the iterations left to the host
+    sh->relres_true = relres_phys;
+    if (!std::isfinite(relres_phys)) { sh->phase = PH_FAIL; sh->status = 5; break; }
+    if (relres_phys <= tol || sh->gamma_new == 0.0) {
+      sh->phase = PH_DONE;
+      sh->status = (relres_phys <= tol) ? 0 : 6;
+      break;
+    }
+    if (sh->iter >= maxit) { sh->phase = PH_MAXIT; sh->status = 6; break; }
+    // resume: direct launches from the buffer roles of iteration sh->iter (a replayed graph
+    // could be stopped mid-block); u may still be on its way to the host
+    if (hout) CK(h, cudaStreamSynchronize(h->io_stream), "sync copy stream");
+    for (int i = 0; i < 2; ++i) { vbuf[i] = vbuf0[i]; zbuf[i] = zbuf0[i]; wbuf[i] = wbuf0[i]; }
+    if (sh->iter & 1) rotate();
+    issued = sh->iter;
+    resumed = true;
+    sh->phase = PH_RUN;
+    CK(h, cudaMemcpyAsync(phase, &sh->phase, sizeof(int), cudaMemcpyHostToDevice, st), "resume");
   }
   CK(h, cudaEventRecord(h->ev[2], st), "event");
   CK(h, cudaStreamSynchronize(st), "sync");
-  if (spectral && sh->normb > 0) relres_phys = std::sqrt(h->scal_host[0]) / sh->normb;
   prof_harvest(h);
   float t_all = 0.f, t_setup = 0.f;
   cudaEventElapsedTime(&t_all, h->ev[0], h->ev[2]);

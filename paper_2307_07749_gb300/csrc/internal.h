@@ -13,7 +13,9 @@ constexpr int kMaxPartials = 1 << 20;
 constexpr int kMaxCols = 256;     // real lines per FFT tile (column info kept in shared memory)
 
 // MINRES scalar state, resident on the device for the whole solve.
-enum Phase { PH_RUN = 0, PH_CHECK = 1, PH_DONE = 2, PH_FAIL = 3, PH_MAXIT = 4 };
+// PH_VERIFY: the recurrence estimate met the stopping rule in a solve whose true residual the
+// host checks (DST basis: the physical-basis residual after the exit transform), iterations halted
+enum Phase { PH_RUN = 0, PH_CHECK = 1, PH_DONE = 2, PH_FAIL = 3, PH_MAXIT = 4, PH_VERIFY = 5 };
 
 struct MinresDev {
   double gamma, gamma_prev, delta, eta, eta0;
@@ -137,6 +139,7 @@ cudaError_t launch_scalar_init(MinresDev* s, const double* partials_zv, int nzv,
 cudaError_t launch_scalar_delta(MinresDev* s, const double* partials, int np, cudaStream_t st);
 cudaError_t launch_scalar_gamma(MinresDev* s, const double* partials, int np, cudaStream_t st);
 cudaError_t launch_scalar_check(MinresDev* s, const double* partials, int np, cudaStream_t st);
+cudaError_t launch_scalar_defer(MinresDev* s, cudaStream_t st);   // PH_CHECK -> PH_VERIFY
 cudaError_t launch_w_update(MinresDev* s, const double* z, double* w_prev, const double* w,
                             double* x, long long n, cudaStream_t st);
 cudaError_t launch_copy_scaled_check(const double* src, double* dst, long long n, cudaStream_t st);

@@ -1040,6 +1040,12 @@ __global__ void __launch_bounds__(256) k_scalar_gamma(MinresDev* st, const doubl
 __global__ void __launch_bounds__(256) k_scalar_check(MinresDev* st, const double* p, int np) {
   scalar_check(st, p, np);
 }
+// the true-residual check left to the host: an estimate that met the stopping rule halts the
+// iterations (PH_VERIFY) instead of launching the residual product here
+__global__ void k_scalar_defer(MinresDev* st) {
+  st->wpending = 0;
+  if (st->phase == PH_CHECK) st->phase = PH_VERIFY;
+}
 
 // w_{j+1} = (z_j - a3 w_{j-1} - a2 w_j)/a1 (written over w_{j-1}); x += c_{j+1} eta w_{j+1}.
 // The coefficients are folded (w_cz = 1/(gamma_j a1), ...) so that each element costs four FP64
@@ -1331,6 +1337,11 @@ cudaError_t launch_scalar_gamma(MinresDev* s, const double* p, int np, cudaStrea
 }
 cudaError_t launch_scalar_check(MinresDev* s, const double* p, int np, cudaStream_t st) {
   k_scalar_check<<<1, 256, 0, st>>>(s, p, np);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scalar_defer(MinresDev* s, cudaStream_t st) {
+  k_scalar_defer<<<1, 1, 0, st>>>(s);
   return cudaGetLastError();
 }
 cudaError_t launch_w_update(MinresDev* s, const double* z, double* w_prev, const double* w,

@@ -314,3 +314,30 @@ def test_solve_host_buffers_chunked_entry(B):
     assert ih["status"] == 0 and ih["iters"] == idev["iters"]
     assert rel(uh.numpy(), to_host(ud)) <= 1e-13
     assert ih["relres_true"] <= 1e-8
+
+
+def test_deferred_check_resumes_exactly(B):
+    # DST basis: the iterations halt when the estimate meets tol and the host checks the true
+    # residual in the physical basis; a tolerance the true residual cannot reach makes every
+    # check fail, and the resumed iterations (direct launches) must continue exactly where the
+    # replayed graph stopped: the same iterate as a run that never stops early (tol = 0)
+    import torch
+    prob = fractional_problem(2, 31, 32, 0.7)
+    f = to_dev(rhs_uniform(prob.n, 40))
+    st = torch.cuda.Stream()
+    s = B.Solver(prob, stream=st)
+    form = dict(precision=32, basis=1, matvec_arith=2, alpha=1e-3, maxit=24, graph=True,
+                raise_on_error=False)
+    with torch.cuda.stream(st):
+        u0, i0 = s.solve(f, tol=0.0, **form)
+        u1, i1 = s.solve(f, tol=1e-15, **form)
+    torch.cuda.synchronize()
+    assert i0["status"] == i1["status"] == 6 and i0["iters"] == i1["iters"] == 24
+    assert torch.equal(u0, u1)
+    assert i1["relres_true"] == i0["relres_true"] and i1["relres_true"] <= 1e-9
+    # and a reachable tolerance stops at the first check, with the physical residual reported
+    with torch.cuda.stream(st):
+        u2, i2 = s.solve(f, tol=1e-8, **form)
+    torch.cuda.synchronize()
+    assert i2["status"] == 0 and i2["relres_true"] <= 1e-8
+    assert rel(O.bltt_matvec(prob, to_host(u2)), to_host(f)) <= 1e-8
