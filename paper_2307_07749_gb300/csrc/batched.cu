@@ -199,6 +199,9 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
       it.l2nc_tp = ilog2ll(nct);
       it.tiles_conv = (it.M + 2 * ncc - 1) / (2 * ncc);
       it.tiles_tp = (it.M + 2 * nct - 1) / (2 * nct);
+      // a large item's time pass is a single-item launch, whose tile may differ (its partial
+      // sums are what the scalar kernels read)
+      if (it.big) it.tiles_tp = timepass_tiles(op, prec);
       // the autotuner may narrow tiles up to 4x: size the partial sums for that
       it.maxtiles = 4 * std::max(it.tiles_conv, it.tiles_tp) + 4;
       long long inner = 1;

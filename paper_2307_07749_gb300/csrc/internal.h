@@ -101,6 +101,8 @@ enum { PREC_F32 = 32, PREC_F64 = 64, PREC_DF = 96 };
 cudaError_t launch_dst(const OpTables& op, int axis, int prec, const Combine& in, double* out,
                        int flip, const double* dot_with, double* partials, int* nparts,
                        const int* phase, cudaStream_t st);
+// blocks (= partial sums) of a single-item launch_timepass of this problem and precision
+long long timepass_tiles(const OpTables& op, int prec);
 cudaError_t launch_timepass(const OpTables& op, const PrecTables& pt, int prec, const Combine& in,
                             double* out, const double* dot_with, double* partials, int* nparts,
                             const int* phase, cudaStream_t st);

@@ -1209,6 +1209,16 @@ cudaError_t launch_dst(const OpTables& op, int axis, int prec, const Combine& in
   return cudaGetLastError();
 }
 
+// tile choice of the single-item time pass (shared by launch_timepass and timepass_tiles)
+static bool tp_wide(const OpTables& op, int prec) {
+  return prec == PREC_F32 && 2 * (kCap / op.N) < 16 && op.N <= WideTileF::CAP;
+}
+
+long long timepass_tiles(const OpTables& op, int prec) {
+  const int NC = tile_columns(op.M, op.N, tp_wide(op, prec) ? WideTileF::CAP : kCap);
+  return (op.M + 2 * NC - 1) / (2 * NC);
+}
+
 cudaError_t launch_timepass(const OpTables& op, const PrecTables& pt, int prec, const Combine& in,
                             double* out, const double* dot_with, double* partials, int* nparts,
                             const int* phase, cudaStream_t st) {
@@ -1236,8 +1246,7 @@ cudaError_t launch_timepass(const OpTables& op, const PrecTables& pt, int prec, 
   if (prec == PREC_F64) return run(ArithD{}, TileCfg<ArithD>{}, op.tw_N);
   if (prec == PREC_DF) return run(ArithDF{}, TileCfg<ArithDF>{}, op.tw_N_df);
   // FP32: the wide tile where the common one would span fewer than 16 lines (N >= 1024)
-  if (2 * (kCap / op.N) < 16 && op.N <= WideTileF::CAP)
-    return run(ArithF{}, WideTileF{}, op.tw_N32);
+  if (tp_wide(op, PREC_F32)) return run(ArithF{}, WideTileF{}, op.tw_N32);
   return run(ArithF{}, TileCfg<ArithF>{}, op.tw_N32);
 }
 

@@ -84,9 +84,11 @@ def test_batched_big_and_small_items_equal_single_solves(B, form):
     """Items of at least 2^21 unknowns run their FFT phases as single-item launches inside the
     batched graph, the smaller ones share the multi-item launches: both kinds reproduce the single
     solves (same iterations, same solution)."""
-    probs = [fractional_problem(2, 127, 256, 0.6), fractional_problem(1, 63, 64, 0.4),
-             fractional_problem(2, 31, 128, 0.8)]
-    assert probs[0].n >= 1 << 21 and probs[1].n < 1 << 21 and probs[2].n < 1 << 21
+    # (the N = 1024 item takes the wide FP32 time-pass tile in its single-item launches)
+    probs = [fractional_problem(2, 127, 256, 0.6), fractional_problem(2, 63, 1024, 0.7),
+             fractional_problem(1, 63, 64, 0.4), fractional_problem(2, 31, 128, 0.8)]
+    assert probs[0].n >= 1 << 21 and probs[1].n >= 1 << 21
+    assert probs[2].n < 1 << 21 and probs[3].n < 1 << 21
     fs = [[rhs_uniform(p.n, 50 + 10 * s + r) for r in range(2)] for s, p in enumerate(probs)]
     fd = [[to_dev(f) for f in row] for row in fs]
     ud = [[to_dev(np.zeros_like(f)) for f in row] for row in fs]
