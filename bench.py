@@ -249,6 +249,25 @@ def time_form(B, solver, fd, steps, warmup, alpha, precision, basis, arith, ws, 
     return {"ms_total": ms, "infos": infos, "profile": prof, "u": u}
 
 
+def copy_bandwidth(f_host, stream):
+    """GB/s of one host->device and one device->host copy of f (pinned), CUDA events."""
+    import torch
+    fd = torch.empty(f_host.shape, dtype=f_host.dtype, device="cuda")
+    back = torch.empty_like(f_host, pin_memory=True)
+    out = {}
+    with torch.cuda.stream(stream):
+        for name, (dst, src) in (("h2d", (fd, f_host)), ("d2h", (back, fd))):
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dst.copy_(src, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out[name] = round(f_host.numel() * 8 / (e0.elapsed_time(e1) / 1e3) / 1e9, 1)
+    return out
+
+
 def time_e2e(B, solver, f_host, steps, alpha, precision, basis, arith, stream):
     """Same metric through the public host-buffer solve: f copied in from pinned host memory,
     solve, u copied back into pinned host memory (the copy overlaps the final residual check)."""
@@ -648,6 +667,7 @@ def main():
     e2e = None
     if not args.no_e2e:
         f_host = torch.from_numpy(f).pin_memory()
+        copy_gbs = copy_bandwidth(f_host, stream)
         with torch.cuda.stream(stream):
             e_ms, e_iters = time_e2e(B, solver, f_host, args.steps, ALPHA_F32, 32,
                                      B.BASIS_SPECTRAL, B.ARITH_F32X2, stream)
@@ -655,7 +675,7 @@ def main():
         e_units = sum_over_ranks(float(prob.n * e_iters), ws)
         e2e = {"value": e_units / (e_ms / 1e3), "unit": "unknown-iter/s",
                "h2d_bytes_per_step": prob.n * 8, "d2h_bytes_per_step": prob.n * 8,
-               "ms_per_step": e_ms / args.steps}
+               "ms_per_step": e_ms / args.steps, "copy_GBps": copy_gbs}
 
     # accuracy of the chosen form against the plain FP64 GPU solve (error stated per result)
     uc = res["chosen"]["u"]
