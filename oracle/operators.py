@@ -23,11 +23,47 @@ def laplacian_1d(m: int, h: float) -> sp.csr_matrix:
     return sp.diags([-e[:-1], 2.0 * e, -e[:-1]], [-1, 0, 1], format="csr") / (h * h)
 
 
+def laplacian_variable(prob) -> sp.csr_matrix:
+    """L_a = -Delta_{a,h}: the central-difference discretisation of -div(a grad) (Sec. 5.2, the
+    paper's Delta_{a,h}; Example heateqvarcoeff), zero Dirichlet values, x fastest.
+
+    Along axis ax, point c of a line couples to c-1 and c+1 through the coefficient at the faces
+    between them: (L_a u)_c = [a_{c-1/2} (u_c - u_{c-1}) + a_{c+1/2} (u_c - u_{c+1})] / h^2, with
+    u = 0 outside.  prob.meta["faces"][ax] holds a at the faces along ax as an array of shape
+    (m_z, m_y, m_x) with that axis one longer (face f sits before point f; face m_ax after the last
+    point).  Written entry by entry from that formula; the result is symmetric.
+    """
+    ms, hs = _axes(prob)
+    M = int(np.prod(ms))
+    shape = tuple(reversed(ms))                       # ([z], [y], x): x is the last array axis
+    idx = np.arange(M).reshape(shape)
+    rows, cols, vals = [], [], []
+    for ax in range(prob.d):
+        arr_axis = len(shape) - 1 - ax
+        fa = np.asarray(prob.meta["faces"][ax], dtype=np.float64)
+        lo = np.take(fa, range(0, ms[ax]), axis=arr_axis)          # a_{c-1/2}
+        hi = np.take(fa, range(1, ms[ax] + 1), axis=arr_axis)      # a_{c+1/2}
+        h2 = hs[ax] ** 2
+        rows.append(idx.ravel()); cols.append(idx.ravel()); vals.append(((lo + hi) / h2).ravel())
+        if ms[ax] > 1:
+            a_ = np.take(idx, range(0, ms[ax] - 1), axis=arr_axis)
+            b_ = np.take(idx, range(1, ms[ax]), axis=arr_axis)
+            w = -np.take(hi, range(0, ms[ax] - 1), axis=arr_axis) / h2   # face between a_ and b_
+            rows += [a_.ravel(), b_.ravel()]
+            cols += [b_.ravel(), a_.ravel()]
+            vals += [w.ravel(), w.ravel()]
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(M, M))
+
+
 def laplacian(prob) -> sp.csr_matrix:
-    """L = -Delta_h on the tensor grid, lexicographic order with x fastest (Sec. 5.2).
+    """L = -Delta_h on the tensor grid, lexicographic order with x fastest (Sec. 5.2); L_a when
+    the problem carries a variable coefficient (prob.meta["faces"], see laplacian_variable).
 
     The d-dimensional operator is the Kronecker sum of the 1-D ones; axis 0 (x) is the fastest.
     """
+    if prob.meta.get("faces") is not None:
+        return laplacian_variable(prob)
     ms, hs = _axes(prob)
     M = int(np.prod(ms))
     L = sp.csr_matrix((M, M))
@@ -83,10 +119,13 @@ def apply_U(prob, V: np.ndarray) -> np.ndarray:
 def block_eigenvalues(prob) -> np.ndarray:
     """lambda_i^(k) = a_k + b_k mu_i, the eigenvalues of A_(k) = U Lambda_k U^T (Sec. 3).
 
-    Returns an (N, M) array: row k holds the diagonal of Lambda_k.
+    Returns an (N, M) array: row k holds the diagonal of Lambda_k.  For a variable-coefficient
+    problem these are the eigenvalues of the mean-coefficient blocks a_k I + abar b_k L (eq.
+    meancoeffheateqtsmat, abar = prob.meta["abar"]), from which the preconditioner is built.
     """
     mu = laplacian_eigenvalues(prob)
-    return prob.a[:, None] + prob.b[:, None] * mu[None, :]
+    b = prob.b * float(prob.meta.get("abar", 1.0)) if prob.meta.get("faces") is not None else prob.b
+    return prob.a[:, None] + b[:, None] * mu[None, :]
 
 
 def assumption_margin(prob) -> float:
@@ -143,13 +182,23 @@ def bltt_matvec_entry(prob, z: np.ndarray, n: int, i: int, flip: bool = False) -
         if prob.b[k] != 0.0:
             lz = 0.0
             stride = 1
+            faces = prob.meta.get("faces")
             for ax in range(prob.d):
                 h2 = prob.h[ax] ** 2
-                lz += 2.0 * zk[i] / h2
+                if faces is None:
+                    alo = ahi = 1.0
+                else:
+                    fa = np.asarray(faces[ax])
+                    pos = list(reversed(coords))              # ([z], [y], x) array index
+                    p_lo = list(pos)
+                    p_hi = list(pos)
+                    p_hi[len(pos) - 1 - ax] += 1
+                    alo, ahi = fa[tuple(p_lo)], fa[tuple(p_hi)]
+                lz += (alo + ahi) * zk[i] / h2
                 if coords[ax] > 0:
-                    lz -= zk[i - stride] / h2
+                    lz -= alo * zk[i - stride] / h2
                 if coords[ax] < ms[ax] - 1:
-                    lz -= zk[i + stride] / h2
+                    lz -= ahi * zk[i + stride] / h2
                 stride *= ms[ax]
             acc += prob.b[k] * lz
     return acc

@@ -311,3 +311,60 @@ def test_theorem1_rate_bound_tiny():
         x = O.minres(Afn, Pinv, b, tol=0.0, maxit=k)["x"]
         rk = np.linalg.norm(Pinv(Afn(x) - b))
         assert rk <= 2 * delta ** (k - 1) * r0 * (1 + 1e-8) + 1e-12 * r0
+
+
+# ------------------------------------------- variable coefficient (Sec. 5.2, Example heateqvarcoeff)
+
+def _var1d(m, coef):
+    """1-D problem on (0, 1) whose L is L_a for the coefficient function coef (faces at (f+1/2)h)."""
+    from workloads import Problem
+    p = heat_cn_problem(1, m, 4)
+    h = p.h[0]
+    faces = coef((np.arange(m + 1) + 0.5) * h)
+    return Problem(p.N, p.d, p.m, p.h, p.a, p.b, name="var1d",
+                   meta=dict(faces=(faces,), abar=float(np.mean(coef((np.arange(m) + 1.0) * h)))))
+
+
+def test_variable_laplacian_exact_on_quadratics():
+    # The conservative central difference is exact when the flux a u' is quadratic: with a(x) = x
+    # and u = x (1 - x) (zero at both ends), -(a u')' = 4x - 1 at every interior point.
+    m = 31
+    p = _var1d(m, lambda x: x)
+    x = (np.arange(m) + 1.0) / (m + 1)
+    Lu = O.laplacian(p) @ (x * (1 - x))
+    assert np.max(np.abs(Lu - (4 * x - 1))) < 1e-10
+
+
+def test_variable_laplacian_properties():
+    from workloads import heat_cn_varcoeff_problem
+    import copy
+    p = heat_cn_varcoeff_problem(7, 4)
+    L = O.laplacian(p)
+    assert abs(L - L.T).max() == 0.0
+    assert np.linalg.eigvalsh(L.toarray()).min() > 0                   # -Delta_{a,h} is SPD
+    one = copy.deepcopy(p)
+    one.meta["faces"] = tuple(np.ones_like(f) for f in p.meta["faces"])
+    plain = copy.deepcopy(p)
+    plain.meta.pop("faces")
+    assert abs(O.laplacian(one) - O.laplacian(plain)).max() == 0.0     # a = 1 gives Delta_h
+    # the block sum entry by entry agrees with the Toeplitz-product matvec
+    from oracle.operators import bltt_matvec_entry
+    z = np.random.default_rng(3).standard_normal(p.n)
+    y = O.bltt_matvec(p, z, flip=True)
+    e = np.array([bltt_matvec_entry(p, z, n, i, flip=True) for n in range(p.N) for i in range(p.M)])
+    assert rel(e, y) < 1e-14
+    # the preconditioner is that of the mean-coefficient blocks (eq. meancoeffheateqtsmat)
+    lam = O.block_eigenvalues(p)
+    mu = O.laplacian_eigenvalues(p)
+    assert np.allclose(lam[0], p.a[0] + p.meta["abar"] * p.b[0] * mu, rtol=1e-15)
+
+
+def test_paper_iteration_counts_varcoeff():
+    from workloads import heat_cn_varcoeff_problem
+    g = json.load(open(os.path.join(GOLDEN, "paper_iteration_counts_varcoeff.json")))
+    for c in g["cases"]:
+        prob = heat_cn_varcoeff_problem(c["m_plus_1"] - 1, c["N"])
+        assert prob.n == c["dof"]
+        f = rhs_uniform(prob.n, 11)
+        r = O.solve(prob, f, alpha=g["alpha"], tol=g["tol"])
+        assert r["iters"] == c["iters"], (c, r["iters"])

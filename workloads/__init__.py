@@ -117,6 +117,27 @@ def heat_cn_problem(d, m, N, T=1.0, length=1.0, name=None) -> Problem:
                    dict(kind="heat_cn", gamma=1.0, tau=tau))
 
 
+def heat_cn_varcoeff_problem(m, N, T=1.0, name=None) -> Problem:
+    """Crank-Nicolson heat equation with the variable coefficient of the paper's Example
+    heateqvarcoeff: d = 2, Omega = (0,1)^2, a(x) = (20 + x_1^2)(20 + x_2^2).  Blocks
+    A_(0) = I/tau + L_a/2, A_(1) = -I/tau + L_a/2 with L_a = -Delta_{a,h} (eq.
+    cnheatvarcoeff_tssystem); meta["faces"] holds a at the cell faces along x and y (arrays
+    (m, m+1) and (m+1, m), y-major), meta["abar"] the mean of a over the interior grid points
+    (the preconditioner's constant coefficient, eq. meancoeffheateqtsmat)."""
+    p = heat_cn_problem(2, m, N, T=T)
+    mm = p.m[0]
+    h = p.h[0]
+    pts = (np.arange(mm) + 1.0) * h                   # interior points
+    fcs = (np.arange(mm + 1) + 0.5) * h               # faces: before point f, and after the last
+    coef = lambda x1, x2: (20.0 + x1 ** 2) * (20.0 + x2 ** 2)
+    fx = coef(fcs[None, :], pts[:, None])             # rows y, columns x faces: (m, m+1)
+    fy = coef(pts[None, :], fcs[:, None])             # rows y faces, columns x: (m+1, m)
+    abar = float(np.mean(coef(pts[None, :], pts[:, None])))
+    return Problem(p.N, p.d, p.m, p.h, p.a, p.b, name or f"heat2d_cnvar_N{N}_m{mm}",
+                   dict(kind="heat_cn_var", gamma=1.0, tau=p.meta["tau"], faces=(fx, fy),
+                        abar=abar))
+
+
 def rhs_uniform(n: int, seed: int) -> np.ndarray:
     """Seeded U[-1, 1] right-hand side of length n (float64)."""
     return np.random.default_rng(seed).uniform(-1.0, 1.0, n)
