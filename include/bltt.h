@@ -133,6 +133,19 @@ bltt_status bltt_create(const bltt_blocks* blocks, int N, long long M, bltt_hand
 /* Release the handle, its tables and workspace.  NULL is accepted. */
 bltt_status bltt_destroy(bltt_handle h);
 
+/* Variable coefficient (Sec. 5.2, Example heateqvarcoeff): the blocks become A_(k) = a_k I + b_k L_a
+ * with L_a = -Delta_{a,h}, the central-difference discretisation of -div(a grad) with zero
+ * Dirichlet values: per axis, (L_a u)_c = [a_{c-1/2} (u_c - u_{c-1}) + a_{c+1/2} (u_c - u_{c+1})]/h^2.
+ *   face[ax] (host, ax < d): a at the faces along axis ax, an array of the grid's shape with that
+ *     axis one longer, x fastest; entry f along the axis sits between points f-1 and f of its line
+ *     (f = 0 and f = m_ax are the boundary faces).  (m_ax + 1) * M / m_ax positive finite values.
+ *   abar: the preconditioner is built for the blocks a_k I + abar b_k L (eq. meancoeffheateqtsmat;
+ *     the paper takes the mean of a over the grid points); > 0.
+ * Matvecs and solves then use L_a.  Solves run in the physical basis (AUTO picks it; SPECTRAL
+ * gives BLTT_ERR_UNSUPPORTED: the DST does not diagonalise L_a), and the tensor-core product is
+ * unsupported.  The face arrays are copied to the device; a later call replaces them. */
+bltt_status bltt_set_variable_coefficient(bltt_handle h, const double* const* face, double abar);
+
 /* Issue all later work of h on `cuda_stream` (a cudaStream_t; NULL = legacy default stream). */
 bltt_status bltt_set_stream(bltt_handle h, void* cuda_stream);
 

@@ -78,6 +78,8 @@ _SIGS = {
     "bltt_set_stream": (ctypes.c_int, [_P, _P]),
     "bltt_matvec": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "bltt_set_matvec_arith": (ctypes.c_int, [_P, ctypes.c_int]),
+    "bltt_set_variable_coefficient": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.POINTER(ctypes.c_double)),
+                                                      ctypes.c_double]),
     "bltt_precond_apply": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, ctypes.c_int]),
     "bltt_minres_solve_ex": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                             ctypes.POINTER(bltt_solve_opts), _P,
@@ -187,6 +189,16 @@ def bltt_set_stream(handle, stream):
 
 def bltt_set_matvec_arith(handle, arith):
     _check(lib().bltt_set_matvec_arith(handle, int(arith)), handle)
+
+
+def bltt_set_variable_coefficient(handle, faces, abar):
+    """faces: one array per axis, the coefficient at the faces along that axis (the grid's shape
+    with that axis one longer, x fastest); abar: the preconditioner's constant coefficient."""
+    arrs = [np.ascontiguousarray(f, dtype=np.float64).reshape(-1) for f in faces]
+    ptrs = (ctypes.POINTER(ctypes.c_double) * 3)(
+        *[a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for a in arrs],
+        *[ctypes.POINTER(ctypes.c_double)() for _ in range(3 - len(arrs))])
+    _check(lib().bltt_set_variable_coefficient(handle, ptrs, float(abar)), handle)
 
 
 def bltt_matvec(handle, x, y, flip=1):
@@ -353,6 +365,10 @@ class Solver:
         self.M = int(np.prod(self.m))
         self.n = self.N * self.M
         self.handle = bltt_create(prob.a, prob.b, self.N, self.d, self.m, tuple(prob.h))
+        meta = getattr(prob, "meta", None) or {}
+        if meta.get("faces") is not None:
+            # variable coefficient: L_a in the matvec, the mean coefficient in the preconditioner
+            bltt_set_variable_coefficient(self.handle, meta["faces"], meta["abar"])
         if stream is not None:
             bltt_set_stream(self.handle, stream)
 

@@ -82,6 +82,8 @@ struct bltt_ctx {
   long long M = 0, n = 0;
   double h[3] = {1, 1, 1};
   std::vector<double> a, b;
+  double pc_bscale = 1.0;     // the preconditioner's blocks are a_k I + pc_bscale b_k L (abar)
+  bool var_coef = false;      // the matvec's L is L_a = -Delta_{a,h} (faces in op.kf)
   cudaStream_t stream = nullptr;
   std::string err;
   OpTables op{};
@@ -231,6 +233,8 @@ cudaError_t upload_twiddles(bltt_ctx* h, int L, const double2** d64, const float
 
 // ensure the tensor-core matvec workspace: digit planes, column exponents, the error flag
 bltt_status ensure_tc(bltt_ctx* h) {
+  if (h->var_coef)
+    return fail(h, BLTT_ERR_UNSUPPORTED, "the tensor-core matvec has no variable coefficient");
   if (!tc_eligible(h->op) || !h->op.tc_hank)
     return fail(h, BLTT_ERR_UNSUPPORTED,
                 "the tensor-core matvec needs b = b0 e_0, more than 4 nonzeros in a and N in "
@@ -278,7 +282,7 @@ bltt_status prepare_precond(bltt_ctx* h, double alpha, int prec) {
       dinv[j] = 1.0 / dj;
       d2[j] = dj * dj;
       ah[j] = cd(dj * h->a[j], 0.0);
-      bh[j] = cd(dj * h->b[j], 0.0);
+      bh[j] = cd(dj * h->b[j] * h->pc_bscale, 0.0);
     }
     host_fft(ah);
     host_fft(bh);
@@ -677,6 +681,28 @@ bltt_status bltt_destroy(bltt_handle h) {
   return BLTT_OK;
 }
 
+bltt_status bltt_set_variable_coefficient(bltt_handle h, const double* const* face, double abar) {
+  if (!h) return BLTT_ERR_INVALID_ARG;
+  if (!face) return fail(h, BLTT_ERR_INVALID_ARG, "null face array");
+  if (!(abar > 0.0) || !std::isfinite(abar)) return fail(h, BLTT_ERR_INVALID_ARG, "abar must be positive");
+  if (h->op.mv_arith == 2) return fail(h, BLTT_ERR_UNSUPPORTED, "the tensor-core matvec has no variable coefficient");
+  double* dev[3] = {nullptr, nullptr, nullptr};
+  for (int ax = 0; ax < h->d; ++ax) {
+    if (!face[ax]) return fail(h, BLTT_ERR_INVALID_ARG, "null face array");
+    const size_t cnt = (size_t)(h->M / h->m[ax]) * (size_t)(h->m[ax] + 1);
+    for (size_t k = 0; k < cnt; ++k)
+      if (!(face[ax][k] > 0.0) || !std::isfinite(face[ax][k]))
+        return fail(h, BLTT_ERR_INVALID_ARG, "face coefficients must be positive and finite");
+    CK(h, upload(h, &dev[ax], face[ax], cnt), "face coefficients");
+  }
+  for (int ax = 0; ax < 3; ++ax) h->op.kf[ax] = dev[ax];
+  h->var_coef = true;
+  h->pc_bscale = abar;
+  h->pc_alpha = -1.0;                        // the preconditioner tables are rebuilt
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }   // kernel arguments changed
+  return BLTT_OK;
+}
+
 bltt_status bltt_set_stream(bltt_handle h, void* s) {
   if (!h) return BLTT_ERR_INVALID_ARG;
   h->stream = reinterpret_cast<cudaStream_t>(s);
@@ -812,7 +838,10 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
   if (!none && !(alpha > 0.0 && alpha <= 1.0)) return fail(h, BLTT_ERR_INVALID_ARG, "alpha must lie in (0, 1]");
   if (!(tol >= 0.0) || maxit < 1) return fail(h, BLTT_ERR_INVALID_ARG, "tol must be >= 0 and maxit >= 1");
   int basis = o.basis;
-  if (basis == BLTT_BASIS_AUTO) basis = BLTT_BASIS_SPECTRAL;
+  // a variable coefficient leaves L undiagonalised by the DST: only the physical basis applies
+  if (h->var_coef && basis == BLTT_BASIS_SPECTRAL)
+    return fail(h, BLTT_ERR_UNSUPPORTED, "a variable coefficient needs the physical basis");
+  if (basis == BLTT_BASIS_AUTO) basis = h->var_coef ? BLTT_BASIS_PHYSICAL : BLTT_BASIS_SPECTRAL;
   if (basis != BLTT_BASIS_SPECTRAL && basis != BLTT_BASIS_PHYSICAL) return fail(h, BLTT_ERR_INVALID_ARG, "bad basis");
   const int spectral = (basis == BLTT_BASIS_SPECTRAL) ? 1 : 0;
   const int sync_every = o.sync_every > 0 ? o.sync_every : 2;

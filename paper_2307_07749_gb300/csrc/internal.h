@@ -56,6 +56,9 @@ struct OpTables {
   const float4* tw_2N_df;
   const float4* tw_dst_df[3];
   const float4* tw_N_df;
+  // variable coefficient (null: L = -Delta_h): a at the cell faces along each axis, arrays of the
+  // grid's shape with that axis one longer (x fastest); L becomes L_a = -Delta_{a,h}
+  const double* kf[3];
   int mv_arith;               // 0: FP64, 1: double-float (matvec and the FP64-accurate DSTs),
                               // 2: tensor-core time product in MV_STORE matvecs, else as 1
   // tensor-core time product (kernels in tcmv.cu): bf16 digit planes of the time-flipped

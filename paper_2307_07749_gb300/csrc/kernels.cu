@@ -678,7 +678,11 @@ __device__ __forceinline__ void conv_tile(const OpTables& op, int spectral, int 
       const long long i = g0 + c;
       if (e >= total || i >= M) continue;
       double val = A::part(buf[t * NC + (c >> 1)], c & 1);
-      if (extra_st) {
+      if (extra_st && op.kf[0]) {
+        int ix, iy, iz;
+        mode_coords(op, i, ix, iy, iz);
+        val = fma(st_coef, stencil_faces(op, st_src + (long long)t * M, i, ix, iy, iz), val);
+      } else if (extra_st) {
         const double* xt = st_src + (long long)t * M;
         const int nb = s_nb[c];
         const double xi2 = 2.0 * xt[i];
@@ -822,7 +826,9 @@ k_direct(OpTables op, const double* __restrict__ x, const double* xscale, double
 #pragma unroll
         for (int k = K - 1; k > 0; --k) { xp[q][k] = xp[q][k - 1]; lp[q][k] = lp[q][k - 1]; }
         xp[q][0] = xs[q];
-        if (lap) lp[q][0] = stencil_xyz(op, x + row, i, cx[q], cy[q], cz[q]);
+        if (lap)
+          lp[q][0] = op.kf[0] ? stencil_faces(op, x + row, i, cx[q], cy[q], cz[q])
+                              : stencil_xyz(op, x + row, i, cx[q], cy[q], cz[q]);
         double val = 0.0;
 #pragma unroll
         for (int k = 0; k < K; ++k) {

@@ -55,4 +55,45 @@ __device__ __forceinline__ double stencil_at(const OpTables& op, const double* _
   return acc;
 }
 
+// coordinates (ix, iy, iz) of spatial index i (x fastest)
+__device__ __forceinline__ void mode_coords(const OpTables& op, long long i, int& ix, int& iy,
+                                            int& iz) {
+  const long long r1 = i / op.m[0];
+  ix = (int)(i - r1 * op.m[0]);
+  iy = 0;
+  iz = 0;
+  if (op.d > 1) {
+    const long long r2 = r1 / op.m[1];
+    iy = (int)(r1 - r2 * op.m[1]);
+    iz = (int)r2;
+  }
+}
+
+// (L_a x)[i] on the time slice x_t with the coefficient at the cell faces (op.kf): per axis
+// [a_lo (x_i - x_{i-s}) + a_hi (x_i - x_{i+s})] / h^2 with zero Dirichlet values, the central-
+// difference discretisation of -div(a grad) (Sec. 5.2, the paper's Delta_{a,h}).  Face (.., f, ..)
+// of axis ax sits between points f-1 and f of its line.
+__device__ __forceinline__ double stencil_faces(const OpTables& op, const double* __restrict__ x_t,
+                                                long long i, int ix, int iy, int iz) {
+  const double xi = x_t[i];
+  const long long m0 = op.m[0], m1 = op.d > 1 ? op.m[1] : 1;
+  double acc = 0.0;
+  long long stride = 1;
+  for (int ax = 0; ax < op.d; ++ax) {
+    const int c = ax == 0 ? ix : (ax == 1 ? iy : iz);
+    const int mm = op.m[ax];
+    long long lo, hi;
+    if (ax == 0) { lo = ((long long)iz * m1 + iy) * (m0 + 1) + ix; hi = lo + 1; }
+    else if (ax == 1) { lo = ((long long)iz * (m1 + 1) + iy) * m0 + ix; hi = lo + m0; }
+    else { lo = ((long long)iz * m1 + iy) * m0 + ix; hi = lo + m1 * m0; }
+    const double alo = op.kf[ax][lo], ahi = op.kf[ax][hi];
+    double s = (alo + ahi) * xi;
+    if (c > 0) s -= alo * x_t[i - stride];
+    if (c < mm - 1) s -= ahi * x_t[i + stride];
+    acc = fma(s, op.h2inv[ax], acc);
+    stride *= mm;
+  }
+  return acc;
+}
+
 }  // namespace bltt
