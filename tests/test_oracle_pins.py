@@ -368,3 +368,26 @@ def test_paper_iteration_counts_varcoeff():
         f = rhs_uniform(prob.n, 11)
         r = O.solve(prob, f, alpha=g["alpha"], tol=g["tol"])
         assert r["iters"] == c["iters"], (c, r["iters"])
+
+
+def _paper_rhs(c):
+    """The paper's own right-hand side of a golden case (its examples' data)."""
+    from workloads import heat_cn_varcoeff_problem, paper_data_fractional, paper_data_heat_var
+    if c["example"] == "heat_cn_var":
+        prob = heat_cn_varcoeff_problem(c["m_plus_1"] - 1, c["N"])
+        F, u0 = paper_data_heat_var(prob)
+        tau = 1.0 / prob.N
+        # CN first block: f^(1/2) - (1/tau) L_{a,2} u_0 with L_{a,2} = -I - (tau/2) Delta_{a,h}
+        F[0] += u0 / tau - 0.5 * (O.laplacian(prob) @ u0)
+        return prob, F.reshape(-1)
+    prob = fractional_problem(2, c["m_plus_1"] - 1, c["N"], c["gamma"], length=math.pi)
+    return prob, paper_data_fractional(prob, c["gamma"])
+
+
+def test_paper_iteration_counts_with_paper_data():
+    # both preconditioners on the paper's own data: MINRES-P_alpha and the comparison MINRES-P_1
+    g = json.load(open(os.path.join(GOLDEN, "paper_iteration_counts_paper_data.json")))
+    for c in g["cases"]:
+        prob, f = _paper_rhs(c)
+        r = O.solve(prob, f, alpha=g["alpha"], tol=g["tol"], precond=c["precond"], maxit=2000)
+        assert abs(r["iters"] - c["iters"]) <= c["slack"], (c, r["iters"])

@@ -21,6 +21,7 @@ import numpy as np
 
 __all__ = [
     "Problem", "l1_weights", "fractional_problem", "heat_bdf_problem", "heat_cn_problem",
+    "heat_cn_varcoeff_problem", "paper_data_fractional", "paper_data_heat_var",
     "rhs_uniform", "rhs_smoothed_field", "WORKLOADS", "workload", "batched_systems",
     "alpha_training_problems",
 ]
@@ -136,6 +137,36 @@ def heat_cn_varcoeff_problem(m, N, T=1.0, name=None) -> Problem:
     return Problem(p.N, p.d, p.m, p.h, p.a, p.b, name or f"heat2d_cnvar_N{N}_m{mm}",
                    dict(kind="heat_cn_var", gamma=1.0, tau=p.meta["tau"], faces=(fx, fy),
                         abar=abar))
+
+
+def paper_data_fractional(prob, gamma: float) -> np.ndarray:
+    """Right-hand side of the paper's non-local Example 3 (Sec. 5.2: Omega = (0, pi)^2, T = 1,
+    u = sin x sin y t^2, a = 1): f(x, y, t_n) = sin x sin y [2 t^(2-gamma)/Gamma(3-gamma) + 2 t^2]
+    at the interior grid points and t_n = n tau, n = 1..N (u_0 = 0 adds nothing)."""
+    import math
+    m, h, N = prob.m[0], prob.h[0], prob.N
+    x = (np.arange(m) + 1.0) * h
+    S = np.outer(np.sin(x), np.sin(x)).reshape(-1)
+    t = (np.arange(N) + 1.0) / N
+    ft = 2.0 * t ** (2.0 - gamma) / math.gamma(3.0 - gamma) + 2.0 * t ** 2
+    return (ft[:, None] * S[None, :]).reshape(-1)
+
+
+def paper_data_heat_var(prob):
+    """Data of the paper's Example heateqvarcoeff on the interior grid (x fastest): the source
+    f(x, t_{n-1/2}), n = 1..N, as an (N, M) array, and u_0 as an (M,) array.  f is the one of the
+    exact solution u = e^t x_1(1-x_1) x_2(1-x_2) for a = (20 + x_1^2)(20 + x_2^2) (the printed f
+    has (20 + x_2^2) in its third term, where the exact solution gives (20 + x_1^2))."""
+    m, h, N = prob.m[0], prob.h[0], prob.N
+    x = (np.arange(m) + 1.0) * h
+    X1, X2 = np.meshgrid(x, x)                        # X1 along rows' entries: x fastest
+    a = (20.0 + X1 ** 2) * (20.0 + X2 ** 2)
+    s = X1 * (1 - X1) * X2 * (1 - X2)
+    g = (s - 2 * X1 * (20 + X2 ** 2) * (1 - 2 * X1) * X2 * (1 - X2)
+         - 2 * X2 * (20 + X1 ** 2) * (1 - 2 * X2) * X1 * (1 - X1)
+         + 2 * a * (X1 * (1 - X1) + X2 * (1 - X2))).reshape(-1)
+    t = (np.arange(N) + 0.5) / N
+    return np.exp(t)[:, None] * g[None, :], s.reshape(-1)
 
 
 def rhs_uniform(n: int, seed: int) -> np.ndarray:
