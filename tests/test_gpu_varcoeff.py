@@ -113,3 +113,20 @@ def test_varcoeff_declined(B):
     with pytest.raises(B.BlttError) as e:
         B.Solver(bad)
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("precond,alpha,printed,slack", [("alpha", 1e-8, 10, 0), ("one", 1.0, 217, 1)],
+                         ids=["P_alpha", "P_1"])
+def test_varcoeff_paper_data_counts(B, precond, alpha, printed, slack):
+    # Table 3 on the example's own data (exact solution e^t x1(1-x1) x2(1-x2), u_0 in the CN first
+    # block): MINRES-P_alpha 10 iterations, MINRES-P_1 (alpha = 1) 217 printed
+    from workloads import paper_data_heat_var
+    prob = heat_cn_varcoeff_problem(31, 32)
+    F, u0 = paper_data_heat_var(prob)
+    F[0] += u0 * prob.N - 0.5 * (O.laplacian(prob) @ u0)
+    f = F.reshape(-1)
+    ref = O.solve(prob, f, alpha=alpha, tol=1e-6, maxit=1000, precond=precond)
+    u, info = B.Solver(prob).solve(to_dev(f), alpha=alpha, tol=1e-6, maxit=1000, precision=64)
+    assert info["status"] == 0
+    assert abs(info["iters"] - printed) <= slack and abs(info["iters"] - ref["iters"]) <= 1
+    assert rel(to_host(u), ref["x"]) <= 1e-5
