@@ -738,40 +738,76 @@ k_conv(OpTables op, int spectral, int which, const double* x, const double* xsca
 // formed once, the K-1 earlier x (and, in the physical basis, L x) stay in registers, and each
 // output costs K FP64 multiply-adds plus the fused dot product (GB300 runs FP64 at 2 FMA per
 // clock per SM, so the FP64 operation count, not the bytes, bounds this kernel).
-__device__ __forceinline__ double stencil_xyz(const OpTables& op, const double* __restrict__ x_t,
-                                              long long i, int ix, int iy, int iz) {
-  const double xi2 = 2.0 * x_t[i];
-  double sx = xi2;
-  if (ix > 0) sx -= x_t[i - 1];
-  if (ix < op.m[0] - 1) sx -= x_t[i + 1];
-  double lap = sx * op.h2inv[0];
-  if (op.d > 1) {
-    const long long s1 = op.m[0];
-    double sy = xi2;
-    if (iy > 0) sy -= x_t[i - s1];
-    if (iy < op.m[1] - 1) sy -= x_t[i + s1];
-    lap = fma(sy, op.h2inv[1], lap);
-    if (op.d > 2) {
-      const long long s2 = s1 * op.m[1];
-      double sz = xi2;
-      if (iz > 0) sz -= x_t[i - s2];
-      if (iz < op.m[2] - 1) sz -= x_t[i + s2];
-      lap = fma(sz, op.h2inv[2], lap);
-    }
-  }
-  return lap;
-}
-
 constexpr int kDirectThreads = 256;
 constexpr int kDirectPts = 4;      // points per thread, kDirectThreads apart: 8 KB rows per block
 
+// per-point stencil weights of L (or L_a): w0 x_i - sum_n wn x_{i + off_n}; a neighbour outside
+// the grid has weight 0 and offset 0 (so its load stays in bounds)
+template <int D2>
+struct PointStencil {
+  double w0;
+  double wn[D2];
+  int off[D2];
+};
+template <int D2>
+__device__ __forceinline__ PointStencil<D2> point_stencil(const OpTables& op, int ix, int iy, int iz) {
+  PointStencil<D2> ps;
+  ps.w0 = 0.0;
+  const long long m0 = op.m[0], m1 = op.d > 1 ? op.m[1] : 1;
+  long long stride = 1;
+#pragma unroll
+  for (int ax = 0; ax < D2 / 2; ++ax) {
+    double alo = 1.0, ahi = 1.0;
+    int c = 0, mm = 1;
+    if (ax < op.d) {
+      c = ax == 0 ? ix : (ax == 1 ? iy : iz);
+      mm = op.m[ax];
+      if (op.kf[0]) {
+        long long lo, hi;
+        if (ax == 0) { lo = ((long long)iz * m1 + iy) * (m0 + 1) + ix; hi = lo + 1; }
+        else if (ax == 1) { lo = ((long long)iz * (m1 + 1) + iy) * m0 + ix; hi = lo + m0; }
+        else { lo = ((long long)iz * m1 + iy) * m0 + ix; hi = lo + m1 * m0; }
+        alo = op.kf[ax][lo];
+        ahi = op.kf[ax][hi];
+      }
+      const double h2 = op.h2inv[ax];
+      ps.w0 = fma(alo + ahi, h2, ps.w0);
+      ps.wn[2 * ax] = c > 0 ? alo * h2 : 0.0;
+      ps.off[2 * ax] = c > 0 ? (int)-stride : 0;
+      ps.wn[2 * ax + 1] = c < mm - 1 ? ahi * h2 : 0.0;
+      ps.off[2 * ax + 1] = c < mm - 1 ? (int)stride : 0;
+      stride *= mm;
+    } else {
+      ps.wn[2 * ax] = ps.wn[2 * ax + 1] = 0.0;
+      ps.off[2 * ax] = ps.off[2 * ax + 1] = 0;
+    }
+  }
+  return ps;
+}
+template <int D2>
+__device__ __forceinline__ double apply_stencil(const PointStencil<D2>& ps,
+                                                const double* __restrict__ x_ti) {
+  double v = ps.w0 * x_ti[0];
+#pragma unroll
+  for (int n = 0; n < D2; ++n)
+    if (ps.wn[n] != 0.0) v = fma(-ps.wn[n], x_ti[ps.off[n]], v);   // absent axes and boundaries
+  return v;
+}
+
+constexpr int kDirectChunk = 32;   // time steps a thread walks per work unit
+
+// One work unit: a group of kDirectThreads x P consecutive points (P per thread, kDirectThreads
+// apart) over a chunk of kDirectChunk time steps; the K-1 earlier values (and their L x in the
+// physical basis) are loaded at the chunk's start.  Units run point groups fastest, so that the
+// blocks in flight read neighbouring runs of the same rows.
 template <int K, bool SPECTRAL>
 __global__ void __launch_bounds__(kDirectThreads)
 k_direct(OpTables op, const double* __restrict__ x, const double* xscale, double* y, int flip,
          int mode, const double* rhs, double* partials, const int* phase, int want) {
   if (skip_phase(phase, want)) return;
   constexpr bool spectral = SPECTRAL;
-  constexpr int P = kDirectPts;
+  constexpr int P = SPECTRAL ? kDirectPts : 1;
+  constexpr int D2 = SPECTRAL ? 1 : 6;          // stencil neighbours kept per point
   __shared__ double red[32];
   const int N = op.N;
   const long long M = op.M;
@@ -780,25 +816,23 @@ k_direct(OpTables op, const double* __restrict__ x, const double* xscale, double
 #pragma unroll
   for (int k = 0; k < K; ++k) any_b |= (op.b_dev[k] != 0.0);
   const bool lap = !spectral && any_b;
+  const long long groups = (M + P * kDirectThreads - 1) / (P * kDirectThreads);
+  const long long units = groups * ((N + kDirectChunk - 1) / kDirectChunk);
   double acc = 0.0;
-  for (long long c0 = (long long)blockIdx.x * (P * kDirectThreads); c0 < M;
-       c0 += (long long)gridDim.x * (P * kDirectThreads)) {
+  for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+    const int chunk = (int)(u / groups);
+    const long long c0 = (u - (long long)chunk * groups) * (P * kDirectThreads);
+    const int t0 = chunk * kDirectChunk, t1 = min(N, t0 + kDirectChunk);
     long long ip[P];
-    int cx[P], cy[P], cz[P];
     double ca[P][K], cb[P][K], xp[P][K], lp[P][K];
+    PointStencil<D2> pst[P];
 #pragma unroll
     for (int q = 0; q < P; ++q) {
       ip[q] = c0 + q * kDirectThreads + threadIdx.x;
       const long long i = ip[q] < M ? ip[q] : M - 1;     // tail points compute, never store
-      const long long r1 = i / op.m[0];
-      cx[q] = (int)(i - r1 * op.m[0]);
-      cy[q] = 0;
-      cz[q] = 0;
-      if (op.d > 1) {
-        const long long r2 = r1 / op.m[1];
-        cy[q] = (int)(r1 - r2 * op.m[1]);
-        cz[q] = (int)r2;
-      }
+      int cx, cy, cz;
+      mode_coords(op, i, cx, cy, cz);
+      if (!spectral && lap) pst[q] = point_stencil<D2>(op, cx, cy, cz);
       // per-point coefficients: spectral s (a_k + b_k mu_i); physical s a_k and s b_k
       const double mu = spectral ? mode_mu(op, i) : 0.0;
 #pragma unroll
@@ -806,11 +840,19 @@ k_direct(OpTables op, const double* __restrict__ x, const double* xscale, double
         const double ak = op.a_dev[k], bk = op.b_dev[k];
         ca[q][k] = spectral ? s * fma(bk, mu, ak) : s * ak;
         cb[q][k] = spectral ? 0.0 : s * bk;
+        // the chunk's earlier steps t0 - k (zero before the first step)
+        const int tk = t0 - k;
         xp[q][k] = 0.0;
         lp[q][k] = 0.0;
+        if (k > 0 && tk >= 0) {
+          const double* xt = x + (long long)tk * M + i;
+          // stored one slot ahead: the step loop shifts before it uses them
+          xp[q][k - 1] = xt[0];
+          if (!spectral && lap) lp[q][k - 1] = apply_stencil<D2>(pst[q], xt);
+        }
       }
     }
-    for (int t = 0; t < N; ++t) {
+    for (int t = t0; t < t1; ++t) {
       const long long row = (long long)t * M;
       const long long orow = (long long)(flip ? (N - 1 - t) : t) * M;
       double xs[P], pr[P];
@@ -826,9 +868,7 @@ k_direct(OpTables op, const double* __restrict__ x, const double* xscale, double
 #pragma unroll
         for (int k = K - 1; k > 0; --k) { xp[q][k] = xp[q][k - 1]; lp[q][k] = lp[q][k - 1]; }
         xp[q][0] = xs[q];
-        if (lap)
-          lp[q][0] = op.kf[0] ? stencil_faces(op, x + row, i, cx[q], cy[q], cz[q])
-                              : stencil_xyz(op, x + row, i, cx[q], cy[q], cz[q]);
+        if (!spectral && lap) lp[q][0] = apply_stencil<D2>(pst[q], x + row + i);
         double val = 0.0;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -1286,8 +1326,8 @@ cudaError_t launch_matvec(const OpTables& op, int spectral, const double* x, con
                           int* nparts, const int* phase, double* tmp, cudaStream_t st) {
   const int want = (mode == MV_RESID) ? PH_CHECK : PH_RUN;
   if (op.ntaps > 0) {
-    const long long per = (long long)kDirectPts * kDirectThreads;
-    long long g = (op.M + per - 1) / per;
+    const long long per = (long long)(spectral ? kDirectPts : 1) * kDirectThreads;
+    long long g = (op.M + per - 1) / per * ((op.N + kDirectChunk - 1) / kDirectChunk);
     if (g > 152LL * 8) g = 152LL * 8;
     if (nparts) *nparts = (int)g;
 #define BLTT_DIRECT(K_)                                                                         \
