@@ -341,3 +341,17 @@ def test_deferred_check_resumes_exactly(B):
     torch.cuda.synchronize()
     assert i2["status"] == 0 and i2["relres_true"] <= 1e-8
     assert rel(O.bltt_matvec(prob, to_host(u2)), to_host(f)) <= 1e-8
+
+
+@pytest.mark.parametrize("gamma,printed_p1", [(0.1, 6), (0.5, 8)])
+def test_paper_data_counts_example3(B, gamma, printed_p1):
+    # Tables 4 and 5 on Example 3's own data (u = sin x sin y t^2 on (0, pi)^2): MINRES-P_alpha
+    # 2 iterations, MINRES-P_1 (alpha = 1) 6 and 8, as printed, at tolerance 1e-6
+    import math
+    from workloads import paper_data_fractional
+    prob = fractional_problem(2, 31, 32, gamma, length=math.pi)
+    f = to_dev(paper_data_fractional(prob, gamma))
+    s = B.Solver(prob)
+    for alpha, printed in ((1e-8, 2), (1.0, printed_p1)):
+        u, info = s.solve(f, alpha=alpha, tol=1e-6, maxit=100, precision=64)
+        assert info["status"] == 0 and info["iters"] == printed, (alpha, info["iters"])
