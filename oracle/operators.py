@@ -56,12 +56,26 @@ def laplacian_variable(prob) -> sp.csr_matrix:
                          shape=(M, M))
 
 
+def dense_eigh(prob):
+    """K = U diag(mu) U^T for a problem with a dense symmetric operator prob.meta["K"] (the
+    commuting-blocks case of Sec. 3: A_(k) = a_k I + b_k K share the eigenvectors of K); numpy's
+    symmetric eigensolver as the step, cached on the problem."""
+    c = prob.meta.get("_eigh")
+    if c is None:
+        c = np.linalg.eigh(np.asarray(prob.meta["K"], dtype=np.float64))
+        prob.meta["_eigh"] = c
+    return c
+
+
 def laplacian(prob) -> sp.csr_matrix:
     """L = -Delta_h on the tensor grid, lexicographic order with x fastest (Sec. 5.2); L_a when
-    the problem carries a variable coefficient (prob.meta["faces"], see laplacian_variable).
+    the problem carries a variable coefficient (prob.meta["faces"], see laplacian_variable); the
+    dense symmetric K when it carries one (prob.meta["K"]).
 
     The d-dimensional operator is the Kronecker sum of the 1-D ones; axis 0 (x) is the fastest.
     """
+    if prob.meta.get("K") is not None:
+        return sp.csr_matrix(np.asarray(prob.meta["K"], dtype=np.float64))
     if prob.meta.get("faces") is not None:
         return laplacian_variable(prob)
     ms, hs = _axes(prob)
@@ -91,6 +105,8 @@ def laplacian_eigenvalues(prob) -> np.ndarray:
     Per axis the 1-D eigenvalue of column k is (4/h^2) sin^2(pi (k+1) / (2 (m+1))) (textbook);
     the d-dimensional ones are their sums over the axes.
     """
+    if prob.meta.get("K") is not None:
+        return dense_eigh(prob)[0]
     ms, hs = _axes(prob)
     mu = np.zeros(1)
     for ax in range(prob.d):            # build with x fastest: later axes are slower
@@ -100,12 +116,18 @@ def laplacian_eigenvalues(prob) -> np.ndarray:
     return mu
 
 
-def apply_U(prob, V: np.ndarray) -> np.ndarray:
-    """Apply I_N (x) U to a time-major array V of shape (N, M): the DST-I along every spatial axis.
+def apply_U(prob, V: np.ndarray, transpose: bool = False) -> np.ndarray:
+    """Apply I_N (x) U (or (I_N (x) U)^T) to a time-major array V of shape (N, M): the DST-I along
+    every spatial axis.
 
-    U = S_z (x) S_y (x) S_x (x fastest) is symmetric and orthogonal, so this is also U^T.
-    Used for Steps 1 and 3 of the preconditioner solve (Sec. 5.1).
+    U = S_z (x) S_y (x) S_x (x fastest) is symmetric and orthogonal, so U^T = U there.  With a
+    dense operator K, U holds the eigenvectors of K as columns (dense_eigh) and the two differ.
+    Used for Steps 1 (U^T) and 3 (U) of the preconditioner solve (Sec. 5.1).
     """
+    if prob.meta.get("K") is not None:
+        U = dense_eigh(prob)[1]
+        X = np.asarray(V, dtype=np.float64)
+        return X @ U if transpose else X @ U.T        # rows are time slices
     ms = list(prob.m)
     N = V.shape[0]
     X = V.reshape((N,) + tuple(reversed(ms)))        # (N, [z], [y], x)
@@ -179,7 +201,9 @@ def bltt_matvec_entry(prob, z: np.ndarray, n: int, i: int, flip: bool = False) -
         zk = Z[row - k]
         if prob.a[k] != 0.0:
             acc += prob.a[k] * zk[i]
-        if prob.b[k] != 0.0:
+        if prob.b[k] != 0.0 and prob.meta.get("K") is not None:
+            acc += prob.b[k] * float(np.asarray(prob.meta["K"])[i] @ zk)
+        elif prob.b[k] != 0.0:
             lz = 0.0
             stride = 1
             faces = prob.meta.get("faces")

@@ -68,13 +68,13 @@ def precond_apply(prob, alpha: float, y: np.ndarray, return_imag: bool = False):
     imag = 0.0
 
     # (C_alpha^{-1/2})^* y
-    yt = apply_U(prob, Y).T                        # Steps 1: U^T per slice, then Pi^T -> (M, N)
+    yt = apply_U(prob, Y, transpose=True).T        # Steps 1: U^T per slice, then Pi^T -> (M, N)
     t = _F(np.conj(lam) ** -0.5 * _F_star(yt / d)) * d     # Step 2
     imag = max(imag, float(np.max(np.abs(t.imag))) / max(float(np.max(np.abs(t.real))), 1e-300))
     yhat = apply_U(prob, np.ascontiguousarray(t.real.T))   # Step 3: Pi, then U per slice
 
     # C_alpha^{-1/2} y^
-    st = apply_U(prob, yhat).T
+    st = apply_U(prob, yhat, transpose=True).T
     s = _F(lam ** -0.5 * _F_star(st * d)) / d
     imag = max(imag, float(np.max(np.abs(s.imag))) / max(float(np.max(np.abs(s.real))), 1e-300))
     z = apply_U(prob, np.ascontiguousarray(s.real.T)).reshape(-1)
@@ -86,7 +86,7 @@ def precond_apply_one_pass_alpha1(prob, y: np.ndarray) -> np.ndarray:
     P_1^{-1} y = (I (x) U) Pi blockdiag(F |Lambda_{1,i}|^{-1} F^*) Pi^T (I (x) U)^T y: one pass."""
     N, M = prob.N, prob.M
     lam = alpha_circulant_eigs(prob, 1.0)
-    yt = apply_U(prob, np.asarray(y, dtype=np.float64).reshape(N, M)).T
+    yt = apply_U(prob, np.asarray(y, dtype=np.float64).reshape(N, M), transpose=True).T
     t = _F(_F_star(yt) / np.abs(lam))
     return apply_U(prob, np.ascontiguousarray(t.real.T)).reshape(-1)
 

@@ -391,3 +391,55 @@ def test_paper_iteration_counts_with_paper_data():
         prob, f = _paper_rhs(c)
         r = O.solve(prob, f, alpha=g["alpha"], tol=g["tol"], precond=c["precond"], maxit=2000)
         assert abs(r["iters"] - c["iters"]) <= c["slack"], (c, r["iters"])
+
+
+# ------------------------------------- dense commuting blocks (Sec. 3: A_(k) = a_k I + b_k K)
+
+def _with_K(p, K):
+    from workloads import Problem
+    return Problem(p.N, p.d, p.m, p.h, p.a, p.b, name=p.name + "_K", meta=dict(p.meta, K=K))
+
+
+def test_dense_operator_reproduces_the_dst_path():
+    # K = the finite-difference Laplacian as a dense matrix: its eigenvectors span the DST basis,
+    # so every operator of the method must agree with the DST path
+    p = fractional_problem(2, (7, 5), 16, 0.6)
+    pk = _with_K(p, O.laplacian(p).toarray())
+    z = np.random.default_rng(71).standard_normal(p.n)
+    assert rel(O.bltt_matvec(pk, z, flip=True), O.bltt_matvec(p, z, flip=True)) < 1e-14
+    assert np.allclose(np.sort(O.laplacian_eigenvalues(pk)), np.sort(O.laplacian_eigenvalues(p)),
+                       rtol=1e-12)
+    for alpha in (1.0, 1e-2, 1e-8):
+        # two FP64 evaluations differ by a few eps times kappa(D_alpha) = alpha^{-(N-1)/N}
+        tol = max(1e-12, 100 * 2.0 ** -52 * alpha ** (-(p.N - 1) / p.N))
+        assert rel(O.precond_apply(pk, alpha, z), O.precond_apply(p, alpha, z)) < tol
+    f = rhs_uniform(p.n, 72)
+    r, rk = O.solve(p, f, alpha=1e-8, tol=1e-10), O.solve(pk, f, alpha=1e-8, tol=1e-10)
+    assert r["iters"] == rk["iters"] and rel(rk["x"], r["x"]) < 1e-9
+
+
+def test_dense_operator_precond_matches_dense_definition():
+    # a random SPD K on a tiny problem: the steps of Sec. 5.1 against P_alpha of Def. 3 built
+    # densely from the blocks a_k I + b_k K
+    p = fractional_problem(1, 5, 6, 0.5)
+    G = np.random.default_rng(73).standard_normal((p.M, p.M))
+    pk = _with_K(p, G @ G.T + p.M * np.eye(p.M))
+    v = np.random.default_rng(74).standard_normal(p.n)
+    for alpha in (1.0, 1e-2):
+        P = precond_dense(pk, alpha)
+        assert rel(O.precond_apply(pk, alpha, v), precond_dense_apply(P, v)) < 1e-9
+
+
+def test_dense_operator_exact_preconditioner_for_variable_coefficient():
+    # with K = L_a the preconditioner is P_alpha of the true blocks (no mean-coefficient
+    # approximation): the clustered spectrum of Theorem 1 gives a few iterations instead of 10
+    from workloads import heat_cn_varcoeff_problem
+    p = heat_cn_varcoeff_problem(15, 32)
+    meta = {k: v for k, v in p.meta.items() if k not in ("faces", "abar")}
+    from workloads import Problem
+    pk = Problem(p.N, p.d, p.m, p.h, p.a, p.b, name="cnvar_K", meta=dict(meta, K=O.laplacian(p).toarray()))
+    f = rhs_uniform(p.n, 75)
+    r_mean = O.solve(p, f, alpha=1e-8, tol=1e-6)
+    r_exact = O.solve(pk, f, alpha=1e-8, tol=1e-6)
+    assert r_mean["iters"] == 10 and r_exact["iters"] <= 3
+    assert rel(O.bltt_matvec(pk, r_exact["x"]), f) <= 1e-6
