@@ -117,6 +117,9 @@ def kernel_cost(name, N, m, d):
         return "alu32", 48.0, 4 * df_fft_ops(N) / 2 + 2 * 82.0 / 2 + 3 * 14.0
     if name == "w_update":
         return "hbm", 48.0, 6.0
+    # basis change of the dense-operator form: an M x M by M x N FP64 GEMM (2M flops per unknown)
+    if name == "basis_gemm":
+        return "alu64", 16.0, 2.0 * float(m) ** d
     return "hbm", 0.0, 0.0
 
 
@@ -594,6 +597,65 @@ def run_varcoef(args):
     return 0
 
 
+def run_dense(args):
+    """Commuting dense blocks a_k I + b_k K (Sec. 3): the L1 time-fractional blocks (gamma = 0.5,
+    N = 1024) with a dense non-local diffusion operator K on a 63 x 63 grid (M = 3969, n =
+    4,064,256 unknowns).  The solve runs in K's eigenbasis: one FP64 GEMM in, the iterations with
+    K's eigenvalue table, one FP64 GEMM out.  The eigendecomposition is set-up (untimed).
+    Right-hand side: seeded U[-1, 1]."""
+    import torch
+    from paper_2307_07749_gb300 import build
+    build.build()
+    import paper_2307_07749_gb300 as B
+    from workloads import nonlocal_diffusion_problem, rhs_uniform
+    prob = nonlocal_diffusion_problem(63, 1024, 0.5)
+    stream = torch.cuda.Stream()
+    t0 = time.time()
+    solver = B.Solver(prob, stream=stream)
+    t_setup = time.time() - t0
+    fd = torch.from_numpy(rhs_uniform(prob.n, 13)).to("cuda")
+    torch.cuda.synchronize()
+    pk = peaks()
+    forms = {"f32_precond": dict(alpha=ALPHA_F32, precision=32, basis=B.BASIS_SPECTRAL,
+                                 arith=B.ARITH_F32X2),
+             "plain_f64": dict(alpha=ALPHA_F64, precision=64, basis=B.BASIS_SPECTRAL,
+                               arith=B.ARITH_F64)}
+    out = {"workload": "nonlocal2d_N1024_m63 (L1 gamma 0.5, dense Gaussian-kernel K)",
+           "unknowns": prob.n, "M": prob.M, "tol": TOL, "steps": args.steps,
+           "warmup": max(args.warmup, 1), "eigendecomposition_s": round(t_setup, 3),
+           "l2": "inputs of 32.5 MB per vector, below L2; no flush (supplementary report)"}
+    with torch.cuda.stream(stream):
+        for key, fm in forms.items():
+            r = time_form(B, solver, fd, args.steps, max(args.warmup, 1), fm["alpha"],
+                          fm["precision"], fm["basis"], fm["arith"], 1, stream, profile=True)
+            iters = [i["iters"] for i in r["infos"]]
+            kern = []
+            for name, (all_l, all_ms, launches, tot_ms) in r["profile"].items():
+                bound, bpu, fpu = kernel_cost(name, prob.N, prob.m[0], prob.d)
+                if launches == 0 or bpu == 0:
+                    continue
+                avg = tot_ms / launches
+                e = {"name": name, "launches": launches, "ms_per_launch": round(avg, 4),
+                     "bound": bound}
+                if name == "basis_gemm":
+                    tf = fpu * prob.n / (avg / 1e3) / 1e12
+                    e.update({"TFLOP/s": round(tf, 3), "frac_fp64": round(tf / FP64_PEAK_TFLOPS, 4)})
+                else:
+                    gbs = bpu * prob.n / (avg / 1e3) / 1e9
+                    e.update({"GB/s": round(gbs, 1), "frac_hbm": round(gbs / pk["hbm_gbs"], 4)})
+                kern.append(e)
+            kern.sort(key=lambda k: -k["ms_per_launch"] * k["launches"])
+            out[key] = {"value": prob.n * sum(iters) / (r["ms_total"] / 1e3),
+                        "unit": "unknown-iter/s", "iters": iters[-1],
+                        "ms_per_solve": r["ms_total"] / args.steps,
+                        "relres_true": max(i["relres_true"] for i in r["infos"]),
+                        "status": max(i["status"] for i in r["infos"]), "form": fm,
+                        "kernels": kern}
+    out["fp64_peak_tflops"] = FP64_PEAK_TFLOPS
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -603,7 +665,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="frac2d",
-                    choices=["frac2d", "batched", "alpha", "once", "heat3d", "varcoef"],
+                    choices=["frac2d", "batched", "alpha", "once", "heat3d", "varcoef", "dense"],
                     help="frac2d: the headline line; batched / alpha / heat3d: supplementary "
                          "reports; once: a single solve of the headline workload (for ncu "
                          "captures)")
@@ -625,6 +687,8 @@ def main():
         return run_heat3d(args)
     if args.workload == "varcoef":
         return run_varcoef(args)
+    if args.workload == "dense":
+        return run_dense(args)
     args.warmup = max(args.warmup, 3)
 
     rank, local, ws = dist_init()

@@ -146,6 +146,20 @@ bltt_status bltt_destroy(bltt_handle h);
  * unsupported.  The face arrays are copied to the device; a later call replaces them. */
 bltt_status bltt_set_variable_coefficient(bltt_handle h, const double* const* face, double abar);
 
+/* Dense commuting blocks (Sec. 3: the blocks A_(k) = a_k I + b_k K share the eigenvectors of one
+ * symmetric K, so the preconditioner of Sec. 5.1 applies with K's eigenbasis in place of the
+ * DST-I).  K (host): M x M, row-major (symmetric, so either order), finite, symmetric to 1e-12 of
+ * its largest entry; M <= 8192.  The handle computes K = U diag(mu) U^T once on the device (a
+ * cuSOLVER symmetric eigensolver: set-up, not the hot path) and re-checks Assumption 1 (ii) with
+ * mu (BLTT_ERR_ASSUMPTION if it fails; the handle then keeps its previous operator).  Matvecs,
+ * preconditioner applies and solves then use K: the solve runs in the eigenbasis (AUTO and
+ * SPECTRAL; PHYSICAL gives BLTT_ERR_UNSUPPORTED), entering and leaving it by one FP64 GEMM each
+ * (cuBLAS), with the true residual checked there (U orthogonal: the same norm as in the physical
+ * basis).  bltt_matvec and bltt_precond_apply take and return physical-basis vectors (a GEMM on
+ * each side).  Exclusive with bltt_set_variable_coefficient and the tensor-core matvec
+ * (BLTT_ERR_UNSUPPORTED).  A later call replaces K. */
+bltt_status bltt_set_dense_operator(bltt_handle h, const double* K);
+
 /* Issue all later work of h on `cuda_stream` (a cudaStream_t; NULL = legacy default stream). */
 bltt_status bltt_set_stream(bltt_handle h, void* cuda_stream);
 

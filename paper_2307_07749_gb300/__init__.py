@@ -80,6 +80,7 @@ _SIGS = {
     "bltt_set_matvec_arith": (ctypes.c_int, [_P, ctypes.c_int]),
     "bltt_set_variable_coefficient": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.POINTER(ctypes.c_double)),
                                                       ctypes.c_double]),
+    "bltt_set_dense_operator": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "bltt_precond_apply": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, ctypes.c_int]),
     "bltt_minres_solve_ex": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                             ctypes.POINTER(bltt_solve_opts), _P,
@@ -199,6 +200,13 @@ def bltt_set_variable_coefficient(handle, faces, abar):
         *[a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for a in arrs],
         *[ctypes.POINTER(ctypes.c_double)() for _ in range(3 - len(arrs))])
     _check(lib().bltt_set_variable_coefficient(handle, ptrs, float(abar)), handle)
+
+
+def bltt_set_dense_operator(handle, K):
+    """K: the dense symmetric spatial operator (M x M); the blocks become a_k I + b_k K."""
+    k = np.ascontiguousarray(K, dtype=np.float64)
+    _check(lib().bltt_set_dense_operator(handle, k.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+           handle)
 
 
 def bltt_matvec(handle, x, y, flip=1):
@@ -369,6 +377,9 @@ class Solver:
         if meta.get("faces") is not None:
             # variable coefficient: L_a in the matvec, the mean coefficient in the preconditioner
             bltt_set_variable_coefficient(self.handle, meta["faces"], meta["abar"])
+        if meta.get("K") is not None:
+            # commuting dense blocks a_k I + b_k K: the solve runs in K's eigenbasis
+            bltt_set_dense_operator(self.handle, meta["K"])
         if stream is not None:
             bltt_set_stream(self.handle, stream)
 

@@ -12,6 +12,9 @@
 #include <string>
 #include <vector>
 
+#include <cublas_v2.h>
+#include <cusolverDn.h>
+
 #include "internal.h"
 
 using namespace bltt;
@@ -84,6 +87,9 @@ struct bltt_ctx {
   std::vector<double> a, b;
   double pc_bscale = 1.0;     // the preconditioner's blocks are a_k I + pc_bscale b_k L (abar)
   bool var_coef = false;      // the matvec's L is L_a = -Delta_{a,h} (faces in op.kf)
+  bool dense = false;         // L is a dense symmetric K: eigenbasis U (dU, columns), op.mu_tab
+  double* dU = nullptr;
+  cublasHandle_t blas = nullptr;
   cudaStream_t stream = nullptr;
   std::string err;
   OpTables op{};
@@ -141,6 +147,7 @@ struct bltt_ctx {
     if (stream_sync_ok) cudaStreamSynchronize(stream);
     if (io_stream) { cudaStreamSynchronize(io_stream); cudaStreamDestroy(io_stream); }
     if (io_ev) cudaEventDestroy(io_ev);
+    if (blas) cublasDestroy(blas);
     for (cudaEvent_t e : io_chunk_ev)
       if (e) cudaEventDestroy(e);
     for (void* p : allocs) cudaFree(p);
@@ -233,8 +240,8 @@ cudaError_t upload_twiddles(bltt_ctx* h, int L, const double2** d64, const float
 
 // ensure the tensor-core matvec workspace: digit planes, column exponents, the error flag
 bltt_status ensure_tc(bltt_ctx* h) {
-  if (h->var_coef)
-    return fail(h, BLTT_ERR_UNSUPPORTED, "the tensor-core matvec has no variable coefficient");
+  if (h->var_coef || h->dense)
+    return fail(h, BLTT_ERR_UNSUPPORTED, "the tensor-core matvec has no variable coefficient or dense operator");
   if (!tc_eligible(h->op) || !h->op.tc_hank)
     return fail(h, BLTT_ERR_UNSUPPORTED,
                 "the tensor-core matvec needs b = b0 e_0, more than 4 nonzeros in a and N in "
@@ -249,6 +256,21 @@ bltt_status ensure_tc(bltt_ctx* h) {
   h->op.tc_xd = xd;
   h->op.tc_xe = xe;
   h->op.tc_err = err;
+  return BLTT_OK;
+}
+
+// basis changes of the dense-operator form (FP64 GEMMs): out = (I (x) U^T) in (to the eigenbasis)
+// or out = (I (x) U) in; a time-major vector is a column-major M x N matrix
+bltt_status eigen_transform(bltt_ctx* h, const double* in, double* out, bool to_eigen) {
+  const double one = 1.0, zero = 0.0;
+  const int M = (int)h->M;
+  cudaEvent_t pa = prof_begin(h);
+  if (cublasSetStream(h->blas, h->stream) != CUBLAS_STATUS_SUCCESS ||
+      cublasDgemm(h->blas, to_eigen ? CUBLAS_OP_T : CUBLAS_OP_N, CUBLAS_OP_N, M, h->N, M, &one,
+                  h->dU, M, in, M, &zero, out, M) != CUBLAS_STATUS_SUCCESS)
+    return fail(h, BLTT_ERR_CUDA, "cuBLAS basis change failed");
+  prof_end(h, "basis_gemm", pa);
+  h->launches++;
   return BLTT_OK;
 }
 
@@ -388,6 +410,22 @@ bltt_status precond_chain(bltt_ctx* h, int spectral, int prec, const PrecTables&
     prof_end(h, tp_name, pa);
     h->launches++;
     return BLTT_OK;
+  }
+  if (h->dense) {
+    // Steps 1 and 3 as FP64 GEMMs with the eigenvectors (a plain input vector: bltt_precond_apply)
+    if (in.in1 || in.in2 || in.vout || dot_with || partials)
+      return fail(h, BLTT_ERR_UNSUPPORTED, "a dense operator solves in its eigenbasis");
+    double* t1 = vec(h, 8);
+    double* t2 = vec(h, 9);
+    bltt_status s = eigen_transform(h, in.in0, t1, true);
+    if (s != BLTT_OK) return s;
+    Combine c{};
+    c.in0 = t1;
+    cudaEvent_t pa = prof_begin(h);
+    CK(h, launch_timepass(op, pt, prec, c, t2, nullptr, nullptr, nullptr, phase, h->stream), "time pass");
+    prof_end(h, tp_name, pa);
+    h->launches++;
+    return eigen_transform(h, t2, out, false);
   }
   for (int ax = 0; ax < op.d; ++ax) {
     Combine c{};
@@ -681,8 +719,91 @@ bltt_status bltt_destroy(bltt_handle h) {
   return BLTT_OK;
 }
 
+bltt_status bltt_set_dense_operator(bltt_handle h, const double* K) {
+  if (!h) return BLTT_ERR_INVALID_ARG;
+  if (!K) return fail(h, BLTT_ERR_INVALID_ARG, "null operator");
+  if (h->var_coef) return fail(h, BLTT_ERR_UNSUPPORTED, "a variable coefficient is set on this handle");
+  if (h->op.mv_arith == 2) return fail(h, BLTT_ERR_UNSUPPORTED, "the tensor-core matvec has no dense operator");
+  const long long M = h->M;
+  if (M > 8192) return fail(h, BLTT_ERR_UNSUPPORTED, "a dense operator needs M <= 8192");
+  double kmax = 0.0;
+  for (long long e = 0; e < M * M; ++e) {
+    if (!std::isfinite(K[e])) return fail(h, BLTT_ERR_INVALID_ARG, "the operator must be finite");
+    kmax = std::max(kmax, std::fabs(K[e]));
+  }
+  for (long long i = 0; i < M; ++i)
+    for (long long j = 0; j < i; ++j)
+      if (std::fabs(K[i * M + j] - K[j * M + i]) > 1e-12 * kmax)
+        return fail(h, BLTT_ERR_INVALID_ARG, "the operator must be symmetric");
+  // eigendecomposition on the device: K = U diag(mu) U^T (cuSOLVER, set-up only)
+  double* dU = nullptr;
+  double* dmu = nullptr;
+  CK(h, h->alloc(&dU, (size_t)(M * M)), "eigenvectors");
+  CK(h, h->alloc(&dmu, (size_t)M), "eigenvalues");
+  CK(h, cudaMemcpy(dU, K, sizeof(double) * M * M, cudaMemcpyHostToDevice), "copy operator");
+  cusolverDnHandle_t sol = nullptr;
+  if (cusolverDnCreate(&sol) != CUSOLVER_STATUS_SUCCESS)
+    return fail(h, BLTT_ERR_CUDA, "cuSOLVER handle");
+  int lwork = 0;
+  cusolverStatus_t cs = cusolverDnDsyevd_bufferSize(sol, CUSOLVER_EIG_MODE_VECTOR,
+                                                    CUBLAS_FILL_MODE_LOWER, (int)M, dU, (int)M,
+                                                    dmu, &lwork);
+  double* work = nullptr;
+  int* dinfo = nullptr;
+  cudaError_t ce = cudaSuccess;
+  if (cs == CUSOLVER_STATUS_SUCCESS) ce = cudaMalloc(&work, sizeof(double) * (size_t)std::max(lwork, 1));
+  if (cs == CUSOLVER_STATUS_SUCCESS && ce == cudaSuccess) ce = cudaMalloc(&dinfo, sizeof(int));
+  if (cs == CUSOLVER_STATUS_SUCCESS && ce == cudaSuccess)
+    cs = cusolverDnDsyevd(sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, (int)M, dU,
+                          (int)M, dmu, work, lwork, dinfo);
+  int info = -1;
+  if (cs == CUSOLVER_STATUS_SUCCESS && ce == cudaSuccess)
+    ce = cudaMemcpy(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(work);
+  cudaFree(dinfo);
+  cusolverDnDestroy(sol);
+  // on any failure below the handle keeps its previous operator
+  struct Drop {
+    bltt_ctx* hh; void* p[3]; bool keep = false;
+    ~Drop() { if (!keep) for (void* q : p) hh->release(q); }
+  } drop{h, {dU, dmu, nullptr}};
+  if (cs != CUSOLVER_STATUS_SUCCESS || ce != cudaSuccess || info != 0)
+    return fail(h, BLTT_ERR_CUDA, "cuSOLVER eigendecomposition failed");
+  std::vector<double> mu(M);
+  CK(h, cudaMemcpy(mu.data(), dmu, sizeof(double) * M, cudaMemcpyDeviceToHost), "eigenvalues");
+  // Assumption 1 (ii) on the new eigenvalues
+  double c0 = 1e300;
+  for (long long i = 0; i < M; ++i) {
+    double v = h->a[0] + h->b[0] * mu[i];
+    for (int k = 1; k < h->N; ++k) v -= std::fabs(h->a[k] + h->b[k] * mu[i]);
+    c0 = std::min(c0, v);
+  }
+  if (!(c0 > 0.0)) return fail(h, BLTT_ERR_ASSUMPTION, "Assumption 1 (ii) fails for the operator's eigenvalues");
+  std::vector<float> mu32(mu.begin(), mu.end());
+  float* dmu32 = nullptr;
+  CK(h, upload(h, &dmu32, mu32.data(), (size_t)M), "eigenvalues");
+  drop.p[2] = dmu32;
+  if (!h->blas && cublasCreate(&h->blas) != CUBLAS_STATUS_SUCCESS)
+    return fail(h, BLTT_ERR_CUDA, "cuBLAS handle");
+  drop.keep = true;
+  if (h->dense) {
+    // a replaced operator: its eigenvectors and tables go
+    h->release(h->dU);
+    h->release(const_cast<double*>(h->op.mu_tab));
+    h->release(const_cast<float*>(h->op.mu_tab32));
+  }
+  h->dU = dU;
+  h->op.mu_tab = dmu;
+  h->op.mu_tab32 = dmu32;
+  h->dense = true;
+  h->pc_alpha = -1.0;
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  return BLTT_OK;
+}
+
 bltt_status bltt_set_variable_coefficient(bltt_handle h, const double* const* face, double abar) {
   if (!h) return BLTT_ERR_INVALID_ARG;
+  if (h->dense) return fail(h, BLTT_ERR_UNSUPPORTED, "a dense operator is set on this handle");
   if (!face) return fail(h, BLTT_ERR_INVALID_ARG, "null face array");
   if (!(abar > 0.0) || !std::isfinite(abar)) return fail(h, BLTT_ERR_INVALID_ARG, "abar must be positive");
   if (h->op.mv_arith == 2) return fail(h, BLTT_ERR_UNSUPPORTED, "the tensor-core matvec has no variable coefficient");
@@ -731,6 +852,17 @@ bltt_status bltt_matvec(bltt_handle h, const double* x, double* y, int flip) {
     if (s != BLTT_OK) return s;
     tmp = vec(h, 9);
   }
+  if (h->dense) {
+    // y = (I (x) U) [Y] A_hat (I (x) U^T) x: the eigenbasis product between two GEMMs
+    bltt_status s = ensure_workspace(h);
+    if (s != BLTT_OK) return s;
+    s = eigen_transform(h, x, vec(h, 8), true);
+    if (s != BLTT_OK) return s;
+    PCK(h, mv_name(h->op), launch_matvec(h->op, 1, vec(h, 8), nullptr, vec(h, 9), flip ? 1 : 0,
+                                         MV_STORE, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                         h->stream), "matvec");
+    return eigen_transform(h, vec(h, 9), y, false);
+  }
   PCK(h, mv_name(h->op), launch_matvec(h->op, 0, x, nullptr, y, flip ? 1 : 0, MV_STORE, nullptr, nullptr, nullptr,
                       nullptr, tmp, h->stream), "matvec");
   return BLTT_OK;
@@ -744,6 +876,10 @@ bltt_status bltt_precond_apply(bltt_handle h, double alpha, const double* v, dou
   if (precision != 64 && precision != 32 && precision != 96) return fail(h, BLTT_ERR_INVALID_ARG, "precision must be 64, 32 or 96");
   bltt_status s = prepare_precond(h, alpha, precision);
   if (s != BLTT_OK) return s;
+  if (h->dense) {
+    s = ensure_workspace(h);
+    if (s != BLTT_OK) return s;
+  }
   PrecTables pt = prec_tables(h, 0);
   Combine c{};
   c.in0 = v;
@@ -841,6 +977,9 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
   // a variable coefficient leaves L undiagonalised by the DST: only the physical basis applies
   if (h->var_coef && basis == BLTT_BASIS_SPECTRAL)
     return fail(h, BLTT_ERR_UNSUPPORTED, "a variable coefficient needs the physical basis");
+  // a dense operator: the solve runs in its eigenbasis (the physical basis would need K per slice)
+  if (h->dense && basis == BLTT_BASIS_PHYSICAL)
+    return fail(h, BLTT_ERR_UNSUPPORTED, "a dense operator solves in its eigenbasis");
   if (basis == BLTT_BASIS_AUTO) basis = h->var_coef ? BLTT_BASIS_PHYSICAL : BLTT_BASIS_SPECTRAL;
   if (basis != BLTT_BASIS_SPECTRAL && basis != BLTT_BASIS_PHYSICAL) return fail(h, BLTT_ERR_INVALID_ARG, "bad basis");
   const int spectral = (basis == BLTT_BASIS_SPECTRAL) ? 1 : 0;
@@ -889,7 +1028,16 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
 
   // b = Y f (spectral: Y (I (x) U) f) with ||b||^2
   int nb = 0, nzv = 0, np = 0;
-  if (spectral && hin) {
+  if (spectral && h->dense) {
+    // b = Y (I (x) U^T) f: one FP64 GEMM into the scratch vector, then the flip with ||b||^2
+    if (hin)
+      CK(h, cudaMemcpyAsync(const_cast<double*>(f), hin->f_host, (size_t)h->n * sizeof(double),
+                            cudaMemcpyHostToDevice, st), "copy f to the device");
+    s = eigen_transform(h, f, tmp, true);
+    if (s != BLTT_OK) return s;
+    PCK(h, "flip", launch_flip_copy(tmp, bvec, h->N, h->M, h->partials[1], &nb, st), "flip");
+    h->launches++;
+  } else if (spectral && hin) {
     s = dst_entry_chunked(h, op, hin->f_host, const_cast<double*>(f), bvec, h->partials[1], &nb);
     if (s != BLTT_OK) return s;
   } else if (spectral) {
@@ -923,7 +1071,7 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
   // DST basis: the true residual is checked by the host in the physical basis once the estimate
   // has met the stopping rule (the iterations halt in PH_VERIFY and resume if the check fails),
   // so the iterations carry no residual product of their own
-  const bool defer = (spectral != 0);
+  const bool defer = (spectral != 0) && !h->dense;
   const long long per_iter = 5 + ((op.b_kind == 1 && op.ntaps == 0 && !spectral) ? 4 : 2) +
                              (spectral || none ? 0 : 2 * op.d) + (tc ? 1 : 0) - (defer ? 1 : 0);
   auto issue_iteration = [&](int c0) -> bltt_status {
@@ -1044,6 +1192,15 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
     }
     relres_phys = sh->relres_true;
     if (!spectral) {
+      s = copy_out();
+      if (s != BLTT_OK) return s;
+      break;
+    }
+    if (h->dense) {
+      // u = (I (x) U) x_hat by one FP64 GEMM; the true residual was checked in the eigenbasis
+      // (U orthogonal: the same norm) by the iterations
+      s = eigen_transform(h, x, u, false);
+      if (s != BLTT_OK) return s;
       s = copy_out();
       if (s != BLTT_OK) return s;
       break;

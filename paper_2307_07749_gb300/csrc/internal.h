@@ -56,6 +56,10 @@ struct OpTables {
   const float4* tw_2N_df;
   const float4* tw_dst_df[3];
   const float4* tw_N_df;
+  // dense operator K (commuting blocks a_k I + b_k K): its eigenvalues per mode, in the order of
+  // the eigenvector columns (null: the Laplacian's, from the per-axis tables)
+  const double* mu_tab;
+  const float* mu_tab32;
   // variable coefficient (null: L = -Delta_h): a at the cell faces along each axis, arrays of the
   // grid's shape with that axis one longer (x fastest); L becomes L_a = -Delta_{a,h}
   const double* kf[3];

@@ -938,13 +938,18 @@ __global__ void k_setup_gdf(OpTables op, const float2* ahat32, const float2* bha
     const float2 a = ahat32[k], b = bhat32[k];
     const float2 g0 = inv_sqrt_principal<float>(fmaf(b.x, mu, a.x), fmaf(b.y, mu, a.y));
     const float4 A4 = ahatdf[k], B4 = bhatdf[k];
-    // mu_i as double-float: sum of the per-axis FP64 eigenvalues
-    long long r = i / op.m[0];
-    dfl m_ = df_from(op.mu_axis[0][i - r * op.m[0]]);
-    if (op.d > 1) {
-      long long r2 = r / op.m[1];
-      m_ = df_add(m_, df_from(op.mu_axis[1][r - r2 * op.m[1]]));
-      if (op.d > 2) m_ = df_add(m_, df_from(op.mu_axis[2][r2]));
+    // mu_i as double-float: sum of the per-axis FP64 eigenvalues (or the dense operator's)
+    dfl m_;
+    if (op.mu_tab) {
+      m_ = df_from(op.mu_tab[i]);
+    } else {
+      long long r = i / op.m[0];
+      m_ = df_from(op.mu_axis[0][i - r * op.m[0]]);
+      if (op.d > 1) {
+        long long r2 = r / op.m[1];
+        m_ = df_add(m_, df_from(op.mu_axis[1][r - r2 * op.m[1]]));
+        if (op.d > 2) m_ = df_add(m_, df_from(op.mu_axis[2][r2]));
+      }
     }
     const float4 lam = ArithDF::pack(df_add(dfl{A4.x, A4.y}, df_mul(m_, dfl{B4.x, B4.y})),
                                      df_add(dfl{A4.z, A4.w}, df_mul(m_, dfl{B4.z, B4.w})));

@@ -12,8 +12,10 @@ __device__ __forceinline__ bool skip_phase(const int* phase, int want) {
   return phase != nullptr && *phase != want;
 }
 
-// eigenvalue of L for spatial mode i (x fastest): sum over axes of the 1-D eigenvalues
+// eigenvalue of L for spatial mode i (x fastest): sum over axes of the 1-D eigenvalues, or the
+// dense operator's eigenvalue from its table
 __device__ __forceinline__ double mode_mu(const OpTables& op, long long i) {
+  if (op.mu_tab) return op.mu_tab[i];
   long long r = i / op.m[0];
   double mu = op.mu_axis[0][i - r * op.m[0]];
   if (op.d > 1) {
@@ -24,6 +26,7 @@ __device__ __forceinline__ double mode_mu(const OpTables& op, long long i) {
   return mu;
 }
 __device__ __forceinline__ float mode_mu32(const OpTables& op, long long i) {
+  if (op.mu_tab32) return op.mu_tab32[i];
   long long r = i / op.m[0];
   float mu = op.mu_axis32[0][i - r * op.m[0]];
   if (op.d > 1) {

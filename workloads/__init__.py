@@ -21,7 +21,7 @@ import numpy as np
 
 __all__ = [
     "Problem", "l1_weights", "fractional_problem", "heat_bdf_problem", "heat_cn_problem",
-    "heat_cn_varcoeff_problem", "paper_data_fractional", "paper_data_heat_var",
+    "heat_cn_varcoeff_problem", "nonlocal_diffusion_problem", "paper_data_fractional", "paper_data_heat_var",
     "rhs_uniform", "rhs_smoothed_field", "WORKLOADS", "workload", "batched_systems",
     "alpha_training_problems",
 ]
@@ -137,6 +137,28 @@ def heat_cn_varcoeff_problem(m, N, T=1.0, name=None) -> Problem:
     return Problem(p.N, p.d, p.m, p.h, p.a, p.b, name or f"heat2d_cnvar_N{N}_m{mm}",
                    dict(kind="heat_cn_var", gamma=1.0, tau=p.meta["tau"], faces=(fx, fy),
                         abar=abar))
+
+
+def nonlocal_diffusion_problem(m, N, gamma, delta_cells=3.0, name=None) -> Problem:
+    """The L1 time-fractional blocks of fractional_problem (d = 2, Omega = (0,1)^2) with a dense
+    non-local spatial operator K in place of -Delta_h: the blocks become a_k I + b_k K, which
+    commute (Sec. 3).  K is the volume-constrained non-local diffusion operator with the Gaussian
+    kernel J(r) = C exp(-r^2/delta^2), u = 0 outside the domain:
+      (K u)_i = C pi delta^2 u_i - h^2 sum_j J(|x_i - x_j|) u_j,
+    C = 4/(pi delta^4) so that K u -> -Delta u for smooth u as delta -> 0, delta = delta_cells h.
+    K is dense (every pair of grid points interacts) and SPD.  meta["K"]: the M x M matrix."""
+    p = fractional_problem(2, m, N, gamma)
+    mm, h = p.m[0], p.h[0]
+    delta = delta_cells * h
+    C = 4.0 / (math.pi * delta ** 4)
+    pts = (np.arange(mm) + 1.0) * h
+    # the Gaussian separates over the axes: J(|x_i - x_j|) = C E[iy, jy] E[ix, jx] (x fastest)
+    E = np.exp(-((pts[:, None] - pts[None, :]) / delta) ** 2)
+    K = np.kron(E, E)
+    K *= -(h * h * C)
+    K[np.diag_indices_from(K)] += C * math.pi * delta * delta
+    return Problem(p.N, p.d, p.m, p.h, p.a, p.b, name or f"nonlocal2d_N{N}_m{mm}_g{gamma}",
+                   dict(p.meta, kind="nonlocal", K=K, delta=delta))
 
 
 def paper_data_fractional(prob, gamma: float) -> np.ndarray:
