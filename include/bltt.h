@@ -153,9 +153,11 @@ bltt_status bltt_set_variable_coefficient(bltt_handle h, const double* const* fa
  * cuSOLVER symmetric eigensolver: set-up, not the hot path) and re-checks Assumption 1 (ii) with
  * mu (BLTT_ERR_ASSUMPTION if it fails; the handle then keeps its previous operator).  Matvecs,
  * preconditioner applies and solves then use K: the solve runs in the eigenbasis (AUTO and
- * SPECTRAL; PHYSICAL gives BLTT_ERR_UNSUPPORTED), entering and leaving it by one FP64 GEMM each
- * (cuBLAS), with the true residual checked there (U orthogonal: the same norm as in the physical
- * basis).  bltt_matvec and bltt_precond_apply take and return physical-basis vectors (a GEMM on
+ * SPECTRAL; PHYSICAL gives BLTT_ERR_UNSUPPORTED), entering and leaving it by one GEMM each, with
+ * the true residual checked there (U orthogonal: the same norm as in the physical basis).  The
+ * GEMMs follow the matvec arithmetic: FP64 (cuBLAS) with BLTT_ARITH_F64, double-float on the
+ * FP32 pipes (about 2^-47 relative per multiply-add) with BLTT_ARITH_F32X2.  The handle keeps U
+ * in FP64 and as double-float planes of U and U^T (5 M^2 floats' worth of device memory).  bltt_matvec and bltt_precond_apply take and return physical-basis vectors (a GEMM on
  * each side).  Exclusive with bltt_set_variable_coefficient and the tensor-core matvec
  * (BLTT_ERR_UNSUPPORTED).  A later call replaces K. */
 bltt_status bltt_set_dense_operator(bltt_handle h, const double* K);

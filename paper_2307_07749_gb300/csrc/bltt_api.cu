@@ -89,6 +89,7 @@ struct bltt_ctx {
   bool var_coef = false;      // the matvec's L is L_a = -Delta_{a,h} (faces in op.kf)
   bool dense = false;         // L is a dense symmetric K: eigenbasis U (dU, columns), op.mu_tab
   double* dU = nullptr;
+  float* dUp[4] = {nullptr, nullptr, nullptr, nullptr};   // double-float planes: U hi, lo; U^T hi, lo
   cublasHandle_t blas = nullptr;
   cudaStream_t stream = nullptr;
   std::string err;
@@ -259,11 +260,21 @@ bltt_status ensure_tc(bltt_ctx* h) {
   return BLTT_OK;
 }
 
-// basis changes of the dense-operator form (FP64 GEMMs): out = (I (x) U^T) in (to the eigenbasis)
-// or out = (I (x) U) in; a time-major vector is a column-major M x N matrix
-bltt_status eigen_transform(bltt_ctx* h, const double* in, double* out, bool to_eigen) {
+// basis changes of the dense-operator form: out = (I (x) U^T) in (to the eigenbasis) or
+// out = (I (x) U) in; a time-major vector is a column-major M x N matrix.  FP64 GEMM (cuBLAS), or
+// with df the double-float GEMM on the FP32 pipes (the precision of the double-float matvec)
+bltt_status eigen_transform(bltt_ctx* h, const double* in, double* out, bool to_eigen, bool df) {
   const double one = 1.0, zero = 0.0;
   const int M = (int)h->M;
+  if (df) {
+    cudaEvent_t pa = prof_begin(h);
+    const float* Ah = to_eigen ? h->dUp[2] : h->dUp[0];
+    const float* Al = to_eigen ? h->dUp[3] : h->dUp[1];
+    CK(h, launch_df_gemm(Ah, Al, in, out, M, h->N, h->stream), "double-float basis change");
+    prof_end(h, "basis_gemm_df", pa);
+    h->launches++;
+    return BLTT_OK;
+  }
   cudaEvent_t pa = prof_begin(h);
   if (cublasSetStream(h->blas, h->stream) != CUBLAS_STATUS_SUCCESS ||
       cublasDgemm(h->blas, to_eigen ? CUBLAS_OP_T : CUBLAS_OP_N, CUBLAS_OP_N, M, h->N, M, &one,
@@ -417,7 +428,8 @@ bltt_status precond_chain(bltt_ctx* h, int spectral, int prec, const PrecTables&
       return fail(h, BLTT_ERR_UNSUPPORTED, "a dense operator solves in its eigenbasis");
     double* t1 = vec(h, 8);
     double* t2 = vec(h, 9);
-    bltt_status s = eigen_transform(h, in.in0, t1, true);
+    const bool df = (h->op.mv_arith == 1);
+    bltt_status s = eigen_transform(h, in.in0, t1, true, df);
     if (s != BLTT_OK) return s;
     Combine c{};
     c.in0 = t1;
@@ -425,7 +437,7 @@ bltt_status precond_chain(bltt_ctx* h, int spectral, int prec, const PrecTables&
     CK(h, launch_timepass(op, pt, prec, c, t2, nullptr, nullptr, nullptr, phase, h->stream), "time pass");
     prof_end(h, tp_name, pa);
     h->launches++;
-    return eigen_transform(h, t2, out, false);
+    return eigen_transform(h, t2, out, false, df);
   }
   for (int ax = 0; ax < op.d; ++ax) {
     Combine c{};
@@ -764,9 +776,9 @@ bltt_status bltt_set_dense_operator(bltt_handle h, const double* K) {
   cusolverDnDestroy(sol);
   // on any failure below the handle keeps its previous operator
   struct Drop {
-    bltt_ctx* hh; void* p[3]; bool keep = false;
+    bltt_ctx* hh; void* p[7]; bool keep = false;
     ~Drop() { if (!keep) for (void* q : p) hh->release(q); }
-  } drop{h, {dU, dmu, nullptr}};
+  } drop{h, {dU, dmu, nullptr, nullptr, nullptr, nullptr, nullptr}};
   if (cs != CUSOLVER_STATUS_SUCCESS || ce != cudaSuccess || info != 0)
     return fail(h, BLTT_ERR_CUDA, "cuSOLVER eigendecomposition failed");
   std::vector<double> mu(M);
@@ -783,6 +795,14 @@ bltt_status bltt_set_dense_operator(bltt_handle h, const double* K) {
   float* dmu32 = nullptr;
   CK(h, upload(h, &dmu32, mu32.data(), (size_t)M), "eigenvalues");
   drop.p[2] = dmu32;
+  // double-float planes of U and U^T for the FP32-pipe basis changes
+  float* planes[4] = {nullptr, nullptr, nullptr, nullptr};
+  for (int k = 0; k < 4; ++k) {
+    CK(h, h->alloc(&planes[k], (size_t)(M * M)), "eigenvector planes");
+    drop.p[3 + k] = planes[k];
+  }
+  CK(h, launch_df_planes(dU, M, planes[0], planes[1], planes[2], planes[3], nullptr), "planes");
+  CK(h, cudaDeviceSynchronize(), "planes");
   if (!h->blas && cublasCreate(&h->blas) != CUBLAS_STATUS_SUCCESS)
     return fail(h, BLTT_ERR_CUDA, "cuBLAS handle");
   drop.keep = true;
@@ -791,7 +811,9 @@ bltt_status bltt_set_dense_operator(bltt_handle h, const double* K) {
     h->release(h->dU);
     h->release(const_cast<double*>(h->op.mu_tab));
     h->release(const_cast<float*>(h->op.mu_tab32));
+    for (float* q : h->dUp) h->release(q);
   }
+  for (int k = 0; k < 4; ++k) h->dUp[k] = planes[k];
   h->dU = dU;
   h->op.mu_tab = dmu;
   h->op.mu_tab32 = dmu32;
@@ -856,12 +878,13 @@ bltt_status bltt_matvec(bltt_handle h, const double* x, double* y, int flip) {
     // y = (I (x) U) [Y] A_hat (I (x) U^T) x: the eigenbasis product between two GEMMs
     bltt_status s = ensure_workspace(h);
     if (s != BLTT_OK) return s;
-    s = eigen_transform(h, x, vec(h, 8), true);
+    const bool df = (h->op.mv_arith == 1);
+    s = eigen_transform(h, x, vec(h, 8), true, df);
     if (s != BLTT_OK) return s;
     PCK(h, mv_name(h->op), launch_matvec(h->op, 1, vec(h, 8), nullptr, vec(h, 9), flip ? 1 : 0,
                                          MV_STORE, nullptr, nullptr, nullptr, nullptr, nullptr,
                                          h->stream), "matvec");
-    return eigen_transform(h, vec(h, 9), y, false);
+    return eigen_transform(h, vec(h, 9), y, false, df);
   }
   PCK(h, mv_name(h->op), launch_matvec(h->op, 0, x, nullptr, y, flip ? 1 : 0, MV_STORE, nullptr, nullptr, nullptr,
                       nullptr, tmp, h->stream), "matvec");
@@ -1033,7 +1056,7 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
     if (hin)
       CK(h, cudaMemcpyAsync(const_cast<double*>(f), hin->f_host, (size_t)h->n * sizeof(double),
                             cudaMemcpyHostToDevice, st), "copy f to the device");
-    s = eigen_transform(h, f, tmp, true);
+    s = eigen_transform(h, f, tmp, true, op.mv_arith == 1);
     if (s != BLTT_OK) return s;
     PCK(h, "flip", launch_flip_copy(tmp, bvec, h->N, h->M, h->partials[1], &nb, st), "flip");
     h->launches++;
@@ -1199,7 +1222,7 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
     if (h->dense) {
       // u = (I (x) U) x_hat by one FP64 GEMM; the true residual was checked in the eigenbasis
       // (U orthogonal: the same norm) by the iterations
-      s = eigen_transform(h, x, u, false);
+      s = eigen_transform(h, x, u, false, op.mv_arith == 1);
       if (s != BLTT_OK) return s;
       s = copy_out();
       if (s != BLTT_OK) return s;

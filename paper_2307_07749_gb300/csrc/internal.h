@@ -141,6 +141,12 @@ cudaError_t launch_setup_g64(const OpTables& op, const double2* ahat, const doub
 cudaError_t launch_setup_gdf(const OpTables& op, const float2* ahat32, const float2* bhat32,
                              const float4* ahatdf, const float4* bhatdf, float4* gdf,
                              cudaStream_t st);
+// dense-operator basis changes in double-float (dfgemm.cu): hi/lo planes of U and U^T
+// (column-major), and C = A X for A given by its planes (M x M) and X, C time-major (M x N)
+cudaError_t launch_df_planes(const double* U, long long M, float* Uh, float* Ul, float* Th,
+                             float* Tl, cudaStream_t st);
+cudaError_t launch_df_gemm(const float* Ah, const float* Al, const double* X, double* C, int M,
+                           int N, cudaStream_t st);
 cudaError_t launch_flip_copy(const double* f, double* b, int N, long long M, double* partials,
                              int* nparts, cudaStream_t st);
 cudaError_t launch_scalar_init(MinresDev* s, const double* partials_zv, int nzv,

@@ -56,15 +56,20 @@ def test_dense_matvec_parity(B, prob, flip, arith):
     s.set_matvec_arith(arith)
     z = np.random.default_rng(83).standard_normal(prob.n)
     y = to_host(s.matvec(to_dev(z), flip=bool(flip)))
-    # two FP64 GEMMs (cuBLAS) move x into K's eigenbasis and back: a few eps sqrt(M) of rounding
+    # two GEMMs move x into K's eigenbasis and back: FP64 (cuBLAS) with the FP64 matvec, double-float
+    # with the double-float one; a few eps sqrt(M) of rounding, or about 2^-47 per multiply-add
     assert rel(y, O.bltt_matvec(prob, z, flip=bool(flip))) <= 1e-11
 
 
 @pytest.mark.parametrize("prob", DPS, ids=DIDS)
 @pytest.mark.parametrize("alpha", [1.0, 1e-3, 1e-8])
 @pytest.mark.parametrize("precision", [64, 96, 32], ids=["f64", "df", "f32"])
-def test_dense_precond_parity(B, prob, alpha, precision):
+@pytest.mark.parametrize("arith", [1, 2], ids=["gemm64", "gemmdf"])
+def test_dense_precond_parity(B, prob, alpha, precision, arith):
+    # the basis changes follow the handle's matvec arithmetic: FP64 GEMMs, or double-float GEMMs
+    # on the FP32 pipes (about 2^-47 per multiply-add, within the 1e-11 floor)
     s = B.Solver(prob)
+    s.set_matvec_arith(arith)
     v = np.random.default_rng(84).standard_normal(prob.n)
     z = to_host(s.precond_apply(alpha, to_dev(v), precision=precision))
     tol = max(precond_tol(prob.N, alpha, precision), 1e-11)
@@ -73,8 +78,9 @@ def test_dense_precond_parity(B, prob, alpha, precision):
 
 @pytest.mark.parametrize("prob", DPS, ids=DIDS)
 @pytest.mark.parametrize("form", [dict(precision=64, alpha=1e-8), dict(precision=64, alpha=1.0),
-                                  dict(precision=32, alpha=1e-3), dict(precision=96, alpha=1e-8)],
-                         ids=["f64", "f64_P1", "f32", "df"])
+                                  dict(precision=32, alpha=1e-3), dict(precision=96, alpha=1e-8),
+                                  dict(precision=32, alpha=1e-3, matvec_arith=2)],
+                         ids=["f64", "f64_P1", "f32", "df", "chosen"])
 def test_dense_solve(B, prob, form):
     f = rhs_uniform(prob.n, 85)
     # alpha = 1 (P_1): 8 to 34 iterations on these problems; alpha = 1e-8: 2
