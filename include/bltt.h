@@ -157,7 +157,7 @@ bltt_status bltt_set_variable_coefficient(bltt_handle h, const double* const* fa
  * the true residual checked there (U orthogonal: the same norm as in the physical basis).  The
  * GEMMs follow the matvec arithmetic: FP64 (cuBLAS) with BLTT_ARITH_F64, double-float on the
  * FP32 pipes (about 2^-47 relative per multiply-add) with BLTT_ARITH_F32X2.  The handle keeps U
- * in FP64 and as double-float planes of U and U^T (5 M^2 floats' worth of device memory).  bltt_matvec and bltt_precond_apply take and return physical-basis vectors (a GEMM on
+ * in FP64 (M^2 doubles) and as double-float planes of U and U^T (4 M^2 floats).  bltt_matvec and bltt_precond_apply take and return physical-basis vectors (a GEMM on
  * each side).  Exclusive with bltt_set_variable_coefficient and the tensor-core matvec
  * (BLTT_ERR_UNSUPPORTED).  A later call replaces K. */
 bltt_status bltt_set_dense_operator(bltt_handle h, const double* K);
