@@ -540,62 +540,82 @@ def run_heat3d(args):
 
 
 def run_varcoef(args):
-    """Variable-coefficient heat equation (Example heateqvarcoeff, CN) at Table 3's largest size:
-    N = 256, m + 1 = 256 (16,646,400 unknowns), tolerance 1e-6 as in the table, physical basis
-    (the DST does not diagonalise L_a), the preconditioner of the mean-coefficient blocks.
-    Right-hand side: seeded U[-1, 1]."""
+    """Variable-coefficient blocks at the largest size of the paper's tables, physical basis (the
+    DST does not diagonalise L_a), the preconditioner of the mean-coefficient blocks, tolerance
+    1e-6 as in the tables:
+      * Example heateqvarcoeff (CN heat, Table 3): N = 256, m + 1 = 256 (16,646,400 unknowns),
+        right-hand side seeded U[-1, 1];
+      * Example 4 (L1 fractional, gamma = 0.6, a = 35 + x^3.5 + y^3.5, Table 8): the same size, on
+        the example's own right-hand side."""
     import torch
     from paper_2307_07749_gb300 import build
     build.build()
     import paper_2307_07749_gb300 as B
-    from workloads import heat_cn_varcoeff_problem, rhs_uniform
-    prob = heat_cn_varcoeff_problem(255, 256)
-    stream = torch.cuda.Stream()
-    solver = B.Solver(prob, stream=stream)
-    fd = torch.from_numpy(rhs_uniform(prob.n, 12)).to("cuda")
-    torch.cuda.synchronize()
+    from workloads import (fractional_varcoeff_problem, heat_cn_varcoeff_problem,
+                           paper_data_frac_var, rhs_uniform)
     pk = peaks()
+    # the FP32-preconditioner form with the double-float matvec, as the headline's chosen form
+    # (the CN blocks' direct product is FP64 whatever the setting)
     forms = {"plain_f64": dict(alpha=ALPHA_F64, precision=64, arith=B.ARITH_F64),
-             "f32_precond": dict(alpha=ALPHA_F32, precision=32, arith=B.ARITH_F64)}
+             "f32_precond": dict(alpha=ALPHA_F32, precision=32, arith=B.ARITH_F32X2)}
+
+    def measure(prob, f_np):
+        stream = torch.cuda.Stream()
+        solver = B.Solver(prob, stream=stream)
+        fd = torch.from_numpy(f_np).to("cuda")
+        torch.cuda.synchronize()
+        res = {}
+        with torch.cuda.stream(stream):
+            for key, fm in forms.items():
+                for _ in range(max(args.warmup, 1)):
+                    solver.solve(fd, alpha=fm["alpha"], tol=1e-6, maxit=200,
+                                 precision=fm["precision"], basis=B.BASIS_PHYSICAL, rebuild=True,
+                                 matvec_arith=fm["arith"])
+                torch.cuda.synchronize()
+                solver.profile(True)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                infos = []
+                e0.record(stream)
+                for _ in range(args.steps):
+                    _, info = solver.solve(fd, alpha=fm["alpha"], tol=1e-6, maxit=200,
+                                           precision=fm["precision"], basis=B.BASIS_PHYSICAL,
+                                           rebuild=True, matvec_arith=fm["arith"])
+                    infos.append(info)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                prof = solver.profile_read()
+                solver.profile(False)
+                iters = [i["iters"] for i in infos]
+                kern = []
+                for name, (_, _, launches, tot_ms) in prof.items():
+                    bound, bpu, fpu = kernel_cost(name, prob.N, prob.m[0], prob.d)
+                    if launches == 0 or bpu == 0:
+                        continue
+                    avg = tot_ms / launches
+                    gbs = bpu * prob.n / (avg / 1e3) / 1e9
+                    kern.append({"name": name, "launches": launches, "ms_per_launch": round(avg, 4),
+                                 "GB/s": round(gbs, 1), "frac_hbm": round(gbs / pk["hbm_gbs"], 4)})
+                kern.sort(key=lambda k: -k["ms_per_launch"] * k["launches"])
+                res[key] = {"value": prob.n * sum(iters) / (ms / 1e3), "unit": "unknown-iter/s",
+                            "iters": iters[-1], "ms_per_solve": ms / args.steps,
+                            "relres_true": max(i["relres_true"] for i in infos),
+                            "status": max(i["status"] for i in infos), "kernels": kern}
+        solver.close()
+        return res
+
+    prob = heat_cn_varcoeff_problem(255, 256)
     out = {"workload": "heat2d_cnvar_N256_m255 (Table 3, largest size)", "unknowns": prob.n,
            "tol": 1e-6, "basis": "physical", "steps": args.steps,
            "warmup": max(args.warmup, 1),
            "paper_context": "Table 3 prints 10 MINRES-P_alpha iterations and 32.40 s (Octave, CPU) at this size"}
-    with torch.cuda.stream(stream):
-        for key, fm in forms.items():
-            for _ in range(max(args.warmup, 1)):
-                solver.solve(fd, alpha=fm["alpha"], tol=1e-6, maxit=200, precision=fm["precision"],
-                             basis=B.BASIS_PHYSICAL, rebuild=True, matvec_arith=fm["arith"])
-            torch.cuda.synchronize()
-            solver.profile(True)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            infos = []
-            e0.record(stream)
-            for _ in range(args.steps):
-                _, info = solver.solve(fd, alpha=fm["alpha"], tol=1e-6, maxit=200,
-                                       precision=fm["precision"], basis=B.BASIS_PHYSICAL,
-                                       rebuild=True, matvec_arith=fm["arith"])
-                infos.append(info)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1)
-            prof = solver.profile_read()
-            solver.profile(False)
-            iters = [i["iters"] for i in infos]
-            kern = []
-            for name, (_, _, launches, tot_ms) in prof.items():
-                bound, bpu, fpu = kernel_cost(name, prob.N, prob.m[0], prob.d)
-                if launches == 0 or bpu == 0:
-                    continue
-                avg = tot_ms / launches
-                gbs = bpu * prob.n / (avg / 1e3) / 1e9
-                kern.append({"name": name, "launches": launches, "ms_per_launch": round(avg, 4),
-                             "GB/s": round(gbs, 1), "frac_hbm": round(gbs / pk["hbm_gbs"], 4)})
-            kern.sort(key=lambda k: -k["ms_per_launch"] * k["launches"])
-            out[key] = {"value": prob.n * sum(iters) / (ms / 1e3), "unit": "unknown-iter/s",
-                        "iters": iters[-1], "ms_per_solve": ms / args.steps,
-                        "relres_true": max(i["relres_true"] for i in infos),
-                        "status": max(i["status"] for i in infos), "kernels": kern}
+    out.update(measure(prob, rhs_uniform(prob.n, 12)))
+    p4 = fractional_varcoeff_problem(255, 256, 0.6)
+    e4 = {"workload": "fracvar2d_N256_m255_g0.6 (Example 4, Table 8, largest size)",
+          "unknowns": p4.n, "rhs": "the example's own data",
+          "paper_context": "Table 8 prints 8 MINRES-P_alpha iterations and 27.14 s (Octave, CPU) at this size"}
+    e4.update(measure(p4, paper_data_frac_var(p4, 0.6)))
+    out["example4"] = e4
     print(json.dumps(out))
     return 0
 

@@ -130,3 +130,35 @@ def test_varcoeff_paper_data_counts(B, precond, alpha, printed, slack):
     assert info["status"] == 0
     assert abs(info["iters"] - printed) <= slack and abs(info["iters"] - ref["iters"]) <= 1
     assert rel(to_host(u), ref["x"]) <= 1e-5
+
+
+def _example4_cases():
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                    "paper_iteration_counts_example4.json")))
+    cases = list(g["cases"])
+    # the largest size of Tables 7-9 (N = 256, m + 1 = 256: 16.6 M unknowns), GPU only
+    for table, gamma, p1 in (("Table 7", 0.3, 8), ("Table 8", 0.6, 10), ("Table 9", 0.9, 10)):
+        cases.append(dict(table=table, gamma=gamma, N=256, m_plus_1=256, precond="alpha", iters=8,
+                          slack=0))
+        cases.append(dict(table=table, gamma=gamma, N=256, m_plus_1=256, precond="one", iters=p1,
+                          slack=1))
+    return g, cases
+
+
+@pytest.mark.parametrize("case", _example4_cases()[1],
+                         ids=[f"{c['table']}_g{c['gamma']}_N{c['N']}_m{c['m_plus_1']}_{c['precond']}"
+                              for c in _example4_cases()[1]])
+def test_example4_paper_counts(B, case):
+    # Tables 7-9 (Example 4: L1 fractional, a = 35 + x^3.5 + y^3.5) on the example's own data:
+    # MINRES-P_alpha 8 iterations everywhere, MINRES-P_1 8 to 10 as printed
+    from workloads import fractional_varcoeff_problem, paper_data_frac_var
+    g = _example4_cases()[0]
+    prob = fractional_varcoeff_problem(case["m_plus_1"] - 1, case["N"], case["gamma"])
+    f = paper_data_frac_var(prob, case["gamma"])
+    alpha = g["alpha"] if case["precond"] == "alpha" else 1.0
+    u, info = B.Solver(prob).solve(to_dev(f), alpha=alpha, tol=g["tol"], maxit=500, precision=64)
+    assert info["status"] == 0 and info["basis"] == 2
+    assert abs(info["iters"] - case["iters"]) <= case["slack"], (case, info["iters"])
+    assert info["relres_true"] <= g["tol"]

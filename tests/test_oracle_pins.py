@@ -393,6 +393,27 @@ def test_paper_iteration_counts_with_paper_data():
         assert abs(r["iters"] - c["iters"]) <= c["slack"], (c, r["iters"])
 
 
+def _example4_cases():
+    g = json.load(open(os.path.join(GOLDEN, "paper_iteration_counts_example4.json")))
+    return g, g["cases"]
+
+
+@pytest.mark.parametrize("case", _example4_cases()[1],
+                         ids=[f"{c['table']}_g{c['gamma']}_N{c['N']}_m{c['m_plus_1']}_{c['precond']}"
+                              for c in _example4_cases()[1]])
+def test_example4_paper_counts(case):
+    # Example 4 (variable coefficient a = 35 + x^3.5 + y^3.5, L1 fractional) on its own data:
+    # Tables 7-9 print 8 iterations for MINRES-P_alpha at every size and order, and 8 to 10 for
+    # MINRES-P_1; the mean-coefficient preconditioner reproduces them
+    from workloads import fractional_varcoeff_problem, paper_data_frac_var
+    g = _example4_cases()[0]
+    prob = fractional_varcoeff_problem(case["m_plus_1"] - 1, case["N"], case["gamma"])
+    f = paper_data_frac_var(prob, case["gamma"])
+    alpha = g["alpha"] if case["precond"] == "alpha" else 1.0
+    r = O.solve(prob, f, alpha=alpha, tol=g["tol"], precond=case["precond"], maxit=500)
+    assert abs(r["iters"] - case["iters"]) <= case["slack"], (case, r["iters"])
+
+
 # ------------------------------------- dense commuting blocks (Sec. 3: A_(k) = a_k I + b_k K)
 
 def _with_K(p, K):

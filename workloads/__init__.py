@@ -21,7 +21,8 @@ import numpy as np
 
 __all__ = [
     "Problem", "l1_weights", "fractional_problem", "heat_bdf_problem", "heat_cn_problem",
-    "heat_cn_varcoeff_problem", "nonlocal_diffusion_problem", "paper_data_fractional", "paper_data_heat_var",
+    "heat_cn_varcoeff_problem", "fractional_varcoeff_problem", "nonlocal_diffusion_problem",
+    "paper_data_fractional", "paper_data_frac_var", "paper_data_heat_var",
     "rhs_uniform", "rhs_smoothed_field", "WORKLOADS", "workload", "batched_systems",
     "alpha_training_problems",
 ]
@@ -139,6 +140,24 @@ def heat_cn_varcoeff_problem(m, N, T=1.0, name=None) -> Problem:
                         abar=abar))
 
 
+def fractional_varcoeff_problem(m, N, gamma, name=None) -> Problem:
+    """The paper's Example 4 (Sec. 5.2): L1 time-fractional blocks (as fractional_problem, d = 2,
+    Omega = (0,1)^2, T = 1) with the variable coefficient a(x, y) = 35 + x^3.5 + y^3.5, i.e. the
+    blocks a_k I + b_k L_a with L_a = -Delta_{a,h}.  meta["faces"] holds a at the cell faces along
+    x and y (arrays (m, m+1) and (m+1, m), y-major), meta["abar"] the mean of a over the interior
+    grid points (the preconditioner's constant coefficient)."""
+    p = fractional_problem(2, m, N, gamma)
+    mm, h = p.m[0], p.h[0]
+    pts = (np.arange(mm) + 1.0) * h
+    fcs = (np.arange(mm + 1) + 0.5) * h
+    coef = lambda x1, x2: 35.0 + x1 ** 3.5 + x2 ** 3.5
+    fx = coef(fcs[None, :], pts[:, None])
+    fy = coef(pts[None, :], fcs[:, None])
+    abar = float(np.mean(coef(pts[None, :], pts[:, None])))
+    return Problem(p.N, p.d, p.m, p.h, p.a, p.b, name or f"fracvar2d_N{N}_m{mm}_g{gamma}",
+                   dict(p.meta, kind="fractional_var", faces=(fx, fy), abar=abar))
+
+
 def nonlocal_diffusion_problem(m, N, gamma, delta_cells=3.0, name=None) -> Problem:
     """The L1 time-fractional blocks of fractional_problem (d = 2, Omega = (0,1)^2) with a dense
     non-local spatial operator K in place of -Delta_h: the blocks become a_k I + b_k K, which
@@ -172,6 +191,26 @@ def paper_data_fractional(prob, gamma: float) -> np.ndarray:
     t = (np.arange(N) + 1.0) / N
     ft = 2.0 * t ** (2.0 - gamma) / math.gamma(3.0 - gamma) + 2.0 * t ** 2
     return (ft[:, None] * S[None, :]).reshape(-1)
+
+
+def paper_data_frac_var(prob, gamma: float) -> np.ndarray:
+    """Right-hand side of the paper's Example 4 (Sec. 5.2; the example writes alpha for the
+    fractional order gamma): u = sin(pi x) sin(pi y) t^2 and a = 35 + x^3.5 + y^3.5 give
+    f = sin(pi x) sin(pi y) [2 t^(2-gamma)/Gamma(3-gamma) + 2 pi^2 a t^2]
+        - pi t^2 [a_x cos(pi x) sin(pi y) + a_y sin(pi x) cos(pi y)],
+    a_x = 3.5 x^2.5, a_y = 3.5 y^2.5, at the interior grid points and t_n = n tau, n = 1..N
+    (u_0 = 0 adds nothing)."""
+    m, h, N = prob.m[0], prob.h[0], prob.N
+    x = (np.arange(m) + 1.0) * h
+    X, Y = np.meshgrid(x, x)                          # rows y, columns x: x fastest
+    a = 35.0 + X ** 3.5 + Y ** 3.5
+    S = np.sin(np.pi * X) * np.sin(np.pi * Y)
+    G = np.pi * (3.5 * X ** 2.5 * np.cos(np.pi * X) * np.sin(np.pi * Y)
+                 + 3.5 * Y ** 2.5 * np.sin(np.pi * X) * np.cos(np.pi * Y))
+    t = (np.arange(N) + 1.0) / N
+    c = 2.0 * t ** (2.0 - gamma) / math.gamma(3.0 - gamma)
+    F = c[:, None] * S.reshape(-1)[None, :] + (t * t)[:, None] * (2 * np.pi ** 2 * a * S - G).reshape(-1)[None, :]
+    return F.reshape(-1)
 
 
 def paper_data_heat_var(prob):
