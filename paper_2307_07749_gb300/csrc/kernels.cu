@@ -388,7 +388,7 @@ __device__ __forceinline__ void tp_freq_mul(typename A::V* buf, const OpTables& 
   }
 }
 
-template <class A, class Cfg = TileCfg<A>>
+template <class A, class Cfg = TileCfg<A>, bool TWS = false>
 __device__ __forceinline__ void timepass_tile(const OpTables& op, const PrecTables& pt,
                                               const Combine& cb, double* out,
                                               const double* dot_with, double* partials,
@@ -401,6 +401,14 @@ __device__ __forceinline__ void timepass_tile(const OpTables& op, const PrecTabl
   V* buf = reinterpret_cast<V*>(smem_raw);
   __shared__ double red[32];
   __shared__ float s_mu[kMaxCols];   // FP32 mode eigenvalues, used by the FP32 G
+  // TWS: the length-N twiddle table staged in shared memory behind the tile (the FFT passes
+  // then read it with shared-memory latency instead of through L1)
+  const V* twp = tw;
+  if constexpr (TWS) {
+    V* tws = buf + CAP;
+    for (int i = threadIdx.x; i < op.N; i += NT) tws[i] = tw[i];
+    twp = tws;
+  }
   const int N = op.N, NC = 1 << log2NC, W = 2 * NC, log2W = log2NC + 1;
   const long long M = op.M;
   const long long g0 = tile * W;
@@ -446,17 +454,17 @@ __device__ __forceinline__ void timepass_tile(const OpTables& op, const PrecTabl
     }
   }
   __syncthreads();
-  fft_columns<A, NT, CAP, false>(buf, N, op.log2N, log2NC, tw);
+  fft_columns<A, NT, CAP, false>(buf, N, op.log2N, log2NC, twp);
   tp_freq_mul<A, true, Cfg>(buf, op, pt, log2NC, g0, s_mu);
   __syncthreads();
-  fft_columns<A, NT, CAP, true>(buf, N, op.log2N, log2NC, tw);
+  fft_columns<A, NT, CAP, true>(buf, N, op.log2N, log2NC, twp);
   for (int e = threadIdx.x; e < N * NC; e += NT)
     buf[e] = A::scale_sc(buf[e], RowSc<A>::d2(pt, e >> log2NC));
   __syncthreads();
-  fft_columns<A, NT, CAP, false>(buf, N, op.log2N, log2NC, tw);
+  fft_columns<A, NT, CAP, false>(buf, N, op.log2N, log2NC, twp);
   tp_freq_mul<A, false, Cfg>(buf, op, pt, log2NC, g0, s_mu);
   __syncthreads();
-  fft_columns<A, NT, CAP, true>(buf, N, op.log2N, log2NC, tw);
+  fft_columns<A, NT, CAP, true>(buf, N, op.log2N, log2NC, twp);
   // read-out in batches: the dot-product partner of a whole batch is loaded before its first use;
   // dot_with == out asks for ||out||^2
   const bool self_dot = (dot_with == out);
@@ -495,7 +503,8 @@ k_timepass(OpTables op, PrecTables pt, Combine cb, double* out, const double* do
            double* partials, const int* phase, int want, int log2NC,
            const typename A::V* __restrict__ tw) {
   if (skip_phase(phase, want)) return;
-  timepass_tile<A, Cfg>(op, pt, cb, out, dot_with, partials, log2NC, tw, blockIdx.x);
+  timepass_tile<A, Cfg, std::is_same<A, ArithF>::value>(op, pt, cb, out, dot_with, partials,
+                                                        log2NC, tw, blockIdx.x);
 }
 
 // identity preconditioner (MINRES-I): z = v, with the same fused load and dot
@@ -1202,10 +1211,12 @@ static void run_dst(const OpTables& op, long long grid, long long nlines, int m,
     k_dst<A, false><<<(unsigned)grid, TileCfg<A>::NT, smem, st>>>(nlines, m, inner, P, ilog2(P), log2NC,
         in, out, flip, op.N, op.M, dot_with, partials, tw, phase, PH_RUN);
 }
+// the FP32 time pass stages its twiddles (at most kCap) behind the tile
+template <class A> constexpr int tp_tw_slots() { return std::is_same<A, ArithF>::value ? kCap : 0; }
 template <class A, class Cfg = TileCfg<A>> static cudaError_t ensure_smem_tp() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = set_smem(k_timepass<A, Cfg>, Cfg::CAP * sizeof(typename A::V));
+  cudaError_t e = set_smem(k_timepass<A, Cfg>, (Cfg::CAP + tp_tw_slots<A>()) * sizeof(typename A::V));
   if (e == cudaSuccess) done = true;
   return e;
 }
@@ -1290,7 +1301,8 @@ cudaError_t launch_timepass(const OpTables& op, const PrecTables& pt, int prec, 
     const int log2NC = ilog2(NC);
     const long long grid = (op.M + 2 * NC - 1) / (2 * NC);
     if (nparts) *nparts = (int)grid;
-    k_timepass<A, Cfg><<<(unsigned)grid, Cfg::NT, Cfg::CAP * sizeof(typename A::V), st>>>(
+    const size_t smem = (Cfg::CAP + (tp_tw_slots<A>() ? op.N : 0)) * sizeof(typename A::V);
+    k_timepass<A, Cfg><<<(unsigned)grid, Cfg::NT, smem, st>>>(
         op, pt, in, out, dot_with, partials, phase, PH_RUN, log2NC, tw);
     return cudaGetLastError();
   };
