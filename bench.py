@@ -29,6 +29,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -83,7 +84,7 @@ def peaks():
 
 
 # --------------------------------------------------------------------------------------------
-# algorithmic cost per unknown of each kernel family (the design doc derives these)
+# algorithmic cost per unknown of each kernel family (bytes and operations the method needs)
 def kernel_cost(name, N, m, d):
     """(bound, bytes per unknown, flops per unknown) of one launch, per unknown it processes."""
     l2N = np.log2(2 * N)
@@ -131,7 +132,8 @@ class ClockSampler:
 
     def __init__(self, index=0):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # a scratch file in the system's temporary directory; the summary goes into the JSON line
+        self.path = os.path.join(tempfile.gettempdir(), f"bltt_clocks_{os.getpid()}_{index}.csv")
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
