@@ -401,13 +401,32 @@ __device__ __forceinline__ void timepass_tile(const OpTables& op, const PrecTabl
   V* buf = reinterpret_cast<V*>(smem_raw);
   __shared__ double red[32];
   __shared__ float s_mu[kMaxCols];   // FP32 mode eigenvalues, used by the FP32 G
-  // TWS: the length-N twiddle table staged in shared memory behind the tile (the FFT passes
-  // then read it with shared-memory latency instead of through L1)
+  // TWS (FP32): the length-N twiddles, the N/2+1 entries of ahat and bhat and the N row scalings
+  // D^{-1} and D^2 staged in shared memory behind the tile, so that the FFT passes, the spectral
+  // products and the scalings read them with shared-memory latency instead of through L1
   const V* twp = tw;
+  PrecTables pts = pt;
   if constexpr (TWS) {
+    const int n = op.N, nh = n / 2 + 1;
     V* tws = buf + CAP;
-    for (int i = threadIdx.x; i < op.N; i += NT) tws[i] = tw[i];
+    float2* sa = reinterpret_cast<float2*>(tws + n);
+    float2* sb = sa + nh;
+    float* sdi = reinterpret_cast<float*>(sb + nh);
+    float* sd2 = sdi + n;
+    for (int i = threadIdx.x; i < n; i += NT) {
+      tws[i] = tw[i];
+      sdi[i] = pt.dinv32[i];
+      sd2[i] = pt.d232[i];
+    }
+    for (int i = threadIdx.x; i < nh; i += NT) {
+      sa[i] = pt.ahat32[i];
+      sb[i] = pt.bhat32[i];
+    }
     twp = tws;
+    pts.ahat32 = sa;
+    pts.bhat32 = sb;
+    pts.dinv32 = sdi;
+    pts.d232 = sd2;
   }
   const int N = op.N, NC = 1 << log2NC, W = 2 * NC, log2W = log2NC + 1;
   const long long M = op.M;
@@ -449,20 +468,20 @@ __device__ __forceinline__ void timepass_tile(const OpTables& op, const PrecTabl
         if (cb.in1) v[u] = fma(c1, a1[u], v[u]);
         if (cb.in2) v[u] = fma(c2, a2[u], v[u]);
         if (cb.vout && g0 + c < M) cb.vout[(long long)p * M + g0 + c] = v[u];
-        A::put_sc(buf, p * NC + (c >> 1), c & 1, v[u], RowSc<A>::dinv(pt, p));
+        A::put_sc(buf, p * NC + (c >> 1), c & 1, v[u], RowSc<A>::dinv(pts, p));
       }
     }
   }
   __syncthreads();
   fft_columns<A, NT, CAP, false>(buf, N, op.log2N, log2NC, twp);
-  tp_freq_mul<A, true, Cfg>(buf, op, pt, log2NC, g0, s_mu);
+  tp_freq_mul<A, true, Cfg>(buf, op, pts, log2NC, g0, s_mu);
   __syncthreads();
   fft_columns<A, NT, CAP, true>(buf, N, op.log2N, log2NC, twp);
   for (int e = threadIdx.x; e < N * NC; e += NT)
-    buf[e] = A::scale_sc(buf[e], RowSc<A>::d2(pt, e >> log2NC));
+    buf[e] = A::scale_sc(buf[e], RowSc<A>::d2(pts, e >> log2NC));
   __syncthreads();
   fft_columns<A, NT, CAP, false>(buf, N, op.log2N, log2NC, twp);
-  tp_freq_mul<A, false, Cfg>(buf, op, pt, log2NC, g0, s_mu);
+  tp_freq_mul<A, false, Cfg>(buf, op, pts, log2NC, g0, s_mu);
   __syncthreads();
   fft_columns<A, NT, CAP, true>(buf, N, op.log2N, log2NC, twp);
   // read-out in batches: the dot-product partner of a whole batch is loaded before its first use;
@@ -485,7 +504,7 @@ __device__ __forceinline__ void timepass_tile(const OpTables& op, const PrecTabl
       const int p = e >> log2W, c = e & (W - 1);
       if (e < total && g0 + c < M) {
         const long long idx = (long long)p * M + g0 + c;
-        const double z = A::part_sc(buf[p * NC + (c >> 1)], c & 1, RowSc<A>::dinv(pt, p));
+        const double z = A::part_sc(buf[p * NC + (c >> 1)], c & 1, RowSc<A>::dinv(pts, p));
         out[idx] = z;
         acc = fma(z, self_dot ? z : dw[u], acc);
       }
@@ -1211,12 +1230,18 @@ static void run_dst(const OpTables& op, long long grid, long long nlines, int m,
     k_dst<A, false><<<(unsigned)grid, TileCfg<A>::NT, smem, st>>>(nlines, m, inner, P, ilog2(P), log2NC,
         in, out, flip, op.N, op.M, dot_with, partials, tw, phase, PH_RUN);
 }
-// the FP32 time pass stages its twiddles (at most kCap) behind the tile
-template <class A> constexpr int tp_tw_slots() { return std::is_same<A, ArithF>::value ? kCap : 0; }
+// shared memory the FP32 time pass stages behind its tile: N twiddles and 2 (N/2+1) spectrum
+// entries (float2), N values of each row scaling (float)
+template <class A> constexpr size_t tp_stage_bytes(int n) {
+  return std::is_same<A, ArithF>::value
+             ? (size_t)(n + 2 * (n / 2 + 1)) * sizeof(float2) + 2 * (size_t)n * sizeof(float)
+             : 0;
+}
 template <class A, class Cfg = TileCfg<A>> static cudaError_t ensure_smem_tp() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = set_smem(k_timepass<A, Cfg>, (Cfg::CAP + tp_tw_slots<A>()) * sizeof(typename A::V));
+  cudaError_t e = set_smem(k_timepass<A, Cfg>,
+                           Cfg::CAP * sizeof(typename A::V) + tp_stage_bytes<A>(kCap));
   if (e == cudaSuccess) done = true;
   return e;
 }
@@ -1301,7 +1326,7 @@ cudaError_t launch_timepass(const OpTables& op, const PrecTables& pt, int prec, 
     const int log2NC = ilog2(NC);
     const long long grid = (op.M + 2 * NC - 1) / (2 * NC);
     if (nparts) *nparts = (int)grid;
-    const size_t smem = (Cfg::CAP + (tp_tw_slots<A>() ? op.N : 0)) * sizeof(typename A::V);
+    const size_t smem = Cfg::CAP * sizeof(typename A::V) + tp_stage_bytes<A>(op.N);
     k_timepass<A, Cfg><<<(unsigned)grid, Cfg::NT, smem, st>>>(
         op, pt, in, out, dot_with, partials, phase, PH_RUN, log2NC, tw);
     return cudaGetLastError();
