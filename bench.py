@@ -45,7 +45,7 @@ ALPHA_F32X2 = 1e-6        # double-float preconditioner: the sweep's fastest alp
 # DRAM bytes (read + write) per unknown of one launch, from one ncu capture of the current kernel
 # (profiles/ncu_chosen_form_frac2d_N1024_m127.md: the m = 127 case, scaled by the unknowns)
 NCU_TRAFFIC_PER_UNKNOWN = {
-    "conv_df": (13.09, "ncu dram__bytes_read.sum + dram__bytes_write.sum, m = 127 case, 13.09 B "
+    "conv_df": (13.07, "ncu dram__bytes_read.sum + dram__bytes_write.sum, m = 127 case, 13.07 B "
                        "per unknown scaled to the launch's unknowns"),
 }
 FP64_PEAK_TFLOPS = 1.259  # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (measured 1.20 at 1995 MHz)
