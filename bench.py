@@ -360,8 +360,12 @@ def run_once(args):
     from paper_2307_07749_gb300 import build
     build.build()
     import paper_2307_07749_gb300 as B
-    from workloads import workload, rhs_uniform, fractional_problem
-    if args.m == 255:
+    from workloads import workload, rhs_uniform, fractional_problem, heat_bdf_problem
+    if args.problem == "heat3d":
+        # the 3-D heat workload's N = 256 on m = 63 per axis: 64 M unknowns, 512 MB per vector
+        prob = heat_bdf_problem(3, args.m, 256)
+        name = f"heat3d_bdf_N256_m{args.m}"
+    elif args.m == 255:
         prob, _ = workload(WORKLOAD)
         name = WORKLOAD
     else:
@@ -703,6 +707,8 @@ def main():
     ap.add_argument("--form", default="chosen", choices=list(FORMS))
     ap.add_argument("--m", type=int, default=255, choices=[63, 127, 255],
                     help="--workload once: interior points per axis (255: the headline workload)")
+    ap.add_argument("--problem", default="frac2d", choices=["frac2d", "heat3d"],
+                    help="--workload once: the 2-D fractional workload or the 3-D heat one")
     ap.add_argument("--alpha-train", type=int, default=2000)
     ap.add_argument("--alpha-heldout", type=int, default=256)
     args = ap.parse_args()
