@@ -76,6 +76,9 @@ def test_null_handle_calls(lib):
     assert L.bltt_matvec(None, None, None, 1) == 1
     assert L.bltt_precond_apply(None, 0.5, None, None, 64) == 1
     assert L.bltt_set_stream(None, None) == 1
+    assert L.bltt_set_matvec_arith(None, 1) == 1
+    assert L.bltt_set_variable_coefficient(None, None, 1.0) == 1
+    assert L.bltt_set_dense_operator(None, None) == 1
 
 
 def test_alpha_label_rule(lib):
