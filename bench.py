@@ -626,6 +626,53 @@ def run_varcoef(args):
     return 0
 
 
+def run_small(args):
+    """The smallest workload (1-D L1 fractional, gamma = 0.5, N = 64, m = 63: 4032 unknowns), DST
+    basis, in FP64 (alpha = 1e-8) and in the chosen form (alpha = 1e-3): whole solves by the
+    multi-launch driver (CUDA-graph replay) against the single-block kernel (one launch per
+    solve).  Right-hand side: seeded U[-1, 1]."""
+    import torch
+    from paper_2307_07749_gb300 import build
+    build.build()
+    import paper_2307_07749_gb300 as B
+    from workloads import workload, rhs_uniform
+    prob, _ = workload("frac1d_N64_m63_g0.5")
+    stream = torch.cuda.Stream()
+    solver = B.Solver(prob, stream=stream)
+    fd = torch.from_numpy(rhs_uniform(prob.n, 1)).to("cuda")
+    torch.cuda.synchronize()
+    out = {"workload": "frac1d_N64_m63_g0.5", "unknowns": prob.n, "tol": TOL,
+           "steps": args.steps * 20, "warmup": max(args.warmup, 3)}
+    f64 = dict(alpha=ALPHA_F64, precision=64, matvec_arith=B.ARITH_F64)
+    chosen = dict(alpha=ALPHA_F32, precision=32, matvec_arith=B.ARITH_F32X2)
+    forms = {"graph_f64": dict(single_block=False, **f64),
+             "single_block_f64": dict(single_block=True, **f64),
+             "graph_chosen": dict(single_block=False, **chosen),
+             "single_block_chosen": dict(single_block=True, **chosen)}
+    with torch.cuda.stream(stream):
+        for key, fm in forms.items():
+            for _ in range(max(args.warmup, 3)):
+                solver.solve(fd, tol=TOL, maxit=100, basis=1, **fm)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            infos = []
+            k = args.steps * 20
+            e0.record(stream)
+            for _ in range(k):
+                _, info = solver.solve(fd, tol=TOL, maxit=100, basis=1, **fm)
+                infos.append(info)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / k
+            out[key] = {"ms_per_solve": ms, "iters": infos[-1]["iters"],
+                        "value": prob.n * infos[-1]["iters"] / (ms / 1e3), "unit": "unknown-iter/s",
+                        "relres_true": max(i["relres_true"] for i in infos),
+                        "kernel_launches": infos[-1]["kernel_launches"],
+                        "status": max(i["status"] for i in infos)}
+    print(json.dumps(out))
+    return 0
+
+
 def run_dense(args):
     """Commuting dense blocks a_k I + b_k K (Sec. 3): the L1 time-fractional blocks (gamma = 0.5,
     N = 1024) with a dense non-local diffusion operator K on a 63 x 63 grid (M = 3969, n =
@@ -700,7 +747,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="frac2d",
-                    choices=["frac2d", "batched", "alpha", "once", "heat3d", "varcoef", "dense"],
+                    choices=["frac2d", "batched", "alpha", "once", "heat3d", "varcoef", "dense",
+                             "small"],
                     help="frac2d: the headline line; batched / alpha / heat3d: supplementary "
                          "reports; once: a single solve of the headline workload (for ncu "
                          "captures)")
@@ -726,6 +774,8 @@ def main():
         return run_varcoef(args)
     if args.workload == "dense":
         return run_dense(args)
+    if args.workload == "small":
+        return run_small(args)
     args.warmup = max(args.warmup, 3)
 
     rank, local, ws = dist_init()

@@ -87,9 +87,9 @@ enum { BLTT_PRECOND_ABAC = 0, BLTT_PRECOND_NONE = 1 };
  * product stays FP64 in memory and agrees with the FP64 result to about 1e-14 relative.
  * TC: the time convolution of the in-loop products y = Y A z (not the residual checks, which stay
  * F32X2) runs on the tensor cores as a dense product with the time-flipped Toeplitz (Hankel)
- * matrix of a: x and a are split into four balanced 8-bit digits relative to a power-of-two
+ * matrix of a: x and a are split into five balanced 8-bit digits relative to a power-of-two
  * bound of each spatial line (of a), the digit products are exact bf16 x bf16 -> FP32 tensor-core
- * sums, and the b_0 term and the scale are double-float.  Relative error about 2^-30 of
+ * sums, and the b_0 term and the scale are double-float.  Relative error about 2^-40 of
  * sum_k |a_k| |x_k| per element.  Requires b = b_0 e_0, an FFT-class a (more than 4 nonzeros)
  * and N in {128, 256, 512, 1024}; elsewhere it is BLTT_ERR_UNSUPPORTED.  Uses a workspace of
  * N * 128 * ceil(M/128) * 8 bytes, allocated on first use.
@@ -106,6 +106,13 @@ typedef struct {
   int no_graph;      /* 1: launch every kernel directly; 0: capture sync_every (rounded up to even)
                         iterations in a CUDA graph, cached per handle, and replay it (used when the
                         handle's stream is not the legacy stream and profiling is off)            */
+  int single_block;  /* 1: run the whole solve (entry transform, every iteration, exit transform)
+                        in one kernel launch of one thread block, for problems whose every phase
+                        is one FFT tile (e.g. N = 64, m = 63); DST basis, the FFT product, device
+                        buffers, ABAC, and either FP64 throughout (precision 64, matvec F64) or
+                        the FP32 preconditioner with the double-float product and DSTs (precision
+                        32, matvec F32X2); the true residual is checked in the DST basis inside the
+                        loop.  Else BLTT_ERR_UNSUPPORTED.                                          */
 } bltt_solve_opts;
 
 typedef struct {
@@ -157,8 +164,8 @@ bltt_status bltt_set_variable_coefficient(bltt_handle h, const double* const* fa
  * the true residual checked there (U orthogonal: the same norm as in the physical basis).  The
  * GEMMs follow the matvec arithmetic: FP64 (cuBLAS) with BLTT_ARITH_F64, double-float on the
  * FP32 pipes (about 2^-47 relative per multiply-add) with BLTT_ARITH_F32X2.  The handle keeps U
- * in FP64 (M^2 doubles) and as double-float planes of U and U^T (4 M^2 floats).  bltt_matvec and bltt_precond_apply take and return physical-basis vectors (a GEMM on
- * each side).  Exclusive with bltt_set_variable_coefficient and the tensor-core matvec
+ * in FP64 (M^2 doubles) and as double-float planes of U and U^T (4 M^2 floats).  bltt_matvec
+ * and bltt_precond_apply take and return physical-basis vectors (a GEMM on each side).  Exclusive with bltt_set_variable_coefficient and the tensor-core matvec
  * (BLTT_ERR_UNSUPPORTED).  A later call replaces K. */
 bltt_status bltt_set_dense_operator(bltt_handle h, const double* K);
 

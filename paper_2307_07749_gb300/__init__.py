@@ -48,7 +48,8 @@ class bltt_blocks(ctypes.Structure):
 class bltt_solve_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("basis", ctypes.c_int), ("precond", ctypes.c_int),
                 ("sync_every", ctypes.c_int), ("rebuild", ctypes.c_int),
-                ("matvec_arith", ctypes.c_int), ("no_graph", ctypes.c_int)]
+                ("matvec_arith", ctypes.c_int), ("no_graph", ctypes.c_int),
+                ("single_block", ctypes.c_int)]
 
 
 class bltt_solve_info(ctypes.Structure):
@@ -220,8 +221,9 @@ def bltt_precond_apply(handle, alpha, v, z, precision=PREC_F64):
 
 def bltt_minres_solve_ex(handle, f, alpha, tol, maxit, u, precision=PREC_F64, basis=BASIS_AUTO,
                          precond=PRECOND_ABAC, sync_every=0, raise_on_error=True, rebuild=0,
-                         matvec_arith=ARITH_DEFAULT, no_graph=0):
-    opts = bltt_solve_opts(precision, basis, precond, sync_every, rebuild, matvec_arith, no_graph)
+                         matvec_arith=ARITH_DEFAULT, no_graph=0, single_block=0):
+    opts = bltt_solve_opts(precision, basis, precond, sync_every, rebuild, matvec_arith, no_graph,
+                           int(single_block))
     info = bltt_solve_info()
     st = lib().bltt_minres_solve_ex(handle, _ptr(f, "f"), float(alpha), float(tol), int(maxit),
                                     ctypes.byref(opts), _ptr(u, "u"), ctypes.byref(info))
@@ -420,12 +422,13 @@ class Solver:
 
     def solve(self, f, alpha=1e-8, tol=1e-8, maxit=200, precision=PREC_F64, basis=BASIS_AUTO,
               precond=PRECOND_ABAC, u=None, sync_every=0, raise_on_error=True, rebuild=False,
-              matvec_arith=ARITH_DEFAULT, graph=True):
+              matvec_arith=ARITH_DEFAULT, graph=True, single_block=False):
+        """single_block: the whole solve in one launch of one block (small problems, FP64)."""
         import torch
         u = torch.empty_like(f) if u is None else u
         st, info = bltt_minres_solve_ex(self.handle, f, alpha, tol, maxit, u, precision, basis,
                                         precond, sync_every, raise_on_error, int(rebuild),
-                                        matvec_arith, 0 if graph else 1)
+                                        matvec_arith, 0 if graph else 1, int(single_block))
         info["status_name"] = STATUS_NAMES.get(st, st)
         return u, info
 

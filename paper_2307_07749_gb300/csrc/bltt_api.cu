@@ -1048,6 +1048,88 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
   sh->phase = PH_RUN;
   CK(h, cudaMemcpyAsync(h->state, sh, sizeof *sh, cudaMemcpyHostToDevice, st), "state upload");
   int* phase = &h->state->phase;
+  // the end of every solve: timings, status and statistics
+  auto finish = [&](double relres_phys) -> bltt_status {
+    CK(h, cudaEventRecord(h->ev[2], st), "event");
+    CK(h, cudaStreamSynchronize(st), "sync");
+    prof_harvest(h);
+    float t_all = 0.f, t_setup = 0.f;
+    cudaEventElapsedTime(&t_all, h->ev[0], h->ev[2]);
+    cudaEventElapsedTime(&t_setup, h->ev[0], h->ev[1]);
+    bltt_status result;
+    if (sh->phase == PH_DONE) result = (sh->status == 0) ? BLTT_OK : BLTT_ERR_NOT_CONVERGED;
+    else if (sh->phase == PH_FAIL) result = BLTT_ERR_NUMERIC;
+    else result = BLTT_ERR_NOT_CONVERGED;
+    if (info) {
+      info->iters = sh->iter;
+      info->relres_est = sh->relres_est;
+      info->relres_true = relres_phys;
+      info->alpha_used = none ? 0.0 : alpha;
+      info->alpha_source = 0;
+      info->precision = o.precision;
+      info->basis = basis;
+      info->t_setup_ms = t_setup;
+      info->t_solve_ms = t_all;
+      info->kernel_launches = h->launches;
+      info->status = result;
+    }
+    if (tc) {
+      // a bounded wait of the tensor-core kernel that gave up shows as NaN partials; name it
+      int flag = 0;
+      CK(h, cudaMemcpy(&flag, op.tc_err, sizeof(int), cudaMemcpyDeviceToHost), "error flag");
+      if (flag) {
+        CK(h, cudaMemset(op.tc_err, 0, sizeof(int)), "error flag");
+        if (info) info->status = BLTT_ERR_TIMEOUT;
+        return fail(h, BLTT_ERR_TIMEOUT, "a bounded wait of the tensor-core matvec gave up");
+      }
+    }
+    if (result == BLTT_ERR_NUMERIC) h->err = "MINRES breakdown: <z, v> negative or non-finite";
+    else if (result == BLTT_ERR_NOT_CONVERGED) h->err = "maxit reached before the stopping rule held";
+    return result;
+  };
+
+  if (o.single_block) {
+    // the whole solve by one block (problems whose every phase is one FFT tile): DST basis, the
+    // residual checked inside the loop; one launch.  Forms: FP64 throughout, or the chosen one
+    // (FP32 preconditioner with the double-float product and DSTs)
+    const bool f64 = (o.precision == 64 && op.mv_arith == 0);
+    const bool chosen = (o.precision == 32 && op.mv_arith == 1);
+    if (!spectral || !(f64 || chosen) || none || op.ntaps > 0 || h->dense || h->var_coef || hin ||
+        hout)
+      return fail(h, BLTT_ERR_UNSUPPORTED,
+                  "single_block needs the DST basis, FP64 or the FP32 preconditioner with the "
+                  "double-float product, the FFT product and device buffers");
+    OneSolve os{};
+    const int ncc = one_tile_columns(h->M, 2 * h->N);
+    const int nct = one_tile_columns(h->M, h->N, chosen ? 2 * kCap : kCap);
+    bool fits = ncc > 0 && nct > 0 && 2 * h->N <= kCap;
+    for (int ax = 0; ax < h->d && fits; ++ax) {
+      const int ncd = one_tile_columns((long long)h->N * h->M / h->m[ax], h->m[ax] + 1);
+      fits = ncd > 0;
+      if (fits) os.log2NC_dst[ax] = ilog2i(ncd);
+    }
+    if (!fits) return fail(h, BLTT_ERR_UNSUPPORTED, "single_block: a phase needs more than one tile");
+    os.log2NC_conv = ilog2i(ncc);
+    os.log2NC_tp = ilog2i(nct);
+    os.op = op;
+    os.pt = pt;
+    os.st = h->state;
+    os.f = f;
+    os.u = u;
+    os.b = vec(h, 0);
+    for (int i = 0; i < 2; ++i) { os.v[i] = vec(h, 1 + i); os.z[i] = vec(h, 3 + i); os.w[i] = vec(h, 5 + i); }
+    os.q = vec(h, 7);
+    os.x = vec(h, 8);
+    os.part = h->partials[0];
+    os.maxit = maxit;
+    cudaEvent_t pa = prof_begin(h);
+    CK(h, launch_solve_one(os, chosen, st), "single-block solve");
+    prof_end(h, "solve_one", pa);
+    h->launches++;
+    CK(h, cudaMemcpyAsync(sh, h->state, sizeof *sh, cudaMemcpyDeviceToHost, st), "state download");
+    CK(h, cudaStreamSynchronize(st), "sync");
+    return finish(sh->relres_true);
+  }
 
   // b = Y f (spectral: Y (I (x) U) f) with ||b||^2
   int nb = 0, nzv = 0, np = 0;
@@ -1262,42 +1344,7 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
     sh->phase = PH_RUN;
     CK(h, cudaMemcpyAsync(phase, &sh->phase, sizeof(int), cudaMemcpyHostToDevice, st), "resume");
   }
-  CK(h, cudaEventRecord(h->ev[2], st), "event");
-  CK(h, cudaStreamSynchronize(st), "sync");
-  prof_harvest(h);
-  float t_all = 0.f, t_setup = 0.f;
-  cudaEventElapsedTime(&t_all, h->ev[0], h->ev[2]);
-  cudaEventElapsedTime(&t_setup, h->ev[0], h->ev[1]);
-  bltt_status result;
-  if (sh->phase == PH_DONE) result = (sh->status == 0) ? BLTT_OK : BLTT_ERR_NOT_CONVERGED;
-  else if (sh->phase == PH_FAIL) result = BLTT_ERR_NUMERIC;
-  else result = BLTT_ERR_NOT_CONVERGED;
-  if (info) {
-    info->iters = sh->iter;
-    info->relres_est = sh->relres_est;
-    info->relres_true = relres_phys;
-    info->alpha_used = none ? 0.0 : alpha;
-    info->alpha_source = 0;
-    info->precision = o.precision;
-    info->basis = basis;
-    info->t_setup_ms = t_setup;
-    info->t_solve_ms = t_all;
-    info->kernel_launches = h->launches;
-    info->status = result;
-  }
-  if (tc) {
-    // a bounded wait of the tensor-core kernel that gave up shows as NaN partials; name it
-    int flag = 0;
-    CK(h, cudaMemcpy(&flag, op.tc_err, sizeof(int), cudaMemcpyDeviceToHost), "error flag");
-    if (flag) {
-      CK(h, cudaMemset(op.tc_err, 0, sizeof(int)), "error flag");
-      if (info) info->status = BLTT_ERR_TIMEOUT;
-      return fail(h, BLTT_ERR_TIMEOUT, "a bounded wait of the tensor-core matvec gave up");
-    }
-  }
-  if (result == BLTT_ERR_NUMERIC) h->err = "MINRES breakdown: <z, v> negative or non-finite";
-  else if (result == BLTT_ERR_NOT_CONVERGED) h->err = "maxit reached before the stopping rule held";
-  return result;
+  return finish(relres_phys);
 }
 }  // namespace
 

@@ -101,6 +101,26 @@ struct Combine {
   double* vout;          // if set, the combined value is stored here
 };
 
+// a whole DST-basis MINRES solve by one block (problems whose every phase is one FFT tile): the
+// operator tables, the solve's vectors and the tile shapes of each phase
+struct OneSolve {
+  OpTables op;
+  PrecTables pt;
+  MinresDev* st;
+  const double* f;       // right-hand side (physical basis)
+  double* u;             // solution (physical basis)
+  double* b;             // Y (I (x) U) f
+  double* v[2];
+  double* z[2];
+  double* w[2];
+  double* q;
+  double* x;             // solution in the DST basis
+  double* part;          // 8 partial-sum slots (one per reduction)
+  int maxit;
+  int log2NC_conv, log2NC_tp;
+  int log2NC_dst[3];     // per axis
+};
+
 // preconditioner / transform arithmetic codes
 enum { PREC_F32 = 32, PREC_F64 = 64, PREC_DF = 96 };
 
@@ -155,6 +175,10 @@ cudaError_t launch_scalar_delta(MinresDev* s, const double* partials, int np, cu
 cudaError_t launch_scalar_gamma(MinresDev* s, const double* partials, int np, cudaStream_t st);
 cudaError_t launch_scalar_check(MinresDev* s, const double* partials, int np, cudaStream_t st);
 cudaError_t launch_scalar_defer(MinresDev* s, cudaStream_t st);   // PH_CHECK -> PH_VERIFY
+// the whole-solve block: nc of a phase's single tile (0 if it needs more than one tile), and the launch
+int one_tile_columns(long long nlines, int Lfft, int cap_points = kCap);
+// chosen: double-float product and DSTs with the FP32 time pass (else FP64 throughout)
+cudaError_t launch_solve_one(const OneSolve& s, bool chosen, cudaStream_t st);
 cudaError_t launch_w_update(MinresDev* s, const double* z, double* w_prev, const double* w,
                             double* x, long long n, cudaStream_t st);
 cudaError_t launch_copy_scaled_check(const double* src, double* dst, long long n, cudaStream_t st);

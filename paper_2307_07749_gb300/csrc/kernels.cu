@@ -1199,6 +1199,144 @@ __global__ void __launch_bounds__(256) k_sum_partials(const double* p, int np, d
 }
 
 // ============================================================================================
+// The whole solve by one block (A5 for the smallest workload, 4032 unknowns): entry DST, the
+// MINRES iterations with the residual check inside the loop (DST basis), exit DST.  The phases are
+// the tile functions of the multi-block kernels, each called on its one tile; the partial sums
+// they write (one per tile, so the totals) are read after a barrier, which orders global memory
+// within the block.  The loop is bounded by maxit.  Two arithmetic forms: FP64 throughout (256
+// threads), and the chosen form (double-float product and DSTs, FP32 time pass; 512 threads), whose
+// work runs on the FP32 pipes: one SM's FP64 rate is 1/64 of its FP32 rate.
+struct OneF64 {
+  using Conv = ArithD;
+  using Tp = ArithD;
+  using TpCfg = TileCfg<ArithD>;
+  using Dst = ArithD;
+  static constexpr int NT = kThreads;
+  static __device__ __forceinline__ const double2* tw_tp(const OpTables& op) { return op.tw_N; }
+  static __device__ __forceinline__ const double2* tw_dst(const OpTables& op, int ax) { return op.tw_dst[ax]; }
+};
+struct OneChosen {
+  using Conv = ArithDF;
+  using Tp = ArithF;
+  using TpCfg = WideTileF;
+  using Dst = ArithDF;
+  static constexpr int NT = 2 * kThreads;
+  static __device__ __forceinline__ const float2* tw_tp(const OpTables& op) { return op.tw_N32; }
+  static __device__ __forceinline__ const float4* tw_dst(const OpTables& op, int ax) { return op.tw_dst_df[ax]; }
+};
+
+template <class F, bool SWZ>
+__device__ __forceinline__ void one_dst(const OneSolve& s, int ax, const double* in, double* out,
+                                        int flip, const double* dot_with, double* partials) {
+  const OpTables& op = s.op;
+  const int m = op.m[ax];
+  long long inner = 1;
+  for (int a = 0; a < ax; ++a) inner *= op.m[a];
+  const long long nlines = (long long)op.N * op.M / m;
+  const int P = m + 1;
+  Combine c{};
+  c.in0 = in;
+  dst_tile<typename F::Dst, SWZ>(nlines, m, inner, P, __ffs(P) - 1, s.log2NC_dst[ax], c, out, flip,
+                                 op.N, op.M, dot_with, partials, F::tw_dst(op, ax), 0);
+}
+
+// out = (I (x) U) in over every axis (flip on the first), ||out||^2 into partials[0] if asked
+template <class F>
+__device__ __forceinline__ void one_dst_all(const OneSolve& s, const double* in, double* out,
+                                            int flip, double* partials) {
+  for (int ax = 0; ax < s.op.d; ++ax) {
+    const bool last = (ax == s.op.d - 1);
+    const double* src = (ax == 0) ? in : out;
+    double* dw = (last && partials) ? out : nullptr;
+    if (ax == 0) one_dst<F, true>(s, ax, src, out, flip, dw, last ? partials : nullptr);
+    else one_dst<F, false>(s, ax, src, out, 0, dw, last ? partials : nullptr);
+    __syncthreads();
+  }
+}
+
+template <class F>
+__global__ void __launch_bounds__(F::NT) k_solve_one(OneSolve s) {
+  constexpr int NT = F::NT;
+  static_assert(TileCfg<typename F::Conv>::NT == NT && F::TpCfg::NT == NT &&
+                TileCfg<typename F::Dst>::NT == NT, "one block size for every phase");
+  const OpTables& op = s.op;
+  MinresDev* st = s.st;
+  const long long n = (long long)op.N * op.M;
+  double* const P_B = s.part + 0;     // ||b||^2
+  double* const P_ZV = s.part + 1;    // <z, v>
+  double* const P_D = s.part + 2;     // delta
+  double* const P_R = s.part + 3;     // ||r||^2
+  // b = Y (I (x) U) f with ||b||^2
+  one_dst_all<F>(s, s.f, s.b, 1, P_B);
+  // v_1 = b, z_1 = P^{-1} v_1, <z_1, v_1>
+  {
+    Combine c{};
+    c.in0 = s.b;
+    c.vout = s.v[0];
+    timepass_tile<typename F::Tp, typename F::TpCfg>(op, s.pt, c, s.z[0], s.v[0], P_ZV,
+                                                     s.log2NC_tp, F::tw_tp(op), 0);
+  }
+  for (long long e = threadIdx.x; e < n; e += NT) {
+    s.x[e] = 0.0;
+    s.v[1][e] = 0.0;
+    s.w[0][e] = 0.0;
+    s.w[1][e] = 0.0;
+  }
+  __syncthreads();
+  scalar_init(st, P_ZV, 1, P_B, 1);
+  __syncthreads();
+  double *vc = s.v[0], *vp = s.v[1], *zc = s.z[0], *zp = s.z[1], *wc = s.w[0], *wp = s.w[1];
+  for (int it = 0; it < s.maxit && st->phase == PH_RUN; ++it) {
+    // q = Y A z_j (z_j = z_u / gamma_j), delta = <q, z_j>
+    conv_tile<typename F::Conv>(op, 1, 0, zc, &st->inv_gamma, s.q, 1, MV_STORE, nullptr, P_D,
+                                nullptr, s.log2NC_conv, 0);
+    __syncthreads();
+    scalar_delta(st, P_D, 1);
+    __syncthreads();
+    if (st->phase != PH_RUN) break;
+    // v_{j+1} = q - (delta/gamma) v_j - (gamma/gamma_prev) v_{j-1} (over v_{j-1}); z_{j+1}; <z, v>
+    Combine c{};
+    c.in0 = s.q;
+    c.in1 = vc;
+    c.in2 = vp;
+    c.coef = st->coef;
+    c.vout = vp;
+    timepass_tile<typename F::Tp, typename F::TpCfg>(op, s.pt, c, zp, vp, P_ZV, s.log2NC_tp,
+                                                     F::tw_tp(op), 0);
+    __syncthreads();
+    scalar_gamma(st, P_ZV, 1);
+    __syncthreads();
+    if (st->wpending)
+      w_update_range(zc, wp, wc, s.x, n, threadIdx.x, NT, st->w_cz, st->w_cwp, st->w_cw,
+                     st->w_ceta);
+    __syncthreads();
+    // the true residual ||b - Y A x|| when the estimate met the stopping rule
+    if (st->phase == PH_CHECK)
+      conv_tile<typename F::Conv>(op, 1, 0, s.x, nullptr, nullptr, 1, MV_RESID, s.b, P_R, nullptr,
+                                  s.log2NC_conv, 0);
+    __syncthreads();
+    scalar_check(st, P_R, 1);
+    __syncthreads();
+    double* t;
+    t = vc; vc = vp; vp = t;
+    t = zc; zc = zp; zp = t;
+    t = wc; wc = wp; wp = t;
+  }
+  // u = (I (x) U) x
+  one_dst_all<F>(s, s.x, s.u, 0, nullptr);
+}
+
+int one_tile_columns(long long nlines, int Lfft, int cap_points) {
+  int cap = cap_points / Lfft;
+  if (cap > kMaxCols / 2) cap = kMaxCols / 2;
+  const long long pairs = (nlines + 1) / 2;
+  if (cap < 1 || pairs > cap) return 0;
+  int nc = 1;
+  while (nc < pairs) nc <<= 1;
+  return nc;
+}
+
+// ============================================================================================
 // launchers
 static int grid_stream(long long n, int threads) {
   long long g = (n + threads - 1) / threads;
@@ -1439,6 +1577,22 @@ cudaError_t launch_scalar_check(MinresDev* s, const double* p, int np, cudaStrea
 
 cudaError_t launch_scalar_defer(MinresDev* s, cudaStream_t st) {
   k_scalar_defer<<<1, 1, 0, st>>>(s);
+  return cudaGetLastError();
+}
+cudaError_t launch_solve_one(const OneSolve& s, bool chosen, cudaStream_t st) {
+  // both forms stage a tile of 64 KB: kCap double2 (FP64), kCap float4 (double-float), 8192 float2
+  static_assert(kCap * sizeof(double2) == kCap * sizeof(float4) &&
+                kCap * sizeof(float4) == WideTileF::CAP * sizeof(float2), "one tile size");
+  const size_t smem = kCap * sizeof(double2);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = set_smem(k_solve_one<OneF64>, smem);
+    if (e == cudaSuccess) e = set_smem(k_solve_one<OneChosen>, smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (chosen) k_solve_one<OneChosen><<<1, OneChosen::NT, smem, st>>>(s);
+  else k_solve_one<OneF64><<<1, OneF64::NT, smem, st>>>(s);
   return cudaGetLastError();
 }
 cudaError_t launch_w_update(MinresDev* s, const double* z, double* w_prev, const double* w,
