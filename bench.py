@@ -43,11 +43,13 @@ ALPHA_F64 = 1e-8          # the paper's alpha rule (Sec. 5.2)
 ALPHA_F32 = 1e-3          # FP32 preconditioner: alpha raised so that FP32 rounding stays below tol
 ALPHA_F32X2 = 1e-6        # double-float preconditioner: the sweep's fastest alpha on this workload
 # DRAM bytes (read + write) per unknown of one launch, from one ncu capture of the current kernel
-# (profiles/ncu_chosen_form_frac2d_N1024_m127.md: the m = 127 case, scaled by the unknowns)
+# (the m = 127 case of the same workload, scaled by the unknowns)
 NCU_TRAFFIC_PER_UNKNOWN = {
     "conv_df": (13.07, "ncu dram__bytes_read.sum + dram__bytes_write.sum, m = 127 case, 13.07 B "
                        "per unknown scaled to the launch's unknowns"),
 }
+# one metric text for both arms (the GPU solve and the CPU oracle), so that their lines compare
+METRIC = "unknown-iterations/s to relres<=1e-8"
 FP64_PEAK_TFLOPS = 1.259  # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (measured 1.20 at 1995 MHz)
 FP32_PEAK_TFLOPS = 80.6   # 128 FFMA/clk/SM x 152 SMs x 2.07 GHz (measured 69.8 at 1995 MHz)
 FP32_PEAK_TOPS = 40.28    # FP32 pipe: 128 instructions/clk/SM x 152 SMs x 2.07 GHz
@@ -327,8 +329,7 @@ def run_reference(args):
               "one P_alpha^{-1} apply by the paper's three steps, alpha = 1e-3) on the full "
               f"{prob.n}-unknown workload per step")
     line = {
-        "impl": "reference", "metric": "unknown-iterations/s to relres<=1e-8 (CPU oracle, "
-        "operator work per iteration)", "value": value, "unit": "unknown-iter/s",
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "unknown-iter/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -916,8 +917,7 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": "unknown-iterations/s to relres<=1e-8 (chosen form: FP32 preconditioner, "
-                      "FP64-accurate matvec (double-float on FP32 pipes), FP64 Lanczos/true residual)",
+            "metric": METRIC,
             "value": ch["value"], "unit": "unknown-iter/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ch["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32 (f32x2 matvec)",
@@ -944,8 +944,10 @@ def main():
             "roofline": roof,
             "kernels": [{k: (round(v, 5) if isinstance(v, float) else v) for k, v in kk.items()}
                         for kk in kern],
-            "kernels_plain_f64": {k: [int(v[2]), round(v[3], 4)] for k, v in res["plain_f64"]["profile"].items()},
-            "kernels_tc": {k: [int(v[2]), round(v[3], 4)] for k, v in res["tc"]["profile"].items()},
+            # every form's kernel families: [active launches, their total ms]
+            "kernels_by_form": {key: {k: [int(v[2]), round(v[3], 4)]
+                                      for k, v in res[key]["profile"].items()}
+                                for key in res},
             "e2e": e2e,
             "gpu_launches": ch["launches"],
             "clocks": res["chosen"]["clocks"],

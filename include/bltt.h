@@ -104,8 +104,9 @@ typedef struct {
   int rebuild;       /* 1: rebuild the per-alpha preconditioner tables even if cached            */
   int matvec_arith;  /* BLTT_ARITH_*                                                             */
   int no_graph;      /* 1: launch every kernel directly; 0: capture sync_every (rounded up to even)
-                        iterations in a CUDA graph, cached per handle, and replay it (used when the
-                        handle's stream is not the legacy stream and profiling is off)            */
+                        iterations in a CUDA graph, cached per handle, and replay it whenever the
+                        handle's stream is not the legacy stream (which cannot be captured); with
+                        profiling on, the graph carries event-record nodes around each kernel    */
   int single_block;  /* 1: run the whole solve (entry transform, every iteration, exit transform)
                         in one kernel launch of one thread block, for problems whose every phase
                         is one FFT tile (e.g. N = 64, m = 63); DST basis, the FFT product, device
@@ -296,15 +297,16 @@ int bltt_profile_read(bltt_handle h, bltt_kernel_stat* out, int max_entries);
 /* Relative true residual ||f - A u||_2 / ||f||_2 of a candidate solution u of A u = f (and, if
  * r_dev is not NULL, the residual vector r = f - A u), with neither a handle nor any allocation.
  * The paper has no counterpart: this entry point exists for callers that cannot allocate memory
- * at all, e.g. code running inside another framework's graph capture or under an allocator that
- * forbids new device allocations, or hosts with a fixed memory budget, which therefore cannot
- * call bltt_create (it allocates tables and workspace).  It calls no cudaMalloc, cudaFree,
+ * at all, e.g. code running under an allocator or memory pool that forbids new device
+ * allocations, or a host process with a fixed device-memory budget, which therefore cannot call
+ * bltt_create (it allocates tables and workspace).  It calls no cudaMalloc, cudaFree,
  * cudaMallocHost or allocating library routine.
  *   blocks, N, M: as for bltt_create (the Assumption 1 check is not made).  u_dev, f_dev,
  *   r_dev: caller-owned device vectors of N*M doubles; r_dev may be NULL and must not alias u or
- *   f.  cuda_stream: the stream to run on (NULL: legacy stream); the call synchronises it before
- *   returning.  relres_out: host double receiving the relative residual (the absolute norm when
- *   f = 0).  Arithmetic: FP64, with the same kernels as bltt_matvec.
+ *   f.  cuda_stream: the stream to run on (NULL: legacy stream).  The call copies its operator
+ *   tables from host memory on that stream and synchronises the stream before it returns, to
+ *   hand the residual to the host.  relres_out: host double receiving the relative residual (the
+ *   absolute norm when f = 0).  Arithmetic: FP64, with the same kernels as bltt_matvec.
  * Scratch: one file-scope device array of 2 MiB, loaded with the operator tables and the partial
  * sums on every call.  It is shared by every call in the process and keeps the last call's
  * contents; calls whose work overlaps on the GPU (other threads, other streams) race on it and
@@ -312,10 +314,11 @@ int bltt_profile_read(bltt_handle h, bltt_kernel_stat* out, int max_entries);
  * same call, so nothing needs clearing.  Set-up: the first call on each device (with that device
  * current) looks up the array's device address with cudaGetSymbolAddress; make that first call
  * before any stream capture.
- * Limits (else BLTT_ERR_UNSUPPORTED): the sizes of bltt_create; at most 131072 FFT tiles
- * (spatial modes / tile width); and blocks with more than 4 nonzero coefficients need
- * b = b0 e_0 (otherwise an N*M temporary would be needed).  Other errors: BLTT_ERR_INVALID_ARG,
- * BLTT_ERR_CUDA, BLTT_ERR_NUMERIC (non-finite residual). */
+ * Limits (else BLTT_ERR_UNSUPPORTED): the sizes of bltt_create (N and every m[ax]+1 powers of
+ * two, at most 2048); at most 131072 FFT tiles (spatial modes / tile width); and blocks with more
+ * than 4 nonzero coefficients need b = b0 e_0 (otherwise an N*M temporary would be needed).
+ * Other errors: BLTT_ERR_INVALID_ARG, BLTT_ERR_CUDA, BLTT_ERR_NUMERIC (a non-finite block
+ * coefficient or residual). */
 bltt_status bltt_residual_noalloc(const bltt_blocks* blocks, int N, long long M,
                                   const double* u_dev, const double* f_dev, double* r_dev,
                                   void* cuda_stream, double* relres_out);

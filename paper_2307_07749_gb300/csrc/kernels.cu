@@ -1,6 +1,7 @@
 // kernels.cu - sm_103a kernels of libbltt: DST-I along a spatial axis, the alpha-scaled time pass
 // of the ABAC preconditioner, the BLTT matvec (2N circulant embedding or direct taps), the
 // preconditioner set-up and the MINRES vector/scalar kernels.
+#include <atomic>
 #include <math.h>
 #include <algorithm>
 #include <type_traits>
@@ -1346,13 +1347,27 @@ static int grid_stream(long long n, int threads) {
   return (int)g;
 }
 
-template <class A> static cudaError_t ensure_smem_dst() {
-  static bool done = false;
-  if (done) return cudaSuccess;
-  cudaError_t e = set_smem(k_dst<A, false>, TileCfg<A>::CAP * sizeof(typename A::V));
-  if (e == cudaSuccess) e = set_smem(k_dst<A, true>, TileCfg<A>::CAP * sizeof(typename A::V));
-  if (e == cudaSuccess) done = true;
+// cudaFuncSetAttribute acts on the current device only, so each helper below records, per device
+// (bit d of a mask), that its attributes are set.  Setting them twice is harmless, so two threads
+// racing on a first call only repeat the work; devices beyond 63 set them on every call.
+template <class F> static cudaError_t once_per_device(std::atomic<unsigned long long>& mask, F&& f) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+  if (bit && (mask.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = f();
+  if (e == cudaSuccess && bit) mask.fetch_or(bit, std::memory_order_acq_rel);
   return e;
+}
+
+template <class A> static cudaError_t ensure_smem_dst() {
+  static std::atomic<unsigned long long> done{0};
+  return once_per_device(done, [] {
+    cudaError_t e = set_smem(k_dst<A, false>, TileCfg<A>::CAP * sizeof(typename A::V));
+    if (e == cudaSuccess) e = set_smem(k_dst<A, true>, TileCfg<A>::CAP * sizeof(typename A::V));
+    return e;
+  });
 }
 
 template <class A>
@@ -1376,19 +1391,14 @@ template <class A> constexpr size_t tp_stage_bytes(int n) {
              : 0;
 }
 template <class A, class Cfg = TileCfg<A>> static cudaError_t ensure_smem_tp() {
-  static bool done = false;
-  if (done) return cudaSuccess;
-  cudaError_t e = set_smem(k_timepass<A, Cfg>,
-                           Cfg::CAP * sizeof(typename A::V) + tp_stage_bytes<A>(kCap));
-  if (e == cudaSuccess) done = true;
-  return e;
+  static std::atomic<unsigned long long> done{0};
+  return once_per_device(done, [] {
+    return set_smem(k_timepass<A, Cfg>, Cfg::CAP * sizeof(typename A::V) + tp_stage_bytes<A>(kCap));
+  });
 }
 template <class A> static cudaError_t ensure_smem_conv() {
-  static bool done = false;
-  if (done) return cudaSuccess;
-  cudaError_t e = set_smem(k_conv<A>, TileCfg<A>::CAP * sizeof(typename A::V));
-  if (e == cudaSuccess) done = true;
-  return e;
+  static std::atomic<unsigned long long> done{0};
+  return once_per_device(done, [] { return set_smem(k_conv<A>, TileCfg<A>::CAP * sizeof(typename A::V)); });
 }
 
 cudaError_t prepare_kernel_attributes() {
@@ -1584,13 +1594,13 @@ cudaError_t launch_solve_one(const OneSolve& s, bool chosen, cudaStream_t st) {
   static_assert(kCap * sizeof(double2) == kCap * sizeof(float4) &&
                 kCap * sizeof(float4) == WideTileF::CAP * sizeof(float2), "one tile size");
   const size_t smem = kCap * sizeof(double2);
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<unsigned long long> attr{0};
+  cudaError_t ea = once_per_device(attr, [smem] {
     cudaError_t e = set_smem(k_solve_one<OneF64>, smem);
     if (e == cudaSuccess) e = set_smem(k_solve_one<OneChosen>, smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+    return e;
+  });
+  if (ea != cudaSuccess) return ea;
   if (chosen) k_solve_one<OneChosen><<<1, OneChosen::NT, smem, st>>>(s);
   else k_solve_one<OneF64><<<1, OneF64::NT, smem, st>>>(s);
   return cudaGetLastError();

@@ -123,7 +123,14 @@ extern "C" bltt_status bltt_residual_noalloc(const bltt_blocks* blocks, int N, l
     prodm *= sp.m[ax];
   }
   if (prodm != M) return na_fail(BLTT_ERR_INVALID_ARG, "M != prod(m)");
+  // the sizes bltt_create accepts: every FFT (2N along time, 2(m+1) along each axis) fits a tile
   if (!pow2(N) || 2 * N > kCap) return na_fail(BLTT_ERR_UNSUPPORTED, "N must be a power of two <= 2048");
+  for (int ax = 0; ax < sp.ndim; ++ax)
+    if (!pow2(sp.m[ax] + 1) || 2 * (sp.m[ax] + 1) > kCap)
+      return na_fail(BLTT_ERR_UNSUPPORTED, "m+1 must be a power of two <= 2048");
+  for (int k = 0; k < N; ++k)
+    if (!std::isfinite(blocks->a[k]) || !std::isfinite(blocks->b[k]))
+      return na_fail(BLTT_ERR_NUMERIC, "non-finite block coefficient");
   if (r_dev && (r_dev == u_dev || r_dev == f_dev))
     return na_fail(BLTT_ERR_INVALID_ARG, "r must not alias u or f");
 

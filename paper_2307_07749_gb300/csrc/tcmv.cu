@@ -27,6 +27,7 @@
 // issues the MMAs, warps 2..17 read the accumulators (tcgen05.ld) and run the epilogue.  Every
 // wait on an mbarrier is bounded (about one second); a block that gives up sets *tc_err,
 // writes NaN partials, lets its copies and MMAs finish and frees its TMEM.
+#include <atomic>
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -484,7 +485,10 @@ __global__ void __launch_bounds__(kThreadsMv, 1) k_tc_mv(const MvParams p) {
   }
 }
 
-int g_num_sms = 0;
+// SM count of each device on which k_tc_mv's shared-memory attribute has been set (0: not yet);
+// cudaFuncSetAttribute acts on the current device only
+constexpr int kTcMaxDevices = 64;
+std::atomic<int> g_num_sms[kTcMaxDevices];
 
 }  // namespace
 
@@ -538,14 +542,19 @@ cudaError_t launch_tc_product(const OpTables& op, int spectral, const double* x,
                               int* nparts, const int* phase, cudaStream_t st) {
   if (!tc_eligible(op) || !op.tc_hank || !op.tc_xd || !op.tc_xe || !op.tc_err)
     return cudaErrorInvalidValue;
-  if (g_num_sms == 0) {
-    int dev = 0, n = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  int dev = 0;
+  cudaError_t ed = cudaGetDevice(&dev);
+  if (ed != cudaSuccess) return ed;
+  if (dev < 0 || dev >= kTcMaxDevices) return cudaErrorInvalidDevice;
+  int num_sms = g_num_sms[dev].load(std::memory_order_acquire);
+  if (num_sms == 0) {
+    int n = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_tc_mv, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMv);
     if (e != cudaSuccess) return e;
-    g_num_sms = n;
+    g_num_sms[dev].store(n, std::memory_order_release);
+    num_sms = n;
   }
   const int nstrips = tc_strips(op.M);
   MvParams prm;
@@ -560,7 +569,7 @@ cudaError_t launch_tc_product(const OpTables& op, int spectral, const double* x,
   prm.nstrips = nstrips;
   prm.NB = op.N / kCols;
   prm.nunits = nstrips * prm.NB;
-  const int grid = prm.nunits < g_num_sms ? prm.nunits : g_num_sms;
+  const int grid = prm.nunits < num_sms ? prm.nunits : num_sms;
   if (nparts) *nparts = grid;
   k_tc_mv<<<grid, kThreadsMv, kSmemMv, st>>>(prm);
   return cudaGetLastError();
