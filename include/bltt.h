@@ -235,8 +235,9 @@ bltt_status bltt_minres_solve_host(bltt_handle h, const double* f_host, double a
  *   nsys systems sys[s] (host structs as for bltt_create; N and m[ax]+1 powers of two) with
  *   nrhs[s] >= 1 right-hand sides each; f_dev / u_dev: host arrays of sum(nrhs) device pointers
  *   (system-major), each a vector of that system's N*M doubles, u not aliasing f.
- *   alpha: host array of nsys values in (0,1], or NULL for the default rule (1e-8; 1e-3 for the
- *   FP32 preconditioner).  opts: precision and matvec_arith as for bltt_minres_solve_ex (basis
+ *   alpha: host array of nsys values in (0,1], or NULL for the default rule (1e-8; 1e-2 for the
+ *   FP32 preconditioner and 1e-6 for the double-float one, where their rounding costs no
+ *   iteration against FP64 at the same alpha).  opts: precision and matvec_arith as for bltt_minres_solve_ex (basis
  *   is always the DST basis); may be NULL.  info: host array of sum(nrhs) entries or NULL;
  *   relres_true is the true residual of the DST-basis system (equal to the physical one up to
  *   the rounding of the exit DST).

@@ -174,7 +174,10 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
     if (r != BLTT_OK) { cleanup(); return r; }
     bltt_set_stream(H[s], st);
     bltt_set_matvec_arith(H[s], arith ? BLTT_ARITH_F32X2 : BLTT_ARITH_F64);
-    alph[s] = alpha ? alpha[s] : (prec == 32 ? 1e-3 : 1e-8);
+    // default alpha per preconditioner arithmetic: the paper's 1e-8 in FP64; raised where the
+    // rounding, amplified by kappa(D_alpha) = alpha^{-(N-1)/N}, would cost iterations (1e-2 for
+    // FP32, 1e-6 for double-float)
+    alph[s] = alpha ? alpha[s] : (prec == PREC_F32 ? 1e-2 : prec == PREC_DF ? 1e-6 : 1e-8);
     if (!(alph[s] > 0.0 && alph[s] <= 1.0)) { cleanup(); return BLTT_ERR_INVALID_ARG; }
     r = ctx_prepare(H[s], alph[s], prec);
     if (r != BLTT_OK) { cleanup(); return r; }

@@ -8,6 +8,14 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def rel_max(a, b):
+    """max_i |a_i - b_i| / max_i |b_i|: the max-norm relative error.  Beside the 2-norm one it
+    catches a wrong block of entries (a ragged tail, one tile) too small to move the 2-norm."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), 1e-300))
+
+
 def precond_tol(N, alpha, prec=64):
     """Tolerance for P_alpha^{-1} between two independent implementations (prec 96: double-float).
 

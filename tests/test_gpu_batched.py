@@ -52,8 +52,9 @@ def test_batched_matches_oracle(B, form):
             u = to_host(ud[s][r])
             assert info["relres_true"] <= 1e-8
             assert rel(O.bltt_matvec(p, u), f) <= 1e-8
-            slack = 1 if form["precision"] == 64 else 4
-            assert abs(info["iters"] - ref["iters"]) <= slack, (s, r, info["iters"], ref["iters"])
+            # every form within one iteration of the FP64 oracle at the same alpha (N <= 128
+            # here, where neither the FP32 nor the double-float rounding costs an iteration)
+            assert abs(info["iters"] - ref["iters"]) <= 1, (s, r, info["iters"], ref["iters"])
             assert rel(u, ref["x"]) <= 1e-6
 
 
