@@ -322,21 +322,35 @@ __device__ __forceinline__ typename A::V w16() {
   else return A::cst(-K::C, g * K::S, -K::Ch, -K::Cl, g * K::Sh, g * K::Sl);   // E == 9
 }
 
-template <class A, bool INV>
+// NR: the second level is not renormalised either (its outputs only feed further sums or
+// products inside the same butterfly).  HALF: only X_0 and X_1 are formed (x2, x3 are left
+// unchanged), for a last pass whose upper outputs are not needed.
+template <class A, bool INV, bool NR = false, bool HALF = false>
 __device__ __forceinline__ void dft4(typename A::V& x0, typename A::V& x1, typename A::V& x2,
                                      typename A::V& x3) {
   using V = typename A::V;
   // the first level's sums are not renormalised: they only feed the second level
   const V t0 = A::add_nr(x0, x2), t1 = A::sub_nr(x0, x2), t2 = A::add_nr(x1, x3);
   const V t3 = A::template rot<INV>(A::sub_nr(x1, x3));
-  x0 = A::add(t0, t2);
-  x1 = A::add(t1, t3);
-  x2 = A::sub(t0, t2);
-  x3 = A::sub(t1, t3);
+  if constexpr (NR) {
+    x0 = A::add_nr(t0, t2);
+    x1 = A::add_nr(t1, t3);
+    if constexpr (!HALF) {
+      x2 = A::sub_nr(t0, t2);
+      x3 = A::sub_nr(t1, t3);
+    }
+  } else {
+    x0 = A::add(t0, t2);
+    x1 = A::add(t1, t3);
+    if constexpr (!HALF) {
+      x2 = A::sub(t0, t2);
+      x3 = A::sub(t1, t3);
+    }
+  }
 }
 
-// in place; on return X_{c' + 4d} is in v[4c' + d]
-template <class A, bool INV>
+// in place; on return X_{c' + 4d} is in v[4c' + d] (HALF: only d < 2 is formed)
+template <class A, bool INV, bool HALF = false>
 __device__ __forceinline__ void dft16(typename A::V (&v)[16]) {
 #pragma unroll
   for (int b = 0; b < 4; ++b) dft4<A, INV>(v[b], v[b + 4], v[b + 8], v[b + 12]);
@@ -350,17 +364,18 @@ __device__ __forceinline__ void dft16(typename A::V (&v)[16]) {
   v[14] = A::mul_nr(v[14], w16<A, 6, INV>());
   v[15] = A::mul_nr(v[15], w16<A, 9, INV>());
 #pragma unroll
-  for (int c = 0; c < 4; ++c) dft4<A, INV>(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+  for (int c = 0; c < 4; ++c) dft4<A, INV, false, HALF>(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
 }
 
 // Radix-8 butterfly.  With r = b + 2c and q = c' + 4d (b, d < 2; c, c' < 4),
 //   X_q = sum_b w2^{b d} w8^{b c'} sum_c w4^{c c'} x_{b+2c}:
 // two length-4 DFTs over c, the twiddles w8^{c'} on the b = 1 half, four length-2 DFTs over b.
-// In place; on return X_{c' + 4d} is in v[2c' + d].
-template <class A, bool INV>
+// In place; on return X_{c' + 4d} is in v[2c' + d] (HALF: only d = 0 is formed).  The length-4
+// DFTs' outputs only feed the twiddles and the last level, so only that level renormalises.
+template <class A, bool INV, bool HALF = false>
 __device__ __forceinline__ void dft8(typename A::V (&v)[8]) {
-  dft4<A, INV>(v[0], v[2], v[4], v[6]);
-  dft4<A, INV>(v[1], v[3], v[5], v[7]);
+  dft4<A, INV, true>(v[0], v[2], v[4], v[6]);
+  dft4<A, INV, true>(v[1], v[3], v[5], v[7]);
   v[3] = A::mul_nr(v[3], w16<A, 2, INV>());   // w8^1 = w16^2
   v[5] = A::template rot<INV>(v[5]);          // w8^2 = -i (forward)
   v[7] = A::mul_nr(v[7], w16<A, 6, INV>());   // w8^3 = w16^6
@@ -368,7 +383,7 @@ __device__ __forceinline__ void dft8(typename A::V (&v)[8]) {
   for (int c = 0; c < 4; ++c) {
     const typename A::V a = v[2 * c], b = v[2 * c + 1];
     v[2 * c] = A::add(a, b);
-    v[2 * c + 1] = A::sub(a, b);
+    if constexpr (!HALF) v[2 * c + 1] = A::sub(a, b);
   }
 }
 
@@ -392,10 +407,13 @@ __device__ __forceinline__ void dft8(typename A::V (&v)[8]) {
 // A pass of radix R with Ns outputs already combined: butterfly j (of L/R) reads x_{j + r L/R},
 // multiplies input r by w_L^{r k L/(R Ns)} (k = j mod Ns), transforms, and writes output q at
 // (j - k) R + k + q Ns.
+//
+// half_out: only the outputs X_k with k < L/2 are needed; a last pass of radix 8 or 16 then forms
+// and stores only those (the rows L/2.. keep whatever they held).
 template <class A, int NT, int CAP, bool INV, bool SWZ = false>
 __device__ __forceinline__ void fft_columns(typename A::V* buf, int L, int log2L, int log2NC,
                             const typename A::V* __restrict__ tw, bool skip_radix2 = false,
-                            int tw_shift = 0) {
+                            int tw_shift = 0, bool half_out = false) {
   using V = typename A::V;
   constexpr int IPT2 = (CAP / 2 + NT - 1) / NT;
   constexpr int IPT4 = (CAP / 4 + NT - 1) / NT;
@@ -508,10 +526,17 @@ __device__ __forceinline__ void fft_columns(typename A::V* buf, int L, int log2L
               v[s][r] = INV ? A::mulc_nr(v[s][r], w) : A::mul_nr(v[s][r], w);
             }
           }
-          dft8<A, INV>(v[s]);
           const int o = (j - k) * 8 + k;
+          if (half_out && log2Ns + 3 == log2L) {
+            // last pass: outputs q < 4 land in rows < L/2
+            dft8<A, INV, true>(v[s]);
 #pragma unroll
-          for (int q = 0; q < 8; ++q) buf[at(o + q * Ns, c)] = v[s][2 * (q & 3) + (q >> 2)];
+            for (int q = 0; q < 4; ++q) buf[at(o + q * Ns, c)] = v[s][2 * q];
+          } else {
+            dft8<A, INV>(v[s]);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) buf[at(o + q * Ns, c)] = v[s][2 * (q & 3) + (q >> 2)];
+          }
         }
       }
       __syncthreads();
@@ -548,10 +573,17 @@ __device__ __forceinline__ void fft_columns(typename A::V* buf, int L, int log2L
             v[s][r] = INV ? A::mulc_nr(v[s][r], w) : A::mul_nr(v[s][r], w);
           }
         }
-        dft16<A, INV>(v[s]);
         const int o = (j - k) * 16 + k;
+        if (half_out && log2Ns + 4 == log2L) {
+          // last pass: outputs q < 8 land in rows < L/2
+          dft16<A, INV, true>(v[s]);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) buf[at(o + q * Ns, c)] = v[s][4 * (q & 3) + (q >> 2)];
+          for (int q = 0; q < 8; ++q) buf[at(o + q * Ns, c)] = v[s][4 * (q & 3) + (q >> 2)];
+        } else {
+          dft16<A, INV>(v[s]);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) buf[at(o + q * Ns, c)] = v[s][4 * (q & 3) + (q >> 2)];
+        }
       }
     }
     __syncthreads();

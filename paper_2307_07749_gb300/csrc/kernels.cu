@@ -599,6 +599,7 @@ __device__ __forceinline__ void conv_tile(const OpTables& op, int spectral, int 
   V* buf = reinterpret_cast<V*>(smem_raw);
   __shared__ double red[32];
   __shared__ MT s_mu[kMaxCols];
+  __shared__ double s_kmu[kMaxCols];
   __shared__ int s_nb[kMaxCols];
   const int N = op.N, L = 2 * N, NC = 1 << log2NC, W = 2 * NC, log2W = log2NC + 1;
   const long long M = op.M;
@@ -606,12 +607,16 @@ __device__ __forceinline__ void conv_tile(const OpTables& op, int spectral, int 
   const double s = xscale ? *xscale : 1.0;
   const bool genb = (op.b_kind == 1);
   const bool extra_st = !spectral && which == 0 && st_src != nullptr;
+  // DST basis with b = b0 e_0: every mode's spectrum is FFT_2N([a;0]) plus the constant b0 mu_i,
+  // so the packed pair is multiplied by the common spectrum (no split) and the b0 mu_i s x term
+  // is added in the time domain at read-out
+  const bool common = spectral && !genb;
   for (int c = threadIdx.x; c < W; c += NT) {
     const long long i = g0 + c;
     double mu = 0.0;
     int nb = 0;
     if (i < M) {
-      if (spectral) mu = genb ? mode_mu(op, i) : op.b0 * mode_mu(op, i) / (4.0 * N);
+      if (spectral) mu = genb ? mode_mu(op, i) : op.b0 * mode_mu(op, i);
       long long r = i;
       for (int ax = 0; ax < op.d; ++ax) {
         const long long q = r / op.m[ax];
@@ -622,6 +627,7 @@ __device__ __forceinline__ void conv_tile(const OpTables& op, int spectral, int 
       }
     }
     s_mu[c] = MuT<A>::make(mu);
+    s_kmu[c] = mu * s;
     s_nb[c] = nb;
   }
   const typename A::Sc ssc = A::make_sc(s);
@@ -654,7 +660,7 @@ __device__ __forceinline__ void conv_tile(const OpTables& op, int spectral, int 
   __syncthreads();
   const V* __restrict__ tw = ConvTables<A>::tw(op);
   fft_columns<A, NT, CAP, false>(buf, L, op.log2N + 1, log2NC, tw, odd);
-  if (!spectral) {
+  if (!spectral || common) {
     const V* __restrict__ H = ConvTables<A>::H(op, which);
     for (int e = threadIdx.x; e < L * NC; e += NT) {
       const int k = e >> log2NC;
@@ -669,8 +675,8 @@ __device__ __forceinline__ void conv_tile(const OpTables& op, int spectral, int 
     for (int it = threadIdx.x; it < items; it += NT) {
       const int cc = it & (NC - 1), k = it >> log2NC;
       const V a_ = HA[k], b_ = HB[k];
-      const V Ha = ConvTables<A>::Hmode(a_, b_, s_mu[2 * cc], genb);
-      const V Hb = ConvTables<A>::Hmode(a_, b_, s_mu[2 * cc + 1], genb);
+      const V Ha = ConvTables<A>::Hmode(a_, b_, s_mu[2 * cc], true);
+      const V Hb = ConvTables<A>::Hmode(a_, b_, s_mu[2 * cc + 1], true);
       const int kb = (L - k) & (L - 1);
       const V Av = buf[k * NC + cc], Bc = A::conj(buf[kb * NC + cc]);
       const V U1 = A::mul(Ha, A::add(Av, Bc));
@@ -680,68 +686,116 @@ __device__ __forceinline__ void conv_tile(const OpTables& op, int spectral, int 
     }
   }
   __syncthreads();
-  fft_columns<A, NT, CAP, true>(buf, L, op.log2N + 1, log2NC, tw);
+  // only the first N of the 2N outputs are kept: the last pass skips the others
+  fft_columns<A, NT, CAP, true>(buf, L, op.log2N + 1, log2NC, tw, false, 0, true);
   double acc = 0.0;
-  const double st_coef = (op.b_kind == 0) ? op.b0 * s : 1.0;
-  const long long s1 = op.m[0], s2 = (long long)op.m[0] * op.m[1];
-  // read-out in batches: the global operand of each output (x for the dot product, or the
-  // right-hand side) is loaded for a whole batch before its first use
-  for (int e0 = threadIdx.x; e0 < total; e0 += kBatch * NT) {
-    double pre[kBatch];
+  if (common) {
+    // read-out of the time pairs (t, N-1-t) of one column: the two x values serve both the
+    // b0 mu_i s x term (at t) and the dot-product partner (at the flipped index)
+    constexpr int PB = kBatch / 2;
+    const int half_total = (N >> 1) * W;
+    for (int e0 = threadIdx.x; e0 < half_total; e0 += PB * NT) {
+      double xa[PB], xb[PB], ra[PB], rb[PB];
 #pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      const int e = e0 + u * NT;
-      const int t = e >> log2W, c = e & (W - 1);
-      pre[u] = 0.0;
-      if (e < total && g0 + c < M) {
-        const int to = flip ? (N - 1 - t) : t;
-        const long long idx = (long long)to * M + g0 + c;
-        if (mode != MV_STORE) pre[u] = __ldcs(rhs + idx);
-        else if (partials) pre[u] = __ldcs(x + idx);
+      for (int u = 0; u < PB; ++u) {
+        const int e = e0 + u * NT;
+        const int t = e >> log2W, c = e & (W - 1);
+        xa[u] = 0.0; xb[u] = 0.0; ra[u] = 0.0; rb[u] = 0.0;
+        if (e < half_total && g0 + c < M) {
+          const long long ia = (long long)t * M + g0 + c, ib = (long long)(N - 1 - t) * M + g0 + c;
+          xa[u] = __ldcs(x + ia);
+          xb[u] = __ldcs(x + ib);
+          if (mode != MV_STORE) { ra[u] = __ldcs(rhs + ia); rb[u] = __ldcs(rhs + ib); }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < PB; ++u) {
+        const int e = e0 + u * NT;
+        const int t = e >> log2W, c = e & (W - 1);
+        if (e >= half_total || g0 + c >= M) continue;
+        const int t2 = N - 1 - t;
+        const double k = s_kmu[c];
+        // (A z)_t and (A z)_{N-1-t}, z = s x
+        const double va = fma(k, xa[u], A::part(buf[t * NC + (c >> 1)], c & 1));
+        const double vb = fma(k, xb[u], A::part(buf[t2 * NC + (c >> 1)], c & 1));
+        // output time of (A z)_t is N-1-t with the flip
+        const long long ia = (long long)(flip ? t2 : t) * M + g0 + c;
+        const long long ib = (long long)(flip ? t : t2) * M + g0 + c;
+        if (mode == MV_STORE) {
+          if (y) { y[ia] = va; y[ib] = vb; }
+          // partner of the output at index ia is x there: x_{t2} with the flip, else x_t
+          acc = fma(va, flip ? xb[u] : xa[u], acc);
+          acc = fma(vb, flip ? xa[u] : xb[u], acc);
+        } else {
+          const double r1 = (flip ? rb[u] : ra[u]) - va, r2 = (flip ? ra[u] : rb[u]) - vb;
+          if (y) { y[ia] = r1; y[ib] = r2; }
+          acc = fma(r1, r1, acc);
+          acc = fma(r2, r2, acc);
+        }
       }
     }
+  } else {
+    const double st_coef = (op.b_kind == 0) ? op.b0 * s : 1.0;
+    const long long s1 = op.m[0], s2 = (long long)op.m[0] * op.m[1];
+    // read-out in batches: the global operand of each output (x for the dot product, or the
+    // right-hand side) is loaded for a whole batch before its first use
+    for (int e0 = threadIdx.x; e0 < total; e0 += kBatch * NT) {
+      double pre[kBatch];
 #pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      const int e = e0 + u * NT;
-      const int t = e >> log2W, c = e & (W - 1);
-      const long long i = g0 + c;
-      if (e >= total || i >= M) continue;
-      double val = A::part(buf[t * NC + (c >> 1)], c & 1);
-      if (extra_st && op.kf[0]) {
-        int ix, iy, iz;
-        mode_coords(op, i, ix, iy, iz);
-        val = fma(st_coef, stencil_faces(op, st_src + (long long)t * M, i, ix, iy, iz), val);
-      } else if (extra_st) {
-        const double* xt = st_src + (long long)t * M;
-        const int nb = s_nb[c];
-        const double xi2 = 2.0 * xt[i];
-        double sx = xi2;
-        if (nb & 1) sx -= xt[i - 1];
-        if (nb & 2) sx -= xt[i + 1];
-        double lap = sx * op.h2inv[0];
-        if (op.d > 1) {
-          double sy = xi2;
-          if (nb & 4) sy -= xt[i - s1];
-          if (nb & 8) sy -= xt[i + s1];
-          lap = fma(sy, op.h2inv[1], lap);
-          if (op.d > 2) {
-            double sz = xi2;
-            if (nb & 16) sz -= xt[i - s2];
-            if (nb & 32) sz -= xt[i + s2];
-            lap = fma(sz, op.h2inv[2], lap);
-          }
+      for (int u = 0; u < kBatch; ++u) {
+        const int e = e0 + u * NT;
+        const int t = e >> log2W, c = e & (W - 1);
+        pre[u] = 0.0;
+        if (e < total && g0 + c < M) {
+          const int to = flip ? (N - 1 - t) : t;
+          const long long idx = (long long)to * M + g0 + c;
+          if (mode != MV_STORE) pre[u] = __ldcs(rhs + idx);
+          else if (partials) pre[u] = __ldcs(x + idx);
         }
-        val = fma(st_coef, lap, val);
       }
-      const int to = flip ? (N - 1 - t) : t;
-      const long long idx = (long long)to * M + i;
-      if (mode == MV_STORE) {
-        y[idx] = val;
-        acc = fma(val, pre[u], acc);     // times s once per block below
-      } else {
-        const double r = pre[u] - val;
-        if (y) y[idx] = r;
-        acc = fma(r, r, acc);
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int e = e0 + u * NT;
+        const int t = e >> log2W, c = e & (W - 1);
+        const long long i = g0 + c;
+        if (e >= total || i >= M) continue;
+        double val = A::part(buf[t * NC + (c >> 1)], c & 1);
+        if (extra_st && op.kf[0]) {
+          int ix, iy, iz;
+          mode_coords(op, i, ix, iy, iz);
+          val = fma(st_coef, stencil_faces(op, st_src + (long long)t * M, i, ix, iy, iz), val);
+        } else if (extra_st) {
+          const double* xt = st_src + (long long)t * M;
+          const int nb = s_nb[c];
+          const double xi2 = 2.0 * xt[i];
+          double sx = xi2;
+          if (nb & 1) sx -= xt[i - 1];
+          if (nb & 2) sx -= xt[i + 1];
+          double lap = sx * op.h2inv[0];
+          if (op.d > 1) {
+            double sy = xi2;
+            if (nb & 4) sy -= xt[i - s1];
+            if (nb & 8) sy -= xt[i + s1];
+            lap = fma(sy, op.h2inv[1], lap);
+            if (op.d > 2) {
+              double sz = xi2;
+              if (nb & 16) sz -= xt[i - s2];
+              if (nb & 32) sz -= xt[i + s2];
+              lap = fma(sz, op.h2inv[2], lap);
+            }
+          }
+          val = fma(st_coef, lap, val);
+        }
+        const int to = flip ? (N - 1 - t) : t;
+        const long long idx = (long long)to * M + i;
+        if (mode == MV_STORE) {
+          y[idx] = val;
+          acc = fma(val, pre[u], acc);     // times s once per block below
+        } else {
+          const double r = pre[u] - val;
+          if (y) y[idx] = r;
+          acc = fma(r, r, acc);
+        }
       }
     }
   }

@@ -158,3 +158,28 @@ def test_heat3d_solve_sampled_residual(B, heat3d, form):
     r2 = sum((f[n * prob.M + i] - bltt_matvec_entry(prob, uh, n, i)) ** 2 for n, i in zip(ns, is_))
     est = np.sqrt(r2 / len(ns) * prob.n) / np.linalg.norm(f)
     assert est <= 3e-8, est
+
+
+@pytest.fixture(scope="module")
+def heat3d_m63(B):
+    # the 3-D backward-Euler heat family at m = 63 (65 M unknowns): small enough for the oracle's
+    # whole solves, whose counts are stored
+    prob = heat_bdf_problem(3, 63, 256)
+    f = rhs_smoothed_field(prob.N, 3, prob.m, 3)
+    return prob, f, B.Solver(prob)
+
+
+# On this family the FP32 preconditioner costs no iteration at alpha = 1e-3 or 1e-2 (N = 256:
+# kappa(D_alpha) = alpha^{-255/256}), and the double-float one none at alpha = 1e-6.
+@pytest.mark.parametrize("form", [
+    dict(alpha=1e-2, precision=32, basis=1, matvec_arith=2),
+    dict(alpha=1e-3, precision=32, basis=1, matvec_arith=2),
+    dict(alpha=1e-6, precision=96, basis=1, matvec_arith=2),
+    dict(alpha=1e-8, precision=64, basis=1, matvec_arith=1),
+], ids=["f32_a1e-2", "f32_a1e-3", "f32x2_a1e-6", "f64_a1e-8"])
+def test_heat3d_m63_form_iterations_vs_stored_oracle(B, heat3d_m63, form):
+    prob, f, s = heat3d_m63
+    u, info = s.solve(to_dev(f), tol=1e-8, maxit=100, rebuild=True, **form)
+    assert info["status"] == 0, info
+    assert info["relres_true"] <= 1e-8
+    assert info["iters"] == oracle_count("heat3d_bdf_N256_m63", form["alpha"]), info["iters"]
