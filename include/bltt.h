@@ -170,6 +170,30 @@ bltt_status bltt_set_variable_coefficient(bltt_handle h, const double* const* fa
  * (BLTT_ERR_UNSUPPORTED).  A later call replaces K. */
 bltt_status bltt_set_dense_operator(bltt_handle h, const double* K);
 
+/* General commuting symmetric blocks (Assumption 1 (i); Sec. 3): the blocks share one
+ * orthonormal eigenbasis U, A_(k) = U diag(lam_k) U^T, and need not be a_k I + b_k L or
+ * functions of one operator.  The preconditioner of Sec. 5.1 then applies with U in place of the
+ * DST-I and each mode's own eigenvalue sequence lam_i^(k) in place of a_k + b_k mu_i.
+ *   U (host): M x M, row-major, column i the eigenvector of mode i; its columns must be
+ *     orthonormal (probed with two fixed vectors: ||U^T U x - x|| <= 1e-10 ||x||, else
+ *     BLTT_ERR_INVALID_ARG).  lam (host): N*M values, lam[k*M + i] the eigenvalue of A_(k) on
+ *     column i of U.  Both finite; M <= 8192.
+ * Assumption 1 (ii) is checked on lam: min_i (lam_i^(0) - sum_{k>=1} |lam_i^(k)|) > 0, else
+ * BLTT_ERR_ASSUMPTION (the handle then keeps its previous operator).  From then on the handle's
+ * blocks are these: the a, b given to bltt_create are no longer used (any that pass its check
+ * will do, e.g. a = e_0, b = 0), but M = prod(m) and N still hold.
+ * Arithmetic: the matvec is the 2N-embedding FFT product with a per-mode spectrum
+ * FFT_2N([lam_i; 0]) (tables of (N+1) M complex values, FP64 and double-float, built on the
+ * host here); the preconditioner's per-(frequency, mode) tables lambda^{-1/2}/(2N) of
+ * eq. hatcalphaieigvaldef are built on the host for each new alpha (one FFT of length N per
+ * mode, FP64, double-float and FP32 copies of (N/2+1) M entries).  Solves run in U's basis
+ * (AUTO and SPECTRAL; PHYSICAL gives BLTT_ERR_UNSUPPORTED) with one GEMM in and one out and the
+ * true residual checked there, as after bltt_set_dense_operator; bltt_matvec and
+ * bltt_precond_apply take and return physical vectors.  Not with bltt_set_variable_coefficient,
+ * the tensor-core product or the single-block solve (BLTT_ERR_UNSUPPORTED).  A later call, or
+ * bltt_set_dense_operator, replaces the blocks. */
+bltt_status bltt_set_block_spectra(bltt_handle h, const double* U, const double* lam);
+
 /* Issue all later work of h on `cuda_stream` (a cudaStream_t; NULL = legacy default stream). */
 bltt_status bltt_set_stream(bltt_handle h, void* cuda_stream);
 

@@ -8,7 +8,9 @@ Everything here is plain, slow and written to be checked against the paper by ey
 
 * ``operators``  - the BLTT operator A (eq. amatdef), the time reversal Y (Sec. 2), the Laplacian,
                    the DST-I matrix U and the eigenvalues of the blocks (Sec. 3), all from their
-                   definitions; dense assembly for tiny sizes.
+                   definitions; dense assembly for tiny sizes.  General commuting blocks given
+                   as matrices (Assumption 1 (i)) get their common eigenbasis from one generic
+                   combination of the blocks and their block sum as written.
 * ``precond``    - the ABAC preconditioner P_alpha = |C_alpha| (Defs. 2-3, eqs. calphaabsdef,
                    precdef): a dense route (C_alpha assembled, principal square root by a Schur
                    method) and the paper's three-step structured route (Sec. 5.1).

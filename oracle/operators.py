@@ -67,6 +67,30 @@ def dense_eigh(prob):
     return c
 
 
+def blocks_of(prob):
+    """The blocks A_(k), k = 0..N-1, as an (N, M, M) array when the problem gives them as dense
+    symmetric matrices (prob.meta["blocks"]: commuting blocks in general, Assumption 1 (i)),
+    else None."""
+    B = prob.meta.get("blocks")
+    return None if B is None else np.asarray(B, dtype=np.float64)
+
+
+def commuting_eigh(prob):
+    """Common orthonormal eigenvectors U of commuting symmetric blocks (Assumption 1 (i), Sec. 3):
+    the eigenvectors of one generic combination S = sum_k r_k A_(k) (numpy's symmetric
+    eigensolver as the step).  Commuting symmetric matrices are simultaneously diagonalisable,
+    and when S has simple eigenvalues its eigenvectors diagonalise every A_(k).  The weights r_k
+    are fixed draws from default_rng(20230717).  Cached on the problem."""
+    U = prob.meta.get("_ceigh")
+    if U is None:
+        B = blocks_of(prob)
+        r = np.random.default_rng(20230717).standard_normal(B.shape[0])
+        S = np.tensordot(r, B, axes=(0, 0))
+        U = np.linalg.eigh(0.5 * (S + S.T))[1]
+        prob.meta["_ceigh"] = U
+    return U
+
+
 def laplacian(prob) -> sp.csr_matrix:
     """L = -Delta_h on the tensor grid, lexicographic order with x fastest (Sec. 5.2); L_a when
     the problem carries a variable coefficient (prob.meta["faces"], see laplacian_variable); the
@@ -124,8 +148,8 @@ def apply_U(prob, V: np.ndarray, transpose: bool = False) -> np.ndarray:
     dense operator K, U holds the eigenvectors of K as columns (dense_eigh) and the two differ.
     Used for Steps 1 (U^T) and 3 (U) of the preconditioner solve (Sec. 5.1).
     """
-    if prob.meta.get("K") is not None:
-        U = dense_eigh(prob)[1]
+    if prob.meta.get("K") is not None or prob.meta.get("blocks") is not None:
+        U = dense_eigh(prob)[1] if prob.meta.get("K") is not None else commuting_eigh(prob)
         X = np.asarray(V, dtype=np.float64)
         return X @ U if transpose else X @ U.T        # rows are time slices
     ms = list(prob.m)
@@ -139,12 +163,22 @@ def apply_U(prob, V: np.ndarray, transpose: bool = False) -> np.ndarray:
 
 
 def block_eigenvalues(prob) -> np.ndarray:
-    """lambda_i^(k) = a_k + b_k mu_i, the eigenvalues of A_(k) = U Lambda_k U^T (Sec. 3).
+    """lambda_i^(k) = a_k + b_k mu_i, the eigenvalues of A_(k) = U Lambda_k U^T (Sec. 3); for
+    general commuting blocks (prob.meta["blocks"]) u_i^T A_(k) u_i with U = commuting_eigh.
 
     Returns an (N, M) array: row k holds the diagonal of Lambda_k.  For a variable-coefficient
     problem these are the eigenvalues of the mean-coefficient blocks a_k I + abar b_k L (eq.
     meancoeffheateqtsmat, abar = prob.meta["abar"]), from which the preconditioner is built.
     """
+    B = blocks_of(prob)
+    if B is not None:
+        # general commuting blocks: lambda_i^(k) = u_i^T A_(k) u_i in the common eigenbasis
+        lam = prob.meta.get("_clam")
+        if lam is None:
+            U = commuting_eigh(prob)
+            lam = np.stack([np.sum(U * (B[k] @ U), axis=0) for k in range(B.shape[0])])
+            prob.meta["_clam"] = lam
+        return lam
     mu = laplacian_eigenvalues(prob)
     b = prob.b * float(prob.meta.get("abar", 1.0)) if prob.meta.get("faces") is not None else prob.b
     return prob.a[:, None] + b[:, None] * mu[None, :]
@@ -162,13 +196,23 @@ def assumption_margin(prob) -> float:
 def bltt_matvec(prob, z: np.ndarray, flip: bool = False) -> np.ndarray:
     """y = A z (or Y A z when flip), A the BLTT matrix of eq. amatdef, computed directly.
 
-    Block row n of A z is sum_{k=0}^{n} A_(k) z_{n-k} = sum_k a_k z_{n-k} + L sum_k b_k z_{n-k}.
+    Block row n of A z is sum_{k=0}^{n} A_(k) z_{n-k} = sum_k a_k z_{n-k} + L sum_k b_k z_{n-k}
+    (or, for general blocks given as matrices, the block sum itself).
     With Z the (N, M) time-major array, the two time sums are the lower-triangular Toeplitz
     products T_a Z and T_b Z (O(N^2 M), a library matmul as the step), and L acts per time slice.
     Y = Y_N (x) I_M reverses the order of the time blocks (Sec. 2).
     """
     N, M = prob.N, prob.M
     Z = np.asarray(z, dtype=np.float64).reshape(N, M)
+    B = blocks_of(prob)
+    if B is not None:
+        # general blocks: block row n is sum_{k<=n} A_(k) z_{n-k}, one matrix product per k
+        Yv = np.zeros((N, M))
+        for k in range(N):
+            Yv[k:] += Z[:N - k] @ B[k].T
+        if flip:
+            Yv = Yv[::-1]
+        return np.ascontiguousarray(Yv).reshape(-1)
     Ta = toeplitz(prob.a, np.zeros(N))
     Yv = Ta @ Z
     if np.any(prob.b != 0):
@@ -189,6 +233,9 @@ def bltt_matvec_entry(prob, z: np.ndarray, n: int, i: int, flip: bool = False) -
     N, M = prob.N, prob.M
     Z = np.asarray(z).reshape(N, M)
     row = N - 1 - n if flip else n
+    B = blocks_of(prob)
+    if B is not None:
+        return float(sum(B[k][i] @ Z[row - k] for k in range(row + 1)))
     ms = list(prob.m)
     # neighbours of i in the Laplacian stencil
     coords = []
@@ -231,14 +278,19 @@ def bltt_matvec_entry(prob, z: np.ndarray, n: int, i: int, flip: bool = False) -
 def assemble_A(prob) -> np.ndarray:
     """Dense A of eq. amatdef: block (p, q) is A_(p-q) for p >= q, zero above (tiny sizes only)."""
     N, M = prob.N, prob.M
-    L = laplacian(prob).toarray()
-    I = np.eye(M)
     A = np.zeros((N * M, N * M))
     for p in range(N):
         for q in range(p + 1):
-            k = p - q
-            A[p * M:(p + 1) * M, q * M:(q + 1) * M] = prob.a[k] * I + prob.b[k] * L
+            A[p * M:(p + 1) * M, q * M:(q + 1) * M] = block_matrix(prob, p - q)
     return A
+
+
+def block_matrix(prob, k: int) -> np.ndarray:
+    """A_(k) as a dense M x M matrix: a_k I + b_k L, or the given block (eq. amatdef)."""
+    B = blocks_of(prob)
+    if B is not None:
+        return B[k]
+    return prob.a[k] * np.eye(prob.M) + prob.b[k] * laplacian(prob).toarray()
 
 
 def assemble_Y(N: int, M: int) -> np.ndarray:
@@ -252,12 +304,10 @@ def assemble_C_alpha(prob, alpha: float) -> np.ndarray:
     H_alpha^(k) = [[0, alpha I_k], [I_{N-k}, 0]] (Sec. 3).
     """
     N, M = prob.N, prob.M
-    L = laplacian(prob).toarray()
-    I = np.eye(M)
-    C = np.kron(np.eye(N), prob.a[0] * I + prob.b[0] * L)
+    C = np.kron(np.eye(N), block_matrix(prob, 0))
     for k in range(1, N):
         H = np.zeros((N, N))
         H[:k, N - k:] = alpha * np.eye(k)
         H[k:, :N - k] = np.eye(N - k)
-        C += np.kron(H, prob.a[k] * I + prob.b[k] * L)
+        C += np.kron(H, block_matrix(prob, k))
     return C

@@ -17,6 +17,17 @@ from .operators import laplacian
 
 def timestep_solve(prob, f: np.ndarray) -> np.ndarray:
     N, M = prob.N, prob.M
+    if prob.meta.get("blocks") is not None:
+        # general blocks given as matrices: a dense LU of A_(0), the block sum as written
+        from scipy.linalg import lu_factor, lu_solve
+        B = np.asarray(prob.meta["blocks"], dtype=np.float64)
+        lu0 = lu_factor(B[0])
+        F = np.asarray(f, dtype=np.float64).reshape(N, M)
+        U = np.zeros((N, M))
+        for n in range(N):
+            rhs = F[n] - sum((B[k] @ U[n - k] for k in range(1, n + 1)), np.zeros(M))
+            U[n] = lu_solve(lu0, rhs)
+        return U.reshape(-1)
     L = laplacian(prob)
     I = sp.identity(M, format="csc")
     A0 = (prob.a[0] * I + prob.b[0] * L).tocsc()

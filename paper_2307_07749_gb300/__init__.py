@@ -82,6 +82,8 @@ _SIGS = {
     "bltt_set_variable_coefficient": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.POINTER(ctypes.c_double)),
                                                       ctypes.c_double]),
     "bltt_set_dense_operator": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "bltt_set_block_spectra": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_double)]),
     "bltt_precond_apply": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, ctypes.c_int]),
     "bltt_minres_solve_ex": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                             ctypes.POINTER(bltt_solve_opts), _P,
@@ -208,6 +210,15 @@ def bltt_set_dense_operator(handle, K):
     k = np.ascontiguousarray(K, dtype=np.float64)
     _check(lib().bltt_set_dense_operator(handle, k.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
            handle)
+
+
+def bltt_set_block_spectra(handle, U, lam):
+    """General commuting blocks A_(k) = U diag(lam[k]) U^T: U (M x M, columns the eigenvectors),
+    lam (N x M, lam[k, i] the eigenvalue of A_(k) on column i)."""
+    u = np.ascontiguousarray(U, dtype=np.float64)
+    la = np.ascontiguousarray(lam, dtype=np.float64)
+    _check(lib().bltt_set_block_spectra(handle, u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        la.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), handle)
 
 
 def bltt_matvec(handle, x, y, flip=1):
@@ -374,14 +385,24 @@ class Solver:
         self.m = tuple(int(v) for v in prob.m)
         self.M = int(np.prod(self.m))
         self.n = self.N * self.M
-        self.handle = bltt_create(prob.a, prob.b, self.N, self.d, self.m, tuple(prob.h))
         meta = getattr(prob, "meta", None) or {}
+        spectra = meta.get("U") is not None and meta.get("lam") is not None
+        if spectra:
+            # general commuting blocks: the handle is created with the identity blocks (a = e_0,
+            # b = 0), which the blocks' eigenvalues then replace
+            a0 = np.zeros(self.N)
+            a0[0] = 1.0
+            self.handle = bltt_create(a0, np.zeros(self.N), self.N, self.d, self.m, tuple(prob.h))
+        else:
+            self.handle = bltt_create(prob.a, prob.b, self.N, self.d, self.m, tuple(prob.h))
         if meta.get("faces") is not None:
             # variable coefficient: L_a in the matvec, the mean coefficient in the preconditioner
             bltt_set_variable_coefficient(self.handle, meta["faces"], meta["abar"])
         if meta.get("K") is not None:
             # commuting dense blocks a_k I + b_k K: the solve runs in K's eigenbasis
             bltt_set_dense_operator(self.handle, meta["K"])
+        if spectra:
+            bltt_set_block_spectra(self.handle, meta["U"], meta["lam"])
         if stream is not None:
             bltt_set_stream(self.handle, stream)
 

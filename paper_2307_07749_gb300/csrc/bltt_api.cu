@@ -88,6 +88,9 @@ struct bltt_ctx {
   double pc_bscale = 1.0;     // the preconditioner's blocks are a_k I + pc_bscale b_k L (abar)
   bool var_coef = false;      // the matvec's L is L_a = -Delta_{a,h} (faces in op.kf)
   bool dense = false;         // L is a dense symmetric K: eigenbasis U (dU, columns), op.mu_tab
+  bool spectra = false;       // general commuting blocks given by U and their eigenvalues (lam)
+  std::vector<double> lam;    // [k][i] eigenvalues of the blocks (spectra), kept for the per-alpha set-up
+  int spectra_b_kind = 0, spectra_ntaps = 0;   // the op fields the blocks a, b gave
   double* dU = nullptr;
   float* dUp[4] = {nullptr, nullptr, nullptr, nullptr};   // double-float planes: U hi, lo; U^T hi, lo
   cublasHandle_t blas = nullptr;
@@ -118,6 +121,7 @@ struct bltt_ctx {
   float4* pc_bhatdf = nullptr;
   bool pc_hasdf = false;
   double2* pc_g64 = nullptr;
+  float2* pc_g32 = nullptr;    // general commuting blocks: the FP32 time pass reads a table too
   float2* pc_ahat32 = nullptr;
   float2* pc_bhat32 = nullptr;
   double2* pc_ahat64 = nullptr;
@@ -302,6 +306,44 @@ bltt_status ensure_workspace(bltt_ctx* h) {
 
 double* vec(bltt_ctx* h, int k) { return h->ws + (size_t)k * h->n; }
 
+// General commuting blocks: per mode i the eigenvalues of the block alpha-circulant,
+// lambda_i^(k,alpha) = FFT_N(D_alpha lam_i)_k (eq. hatcalphaieigvaldef), and the tables
+// lambda^{-1/2}/(2N) (principal branch, Def. 2) over (k <= N/2, mode i) in FP64, double-float and
+// FP32, built on the host for every precision at once (one FFT of length N per mode).
+bltt_status prepare_spectra_tables(bltt_ctx* h, double alpha) {
+  if (h->pc_has64 && h->pc_hasdf && h->pc_has32) return BLTT_OK;
+  const int N = h->N, half = N / 2;
+  const long long M = h->M;
+  const size_t count = (size_t)(half + 1) * (size_t)M;
+  std::vector<double2> g64(count);
+  std::vector<float4> gdf(count);
+  std::vector<float2> g32(count);
+  std::vector<double> dj(N);
+  for (int j = 0; j < N; ++j) dj[j] = std::pow(alpha, (double)j / N);
+  const double sc = 0.5 / N;
+  std::vector<cd> x(N);
+  for (long long i = 0; i < M; ++i) {
+    for (int j = 0; j < N; ++j) x[j] = cd(dj[j] * h->lam[(size_t)j * M + i], 0.0);
+    host_fft(x);
+    for (int k = 0; k <= half; ++k) {
+      const cd g = sc / std::sqrt(x[k]);          // std::sqrt: the principal branch
+      const size_t e = (size_t)k * M + i;
+      g64[e] = make_double2(g.real(), g.imag());
+      gdf[e] = split_df(g.real(), g.imag());
+      g32[e] = make_float2((float)g.real(), (float)g.imag());
+    }
+  }
+  if (!h->pc_g64) CK(h, h->alloc(&h->pc_g64, count), "alloc g64 table");
+  if (!h->pc_gdf) CK(h, h->alloc(&h->pc_gdf, count), "alloc gdf table");
+  if (!h->pc_g32) CK(h, h->alloc(&h->pc_g32, count), "alloc g32 table");
+  CK(h, cudaMemcpyAsync(h->pc_g64, g64.data(), count * sizeof(double2), cudaMemcpyHostToDevice, h->stream), "copy g64");
+  CK(h, cudaMemcpyAsync(h->pc_gdf, gdf.data(), count * sizeof(float4), cudaMemcpyHostToDevice, h->stream), "copy gdf");
+  CK(h, cudaMemcpyAsync(h->pc_g32, g32.data(), count * sizeof(float2), cudaMemcpyHostToDevice, h->stream), "copy g32");
+  CK(h, cudaStreamSynchronize(h->stream), "sync after table upload");   // host vectors die here
+  h->pc_has64 = h->pc_hasdf = h->pc_has32 = true;
+  return BLTT_OK;
+}
+
 // per-alpha tables: D_alpha scalings, ahat = FFT_N(D a), bhat = FFT_N(D b) and, for the FP64
 // preconditioner, the table lambda^{-1/2}/(2N) over (k <= N/2, mode i)
 bltt_status prepare_precond(bltt_ctx* h, double alpha, int prec) {
@@ -368,6 +410,7 @@ bltt_status prepare_precond(bltt_ctx* h, double alpha, int prec) {
     CK(h, cudaStreamSynchronize(h->stream), "sync after table upload");
     h->pc_alpha = alpha;
   }
+  if (h->spectra) return prepare_spectra_tables(h, alpha);
   // the FP32 time pass evaluates lambda^{-1/2} from ahat32 and bhat32 where it needs it: no table
   if (prec == PREC_F32) h->pc_has32 = true;
   if (prec == PREC_F64 && !h->pc_has64) {
@@ -403,6 +446,7 @@ PrecTables prec_tables(bltt_ctx* h, int none) {
   pt.g64 = h->pc_g64;
   pt.ahat32 = h->pc_ahat32;
   pt.bhat32 = h->pc_bhat32;
+  pt.g32 = h->spectra ? h->pc_g32 : nullptr;
   pt.none = none;
   return pt;
 }
@@ -731,6 +775,32 @@ bltt_status bltt_destroy(bltt_handle h) {
   return BLTT_OK;
 }
 
+namespace {
+// release the handle's eigenbasis and its tables (a dense operator's or general blocks'), so
+// that a new one can take their place; the blocks then read a, b again
+void drop_eigenbasis(bltt_ctx* h) {
+  if (!h->dense) return;
+  h->release(h->dU);
+  h->dU = nullptr;
+  h->release(const_cast<double*>(h->op.mu_tab));
+  h->release(const_cast<float*>(h->op.mu_tab32));
+  h->op.mu_tab = nullptr;
+  h->op.mu_tab32 = nullptr;
+  for (float*& q : h->dUp) { h->release(q); q = nullptr; }
+  if (h->spectra) {
+    h->release(const_cast<double2*>(h->op.Hm64));
+    h->release(const_cast<float4*>(h->op.Hmdf));
+    h->op.Hm64 = nullptr;
+    h->op.Hmdf = nullptr;
+    h->op.b_kind = h->spectra_b_kind;
+    h->op.ntaps = h->spectra_ntaps;
+    h->lam.clear();
+    h->spectra = false;
+  }
+  h->dense = false;
+}
+}  // namespace
+
 bltt_status bltt_set_dense_operator(bltt_handle h, const double* K) {
   if (!h) return BLTT_ERR_INVALID_ARG;
   if (!K) return fail(h, BLTT_ERR_INVALID_ARG, "null operator");
@@ -806,18 +876,119 @@ bltt_status bltt_set_dense_operator(bltt_handle h, const double* K) {
   if (!h->blas && cublasCreate(&h->blas) != CUBLAS_STATUS_SUCCESS)
     return fail(h, BLTT_ERR_CUDA, "cuBLAS handle");
   drop.keep = true;
-  if (h->dense) {
-    // a replaced operator: its eigenvectors and tables go
-    h->release(h->dU);
-    h->release(const_cast<double*>(h->op.mu_tab));
-    h->release(const_cast<float*>(h->op.mu_tab32));
-    for (float* q : h->dUp) h->release(q);
-  }
+  drop_eigenbasis(h);
   for (int k = 0; k < 4; ++k) h->dUp[k] = planes[k];
   h->dU = dU;
   h->op.mu_tab = dmu;
   h->op.mu_tab32 = dmu32;
   h->dense = true;
+  h->pc_alpha = -1.0;
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  return BLTT_OK;
+}
+
+bltt_status bltt_set_block_spectra(bltt_handle h, const double* U, const double* lam) {
+  if (!h) return BLTT_ERR_INVALID_ARG;
+  if (!U || !lam) return fail(h, BLTT_ERR_INVALID_ARG, "null eigenvectors or eigenvalues");
+  if (h->var_coef) return fail(h, BLTT_ERR_UNSUPPORTED, "a variable coefficient is set on this handle");
+  if (h->op.mv_arith == 2) return fail(h, BLTT_ERR_UNSUPPORTED, "the tensor-core matvec has no general blocks");
+  const long long M = h->M;
+  const int N = h->N;
+  if (M > 8192) return fail(h, BLTT_ERR_UNSUPPORTED, "general commuting blocks need M <= 8192");
+  for (long long e = 0; e < M * M; ++e)
+    if (!std::isfinite(U[e])) return fail(h, BLTT_ERR_INVALID_ARG, "U must be finite");
+  for (long long e = 0; e < (long long)N * M; ++e)
+    if (!std::isfinite(lam[e])) return fail(h, BLTT_ERR_INVALID_ARG, "the eigenvalues must be finite");
+  // orthonormal columns, probed with two fixed vectors: ||U^T (U x) - x|| <= 1e-10 ||x||
+  {
+    std::vector<double> x(M), y(M), z(M);
+    uint64_t st = 0x9E3779B97F4A7C15ull;
+    for (int probe = 0; probe < 2; ++probe) {
+      double nx = 0.0;
+      for (long long i = 0; i < M; ++i) {
+        st = st * 6364136223846793005ull + 1442695040888963407ull;
+        x[i] = (double)(st >> 11) * 0x1.0p-53 - 0.5;
+        nx += x[i] * x[i];
+      }
+      for (long long r = 0; r < M; ++r) {
+        double acc = 0.0;
+        for (long long c = 0; c < M; ++c) acc += U[r * M + c] * x[c];
+        y[r] = acc;
+      }
+      double err = 0.0;
+      for (long long c = 0; c < M; ++c) {
+        double acc = 0.0;
+        for (long long r = 0; r < M; ++r) acc += U[r * M + c] * y[r];
+        err += (acc - x[c]) * (acc - x[c]);
+      }
+      if (!(std::sqrt(err) <= 1e-10 * std::sqrt(nx)))
+        return fail(h, BLTT_ERR_INVALID_ARG, "U must have orthonormal columns");
+    }
+  }
+  // Assumption 1 (ii) on the blocks' eigenvalues (Proposition after Lemma 3.1)
+  double c0 = 1e300;
+  for (long long i = 0; i < M; ++i) {
+    double v = lam[i];
+    for (int k = 1; k < N; ++k) v -= std::fabs(lam[(size_t)k * M + i]);
+    c0 = std::min(c0, v);
+  }
+  if (!(c0 > 0.0)) return fail(h, BLTT_ERR_ASSUMPTION, "Assumption 1 (ii) fails for the blocks' eigenvalues");
+  // per-mode matvec spectra FFT_2N([lam_i; 0]) / (2N), k = 0..N (Sec. 5.1, the 2N embedding)
+  const size_t cnt = (size_t)(N + 1) * (size_t)M;
+  std::vector<double2> H64(cnt);
+  std::vector<float4> Hdf(cnt);
+  {
+    std::vector<cd> x(2 * N);
+    const double inv = 1.0 / (2.0 * N);
+    for (long long i = 0; i < M; ++i) {
+      for (int j = 0; j < 2 * N; ++j) x[j] = cd(j < N ? lam[(size_t)j * M + i] : 0.0, 0.0);
+      host_fft(x);
+      for (int k = 0; k <= N; ++k) {
+        const size_t e = (size_t)k * M + i;
+        H64[e] = make_double2(x[k].real() * inv, x[k].imag() * inv);
+        Hdf[e] = split_df(H64[e].x, H64[e].y);
+      }
+    }
+  }
+  // U on the device, column-major (column i = mode i), and its double-float planes
+  std::vector<double> Ucm((size_t)M * M);
+  for (long long r = 0; r < M; ++r)
+    for (long long c = 0; c < M; ++c) Ucm[(size_t)c * M + r] = U[r * M + c];
+  double* dU = nullptr;
+  double2* dH64 = nullptr;
+  float4* dHdf = nullptr;
+  float* planes[4] = {nullptr, nullptr, nullptr, nullptr};
+  struct Drop {
+    bltt_ctx* hh; void* p[7]; bool keep = false;
+    ~Drop() { if (!keep) for (void* q : p) hh->release(q); }
+  } drop{h, {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr}};
+  CK(h, upload(h, &dU, Ucm.data(), Ucm.size()), "eigenvectors");
+  drop.p[0] = dU;
+  CK(h, upload(h, &dH64, H64.data(), cnt), "matvec spectra");
+  drop.p[1] = dH64;
+  CK(h, upload(h, &dHdf, Hdf.data(), cnt), "matvec spectra");
+  drop.p[2] = dHdf;
+  for (int k = 0; k < 4; ++k) {
+    CK(h, h->alloc(&planes[k], (size_t)(M * M)), "eigenvector planes");
+    drop.p[3 + k] = planes[k];
+  }
+  CK(h, launch_df_planes(dU, M, planes[0], planes[1], planes[2], planes[3], nullptr), "planes");
+  CK(h, cudaDeviceSynchronize(), "planes");
+  if (!h->blas && cublasCreate(&h->blas) != CUBLAS_STATUS_SUCCESS)
+    return fail(h, BLTT_ERR_CUDA, "cuBLAS handle");
+  drop.keep = true;
+  drop_eigenbasis(h);
+  h->spectra_b_kind = h->op.b_kind;
+  h->spectra_ntaps = h->op.ntaps;
+  for (int k = 0; k < 4; ++k) h->dUp[k] = planes[k];
+  h->dU = dU;
+  h->op.Hm64 = dH64;
+  h->op.Hmdf = dHdf;
+  h->op.b_kind = 1;          // no common spectrum: every mode has its own
+  h->op.ntaps = 0;           // always the FFT product
+  h->lam.assign(lam, lam + (size_t)N * M);
+  h->dense = true;           // the solve runs in U's basis, as for a dense operator
+  h->spectra = true;
   h->pc_alpha = -1.0;
   if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
   return BLTT_OK;

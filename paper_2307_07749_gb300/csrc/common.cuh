@@ -83,6 +83,15 @@ __device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
   return {h, __fsub_rn(e, __fsub_rn(h, p))};
 }
 
+// a * b without the final renormalisation (see df_add_nr)
+__device__ __forceinline__ dfl df_mul_nr(dfl a, dfl b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return {p, e};
+}
+
 // a * b + c * d with one renormalisation
 __device__ __forceinline__ dfl df_dot2(dfl a, dfl b, dfl c, dfl d) {
   float p1 = __fmul_rn(a.hi, b.hi);
@@ -178,9 +187,10 @@ struct ArithF {
   static __device__ __forceinline__ Sc row_sc(const double*, const float* t32, int p) { return t32[p]; }
   static __device__ __forceinline__ V scale_sc(V a, Sc s) { return make_float2(a.x * s, a.y * s); }
   static __device__ __forceinline__ Sc neg_imag_sc(V a) { return -a.y; }
-  static __device__ __forceinline__ double part_sc(V a, int comp, Sc s) { return f2d_bits((comp ? a.y : a.x) * s); }
+  // the scaled loads and read-outs of the FP32 time pass use the cheaper conversions
+  static __device__ __forceinline__ double part_sc(V a, int comp, Sc s) { return f2d_fast((comp ? a.y : a.x) * s); }
   static __device__ __forceinline__ void put_sc(V* buf, int idx, int comp, double x, Sc s) {
-    reinterpret_cast<float*>(buf)[2 * idx + comp] = d2f_bits(x) * s;
+    reinterpret_cast<float*>(buf)[2 * idx + comp] = d2f_fast(x) * s;
   }
   static __device__ __forceinline__ void put_sc2(V* buf, int i1, int i2, int comp, double x, Sc s) {
     const float v = d2f_bits(x) * s;
@@ -322,10 +332,17 @@ __device__ __forceinline__ typename A::V w16() {
   else return A::cst(-K::C, g * K::S, -K::Ch, -K::Cl, g * K::Sh, g * K::Sl);   // E == 9
 }
 
-// NR: the second level is not renormalised either (its outputs only feed further sums or
-// products inside the same butterfly).  HALF: only X_0 and X_1 are formed (x2, x3 are left
-// unchanged), for a last pass whose upper outputs are not needed.
-template <class A, bool INV, bool NR = false, bool HALF = false>
+// Double-float sums inside the FFT passes are not renormalised.  A pair (s, e) left by a two-sum
+// still represents its value exactly; without the final fast two-sum the trailing part may grow
+// to a few ulp of the leading one over the levels of a transform, and the FP32 rounding of the
+// trailing-part sums then costs about 2^-24 of that, i.e. of order L_levels * 2^-48 of the
+// operands' size, far inside the FP64-accurate bound.  Every product that leaves a transform
+// (spectral products, scalings, the conversion back to FP64) takes unnormalised pairs.
+constexpr bool kFftNoRenorm = true;
+
+// NR: the second level is not renormalised either.  HALF: only X_0 and X_1 are formed (x2, x3
+// are left unchanged), for a last pass whose upper outputs are not needed.
+template <class A, bool INV, bool NR = kFftNoRenorm, bool HALF = false>
 __device__ __forceinline__ void dft4(typename A::V& x0, typename A::V& x1, typename A::V& x2,
                                      typename A::V& x3) {
   using V = typename A::V;
@@ -370,8 +387,7 @@ __device__ __forceinline__ void dft16(typename A::V (&v)[16]) {
 // Radix-8 butterfly.  With r = b + 2c and q = c' + 4d (b, d < 2; c, c' < 4),
 //   X_q = sum_b w2^{b d} w8^{b c'} sum_c w4^{c c'} x_{b+2c}:
 // two length-4 DFTs over c, the twiddles w8^{c'} on the b = 1 half, four length-2 DFTs over b.
-// In place; on return X_{c' + 4d} is in v[2c' + d] (HALF: only d = 0 is formed).  The length-4
-// DFTs' outputs only feed the twiddles and the last level, so only that level renormalises.
+// In place; on return X_{c' + 4d} is in v[2c' + d] (HALF: only d = 0 is formed).
 template <class A, bool INV, bool HALF = false>
 __device__ __forceinline__ void dft8(typename A::V (&v)[8]) {
   dft4<A, INV, true>(v[0], v[2], v[4], v[6]);
@@ -382,8 +398,13 @@ __device__ __forceinline__ void dft8(typename A::V (&v)[8]) {
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const typename A::V a = v[2 * c], b = v[2 * c + 1];
-    v[2 * c] = A::add(a, b);
-    if constexpr (!HALF) v[2 * c + 1] = A::sub(a, b);
+    if constexpr (kFftNoRenorm) {
+      v[2 * c] = A::add_nr(a, b);
+      if constexpr (!HALF) v[2 * c + 1] = A::sub_nr(a, b);
+    } else {
+      v[2 * c] = A::add(a, b);
+      if constexpr (!HALF) v[2 * c + 1] = A::sub(a, b);
+    }
   }
 }
 
@@ -445,8 +466,8 @@ __device__ __forceinline__ void fft_columns(typename A::V* buf, int L, int log2L
         const int it = tid + s * NT;
         if (it < total) {
           const int c = it & cmask, j = it >> log2NC;
-          buf[at(2 * j, c)] = A::add(v[s][0], v[s][1]);
-          buf[at(2 * j + 1, c)] = A::sub(v[s][0], v[s][1]);
+          buf[at(2 * j, c)] = A::add_nr(v[s][0], v[s][1]);
+          buf[at(2 * j + 1, c)] = A::sub_nr(v[s][0], v[s][1]);
         }
       }
       __syncthreads();

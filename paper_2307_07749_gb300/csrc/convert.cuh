@@ -49,4 +49,34 @@ BLTT_HD double f2d_bits(float x) {
   return from_bits_d(((uint64_t)hi << 32) | lo);
 }
 
+// Cheaper conversions for the FP32 kernels, whose values only need FP32 accuracy on the way in
+// and exactness on the way out.
+//
+// double -> float rounded to nearest with ties away from zero (ties to even differs only on
+// exact ties, by one ulp); magnitudes below 2^-126 flush to signed zero; |x| >= 2^128, Inf and
+// NaN become NaN (so that a breakdown stays visible).
+BLTT_HD float d2f_fast(double x) {
+  const uint64_t b = bits_d(x);
+  const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+  const uint32_t sign = hi & 0x80000000u, e = hi & 0x7FF00000u;
+  const uint32_t t = hi - 0x38000000u;                 // exponent - (1023 - 127), in place
+  uint32_t f = ((t << 3) | (lo >> 29)) & 0x7FFFFFFFu;  // exponent and top 23 mantissa bits
+  f += (lo >> 28) & 1u;                                // the first dropped bit rounds
+  f |= sign;
+  if (e < 0x38100000u) f = sign;                       // below 2^-126
+  if (e >= 0x47F00000u) f = 0x7FC00000u | sign;        // 2^128 and beyond, Inf, NaN
+  return from_bits_f(f);
+}
+
+// float -> double, exact for normal numbers and zeros; Inf and NaN become NaN; subnormal inputs
+// (below 2^-126) are not exact
+BLTT_HD double f2d_fast(float x) {
+  const uint32_t b = bits_f(x);
+  const uint32_t a = b & 0x7FFFFFFFu, sign = b & 0x80000000u;
+  uint32_t hi = ((a >> 3) + 0x38000000u) | sign;
+  if (a == 0u) hi = sign;
+  if (a >= 0x7F800000u) hi = 0x7FF80000u | sign;
+  return from_bits_d(((uint64_t)hi << 32) | (uint32_t)(b << 29));
+}
+
 }  // namespace bltt

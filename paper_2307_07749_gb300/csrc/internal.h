@@ -60,6 +60,10 @@ struct OpTables {
   // the eigenvector columns (null: the Laplacian's, from the per-axis tables)
   const double* mu_tab;
   const float* mu_tab32;
+  // general commuting blocks (given by their eigenvalues per mode): the matvec spectrum of each
+  // mode, FFT_2N([lam_i; 0]) / (2N) for k = 0..N, frequency-major [k][i] (null: a + mu_i b)
+  const double2* Hm64;
+  const float4* Hmdf;
   // variable coefficient (null: L = -Delta_h): a at the cell faces along each axis, arrays of the
   // grid's shape with that axis one longer (x fastest); L becomes L_a = -Delta_{a,h}
   const double* kf[3];
@@ -88,6 +92,7 @@ struct PrecTables {
   const double2* g64;    // [(N/2+1)][M]: lambda^{-1/2}/(2N), FP64 form
   const float2* ahat32;  // [N/2+1]: FFT_N(D a); the FP32 form evaluates lambda^{-1/2}/(2N) from
   const float2* bhat32;  // these two where it uses it
+  const float2* g32;     // [(N/2+1)][M]: the table in FP32 for general commuting blocks (else null)
   int none;              // 1: identity preconditioner (MINRES-I)
 };
 

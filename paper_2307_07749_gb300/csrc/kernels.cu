@@ -261,7 +261,10 @@ __device__ __forceinline__ void dst_tile(long long nlines, int m, long long inne
     }
   }
   __syncthreads();
-  const Sc scale = A::make_sc(sqrt(2.0 / (double)P));
+  // sqrt(2/P) for P = 2^log2P: a power of two (log2P odd) or sqrt(2) times one, without the
+  // FP64 square root and division every thread would otherwise run
+  const Sc scale = A::make_sc((log2P & 1) ? ldexp(1.0, (1 - log2P) / 2)
+                                          : ldexp(1.4142135623730951, -(log2P / 2)));
   // read-out in batches: the global loads of a batch (the dot-product partner) are all issued
   // before the first use, so that their latencies overlap.  dot_with == out asks for ||out||^2.
   // Output j = p + 1: S_j from row j/2 (j odd: the prefix sums) or row P/2 + j/2 (j even).
@@ -357,7 +360,8 @@ template <> struct GSrc<ArithD> {
 };
 template <> struct GSrc<ArithF> {
   static __device__ __forceinline__ float2 get(const OpTables& op, const PrecTables& pt, int k,
-                                              long long, float mu32) {
+                                              long long i, float mu32) {
+    if (pt.g32) return pt.g32[(long long)k * op.M + i];   // general commuting blocks
     const float2 a = pt.ahat32[k], b = pt.bhat32[k];
     const float2 g = inv_sqrt_principal_fast(fmaf(b.x, mu32, a.x), fmaf(b.y, mu32, a.y));
     const float sc = 0.5f / (float)op.N;
@@ -428,6 +432,8 @@ __device__ __forceinline__ void timepass_tile(const OpTables& op, const PrecTabl
     pts.bhat32 = sb;
     pts.dinv32 = sdi;
     pts.d232 = sd2;
+    // the load loop below reads the staged row scalings written by other threads
+    __syncthreads();
   }
   const int N = op.N, NC = 1 << log2NC, W = 2 * NC, log2W = log2NC + 1;
   const long long M = op.M;
@@ -568,6 +574,8 @@ template <> struct ConvTables<ArithD> {
     return make_double2(fma(0.5, a.x, mu_or_sh), 0.5 * a.y);
   }
   static __device__ __forceinline__ double sc_mu(double v) { return v; }
+  static __device__ __forceinline__ const double2* Hm(const OpTables& op) { return op.Hm64; }
+  static __device__ __forceinline__ double2 half(double2 v) { return make_double2(0.5 * v.x, 0.5 * v.y); }
 };
 template <> struct ConvTables<ArithDF> {
   static __device__ __forceinline__ const float4* tw(const OpTables& op) { return op.tw_2N_df; }
@@ -579,6 +587,10 @@ template <> struct ConvTables<ArithDF> {
       return ArithDF::pack(df_add(ar, df_mul(mu_or_sh, br)), df_add(ai, df_mul(mu_or_sh, bi)));
     }
     return ArithDF::pack(df_add(ar, mu_or_sh), ai);
+  }
+  static __device__ __forceinline__ const float4* Hm(const OpTables& op) { return op.Hmdf; }
+  static __device__ __forceinline__ float4 half(float4 v) {   // exact halving of every part
+    return make_float4(0.5f * v.x, 0.5f * v.y, 0.5f * v.z, 0.5f * v.w);
   }
 };
 template <class A> struct MuT;
@@ -610,7 +622,8 @@ __device__ __forceinline__ void conv_tile(const OpTables& op, int spectral, int 
   // DST basis with b = b0 e_0: every mode's spectrum is FFT_2N([a;0]) plus the constant b0 mu_i,
   // so the packed pair is multiplied by the common spectrum (no split) and the b0 mu_i s x term
   // is added in the time domain at read-out
-  const bool common = spectral && !genb;
+  const V* __restrict__ Hm = ConvTables<A>::Hm(op);     // per-mode spectra (general blocks)
+  const bool common = spectral && !genb && Hm == nullptr;
   for (int c = threadIdx.x; c < W; c += NT) {
     const long long i = g0 + c;
     double mu = 0.0;
@@ -674,9 +687,17 @@ __device__ __forceinline__ void conv_tile(const OpTables& op, int spectral, int 
     const int items = (N + 1) << log2NC;
     for (int it = threadIdx.x; it < items; it += NT) {
       const int cc = it & (NC - 1), k = it >> log2NC;
-      const V a_ = HA[k], b_ = HB[k];
-      const V Ha = ConvTables<A>::Hmode(a_, b_, s_mu[2 * cc], true);
-      const V Hb = ConvTables<A>::Hmode(a_, b_, s_mu[2 * cc + 1], true);
+      V Ha, Hb;
+      if (Hm) {
+        // general commuting blocks: the modes' own spectra, halved for the split
+        const long long ia = g0 + 2 * cc;
+        Ha = ia < M ? ConvTables<A>::half(Hm[(long long)k * M + ia]) : A::zero();
+        Hb = ia + 1 < M ? ConvTables<A>::half(Hm[(long long)k * M + ia + 1]) : A::zero();
+      } else {
+        const V a_ = HA[k], b_ = HB[k];
+        Ha = ConvTables<A>::Hmode(a_, b_, s_mu[2 * cc], true);
+        Hb = ConvTables<A>::Hmode(a_, b_, s_mu[2 * cc + 1], true);
+      }
       const int kb = (L - k) & (L - 1);
       const V Av = buf[k * NC + cc], Bc = A::conj(buf[kb * NC + cc]);
       const V U1 = A::mul(Ha, A::add(Av, Bc));

@@ -22,6 +22,7 @@ import numpy as np
 __all__ = [
     "Problem", "l1_weights", "fractional_problem", "heat_bdf_problem", "heat_cn_problem",
     "heat_cn_varcoeff_problem", "fractional_varcoeff_problem", "nonlocal_diffusion_problem",
+    "commuting_blocks_problem",
     "paper_data_fractional", "paper_data_frac_var", "paper_data_heat_var",
     "rhs_uniform", "rhs_smoothed_field", "WORKLOADS", "workload", "batched_systems",
     "alpha_training_problems",
@@ -178,6 +179,42 @@ def nonlocal_diffusion_problem(m, N, gamma, delta_cells=3.0, name=None) -> Probl
     K[np.diag_indices_from(K)] += C * math.pi * delta * delta
     return Problem(p.N, p.d, p.m, p.h, p.a, p.b, name or f"nonlocal2d_N{N}_m{mm}_g{gamma}",
                    dict(p.meta, kind="nonlocal", K=K, delta=delta))
+
+
+def commuting_blocks_problem(M, N, seed=0, kind="modal", T=1.0, name=None) -> Problem:
+    """General commuting symmetric blocks (Assumption 1 (i), Sec. 3): A_(k) = U diag(lam_k) U^T
+    with one orthonormal U for every block, not tied to a grid or a single operator.
+
+    U is the Q factor of a seeded Gaussian M x M matrix (default_rng(seed)).  lam[k, i] is the
+    eigenvalue of A_(k) on column i of U:
+      kind "modal": every eigenmode carries its own L1 time-fractional order and diffusion rate,
+        lam[0, i] = l_0^(g_i)/tau^(g_i) + nu_i, lam[k, i] = l_k^(g_i)/tau^(g_i) (k >= 1), with
+        g_i ~ U[0.3, 0.9] and log10 nu_i ~ U[0, 3];
+      kind "poly": blocks a_k I + b_k K + c_k K^2 of one SPD K = U diag(nu) U^T (L1 weights
+        of order 0.6 in a, b = e_0, c = 1e-3 e_0: a fourth-order term in the first block).
+    Assumption 1 (ii) holds for both (the L1 weights' sums are positive, nu > 0).  meta["U"],
+    meta["lam"] are what the library takes; meta["blocks"] holds the (N, M, M) matrices the
+    oracle works from.  The grid fields describe a 1-D line of M points (unused by the blocks)."""
+    rng = np.random.default_rng(seed)
+    Q, R = np.linalg.qr(rng.standard_normal((M, M)))
+    U = Q * np.sign(np.diag(R))[None, :]
+    tau = T / N
+    nu = 10.0 ** rng.uniform(0.0, 3.0, M)
+    if kind == "modal":
+        g = rng.uniform(0.3, 0.9, M)
+        lam = np.stack([l1_weights(gi, N) / tau ** gi for gi in g], axis=1)
+        lam[0] += nu
+    elif kind == "poly":
+        a = l1_weights(0.6, N) / tau ** 0.6
+        lam = np.repeat(a[:, None], M, axis=1)
+        lam[0] += nu + 1e-3 * nu ** 2
+    else:
+        raise ValueError(kind)
+    blocks = np.einsum("ij,kj,lj->kil", U, lam, U)
+    blocks = 0.5 * (blocks + np.transpose(blocks, (0, 2, 1)))
+    m, h = _grid(1, M, 1.0)
+    return Problem(N, 1, m, h, np.zeros(N), np.zeros(N), name or f"commuting_{kind}_N{N}_M{M}_s{seed}",
+                   dict(kind="commuting", U=U, lam=lam, blocks=blocks, tau=tau))
 
 
 def paper_data_fractional(prob, gamma: float) -> np.ndarray:
