@@ -8,6 +8,7 @@ counts are computed once by this script and stored; it calls nothing but ``oracl
 Usage (from the repository root):
     python tests/golden/make_oracle_solve_counts.py [--workloads a,b] [--alphas 1e-8,1e-6,1e-3]
         [--out tests/golden/oracle_solve_counts.json]
+    python tests/golden/make_oracle_solve_counts.py --batched --alphas 1e-8,1e-2,1e-6
 
 Each entry records the workload, alpha, tol, the iteration count, the recurrence estimates
 |eta_j|/eta_0 and the true relative residual ||Yf - YAu|| / ||Yf|| of the returned iterate
@@ -26,7 +27,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 import oracle as O  # noqa: E402
-from workloads import heat_bdf_problem, rhs_smoothed_field, workload  # noqa: E402
+from workloads import batched_systems, heat_bdf_problem, rhs_smoothed_field, workload  # noqa: E402
 
 
 def _heat3d_m63():
@@ -38,6 +39,28 @@ def _heat3d_m63():
 EXTRA = {"heat3d_bdf_N256_m63": _heat3d_m63}
 
 
+def batched_sample(out, alphas, tol):
+    """The oracle's counts for the small systems of the 96-system batched workload (M <= 3969
+    and at most 600,000 unknowns), every right-hand side (seeded U[-1, 1], seed 4 + 1000 s + r),
+    at each alpha."""
+    doc = {"source": "FP64 oracle (oracle.solve) on the small systems of batched_systems(96, 4, "
+                     "seed=4); written by tests/golden/make_oracle_solve_counts.py --batched",
+           "tol": tol, "cases": []}
+    for s, (p, rhs) in enumerate(batched_systems(96, 4, seed=4)):
+        if p.M > 3969 or p.n > 600_000:
+            continue
+        for r, rf in enumerate(rhs):
+            f = rf()
+            for alpha in alphas:
+                res = O.solve(p, f, alpha=alpha, tol=tol, maxit=100)
+                entry = dict(system=s, rhs=r, name=p.name, N=p.N, M=p.M, alpha=alpha,
+                             iters=int(res["iters"]), status=res["status"])
+                print(json.dumps(entry), flush=True)
+                doc["cases"].append(entry)
+    with open(out, "w") as fh:
+        json.dump(doc, fh, indent=0)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workloads", default="frac1d_N64_m63_g0.5,frac2d_N1024_m255_g0.7")
@@ -45,7 +68,14 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)),
                                                   "oracle_solve_counts.json"))
+    ap.add_argument("--batched", action="store_true",
+                    help="write oracle_counts_batched_sample.json instead")
     args = ap.parse_args()
+    if args.batched:
+        batched_sample(os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                    "oracle_counts_batched_sample.json"),
+                       [float(a) for a in args.alphas.split(",")], args.tol)
+        return
     doc = {"source": "FP64 oracle (oracle.solve: textbook preconditioned MINRES, structured "
                      "P_alpha^{-1} of Sec. 5.1) on the named seeded workloads; written by "
                      "tests/golden/make_oracle_solve_counts.py",

@@ -75,10 +75,9 @@ def _family(seed, count):
 
 def test_learned_alpha_beats_the_fixed_rules(B):
     """FP32-preconditioner form: on held-out problems the network trained on this solver's own
-    sweeps needs at most 10% more iterations than the best fixed alpha, which is picked with
+    sweeps needs no more iterations in total than the best fixed alpha, which is picked with
     hindsight on the held-out set itself, and far fewer than the paper's alpha = 1e-8, with which
-    the FP32 form does not converge.  The iteration counts of the FP32 form move by one here and
-    there with the rounding of its FFTs, hence the margin."""
+    the FP32 form does not converge."""
     from paper_2307_07749_gb300 import learned_alpha as LA
     train_set, held = _family(11, 80), _family(12, 16)
     X, t, _ = LA.build_dataset(train_set)
@@ -98,7 +97,7 @@ def test_learned_alpha_beats_the_fixed_rules(B):
         return np.array(tot)
 
     learned = iters(alphas)
-    best_fixed = min((iters([a] * len(held)).sum(), a) for a in (1e-2, 1e-3, 1e-4))
+    best_fixed = min((iters([a] * len(held)).sum(), a) for a in (1e-2, 3e-3, 1e-3, 1e-4))
     paper = iters([1e-8] * len(held))
-    assert learned.sum() <= best_fixed[0] * 1.10, (learned.sum(), best_fixed)
+    assert learned.sum() <= best_fixed[0], (learned.sum(), best_fixed)
     assert learned.sum() < paper.sum()

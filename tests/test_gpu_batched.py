@@ -108,3 +108,52 @@ def test_batched_big_and_small_items_equal_single_solves(B, form):
             assert infos[k]["iters"] == inf1["iters"], (s, r, infos[k]["iters"], inf1["iters"])
             assert rel(to_host(ud[s][r]), to_host(u1)) <= 1e-10
             k += 1
+
+
+def test_batched_memory_cap_below_one_item_reports_oom(B, monkeypatch):
+    """A workspace budget smaller than one item's vectors: the call returns BLTT_ERR_OOM (3)
+    before any iteration, leaves the outputs untouched, and the library stays usable."""
+    probs, fs = small_batch(seed=9)
+    fd = [[to_dev(f) for f in row] for row in fs]
+    ud = [[to_dev(np.full_like(f, 7.0)) for f in row] for row in fs]
+    monkeypatch.setenv("BLTT_BATCH_MAX_BYTES", "4096")
+    st, infos = B.bltt_solve_batched(probs, fd, ud, tol=1e-8, maxit=100)
+    assert st == 3
+    assert all(float(u.min()) == 7.0 == float(u.max()) for row in ud for u in row)
+    monkeypatch.delenv("BLTT_BATCH_MAX_BYTES")
+    st, infos = B.bltt_solve_batched(probs, fd, ud, tol=1e-8, maxit=100)
+    assert st == 0 and all(i["relres_true"] <= 1e-8 for i in infos)
+
+
+@pytest.mark.parametrize("form", [
+    dict(precision=64, matvec_arith=1, alpha=1e-8),
+    dict(precision=32, matvec_arith=2, alpha=1e-2),
+    dict(precision=96, matvec_arith=2, alpha=1e-6),
+], ids=["f64", "f32_prec", "f32x2_prec"])
+def test_batched_workload_sample_vs_stored_oracle(B, form):
+    """The small systems of the 96-system batched workload (M <= 3969, at most 600,000 unknowns:
+    24 systems, 96 items) solved in one batched call; every item's count against the FP64
+    oracle's stored count at the same alpha (tests/golden/make_oracle_solve_counts.py)."""
+    import json
+    import os
+    from workloads import batched_systems
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                           "oracle_counts_batched_sample.json")) as fh:
+        golden = {(c["system"], c["rhs"], c["alpha"]): c["iters"] for c in json.load(fh)["cases"]}
+    sysl = batched_systems(96, 4, seed=4)
+    sample = [s for s, (p, _) in enumerate(sysl) if p.M <= 3969 and p.n <= 600_000]
+    assert len(sample) == 24
+    probs = [sysl[s][0] for s in sample]
+    fd = [[to_dev(rf()) for rf in sysl[s][1]] for s in sample]
+    ud = [[to_dev(np.zeros(p.n)) for _ in range(4)] for p in probs]
+    st, infos = B.bltt_solve_batched(probs, fd, ud, alpha=[form["alpha"]] * len(probs), tol=1e-8,
+                                     maxit=100, precision=form["precision"],
+                                     matvec_arith=form["matvec_arith"])
+    assert st == 0
+    deltas = []
+    for j, s in enumerate(sample):
+        for r in range(4):
+            info = infos[4 * j + r]
+            assert info["relres_true"] <= 1e-8
+            deltas.append(info["iters"] - golden[(s, r, form["alpha"])])
+    assert max(abs(d) for d in deltas) <= 1, deltas
