@@ -50,10 +50,10 @@ ALPHA_F64 = 1e-8          # the paper's alpha rule (Sec. 5.2)
 ALPHA_F32 = 1e-2
 ALPHA_F32X2 = 1e-6        # double-float preconditioner: 2 iterations, as the FP64 oracle at 1e-6
 # DRAM bytes (read + write) per unknown of one launch, from one ncu capture of the current kernel
-# (the m = 127 case of the same workload, scaled by the unknowns)
+# on the full workload
 NCU_TRAFFIC_PER_UNKNOWN = {
-    "conv_df": (13.07, "ncu dram__bytes_read.sum + dram__bytes_write.sum, m = 127 case, 13.07 B "
-                       "per unknown scaled to the launch's unknowns"),
+    "conv_df": (15.35, "ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch "
+                       "(545.5 + 476.9 MB over 66,585,600 unknowns; one pass)"),
 }
 # one metric text for both arms (the GPU solve and the CPU oracle), so that their lines compare
 METRIC = "unknown-iterations/s to relres<=1e-8"
@@ -62,21 +62,57 @@ FP32_PEAK_TFLOPS = 80.6   # 128 FFMA/clk/SM x 152 SMs x 2.07 GHz (measured 69.8 
 FP32_PEAK_TOPS = 40.28    # FP32 pipe: 128 instructions/clk/SM x 152 SMs x 2.07 GHz
 
 
-def df_fft_ops(L):
-    """FP32 operations of one double-float complex FFT of length L, per point (radix 4, plus one
-    radix-2 pass when log2 L is odd): df add = 11 ops, df complex multiply = 2 dot2 = 38 ops."""
+# FP32 operations of the double-float arithmetic as the kernels implement it (common.cuh): a sum
+# inside an FFT pass is a two-sum plus the trailing parts (8 operations, not renormalised), a
+# twiddle product a dot product of two such products (16), a renormalised sum 11, a renormalised
+# complex product 38.  One complex point, per pass:
+DF_ADD_NR, DF_CMUL_NR, DF_ADD, DF_CMUL = 8.0, 32.0, 11.0, 38.0
+R4_PASS = (8 * 2 * DF_ADD_NR + 3 * DF_CMUL_NR) / 4          # one length-4 DFT + 3 twiddles / 4 pts
+R8_PASS = (2 * 8 * 2 * DF_ADD_NR + 2 * DF_CMUL_NR + 8 * 2 * DF_ADD_NR + 7 * DF_CMUL_NR) / 8
+R8_HALF = (2 * 8 * 2 * DF_ADD_NR + 2 * DF_CMUL_NR + 4 * 2 * DF_ADD_NR + 7 * DF_CMUL_NR) / 8
+
+
+def df_fft_ops(L, skip_radix2=False, half_out=False):
+    """FP32 operations per complex point of one double-float FFT of length L as planned by the
+    512-thread tiles: radix 2 only when the caller applied it (skip_radix2: free), one or two
+    radix-4 passes, radix-8 passes for the rest; half_out: the last radix-8 pass forms half of
+    its outputs."""
     lg = int(np.log2(L))
-    ops = 0.0
-    if lg % 2:
-        ops += 2 * 22.0 / 2          # radix-2 pass: 2 complex add/sub per 2 points
-    ops += (lg // 2) * (3 * 38.0 + 8 * 22.0) / 4   # radix-4 passes: 3 twiddle muls, 8 adds
+    rem = lg - (1 if (lg % 2 and skip_radix2) else 0)
+    n4 = 1 if rem % 3 == 2 else (2 if rem % 3 == 1 else 0)
+    n8 = (rem - 2 * n4) // 3
+    ops = n4 * R4_PASS + n8 * R8_PASS
+    if half_out and n8 > 0:
+        ops += R8_HALF - R8_PASS
     return ops
 
 
 def df_conv_ops(N):
-    """FP32 operations per unknown of the double-float matvec: forward + inverse FFT of 2N per
-    complex column (one complex point per real unknown), the spectral product, the epilogue."""
-    return 2 * df_fft_ops(2 * N) + 38.0 + 4.0
+    """FP32 operations per unknown of the double-float matvec in the DST basis: the forward FFT of
+    2N (its first radix-2 pass is the zero padding's copy), the common spectral product, the
+    inverse FFT forming the first N outputs, the scaled load (one double-float product)."""
+    return df_fft_ops(2 * N, skip_radix2=True) + DF_CMUL + df_fft_ops(2 * N, half_out=True) + 7.0
+
+
+def df_timepass_ops(N):
+    """FP32 operations per unknown of the double-float time pass: four FFTs of N per complex
+    column (two real modes), two split spectral products (per frequency pair: four renormalised
+    complex sums and two complex products), the three row scalings."""
+    ffts = 4 * df_fft_ops(N) / 2
+    prods = 2 * (4 * 2 * DF_ADD + 2 * DF_CMUL) / 2 / 2
+    return ffts + prods + 3 * 7.0
+
+
+def df_dst_ops(m):
+    """FP32 operations per unknown of the double-float DST-I of length m: one complex FFT of
+    P = m + 1 per two lines, the pre-pass and the split (two renormalised complex sums and two
+    scalings per row pair and column), the prefix sum, the scaled read-out."""
+    P = m + 1
+    fft = P * df_fft_ops(P) / (2 * m)
+    pre = P / 2 * (4 * 2 * DF_ADD + 2 * 2 * 7.0) / (2 * m)
+    split = P / 2 * (2 * 2 * DF_ADD + 2 * 2 * 7.0) / (2 * m)
+    prefix = P / 2 * 2 * 2 * DF_ADD / (2 * m)
+    return fft + pre + split + prefix + 7.0
 
 
 def peaks():
@@ -122,9 +158,9 @@ def kernel_cost(name, N, m, d):
     if name in ("dst64", "dst32"):
         return ("alu64" if name == "dst64" else "hbm"), 16.0, 5.0 * P * np.log2(P) / (2 * m) + 6.0
     if name == "dst_df":
-        return "alu32", 16.0, P * df_fft_ops(P) / (2 * m) + 61.0
+        return "alu32", 16.0, df_dst_ops(m)
     if name == "timepass_df":
-        return "alu32", 48.0, 4 * df_fft_ops(N) / 2 + 2 * 82.0 / 2 + 3 * 14.0
+        return "alu32", 48.0, df_timepass_ops(N)
     if name == "w_update":
         return "hbm", 48.0, 6.0
     # basis change of the dense-operator form: an M x M by M x N FP64 GEMM (2M flops per unknown)
@@ -333,8 +369,8 @@ def run_reference(args):
     value = prob.n * args.steps / tot
     cores = os.cpu_count()
     sample = ("one MINRES iteration's operator work (one Y A z by the direct Toeplitz product and "
-              "one P_alpha^{-1} apply by the paper's three steps, alpha = 1e-3) on the full "
-              f"{prob.n}-unknown workload per step")
+              f"one P_alpha^{{-1}} apply by the paper's three steps, alpha = {ALPHA_F32:g}) on the "
+              f"full {prob.n}-unknown workload per step")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "unknown-iter/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,

@@ -1344,10 +1344,13 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
   h->launches++;
 
   // one MINRES iteration (A1..A4 of the hot loop); the caller rotates the buffers afterwards
-  // DST basis: the true residual is checked by the host in the physical basis once the estimate
-  // has met the stopping rule (the iterations halt in PH_VERIFY and resume if the check fails),
-  // so the iterations carry no residual product of their own
-  const bool defer = (spectral != 0) && !h->dense;
+  // DST basis with the FFT product: the true residual is checked by the host in the physical
+  // basis once the estimate has met the stopping rule (the iterations halt in PH_VERIFY and
+  // resume if the check fails), so the iterations carry no residual product of their own.  With
+  // the direct product (a few taps) the physical residual would need the FP64 stencil of every
+  // tap, several times the cost of the product itself: there the iterations check the residual
+  // in the DST basis, where (I (x) U) is orthogonal and the norm is the same.
+  const bool defer = (spectral != 0) && !h->dense && op.ntaps == 0;
   const long long per_iter = 5 + ((op.b_kind == 1 && op.ntaps == 0 && !spectral) ? 4 : 2) +
                              (spectral || none ? 0 : 2 * op.d) + (tc ? 1 : 0) - (defer ? 1 : 0);
   auto issue_iteration = [&](int c0) -> bltt_status {
@@ -1476,6 +1479,14 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
       // u = (I (x) U) x_hat by one FP64 GEMM; the true residual was checked in the eigenbasis
       // (U orthogonal: the same norm) by the iterations
       s = eigen_transform(h, x, u, false, op.mv_arith == 1);
+      if (s != BLTT_OK) return s;
+      s = copy_out();
+      if (s != BLTT_OK) return s;
+      break;
+    }
+    if (!defer) {
+      // the direct product's iterations checked the residual in the DST basis: u = (I (x) U) x_hat
+      s = dst_all(h, op, x, u, 0, nullptr, nullptr);
       if (s != BLTT_OK) return s;
       s = copy_out();
       if (s != BLTT_OK) return s;
