@@ -92,7 +92,10 @@ enum { BLTT_PRECOND_ABAC = 0, BLTT_PRECOND_NONE = 1 };
  * sums, and the b_0 term and the scale are double-float.  Relative error about 2^-40 of
  * sum_k |a_k| |x_k| per element.  Requires b = b_0 e_0, an FFT-class a (more than 4 nonzeros)
  * and N in {128, 256, 512, 1024}; elsewhere it is BLTT_ERR_UNSUPPORTED.  Uses a workspace of
- * N * 128 * ceil(M/128) * 8 bytes, allocated on first use.
+ * N * 128 * ceil(M/128) * 8 bytes, allocated on first use.  Every wait of its kernel is bounded:
+ * a wait for progress gives up after about a second (BLTT_TC_WAIT_CYCLES in the environment, in
+ * SM cycles, shortens it), the block then drains its own copies and MMAs and frees its tensor
+ * memory, and the solve returns BLTT_ERR_TIMEOUT with the context still usable.
  * DEFAULT: the handle's setting (F64 unless bltt_set_matvec_arith changed it). */
 enum { BLTT_ARITH_DEFAULT = 0, BLTT_ARITH_F64 = 1, BLTT_ARITH_F32X2 = 2, BLTT_ARITH_TC = 3 };
 

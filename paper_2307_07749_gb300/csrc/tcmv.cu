@@ -28,6 +28,7 @@
 // wait on an mbarrier is bounded (about one second); a block that gives up sets *tc_err,
 // writes NaN partials, lets its copies and MMAs finish and frees its TMEM.
 #include <atomic>
+#include <cstdlib>
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -113,8 +114,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
-// wait for the phase of the given parity to complete; false after about a second
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// wait for the phase of the given parity to complete; false after `limit` SM cycles (about a
+// second by default)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          long long limit = kWaitCycles) {
   const long long t0 = clock64();
   for (;;) {
     uint32_t done;
@@ -125,7 +128,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
@@ -267,6 +270,9 @@ struct MvParams {
   double* partials;
   const int* phase;
   int flip, spectral, nstrips, NB, nunits;
+  // limit of the waits for progress (copies landed, MMAs done, accumulators read); the waits
+  // that drain the block's own copies and MMAs before TMEM is freed keep kWaitCycles
+  long long wait_cycles;
 };
 
 // unit u -> (strip, row block): groups of kGroup strips, row blocks in order inside a group
@@ -352,7 +358,8 @@ __global__ void __launch_bounds__(kThreadsMv, 1) k_tc_mv(const MvParams p) {
         const unsigned char* src = xd + (size_t)strip * NKS * kStageBytes;
         for (int ks = 0; ks < nks; ++ks, ++it) {
           const int s = (int)(it % kStages);
-          if (it >= (uint32_t)kStages && !mbar_wait(empty_bar(s), ((it / kStages) & 1u) ^ 1u)) {
+          if (it >= (uint32_t)kStages &&
+              !mbar_wait(empty_bar(s), ((it / kStages) & 1u) ^ 1u, p.wait_cycles)) {
             *err = 1;
             break;
           }
@@ -374,7 +381,7 @@ __global__ void __launch_bounds__(kThreadsMv, 1) k_tc_mv(const MvParams p) {
       for (int i = 0; i < kTcDigits; ++i) bplane[i] = (uint64_t)(i * ncores * 8);
       uint32_t it = 0, ui = 0;
       for (int u = blockIdx.x; u < p.nunits && !*err; u += gridDim.x, ++ui) {
-        if (ui > 0 && !mbar_wait(tempty, (ui - 1) & 1u)) { *err = 1; break; }
+        if (ui > 0 && !mbar_wait(tempty, (ui - 1) & 1u, p.wait_cycles)) { *err = 1; break; }
         tc_after_sync();
         int strip, rb;
         unit_of(u, p.nstrips, NB, strip, rb);
@@ -382,7 +389,7 @@ __global__ void __launch_bounds__(kThreadsMv, 1) k_tc_mv(const MvParams p) {
         bool ok = true;
         for (int ks = 0; ks < nks; ++ks, ++it) {
           const int s = (int)(it % kStages);
-          if (!mbar_wait(full_bar(s), (it / kStages) & 1u)) { ok = false; break; }
+          if (!mbar_wait(full_bar(s), (it / kStages) & 1u, p.wait_cycles)) { ok = false; break; }
           tc_after_sync();
           const uint64_t ad = adesc0 + (uint64_t)(s * (kStageBytes / 16));
           const uint64_t bd = bdesc0 + (uint64_t)((16 * rb + 2 * ks) * 8);
@@ -411,7 +418,7 @@ __global__ void __launch_bounds__(kThreadsMv, 1) k_tc_mv(const MvParams p) {
     const double s = p.xscale ? *p.xscale : 1.0;
     uint32_t ui = 0;
     for (int u = blockIdx.x; u < p.nunits; u += gridDim.x, ++ui) {
-      if (*err || !mbar_wait(tfull, ui & 1u)) { *err = 1; break; }
+      if (*err || !mbar_wait(tfull, ui & 1u, p.wait_cycles)) { *err = 1; break; }
       tc_after_sync();
       float hh[32], ll[32];
 #pragma unroll
@@ -567,6 +574,14 @@ cudaError_t launch_tc_product(const OpTables& op, int spectral, const double* x,
   prm.flip = flip;
   prm.spectral = spectral;
   prm.nstrips = nstrips;
+  // BLTT_TC_WAIT_CYCLES (environment, SM cycles >= 0) shortens the progress waits, so that a
+  // test can make them give up; the default is about a second
+  prm.wait_cycles = kWaitCycles;
+  if (const char* w = std::getenv("BLTT_TC_WAIT_CYCLES")) {
+    char* end = nullptr;
+    const long long v = std::strtoll(w, &end, 10);
+    if (end != w && v >= 0 && v < kWaitCycles) prm.wait_cycles = v;
+  }
   prm.NB = op.N / kCols;
   prm.nunits = nstrips * prm.NB;
   const int grid = prm.nunits < num_sms ? prm.nunits : num_sms;

@@ -129,3 +129,23 @@ def test_tc_unsupported(B):
     with pytest.raises(B.BlttError) as e:
         s.solve(to_dev(rhs_uniform(genb.n, 45)), matvec_arith=ARITH_TC)
     assert e.value.status == 8
+
+
+def test_tc_bounded_wait_gives_up_and_the_context_stays_usable(B, monkeypatch):
+    """Failure detection without a fault: BLTT_TC_WAIT_CYCLES = 0 makes the tensor-core kernel's
+    waits for progress (a stage's copy landed, its MMAs done, the accumulators read) give up at
+    the first miss.  The block then sets its error flag, writes NaN partials, waits (with the
+    default limit) for its own copies and MMAs and frees its tensor memory; the solve returns
+    BLTT_ERR_TIMEOUT (7).  Without the setting the next solve on the same handle is correct."""
+    prob = fractional_problem(2, 63, 512, 0.6)          # M = 3969: many units per block
+    f = rhs_uniform(prob.n, 71)
+    s = B.Solver(prob)
+    monkeypatch.setenv("BLTT_TC_WAIT_CYCLES", "0")
+    _, info = s.solve(to_dev(f), alpha=1e-2, tol=1e-8, maxit=20, precision=32, basis=1,
+                      matvec_arith=ARITH_TC, graph=False, raise_on_error=False)
+    assert info["status"] == 7, info
+    monkeypatch.delenv("BLTT_TC_WAIT_CYCLES")
+    u, info = s.solve(to_dev(f), alpha=1e-2, tol=1e-8, maxit=50, precision=32, basis=1,
+                      matvec_arith=ARITH_TC, graph=False)
+    assert info["status"] == 0 and info["relres_true"] <= 1e-8
+    assert rel(O.bltt_matvec(prob, to_host(u)), f) <= 1e-8
