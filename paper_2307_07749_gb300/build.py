@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbltt.so")
-SOURCES = ["kernels.cu", "bltt_api.cu", "noalloc.cu", "batched.cu", "mlp.cu", "tcmv.cu", "dfgemm.cu"]
+SOURCES = ["kernels.cu", "spec_conv.cu", "spec_tp.cu", "spec_dst.cu", "bltt_api.cu", "noalloc.cu",
+           "batched.cu", "mlp.cu", "tcmv.cu", "dfgemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -9,6 +9,9 @@
 
 namespace bltt {
 
+// log2 of a power of two, at compile time
+__host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
+
 // ------------------------------------------------------------------------------------------
 // complex numbers as CUDA vector types
 template <typename T> struct cplx;
