@@ -130,8 +130,9 @@ def peaks():
 
 # --------------------------------------------------------------------------------------------
 # algorithmic cost per unknown of each kernel family (bytes and operations the method needs)
-def kernel_cost(name, N, m, d):
-    """(bound, bytes per unknown, flops per unknown) of one launch, per unknown it processes."""
+def kernel_cost(name, N, m, d, iters=None):
+    """(bound, bytes per unknown, flops per unknown) of one launch, per unknown it processes.
+    iters: the solve's iteration count, which sets the size of a deferred-update fold."""
     l2N = np.log2(2 * N)
     lN = np.log2(N)
     if name == "conv":      # FP64: real FFT 2N fwd + inv (2 x 2.5 * 2N log2 2N / N), 6 mul, 4 epilogue
@@ -163,6 +164,10 @@ def kernel_cost(name, N, m, d):
         return "alu32", 48.0, df_timepass_ops(N)
     if name == "w_update":
         return "hbm", 48.0, 6.0
+    # deferred-update fold at the stop: x = sum of k = min(iters, 8) stored z's (k read, x written)
+    if name == "fold":
+        k = min(int(iters), 8) if iters else 8
+        return "hbm", 8.0 * (k + 1), 2.0 * k
     # basis change of the dense-operator form: an M x M by M x N FP64 GEMM (2M flops per unknown)
     if name == "basis_gemm":
         return "alu64", 16.0, 2.0 * float(m) ** d
@@ -611,7 +616,7 @@ def run_heat3d(args):
             iters = [i["iters"] for i in r["infos"]]
             kern = []
             for name, (all_l, all_ms, launches, tot_ms) in r["profile"].items():
-                bound, bpu, fpu = kernel_cost(name, prob.N, prob.m[0], prob.d)
+                bound, bpu, fpu = kernel_cost(name, prob.N, prob.m[0], prob.d, iters[-1])
                 if launches == 0 or bpu == 0:
                     continue
                 avg = tot_ms / launches
@@ -682,7 +687,7 @@ def run_varcoef(args):
                 iters = [i["iters"] for i in infos]
                 kern = []
                 for name, (_, _, launches, tot_ms) in prof.items():
-                    bound, bpu, fpu = kernel_cost(name, prob.N, prob.m[0], prob.d)
+                    bound, bpu, fpu = kernel_cost(name, prob.N, prob.m[0], prob.d, iters[-1])
                     if launches == 0 or bpu == 0:
                         continue
                     avg = tot_ms / launches
@@ -795,7 +800,7 @@ def run_dense(args):
             iters = [i["iters"] for i in r["infos"]]
             kern = []
             for name, (all_l, all_ms, launches, tot_ms) in r["profile"].items():
-                bound, bpu, fpu = kernel_cost(name, prob.N, prob.m[0], prob.d)
+                bound, bpu, fpu = kernel_cost(name, prob.N, prob.m[0], prob.d, iters[-1])
                 if launches == 0 or bpu == 0:
                     continue
                 avg = tot_ms / launches
@@ -945,7 +950,8 @@ def main():
     prof = res[HEAD]["profile"]
     kern = []
     for name, (all_launches, all_ms, launches, tot_ms) in prof.items():
-        bound, bpu, fpu = kernel_cost(name, prob.N, prob.m[0], prob.d)
+        bound, bpu, fpu = kernel_cost(name, prob.N, prob.m[0], prob.d,
+                                      res[HEAD]["infos"][-1]["iters"])
         avg_ms = tot_ms / max(launches, 1)
         units = prob.n
         if bound == "alu64":

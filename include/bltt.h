@@ -117,6 +117,16 @@ typedef struct {
                         the FP32 preconditioner with the double-float product and DSTs (precision
                         32, matvec F32X2); the true residual is checked in the DST basis inside the
                         loop.  Else BLTT_ERR_UNSUPPORTED.                                          */
+  int defer_window;  /* deferred solution update.  MINRES updates its direction vectors w and the
+                        iterate x every iteration (Sec. 4: three vectors read, two written).  With a
+                        window of S iterations the first S iterations instead keep their
+                        preconditioned vectors z_0 .. z_{S-1} in S - 1 extra workspace vectors and
+                        track x and w as coefficients over them; x is formed by one pass over the
+                        stored z's when a stop or a true-residual check needs it, and the two w
+                        vectors once, if the iterations go past the window.  Same iterates up to
+                        rounding.  0: S = 8; 1..16: S (rounded down to a multiple of the graph
+                        block, at least one block); -1: off (an update every iteration).  If the
+                        extra vectors cannot be allocated the solve runs without the window.      */
 } bltt_solve_opts;
 
 typedef struct {

@@ -131,8 +131,15 @@ struct bltt_ctx {
   // cached CUDA graph of the MINRES iterations and the key it was captured for; when captured
   // with profiling on, its event-record nodes (graph_prof) are read after every replay
   cudaGraphExec_t gexec = nullptr;
-  const void* gkey[13] = {nullptr};
+  const void* gkey[14] = {nullptr};
   std::vector<Pending> graph_prof;
+  // with a deferred-update window, the window's iteration blocks have graphs of their own (their
+  // z slots differ from block to block); gexec above serves the iterations after the window
+  struct WinGraph { cudaGraphExec_t exec = nullptr; std::vector<Pending> prof; };
+  std::vector<WinGraph> win_graphs;
+  // the window's z slots beyond the two of the workspace (S - 1 vectors of n doubles)
+  double* win_ws = nullptr;
+  int win_vectors = 0;
   bool capturing = false;
   // per-launch profiling
   bool prof = false;
@@ -162,6 +169,10 @@ struct bltt_ctx {
     for (auto& e : ev_pool) cudaEventDestroy(e);
     if (gexec) cudaGraphExecDestroy(gexec);
     for (auto& p : graph_prof) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto& w : win_graphs) {
+      if (w.exec) cudaGraphExecDestroy(w.exec);
+      for (auto& p : w.prof) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    }
   }
   bool stream_sync_ok = true;
 
@@ -305,6 +316,34 @@ bltt_status ensure_workspace(bltt_ctx* h) {
 }
 
 double* vec(bltt_ctx* h, int k) { return h->ws + (size_t)k * h->n; }
+
+// every cached graph of the iterations (their kernel arguments changed, or their key did)
+void drop_graphs(bltt_ctx* h) {
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  for (auto& p : h->graph_prof) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+  h->graph_prof.clear();
+  for (auto& w : h->win_graphs) {
+    if (w.exec) cudaGraphExecDestroy(w.exec);
+    for (auto& p : w.prof) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+  }
+  h->win_graphs.clear();
+}
+
+// the deferred-update window's z slots beyond the workspace's two: S - 1 vectors, allocated once
+// for the largest window asked for
+bltt_status ensure_window(bltt_ctx* h, int S) {
+  if (S - 1 <= h->win_vectors) return BLTT_OK;
+  if (h->win_ws) {
+    cudaStreamSynchronize(h->stream);
+    h->release(h->win_ws);
+    h->win_ws = nullptr;
+    h->win_vectors = 0;
+  }
+  drop_graphs(h);
+  CK(h, h->alloc(&h->win_ws, (size_t)(S - 1) * (size_t)h->n), "deferred-update slots");
+  h->win_vectors = S - 1;
+  return BLTT_OK;
+}
 
 // General commuting blocks: per mode i the eigenvalues of the block alpha-circulant,
 // lambda_i^(k,alpha) = FFT_N(D_alpha lam_i)_k (eq. hatcalphaieigvaldef), and the tables
@@ -566,14 +605,13 @@ void prof_end(bltt_ctx* h, const char* name, cudaEvent_t a) {
   h->pending.push_back({name, a, b});
 }
 // accumulate the event pairs of the last graph replay (the caller has synchronised)
-void prof_harvest_graph(bltt_ctx* h) {
-  std::map<std::string, float> mx;
-  std::vector<float> ms(h->graph_prof.size(), -1.f);
-  for (size_t i = 0; i < h->graph_prof.size(); ++i)
-    if (cudaEventElapsedTime(&ms[i], h->graph_prof[i].a, h->graph_prof[i].b) != cudaSuccess) ms[i] = -1.f;
-  for (size_t i = 0; i < h->graph_prof.size(); ++i) {
+void prof_harvest_graph(bltt_ctx* h, const std::vector<bltt_ctx::Pending>& gp) {
+  std::vector<float> ms(gp.size(), -1.f);
+  for (size_t i = 0; i < gp.size(); ++i)
+    if (cudaEventElapsedTime(&ms[i], gp[i].a, gp[i].b) != cudaSuccess) ms[i] = -1.f;
+  for (size_t i = 0; i < gp.size(); ++i) {
     if (ms[i] < 0.f) continue;
-    auto& st = h->stats[h->graph_prof[i].name];
+    auto& st = h->stats[gp[i].name];
     st.launches += 1;
     st.ms += ms[i];
     st.max_ms = std::max(st.max_ms, (double)ms[i]);
@@ -883,7 +921,7 @@ bltt_status bltt_set_dense_operator(bltt_handle h, const double* K) {
   h->op.mu_tab32 = dmu32;
   h->dense = true;
   h->pc_alpha = -1.0;
-  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  drop_graphs(h);
   return BLTT_OK;
 }
 
@@ -990,7 +1028,7 @@ bltt_status bltt_set_block_spectra(bltt_handle h, const double* U, const double*
   h->dense = true;           // the solve runs in U's basis, as for a dense operator
   h->spectra = true;
   h->pc_alpha = -1.0;
-  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  drop_graphs(h);
   return BLTT_OK;
 }
 
@@ -1013,7 +1051,7 @@ bltt_status bltt_set_variable_coefficient(bltt_handle h, const double* const* fa
   h->var_coef = true;
   h->pc_bscale = abar;
   h->pc_alpha = -1.0;                        // the preconditioner tables are rebuilt
-  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }   // kernel arguments changed
+  drop_graphs(h);                           // kernel arguments changed
   return BLTT_OK;
 }
 
@@ -1204,19 +1242,27 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
 
   double* bvec = vec(h, 0);
   double* vbuf[2] = {vec(h, 1), vec(h, 2)};
-  double* zbuf[2] = {vec(h, 3), vec(h, 4)};
-  double* wbuf[2] = {vec(h, 5), vec(h, 6)};
   double* q = vec(h, 7);
   double* x = spectral ? vec(h, 8) : u;
   double* tmp = vec(h, 9);
   const long long n = h->n;
 
   // state: tol, maxit
+  // deferred solution update: the first S iterations store their z vectors and keep x and w as
+  // coefficients over them (no per-iteration (w, x) update); S is a multiple of the graph block
+  const int G = (sync_every + 1) & ~1;
+  int S = 0;
+  if (!o.single_block && o.defer_window >= 0 && G <= kMaxWin) {
+    const int want = o.defer_window > 0 ? std::min(o.defer_window, kMaxWin) : 8;
+    S = std::max(G, (want / G) * G);
+    if (ensure_window(h, S) != BLTT_OK) { S = 0; (void)cudaGetLastError(); }
+  }
   MinresDev* sh = h->state_host;
   std::memset(sh, 0, sizeof *sh);
   sh->tol = tol;
   sh->maxit = maxit;
   sh->phase = PH_RUN;
+  sh->win = S;
   CK(h, cudaMemcpyAsync(h->state, sh, sizeof *sh, cudaMemcpyHostToDevice, st), "state upload");
   int* phase = &h->state->phase;
   // the end of every solve: timings, status and statistics
@@ -1326,24 +1372,49 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
     PCK(h, "flip", launch_flip_copy(f, bvec, h->N, h->M, h->partials[1], &nb, st), "flip");
     h->launches++;
   }
-  const int cur0 = 0;
-  int cur = cur0;
-  // v_1 = b (copied into vbuf[cur]), z_1 = P^{-1} v_1, <z_1, v_1>
+  // buffer roles by iteration t: v_t and v_{t-1} alternate between two vectors; inside the window
+  // (t < S) iteration t reads z_t from slot t and writes z_{t+1} into slot t + 1; after it, z and w
+  // alternate between two vectors each, starting from slot S (z_S) and the w vectors the fold
+  // formed (wc = w_{S-1}, wo = w_{S-2})
+  double* Zs[kMaxWin + 1] = {vec(h, 3), vec(h, 4)};
+  for (int k = 2; k <= S; ++k) Zs[k] = h->win_ws + (size_t)(k - 2) * (size_t)n;
+  double* const Zc[2] = {S ? Zs[S] : vec(h, 3), S ? Zs[S - 1] : vec(h, 4)};
+  double* const Wc[2] = {vec(h, 5), vec(h, 6)};
+  double* const V0[2] = {vbuf[0], vbuf[1]};
+  struct Roles { double *vc, *vp, *zc, *zp, *wc, *wp; };
+  auto roles = [&](int t) -> Roles {
+    Roles r;
+    r.vc = V0[t & 1];
+    r.vp = V0[(t + 1) & 1];
+    if (t < S) {
+      r.zc = Zs[t]; r.zp = Zs[t + 1]; r.wc = r.wp = nullptr;
+    } else {
+      const int k = (t - S) & 1;
+      r.zc = Zc[k]; r.zp = Zc[1 - k]; r.wc = Wc[k]; r.wp = Wc[1 - k];
+    }
+    return r;
+  };
+  FoldArgs fa{};
+  for (int k = 0; k < S; ++k) fa.z[k] = Zs[k];
+  fa.x = x; fa.wo = Wc[1]; fa.wc = Wc[0]; fa.n = n; fa.S = S;
+  // v_1 = b (copied into V0[0]), z_0 = P^{-1} v_1 (into slot 0), <z_0, v_1>
   {
     Combine c{};
     c.in0 = bvec;
-    c.vout = vbuf[cur];
-    s = precond_chain(h, spectral, o.precision, pt, c, zbuf[cur], vbuf[cur], h->partials[0], &nzv, nullptr);
+    c.vout = V0[0];
+    s = precond_chain(h, spectral, o.precision, pt, c, Zs[0], V0[0], h->partials[0], &nzv, nullptr);
     if (s != BLTT_OK) return s;
   }
-  CK(h, cudaMemsetAsync(x, 0, n * sizeof(double), st), "memset x");
-  CK(h, cudaMemsetAsync(vbuf[1 - cur], 0, n * sizeof(double), st), "memset v0");
-  CK(h, cudaMemsetAsync(wbuf[0], 0, n * sizeof(double), st), "memset w0");
-  CK(h, cudaMemsetAsync(wbuf[1], 0, n * sizeof(double), st), "memset w1");
+  CK(h, cudaMemsetAsync(V0[1], 0, n * sizeof(double), st), "memset v0");
+  if (S == 0) {
+    CK(h, cudaMemsetAsync(x, 0, n * sizeof(double), st), "memset x");
+    CK(h, cudaMemsetAsync(Wc[0], 0, n * sizeof(double), st), "memset w0");
+    CK(h, cudaMemsetAsync(Wc[1], 0, n * sizeof(double), st), "memset w1");
+  }
   PCK(h, "scalar", launch_scalar_init(h->state, h->partials[0], nzv, h->partials[1], nb, st), "scalar init");
   h->launches++;
 
-  // one MINRES iteration (A1..A4 of the hot loop); the caller rotates the buffers afterwards
+  // one MINRES iteration (A1..A4 of the hot loop)
   // DST basis with the FFT product: the true residual is checked by the host in the physical
   // basis once the estimate has met the stopping rule (the iterations halt in PH_VERIFY and
   // resume if the check fails), so the iterations carry no residual product of their own.  With
@@ -1353,33 +1424,37 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
   const bool defer = (spectral != 0) && !h->dense && op.ntaps == 0;
   const long long per_iter = 5 + ((op.b_kind == 1 && op.ntaps == 0 && !spectral) ? 4 : 2) +
                              (spectral || none ? 0 : 2 * op.d) + (tc ? 1 : 0) - (defer ? 1 : 0);
-  auto issue_iteration = [&](int c0) -> bltt_status {
-    const long long saved = h->launches;   // counted per iteration by the caller (per_iter)
+  // kernels of iteration t: the last window iteration of a solve that checks its residual on the
+  // device folds a second time (the w vectors, if the check sends the iterations on)
+  auto launches_of = [&](int t) -> long long { return per_iter + ((!defer && t == S - 1) ? 1 : 0); };
+  auto issue_iteration = [&](int t) -> bltt_status {
+    const long long saved = h->launches;   // counted per iteration by the caller (launches_of)
     struct Restore { bltt_ctx* hh; long long v; ~Restore() { hh->launches = v; } } restore{h, saved};
-    const int prv = 1 - c0;
-    // q = Y A z_j  (z_j = z_u / gamma_j), delta_j = <q, z_j>
+    const Roles r = roles(t);
+    // q = Y A z_t  (z_t = z_u / gamma_t), delta_t = <q, z_t>
     if (tc) {
       // the two kernels of the tensor-core product, profiled apart
-      PCK(h, "tc_digits", launch_tc_digits(op, zbuf[c0], &h->state->inv_gamma, phase, st),
+      PCK(h, "tc_digits", launch_tc_digits(op, r.zc, &h->state->inv_gamma, phase, st),
           "digit planes");
-      PCK(h, "conv_tc", launch_tc_product(op, spectral, zbuf[c0], &h->state->inv_gamma, q, 1,
+      PCK(h, "conv_tc", launch_tc_product(op, spectral, r.zc, &h->state->inv_gamma, q, 1,
                                           h->partials[0], &np, phase, st), "matvec");
     } else {
-      PCK(h, mv_name(op), launch_matvec(op, spectral, zbuf[c0], &h->state->inv_gamma, q, 1,
+      PCK(h, mv_name(op), launch_matvec(op, spectral, r.zc, &h->state->inv_gamma, q, 1,
                                         MV_STORE, nullptr, h->partials[0], &np, phase, tmp, st),
           "matvec");
     }
     PCK(h, "scalar", launch_scalar_delta(h->state, h->partials[0], np, st), "scalar delta");
-    // v_{j+1} = q - (delta/gamma) v_j - (gamma/gamma_prev) v_{j-1} (over v_{j-1});
-    // z_{j+1} = P^{-1} v_{j+1} (over z_{j-1}); <z_{j+1}, v_{j+1}>
+    // v_{t+1} = q - (delta/gamma) v_t - (gamma/gamma_prev) v_{t-1} (over v_{t-1});
+    // z_{t+1} = P^{-1} v_{t+1}; <z_{t+1}, v_{t+1}>
     Combine c{};
-    c.in0 = q; c.in1 = vbuf[c0]; c.in2 = vbuf[prv];
-    c.coef = h->state->coef; c.vout = vbuf[prv];
-    bltt_status r = precond_chain(h, spectral, o.precision, pt, c, zbuf[prv], vbuf[prv],
-                                  h->partials[1], &np, phase);
-    if (r != BLTT_OK) return r;
+    c.in0 = q; c.in1 = r.vc; c.in2 = r.vp;
+    c.coef = h->state->coef; c.vout = r.vp;
+    bltt_status rs = precond_chain(h, spectral, o.precision, pt, c, r.zp, r.vp, h->partials[1],
+                                   &np, phase);
+    if (rs != BLTT_OK) return rs;
     PCK(h, "scalar", launch_scalar_gamma(h->state, h->partials[1], np, st), "scalar gamma");
-    PCK(h, "w_update", launch_w_update(h->state, zbuf[c0], wbuf[prv], wbuf[c0], x, n, st), "w update");
+    if (t < S) PCK(h, "fold", launch_fold(h->state, fa, st), "fold");
+    else PCK(h, "w_update", launch_w_update(h->state, r.zc, r.wp, r.wc, x, n, st), "w update");
     if (defer) {
       PCK(h, "scalar", launch_scalar_defer(h->state, st), "scalar check");
       return BLTT_OK;
@@ -1388,23 +1463,15 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
     PCK(h, mv_name(op, MV_RESID), launch_matvec(op, spectral, x, nullptr, nullptr, 1, MV_RESID, bvec,
                                       h->partials[0], &np, phase, tmp, st), "residual");
     PCK(h, "scalar", launch_scalar_check(h->state, h->partials[0], np, st), "scalar check");
+    if (t == S - 1) PCK(h, "fold", launch_fold(h->state, fa, st), "fold");
     return BLTT_OK;
   };
-  auto rotate = [&]() {
-    std::swap(vbuf[0], vbuf[1]);
-    std::swap(zbuf[0], zbuf[1]);
-    std::swap(wbuf[0], wbuf[1]);
-  };
-  // A5: blocks of G iterations captured once in a CUDA graph (G even, so that the buffers return
-  // to their roles) and replayed; the legacy stream cannot be captured, profiling needs the
-  // direct launches
-  const int G = (sync_every + 1) & ~1;
+  // A5: blocks of G iterations captured once in a CUDA graph and replayed (G even, so that the
+  // alternating roles return to the same vectors; the window's blocks have a graph each); the
+  // legacy stream cannot be captured
   const bool graph_mode = (st != nullptr) && !o.no_graph;
+  const int nwin = S / G;
   int issued = 0;
-  // buffer roles of the first iteration; iteration j uses them rotated j times
-  double* const vbuf0[2] = {vbuf[0], vbuf[1]};
-  double* const zbuf0[2] = {zbuf[0], zbuf[1]};
-  double* const wbuf0[2] = {wbuf[0], wbuf[1]};
   bool resumed = false;
   double relres_phys = 0.0;
   // host-buffer solve: u goes back on the copy stream once final
@@ -1418,49 +1485,58 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
   };
   for (;;) {
     if (graph_mode && !resumed) {
-      const void* key[13] = {(const void*)(intptr_t)spectral, (const void*)(intptr_t)o.precision,
+      const void* key[14] = {(const void*)(intptr_t)spectral, (const void*)(intptr_t)o.precision,
                              (const void*)(intptr_t)op.mv_arith, (const void*)(intptr_t)none,
                              (const void*)(intptr_t)G, x, pt.g64, pt.ahat32, pt.gdf, pt.dinv, st,
-                             (const void*)(intptr_t)op.ntaps, (const void*)(intptr_t)h->prof};
-      if (!h->gexec || std::memcmp(key, h->gkey, sizeof key) != 0) {
-        if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
-        for (auto& p : h->graph_prof) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
-        h->graph_prof.clear();
-        prof_harvest(h);                     // nothing of the capture may mix with earlier events
+                             (const void*)(intptr_t)op.ntaps, (const void*)(intptr_t)h->prof,
+                             (const void*)(intptr_t)S};
+      if (std::memcmp(key, h->gkey, sizeof key) != 0) {
+        drop_graphs(h);
+        std::memcpy(h->gkey, key, sizeof key);
+      }
+      if ((int)h->win_graphs.size() != nwin) h->win_graphs.resize(nwin);
+      prof_harvest(h);   // nothing of a capture may mix with earlier events
+      // capture (once) the graph of the block that starts at iteration t0
+      auto graph_for = [&](int t0, cudaGraphExec_t& ex, std::vector<bltt_ctx::Pending>& gp) -> bltt_status {
+        if (ex) return BLTT_OK;
+        for (auto& p : gp) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+        gp.clear();
         cudaGraph_t g = nullptr;
         CK(h, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
         h->capturing = true;
         bltt_status cap = BLTT_OK;
-        for (int i = 0; i < G && cap == BLTT_OK; ++i) {
-          cap = issue_iteration(cur);
-          rotate();
-        }
+        for (int i = 0; i < G && cap == BLTT_OK; ++i) cap = issue_iteration(t0 + i);
         h->capturing = false;
-        h->graph_prof.swap(h->pending);      // the event-record nodes of this graph
+        gp.swap(h->pending);                 // the event-record nodes of this graph
         h->pending.clear();
         cudaError_t ce = cudaStreamEndCapture(st, &g);
         if (cap != BLTT_OK) { if (g) cudaGraphDestroy(g); return cap; }
         CK(h, ce, "end capture");
-        ce = cudaGraphInstantiate(&h->gexec, g, 0);
+        ce = cudaGraphInstantiate(&ex, g, 0);
         cudaGraphDestroy(g);
         CK(h, ce, "graph instantiate");
-        std::memcpy(h->gkey, key, sizeof key);
-      }
+        return BLTT_OK;
+      };
       for (;;) {
-        CK(h, cudaGraphLaunch(h->gexec, st), "graph launch");
-        h->launches += per_iter * G;
+        const bool in_win = issued < S;
+        const int b = issued / G;
+        cudaGraphExec_t& ex = in_win ? h->win_graphs[b].exec : h->gexec;
+        std::vector<bltt_ctx::Pending>& gp = in_win ? h->win_graphs[b].prof : h->graph_prof;
+        s = graph_for(in_win ? issued : S, ex, gp);
+        if (s != BLTT_OK) return s;
+        CK(h, cudaGraphLaunch(ex, st), "graph launch");
+        for (int i = 0; i < G; ++i) h->launches += launches_of(issued + i);
         issued += G;
         CK(h, cudaMemcpyAsync(sh, h->state, sizeof *sh, cudaMemcpyDeviceToHost, st), "state download");
         CK(h, cudaStreamSynchronize(st), "sync");
-        if (h->prof) prof_harvest_graph(h);
+        if (h->prof) prof_harvest_graph(h, gp);
         if (sh->phase != PH_RUN || issued >= maxit) break;
       }
     } else {
       for (;;) {
-        s = issue_iteration(cur);
+        s = issue_iteration(issued);
         if (s != BLTT_OK) return s;
-        h->launches += per_iter;
-        rotate();
+        h->launches += launches_of(issued);
         ++issued;
         if (issued % sync_every == 0 || issued >= maxit) {
           CK(h, cudaMemcpyAsync(sh, h->state, sizeof *sh, cudaMemcpyDeviceToHost, st), "state download");
@@ -1468,6 +1544,16 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
           if (sh->phase != PH_RUN || issued >= maxit) break;
         }
       }
+    }
+    // a window solve forms x at every stop on the device; not when it failed before its fold,
+    // nor when it took no iteration (x = 0)
+    if (S > 0 && sh->iter == 0) {
+      CK(h, cudaMemsetAsync(x, 0, n * sizeof(double), st), "memset x");
+    } else if (S > 0 && sh->phase == PH_FAIL && sh->iter <= S) {
+      FoldArgs fx = fa;
+      fx.req = 1;
+      PCK(h, "fold", launch_fold(h->state, fx, st), "fold");
+      h->launches++;
     }
     relres_phys = sh->relres_true;
     if (!spectral) {
@@ -1516,15 +1602,20 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
       break;
     }
     if (sh->iter >= maxit) { sh->phase = PH_MAXIT; sh->status = 6; break; }
-    // resume: direct launches from the buffer roles of iteration sh->iter (a replayed graph
-    // could be stopped mid-block); u may still be on its way to the host
+    // resume: direct launches from iteration sh->iter (a replayed graph could be stopped
+    // mid-block); u may still be on its way to the host.  At the window's end the iterations
+    // after it need the w vectors, which the fold at the stop left out
     if (hout) CK(h, cudaStreamSynchronize(h->io_stream), "sync copy stream");
-    for (int i = 0; i < 2; ++i) { vbuf[i] = vbuf0[i]; zbuf[i] = zbuf0[i]; wbuf[i] = wbuf0[i]; }
-    if (sh->iter & 1) rotate();
     issued = sh->iter;
     resumed = true;
     sh->phase = PH_RUN;
     CK(h, cudaMemcpyAsync(phase, &sh->phase, sizeof(int), cudaMemcpyHostToDevice, st), "resume");
+    if (S > 0 && issued == S) {
+      FoldArgs fw = fa;
+      fw.req = 2;
+      PCK(h, "fold", launch_fold(h->state, fw, st), "fold");
+      h->launches++;
+    }
   }
   return finish(relres_phys);
 }

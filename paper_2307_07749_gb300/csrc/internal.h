@@ -11,6 +11,7 @@ constexpr int kThreads = 256;      // threads of an FFT tile kernel (double-floa
 constexpr int kCap = 4096;         // complex points per FFT tile (64 KB of FP64 smem)
 constexpr int kMaxPartials = 1 << 20;
 constexpr int kMaxCols = 256;     // real lines per FFT tile (column info kept in shared memory)
+constexpr int kMaxWin = 16;       // iterations whose solution update a solve may defer
 
 // MINRES scalar state, resident on the device for the whole solve.
 // PH_VERIFY: the recurrence estimate met the stopping rule in a solve whose true residual the
@@ -28,6 +29,23 @@ struct MinresDev {
   double normb, relres_est, relres_true, tol;
   double gamma_new;
   int iter, maxit, phase, status, wpending, pad;
+  // deferred solution update over the first `win` iterations: their w vectors and x are kept as
+  // coefficients over the stored z_0 .. z_{win-1} (xi: x, cwo / cwc: the two latest w), and
+  // k_fold forms the vectors only when needed.  fold_req: bit 0 x, bit 1 the two w vectors.
+  int win, fold_req;
+  double xi[kMaxWin], cwo[kMaxWin], cwc[kMaxWin];
+};
+
+// the vectors of a deferred-update fold: x = sum_s xi_s z_s, wo = sum_s cwo_s z_s,
+// wc = sum_s cwc_s z_s over the first min(iter, S) window slots
+struct FoldArgs {
+  const double* z[kMaxWin];
+  double* x;
+  double* wo;
+  double* wc;
+  long long n;
+  int S;
+  int req;       // 0: the device's fold_req decides; else this request
 };
 
 // Operator data handed to the kernels (device pointers).
@@ -186,6 +204,7 @@ int one_tile_columns(long long nlines, int Lfft, int cap_points = kCap);
 cudaError_t launch_solve_one(const OneSolve& s, bool chosen, cudaStream_t st);
 cudaError_t launch_w_update(MinresDev* s, const double* z, double* w_prev, const double* w,
                             double* x, long long n, cudaStream_t st);
+cudaError_t launch_fold(const MinresDev* s, const FoldArgs& a, cudaStream_t st);
 cudaError_t launch_copy_scaled_check(const double* src, double* dst, long long n, cudaStream_t st);
 cudaError_t launch_sum_partials(const double* partials, int np, double* out, cudaStream_t st);
 

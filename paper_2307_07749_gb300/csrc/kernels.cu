@@ -110,12 +110,16 @@ __device__ __forceinline__ double apply_stencil(const PointStencil<D2>& ps,
   return v;
 }
 
-constexpr int kDirectChunk = 32;   // time steps a thread walks per work unit
+constexpr int kDirectChunk = 32;   // time steps of one work unit (two walks of half as many)
 
 // One work unit: a group of kDirectThreads x P consecutive points (P per thread, kDirectThreads
-// apart) over a chunk of kDirectChunk time steps; the K-1 earlier values (and their L x in the
-// physical basis) are loaded at the chunk's start.  Units run point groups fastest, so that the
-// blocks in flight read neighbouring runs of the same rows.
+// apart) over two walks of kDirectChunk/2 time steps: t = t0, t0+1, ... in the first half of the
+// time axis and its mirror tau = N-1-t downwards.  The fused dot product delta = <Y A x, x>
+// multiplies the output of step t, stored at row N-1-t = tau, by x_tau, which the mirror walk has
+// in a register at the same step (and the other way round), so x is read once and y written once:
+// 16 B per unknown.  Each walk keeps the K-1 neighbouring values (and their L x in the physical
+// basis) in registers; they are loaded at the walk's start.  Units run point groups fastest, so
+// that the blocks in flight read neighbouring runs of the same rows.
 template <int K, bool SPECTRAL>
 __global__ void __launch_bounds__(kDirectThreads)
 k_direct(OpTables op, const double* __restrict__ x, const double* xscale, double* y, int flip,
@@ -124,8 +128,9 @@ k_direct(OpTables op, const double* __restrict__ x, const double* xscale, double
   constexpr bool spectral = SPECTRAL;
   constexpr int P = SPECTRAL ? kDirectPts : 1;
   constexpr int D2 = SPECTRAL ? 1 : 6;          // stencil neighbours kept per point
+  constexpr int HALF = kDirectChunk / 2;
   __shared__ double red[32];
-  const int N = op.N;
+  const int N = op.N, Nh = op.N / 2;            // N is even (a power of two >= 2)
   const long long M = op.M;
   const double s = xscale ? *xscale : 1.0;
   bool any_b = false;
@@ -133,14 +138,16 @@ k_direct(OpTables op, const double* __restrict__ x, const double* xscale, double
   for (int k = 0; k < K; ++k) any_b |= (op.b_dev[k] != 0.0);
   const bool lap = !spectral && any_b;
   const long long groups = (M + P * kDirectThreads - 1) / (P * kDirectThreads);
-  const long long units = groups * ((N + kDirectChunk - 1) / kDirectChunk);
+  const long long units = groups * ((Nh + HALF - 1) / HALF);
   double acc = 0.0;
   for (long long u = blockIdx.x; u < units; u += gridDim.x) {
     const int chunk = (int)(u / groups);
     const long long c0 = (u - (long long)chunk * groups) * (P * kDirectThreads);
-    const int t0 = chunk * kDirectChunk, t1 = min(N, t0 + kDirectChunk);
+    const int t0 = chunk * HALF, t1 = min(Nh, t0 + HALF);
+    const int tau0 = N - 1 - t0;
     long long ip[P];
-    double ca[P][K], cb[P][K], xp[P][K], lp[P][K];
+    // xf[k] = x_{t-k} (forward walk), xb[k] = x_{tau-k} (mirror walk); lf, lb: their L x
+    double ca[P][K], cb[P][K], xf[P][K], lf[P][K], xb[P][K], lb[P][K];
     PointStencil<D2> pst[P];
 #pragma unroll
     for (int q = 0; q < P; ++q) {
@@ -156,51 +163,73 @@ k_direct(OpTables op, const double* __restrict__ x, const double* xscale, double
         const double ak = op.a_dev[k], bk = op.b_dev[k];
         ca[q][k] = spectral ? s * fma(bk, mu, ak) : s * ak;
         cb[q][k] = spectral ? 0.0 : s * bk;
-        // the chunk's earlier steps t0 - k (zero before the first step)
+        xf[q][k] = 0.0; lf[q][k] = 0.0; xb[q][k] = 0.0; lb[q][k] = 0.0;
+      }
+#pragma unroll
+      for (int k = 1; k < K; ++k) {
+        // the forward walk's earlier steps t0 - k (zero before the first step), stored one slot
+        // ahead: the step loop shifts before it uses them
         const int tk = t0 - k;
-        xp[q][k] = 0.0;
-        lp[q][k] = 0.0;
-        if (k > 0 && tk >= 0) {
+        if (tk >= 0) {
           const double* xt = x + (long long)tk * M + i;
-          // stored one slot ahead: the step loop shifts before it uses them
-          xp[q][k - 1] = xt[0];
-          if (!spectral && lap) lp[q][k - 1] = apply_stencil<D2>(pst[q], xt);
+          xf[q][k - 1] = xt[0];
+          if (!spectral && lap) lf[q][k - 1] = apply_stencil<D2>(pst[q], xt);
+        }
+        // the mirror walk's first K-1 values tau0 - (k-1); its step loop loads the K-th
+        const int tb = tau0 - (k - 1);
+        if (tb >= 0) {
+          const double* xt = x + (long long)tb * M + i;
+          xb[q][k - 1] = xt[0];
+          if (!spectral && lap) lb[q][k - 1] = apply_stencil<D2>(pst[q], xt);
         }
       }
     }
     for (int t = t0; t < t1; ++t) {
-      const long long row = (long long)t * M;
-      const long long orow = (long long)(flip ? (N - 1 - t) : t) * M;
-      double xs[P], pr[P];
+      const int tau = N - 1 - t;
+      const int tn = tau - (K - 1);                // the mirror walk's new value: x_{tau-K+1}
+      const long long rf = (long long)(flip ? tau : t) * M;   // where the outputs of t and tau go
+      const long long rb = (long long)(flip ? t : tau) * M;
+      double xsf[P], xsb[P], prf[P], prb[P];
 #pragma unroll
       for (int q = 0; q < P; ++q) {
         const long long i = ip[q] < M ? ip[q] : M - 1;
-        xs[q] = x[row + i];
-        pr[q] = (mode != MV_STORE) ? rhs[orow + i] : (partials ? x[orow + i] : 0.0);
+        xsf[q] = x[(long long)t * M + i];
+        xsb[q] = tn >= 0 ? x[(long long)tn * M + i] : 0.0;
+        prf[q] = 0.0; prb[q] = 0.0;
+        if (mode != MV_STORE) { prf[q] = rhs[rf + i]; prb[q] = rhs[rb + i]; }
       }
 #pragma unroll
       for (int q = 0; q < P; ++q) {
         const long long i = ip[q] < M ? ip[q] : M - 1;
 #pragma unroll
-        for (int k = K - 1; k > 0; --k) { xp[q][k] = xp[q][k - 1]; lp[q][k] = lp[q][k - 1]; }
-        xp[q][0] = xs[q];
-        if (!spectral && lap) lp[q][0] = apply_stencil<D2>(pst[q], x + row + i);
-        double val = 0.0;
+        for (int k = K - 1; k > 0; --k) { xf[q][k] = xf[q][k - 1]; lf[q][k] = lf[q][k - 1]; }
+        xf[q][0] = xsf[q];
+        xb[q][K - 1] = xsb[q];
+        if (!spectral && lap) {
+          lf[q][0] = apply_stencil<D2>(pst[q], x + (long long)t * M + i);
+          lb[q][K - 1] = tn >= 0 ? apply_stencil<D2>(pst[q], x + (long long)tn * M + i) : 0.0;
+        }
+        double vf = 0.0, vb = 0.0;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-          val = fma(ca[q][k], xp[q][k], val);
-          if (!spectral) val = fma(cb[q][k], lp[q][k], val);
+          vf = fma(ca[q][k], xf[q][k], vf);
+          vb = fma(ca[q][k], xb[q][k], vb);
+          if (!spectral) { vf = fma(cb[q][k], lf[q][k], vf); vb = fma(cb[q][k], lb[q][k], vb); }
         }
         if (ip[q] < M) {
           if (mode == MV_STORE) {
-            y[orow + i] = val;
-            acc = fma(val, pr[q], acc);               // times s once per block below
+            y[rf + i] = vf;
+            y[rb + i] = vb;
+            // partner of each output: x at the row it is stored in (times s once per block)
+            if (partials) acc = fma(vb, flip ? xf[q][0] : xb[q][0], fma(vf, flip ? xb[q][0] : xf[q][0], acc));
           } else {
-            const double r = pr[q] - val;
-            if (y) y[orow + i] = r;
-            acc = fma(r, r, acc);
+            const double r1 = prf[q] - vf, r2 = prb[q] - vb;
+            if (y) { y[rf + i] = r1; y[rb + i] = r2; }
+            acc = fma(r2, r2, fma(r1, r1, acc));
           }
         }
+#pragma unroll
+        for (int k = 0; k < K - 1; ++k) { xb[q][k] = xb[q][k + 1]; lb[q][k] = lb[q][k + 1]; }
       }
     }
   }
@@ -313,6 +342,7 @@ __device__ __forceinline__ void scalar_init(MinresDev* st, const double* pzv, in
   st->normb = sqrt(nb2);
   st->iter = 0;
   st->wpending = 0;
+  st->fold_req = 0;
   st->relres_est = 1.0;
   st->relres_true = 1.0;
   st->gamma_new = 0.0;
@@ -369,10 +399,30 @@ __device__ __forceinline__ void scalar_gamma(MinresDev* st, const double* p, int
   st->inv_gamma = gn > 0.0 ? 1.0 / gn : 0.0;
   st->s_prev = s; st->s = sn;
   st->c_prev = c; st->c = cn;
+  const int t = st->iter;   // this iteration's index
   st->iter += 1;
-  st->wpending = 1;
   st->relres_est = fabs(st->eta) / st->eta0;
   if (gn == 0.0 || st->relres_est <= st->tol || st->iter >= st->maxit) st->phase = PH_CHECK;
+  if (t >= st->win) {
+    st->wpending = 1;
+    st->fold_req = 0;
+    return;
+  }
+  // deferred update: w_t = w_cz z_t + w_cwp w_{t-2} + w_cw w_{t-1} and x += w_ceta w_t, applied to
+  // the coefficients over z_0 .. z_t (w_{-1} = w_{-2} = 0, x_0 = 0)
+  st->wpending = 0;
+  for (int k = 0; k <= t; ++k) {
+    double wn = fma(st->w_cwp, st->cwo[k], st->w_cw * st->cwc[k]);
+    if (k == t) wn += st->w_cz;
+    st->xi[k] = fma(st->w_ceta, wn, st->xi[k]);
+    st->cwo[k] = st->cwc[k];
+    st->cwc[k] = wn;
+  }
+  // a stop or a true-residual check needs x now; the window's last iteration hands the two latest
+  // w vectors (and x) to the per-iteration update of the iterations after it
+  int req = (st->phase != PH_RUN) ? 1 : 0;
+  if (st->iter == st->win && st->phase == PH_RUN) req = 3;
+  st->fold_req = req;
 }
 
 __device__ __forceinline__ void scalar_check(MinresDev* st, const double* p, int np) {
@@ -381,6 +431,7 @@ __device__ __forceinline__ void scalar_check(MinresDev* st, const double* p, int
   double r2 = check ? reduce_partials(p, np, red) : 0.0;
   if (threadIdx.x != 0) return;
   st->wpending = 0;
+  st->fold_req = 0;
   if (!check) return;
   const double rr = sqrt(r2) / st->normb;
   st->relres_true = rr;
@@ -391,6 +442,8 @@ __device__ __forceinline__ void scalar_check(MinresDev* st, const double* p, int
     st->phase = PH_MAXIT; st->status = 6;
   } else {
     st->phase = PH_RUN;
+    // the check failed at the last deferred iteration: the iterations after it need the w vectors
+    if (st->win > 0 && st->iter == st->win) st->fold_req = 2;
   }
 }
 
@@ -411,6 +464,7 @@ __global__ void __launch_bounds__(256) k_scalar_check(MinresDev* st, const doubl
 // iterations (PH_VERIFY) instead of launching the residual product here
 __global__ void k_scalar_defer(MinresDev* st) {
   st->wpending = 0;
+  st->fold_req = 0;
   if (st->phase == PH_CHECK) st->phase = PH_VERIFY;
 }
 
@@ -478,6 +532,87 @@ __global__ void __launch_bounds__(256) k_w_update(const MinresDev* st, const dou
   if (!st->wpending) return;
   w_update_range(z, w_prev, w, x, n, blockIdx.x * (long long)blockDim.x + threadIdx.x,
                  (long long)gridDim.x * blockDim.x, st->w_cz, st->w_cwp, st->w_cw, st->w_ceta);
+}
+
+// Deferred-update fold: x = sum_s xi_s z_s (bit 0 of the request) and the two latest w vectors
+// wo = sum_s cwo_s z_s, wc = sum_s cwc_s z_s (bit 1) over the k = min(iter, S) stored z's, in FP64,
+// summed in slot order.  Pairs of elements as 16-byte accesses.  The loop is latency-bound unless
+// each thread keeps several loads in flight: a thread takes U = 8 / KB pairs per step (KB >= k, a
+// power of two picked on the device from k) and issues all their loads before the first
+// multiply-add, so that about eight loads are in flight per thread whatever k is (with one pair
+// per step the fold took the same 0.9 ms on the 66.6 M-unknown workload for k = 1 and k = 8).
+template <int R, int KB>
+__device__ __forceinline__ void fold_pairs(const FoldArgs& a, int k, const double* cx,
+                                           const double* co, const double* cc, long long e,
+                                           long long stride) {
+  constexpr int U = KB >= 8 ? 1 : 8 / KB;
+  const long long n2 = a.n >> 1;
+  auto one = [&](const double2* zv, long long i) {
+    double2 x = make_double2(0.0, 0.0), wo = x, wc = x;
+#pragma unroll
+    for (int s = 0; s < KB; ++s) {
+      if (s < k) {
+        if (R & 1) { x.x = fma(cx[s], zv[s].x, x.x); x.y = fma(cx[s], zv[s].y, x.y); }
+        if (R & 2) {
+          wo.x = fma(co[s], zv[s].x, wo.x); wo.y = fma(co[s], zv[s].y, wo.y);
+          wc.x = fma(cc[s], zv[s].x, wc.x); wc.y = fma(cc[s], zv[s].y, wc.y);
+        }
+      }
+    }
+    if (R & 1) __stcs(reinterpret_cast<double2*>(a.x) + i, x);
+    if (R & 2) {
+      __stcs(reinterpret_cast<double2*>(a.wo) + i, wo);
+      __stcs(reinterpret_cast<double2*>(a.wc) + i, wc);
+    }
+  };
+  for (; e + (U - 1) * stride < n2; e += U * stride) {
+    double2 zv[U][KB];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int s = 0; s < KB; ++s)
+        if (s < k) zv[u][s] = __ldcs(reinterpret_cast<const double2*>(a.z[s]) + e + u * stride);
+#pragma unroll
+    for (int u = 0; u < U; ++u) one(zv[u], e + u * stride);
+  }
+  for (; e < n2; e += stride) {
+    double2 zv[KB];
+#pragma unroll
+    for (int s = 0; s < KB; ++s)
+      if (s < k) zv[s] = __ldcs(reinterpret_cast<const double2*>(a.z[s]) + e);
+    one(zv, e);
+  }
+}
+
+template <int R, int KMAX>
+__device__ __forceinline__ void fold_dispatch(const FoldArgs& a, int k, const double* cx,
+                                              const double* co, const double* cc, long long e,
+                                              long long stride) {
+  if (k <= 1) fold_pairs<R, 1>(a, k, cx, co, cc, e, stride);
+  else if (k <= 2) fold_pairs<R, 2>(a, k, cx, co, cc, e, stride);
+  else if (KMAX >= 4 && k <= 4) fold_pairs<R, (KMAX >= 4 ? 4 : 2)>(a, k, cx, co, cc, e, stride);
+  else if (KMAX >= 8 && k <= 8) fold_pairs<R, (KMAX >= 8 ? 8 : 2)>(a, k, cx, co, cc, e, stride);
+  else if (KMAX >= 16) fold_pairs<R, (KMAX >= 16 ? 16 : 2)>(a, k, cx, co, cc, e, stride);
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(256, 2) k_fold(const MinresDev* st, FoldArgs a) {
+  const int req = a.req ? a.req : st->fold_req;
+  if (!req) return;
+  const int k = min(st->iter, a.S);
+  __shared__ double cx[kMaxWin], co[kMaxWin], cc[kMaxWin];
+  if (threadIdx.x < kMaxWin) {
+    cx[threadIdx.x] = st->xi[threadIdx.x];
+    co[threadIdx.x] = st->cwo[threadIdx.x];
+    cc[threadIdx.x] = st->cwc[threadIdx.x];
+  }
+  __syncthreads();
+  if (k < 1 || k > KMAX) return;   // the launcher picks KMAX >= the window, so k > KMAX never
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  if (req == 1) fold_dispatch<1, KMAX>(a, k, cx, co, cc, e, stride);
+  else if (req == 2) fold_dispatch<2, KMAX>(a, k, cx, co, cc, e, stride);
+  else fold_dispatch<3, KMAX>(a, k, cx, co, cc, e, stride);
 }
 
 __global__ void __launch_bounds__(256) k_sum_partials(const double* p, int np, double* out) {
@@ -797,7 +932,8 @@ cudaError_t launch_matvec(const OpTables& op, int spectral, const double* x, con
   const int want = (mode == MV_RESID) ? PH_CHECK : PH_RUN;
   if (op.ntaps > 0) {
     const long long per = (long long)(spectral ? kDirectPts : 1) * kDirectThreads;
-    long long g = (op.M + per - 1) / per * ((op.N + kDirectChunk - 1) / kDirectChunk);
+    const int half = kDirectChunk / 2;
+    long long g = (op.M + per - 1) / per * ((op.N / 2 + half - 1) / half);
     if (g > 152LL * 8) g = 152LL * 8;
     if (nparts) *nparts = (int)g;
 #define BLTT_DIRECT(K_)                                                                         \
@@ -885,6 +1021,21 @@ cudaError_t launch_solve_one(const OneSolve& s, bool chosen, cudaStream_t st) {
   else k_solve_one<OneF64><<<1, OneF64::NT, smem, st>>>(s);
   return cudaGetLastError();
 }
+// the fold of a window of S slots (the vectors' element count is even: N >= 2 is a power of two)
+cudaError_t launch_fold(const MinresDev* s, const FoldArgs& a, cudaStream_t st) {
+  for (int i = 0; i < a.S; ++i)
+    if (!a.z[i] || (((uintptr_t)a.z[i]) & 15)) return cudaErrorInvalidValue;
+  if ((((uintptr_t)a.x | (uintptr_t)a.wo | (uintptr_t)a.wc) & 15) || a.S > kMaxWin || a.S < 1 ||
+      (a.n & 1))
+    return cudaErrorInvalidValue;
+  const int g = grid_stream(a.n / 2, 256);
+  if (a.S <= 2) k_fold<2><<<g, 256, 0, st>>>(s, a);
+  else if (a.S <= 4) k_fold<4><<<g, 256, 0, st>>>(s, a);
+  else if (a.S <= 8) k_fold<8><<<g, 256, 0, st>>>(s, a);
+  else k_fold<16><<<g, 256, 0, st>>>(s, a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_w_update(MinresDev* s, const double* z, double* w_prev, const double* w,
                             double* x, long long n, cudaStream_t st) {
   k_w_update<<<grid_stream(n, 256), 256, 0, st>>>(s, z, w_prev, w, x, n);
