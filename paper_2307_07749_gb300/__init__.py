@@ -304,7 +304,7 @@ def bltt_residual_noalloc(a, b, N, ndim, m, h, u, f, r=None, stream=None):
 
 
 def bltt_solve_batched(problems, fs, us, alpha=None, tol=1e-8, maxit=200, precision=PREC_F64,
-                       matvec_arith=ARITH_DEFAULT, autotune=True):
+                       matvec_arith=ARITH_DEFAULT, autotune=True, defer_window=0):
     """Batched solve.  problems: list of objects with N, d, m, h, a, b; fs / us: list (per
     problem) of lists of float64 CUDA tensors.  Returns (status, list of info dicts, system-major)."""
     nsys = len(problems)
@@ -325,7 +325,7 @@ def bltt_solve_batched(problems, fs, us, alpha=None, tol=1e-8, maxit=200, precis
     up = (_P * tot)(*[_ptr(t, "u").value for u in us for t in u])
     al = None if alpha is None else (ctypes.c_double * nsys)(*[float(x) for x in alpha])
     opts = bltt_solve_opts(precision, BASIS_SPECTRAL, PRECOND_ABAC, 0 if autotune else -1, 0,
-                           matvec_arith, 0)
+                           matvec_arith, 0, 0, int(defer_window))
     infos = (bltt_solve_info * tot)()
     st = lib().bltt_solve_batched(nsys, blocks, nrhs, fp, up, al, float(tol), int(maxit),
                                   ctypes.byref(opts), infos)

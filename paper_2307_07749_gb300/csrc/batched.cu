@@ -6,7 +6,8 @@
 // launch per phase covers the tiles of every item of a wave (persistent blocks stride over the
 // concatenated tile list; items that have converged skip their tiles).  The phase sequence of two
 // MINRES iterations is captured once per wave in a CUDA graph and replayed until every item has
-// stopped.  Waves are sized so that their workspace fits the device memory that is free.
+// stopped; the first S iterations defer their (w, x) update as a single solve does (one graph
+// per two of them, their z slots differ).  Waves are sized so that their workspace fits the device memory that is free.
 // Items of at least kBigItem unknowns fill the GPU on their own: their FFT phases use the
 // single-item kernels (operator tables as kernel parameters, two blocks per SM) inside the same
 // graph, and only the smaller items share the multi-item launches, whose tile width for each
@@ -40,6 +41,7 @@ struct Item {
   double* u;
   // workspace (device)
   double *b, *v[2], *z[2], *w[2], *q, *x, *p0, *p1;
+  double* zs[kMaxWin + 1];   // deferred-update window: z slots (zs[0], zs[1] are z[0], z[1])
   MinresDev* st;
   long long tiles_conv, tiles_tp, tiles_dst[3], maxtiles;
   int l2nc_conv, l2nc_tp, l2nc_dst[3];
@@ -235,8 +237,12 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
     const double v = std::atof(cap);
     if (v > 0 && v < (double)budget) budget = (size_t)v;
   }
-  auto item_bytes = [](const Item& it) {
-    return (size_t)(9 * it.n + 2 * it.maxtiles) * sizeof(double) + sizeof(MinresDev) + 4096;
+  // deferred solution update over the first S iterations (as in a single solve): S - 1 more z
+  // slots per item; S = 0 with a negative defer_window
+  const int S = (o.defer_window < 0) ? 0 : (o.defer_window > 0 ? std::max(2, (std::min(o.defer_window, kMaxWin) / 2) * 2) : 8);
+  auto item_bytes = [S](const Item& it) {
+    return (size_t)((9 + (S ? S - 1 : 0)) * it.n + 2 * it.maxtiles) * sizeof(double) +
+           sizeof(MinresDev) + 4096 + (size_t)(S ? S - 1 : 0) * 256;
   };
   std::vector<std::vector<int>> waves;
   {
@@ -297,6 +303,8 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
       it.w[0] = carve(it.n * 8); it.w[1] = carve(it.n * 8);
       it.q = carve(it.n * 8);
       it.x = carve(it.n * 8);
+      it.zs[0] = it.z[0]; it.zs[1] = it.z[1];
+      for (int k = 2; k <= S; ++k) it.zs[k] = carve(it.n * 8);
       it.p0 = carve(it.maxtiles * 8);
       it.p1 = carve(it.maxtiles * 8);
       it.st = states + j;
@@ -304,7 +312,10 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
     // states: tol, maxit, phase
     {
       std::vector<MinresDev> sh(ni);
-      for (auto& s0 : sh) { std::memset(&s0, 0, sizeof s0); s0.tol = tol; s0.maxit = maxit; s0.phase = PH_RUN; }
+      for (auto& s0 : sh) {
+        std::memset(&s0, 0, sizeof s0);
+        s0.tol = tol; s0.maxit = maxit; s0.phase = PH_RUN; s0.win = S;
+      }
       cudaMemcpyAsync(states, sh.data(), sizeof(MinresDev) * ni, cudaMemcpyHostToDevice, st);
       cudaStreamSynchronize(st);
     }
@@ -325,9 +336,21 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
     std::vector<DstItem> dst_in[3], dst_out[3];
     std::vector<long long> pre_dst[3];
     std::vector<long long> pre_conv, pre_tp;
-    std::vector<TpItem> tp_init, tp_loop[2];
-    std::vector<ConvItem> cv_loop[2], cv_res;
+    // iteration roles j = 0 .. S-1 (the window's iterations) and j = S, S+1 (the alternating roles
+    // after it; without a window, j = 0, 1)
+    const int nj = S + 2;
+    auto zc_of = [&](const Item& it, int t) -> double* {
+      if (S == 0) return it.zs[t & 1];
+      return t < S ? it.zs[t] : it.zs[((t - S) & 1) ? S - 1 : S];
+    };
+    auto zp_of = [&](const Item& it, int t) -> double* {
+      if (S == 0) return it.zs[(t + 1) & 1];
+      return t < S ? it.zs[t + 1] : it.zs[((t - S) & 1) ? S : S - 1];
+    };
+    std::vector<TpItem> tp_init, tp_it[kMaxWin + 2];
+    std::vector<ConvItem> cv_it[kMaxWin + 2], cv_res;
     std::vector<VecItem> w_loop[2];
+    std::vector<FoldItem> folds;
     std::vector<ScalItem> sc_init, sc_delta, sc_gamma, sc_check;
     long long tot_conv = 0, tot_tp = 0, tot_dst[3] = {0, 0, 0};
     std::vector<int> bigs;   // wave positions of the items with single-item launches
@@ -382,23 +405,33 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
       si.st = it.st; si.p0 = it.p0; si.n0 = (int)it.tiles_tp; si.p1 = it.p1;
       si.n1 = (int)it.tiles_dst[it.d - 1];
       sc_init.push_back(si);
-      for (int e = 0; e < 2; ++e) {
-        const int cur = e, prv = 1 - e;
+      for (int j = 0; j < nj; ++j) {
+        const int cur = j & 1, prv = 1 - cur;
         ConvItem ci{};
-        ci.op = op; ci.x = it.z[cur]; ci.xscale = &it.st->inv_gamma; ci.y = it.q; ci.flip = 1;
+        ci.op = op; ci.x = zc_of(it, j); ci.xscale = &it.st->inv_gamma; ci.y = it.q; ci.flip = 1;
         ci.mode = MV_STORE; ci.spectral = 1; ci.log2NC = it.l2nc_conv; ci.partials = it.p0;
         ci.phase = &it.st->phase; ci.want = PH_RUN;
-        if (!it.big) cv_loop[e].push_back(ci);
+        if (!it.big) cv_it[j].push_back(ci);
         TpItem tl{};
         tl.op = op; tl.pt = pt; tl.log2NC = it.l2nc_tp;
         tl.cb.in0 = it.q; tl.cb.in1 = it.v[cur]; tl.cb.in2 = it.v[prv]; tl.cb.coef = it.st->coef;
-        tl.cb.vout = it.v[prv]; tl.out = it.z[prv]; tl.dot_with = it.v[prv]; tl.partials = it.p1;
+        tl.cb.vout = it.v[prv]; tl.out = zp_of(it, j); tl.dot_with = it.v[prv]; tl.partials = it.p1;
         tl.phase = &it.st->phase; tl.want = PH_RUN;
-        if (!it.big) tp_loop[e].push_back(tl);
-        VecItem vi{};
-        vi.st = it.st; vi.z = it.z[cur]; vi.w_prev = it.w[prv]; vi.w = it.w[cur]; vi.x = it.x;
-        vi.n = it.n;
-        w_loop[e].push_back(vi);
+        if (!it.big) tp_it[j].push_back(tl);
+        if (j >= S) {
+          const int k = (j - S) & 1;
+          VecItem vi{};
+          vi.st = it.st; vi.z = zc_of(it, j); vi.w_prev = it.w[1 - k]; vi.w = it.w[k];
+          vi.x = it.x; vi.n = it.n;
+          w_loop[k].push_back(vi);
+        }
+      }
+      if (S > 0) {
+        FoldItem fi{};
+        fi.st = it.st;
+        for (int k = 0; k < S; ++k) fi.a.z[k] = it.zs[k];
+        fi.a.x = it.x; fi.a.wo = it.w[1]; fi.a.wc = it.w[0]; fi.a.n = it.n; fi.a.S = S;
+        folds.push_back(fi);
       }
       ConvItem cr{};
       cr.op = op; cr.x = it.x; cr.y = nullptr; cr.rhs = it.b; cr.flip = 1; cr.mode = MV_RESID;
@@ -428,8 +461,10 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
     long long* d_pre_conv = up(pre_conv);
     long long* d_pre_tp = up(pre_tp);
     TpItem* d_tp_init = up(tp_init);
-    TpItem* d_tp_loop[2] = {up(tp_loop[0]), up(tp_loop[1])};
-    ConvItem* d_cv_loop[2] = {up(cv_loop[0]), up(cv_loop[1])};
+    TpItem* d_tp_it[kMaxWin + 2];
+    ConvItem* d_cv_it[kMaxWin + 2];
+    for (int j = 0; j < nj; ++j) { d_tp_it[j] = up(tp_it[j]); d_cv_it[j] = up(cv_it[j]); }
+    FoldItem* d_folds = up(folds);
     ConvItem* d_cv_res = up(cv_res);
     VecItem* d_w_loop[2] = {up(w_loop[0]), up(w_loop[1])};
     ScalItem* d_sc_init = up(sc_init);
@@ -458,7 +493,8 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
       }
       return r;
     };
-    auto big_tp = [&](int par, bool init) {
+    // iteration role t of the big items: t < S the window's iteration t; S, S+1 after it
+    auto big_tp = [&](int t, bool init) {
       cudaError_t r = cudaSuccess;
       for (int j : bigs) {
         if (r != cudaSuccess) break;
@@ -470,16 +506,16 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
           c.in0 = it.b; c.vout = it.v[0];
           r = launch_timepass(op, pt, prec, c, it.z[0], it.v[0], it.p0, nullptr, nullptr, st);
         } else {
-          const int cur = par, prv = 1 - par;
+          const int cur = t & 1, prv = 1 - cur;
           c.in0 = it.q; c.in1 = it.v[cur]; c.in2 = it.v[prv]; c.coef = it.st->coef;
           c.vout = it.v[prv];
-          r = launch_timepass(op, pt, prec, c, it.z[prv], it.v[prv], it.p1, nullptr,
+          r = launch_timepass(op, pt, prec, c, zp_of(it, t), it.v[prv], it.p1, nullptr,
                               &it.st->phase, st);
         }
       }
       return r;
     };
-    auto big_conv = [&](int par, bool resid) {
+    auto big_conv = [&](int t, bool resid) {
       cudaError_t r = cudaSuccess;
       for (int j : bigs) {
         if (r != cudaSuccess) break;
@@ -489,7 +525,7 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
           r = launch_matvec(op, 1, it.x, nullptr, nullptr, 1, MV_RESID, it.b, it.p0, nullptr,
                             &it.st->phase, nullptr, st);
         else
-          r = launch_matvec(op, 1, it.z[par], &it.st->inv_gamma, it.q, 1, MV_STORE, nullptr,
+          r = launch_matvec(op, 1, zc_of(it, t), &it.st->inv_gamma, it.q, 1, MV_STORE, nullptr,
                             it.p0, nullptr, &it.st->phase, nullptr, st);
       }
       return r;
@@ -504,37 +540,48 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
       Item& it = items[wave[j]];
       e = cudaMemsetAsync(it.x, 0, it.n * 8, st);
       if (e == cudaSuccess) e = cudaMemsetAsync(it.v[1], 0, it.n * 8, st);
-      if (e == cudaSuccess) e = cudaMemsetAsync(it.w[0], 0, it.n * 8, st);
-      if (e == cudaSuccess) e = cudaMemsetAsync(it.w[1], 0, it.n * 8, st);
+      if (S == 0 && e == cudaSuccess) e = cudaMemsetAsync(it.w[0], 0, it.n * 8, st);
+      if (S == 0 && e == cudaSuccess) e = cudaMemsetAsync(it.w[1], 0, it.n * 8, st);
     }
     if (e == cudaSuccess) e = launch_scalar_multi(0, d_sc_init, ni, st);
     // warm the persistent-grid queries outside the capture
     persistent_grid(0, dprec); persistent_grid(1, prec); persistent_grid(2, dprec);
-    // capture two iterations
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    if (e == cudaSuccess) e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      cudaError_t ce = cudaSuccess;
-      for (int par = 0; par < 2 && ce == cudaSuccess; ++par) {
-        ce = big_conv(par, false);
-        if (ce == cudaSuccess && ns > 0) ce = launch_conv_multi(arith, d_cv_loop[par], d_pre_conv, ns, tot_conv, st);
-        if (ce == cudaSuccess) ce = launch_scalar_multi(1, d_sc_delta, ni, st);
-        if (ce == cudaSuccess) ce = big_tp(par, false);
-        if (ce == cudaSuccess && ns > 0) ce = launch_timepass_multi(prec, d_tp_loop[par], d_pre_tp, ns, tot_tp, st);
-        if (ce == cudaSuccess) ce = launch_scalar_multi(2, d_sc_gamma, ni, st);
-        if (ce == cudaSuccess) ce = launch_w_update_multi(d_w_loop[par], ni, st);
-        if (ce == cudaSuccess) ce = big_conv(par, true);
-        if (ce == cudaSuccess && ns > 0) ce = launch_conv_multi(arith, d_cv_res, d_pre_conv, ns, tot_conv, st);
-        if (ce == cudaSuccess) ce = launch_scalar_multi(3, d_sc_check, ni, st);
-      }
+    // one MINRES iteration of every item of the wave, in role j
+    auto iteration = [&](int j) -> cudaError_t {
+      cudaError_t ce = big_conv(j, false);
+      if (ce == cudaSuccess && ns > 0) ce = launch_conv_multi(arith, d_cv_it[j], d_pre_conv, ns, tot_conv, st);
+      if (ce == cudaSuccess) ce = launch_scalar_multi(1, d_sc_delta, ni, st);
+      if (ce == cudaSuccess) ce = big_tp(j, false);
+      if (ce == cudaSuccess && ns > 0) ce = launch_timepass_multi(prec, d_tp_it[j], d_pre_tp, ns, tot_tp, st);
+      if (ce == cudaSuccess) ce = launch_scalar_multi(2, d_sc_gamma, ni, st);
+      if (ce == cudaSuccess)
+        ce = (j < S) ? launch_fold_multi(d_folds, ni, S, st)
+                     : launch_w_update_multi(d_w_loop[(j - S) & 1], ni, st);
+      if (ce == cudaSuccess) ce = big_conv(j, true);
+      if (ce == cudaSuccess && ns > 0) ce = launch_conv_multi(arith, d_cv_res, d_pre_conv, ns, tot_conv, st);
+      if (ce == cudaSuccess) ce = launch_scalar_multi(3, d_sc_check, ni, st);
+      // a check that failed at the window's last iteration: the w vectors for the iterations after
+      if (ce == cudaSuccess && j == S - 1) ce = launch_fold_multi(d_folds, ni, S, st);
+      return ce;
+    };
+    // graphs of two iterations: one per block of the window, one for the iterations after it
+    const int nblk = S / 2 + 1;
+    std::vector<cudaGraphExec_t> gexec(nblk, nullptr);
+    for (int g = 0; g < nblk && e == cudaSuccess; ++g) {
+      const int j0 = (g < nblk - 1) ? 2 * g : S;
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) break;
+      cudaError_t ce = iteration(j0);
+      if (ce == cudaSuccess) ce = iteration(j0 + 1);
       e = cudaStreamEndCapture(st, &graph);
       if (e == cudaSuccess) e = ce;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec[g], graph, 0);
+      if (graph) cudaGraphDestroy(graph);
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, graph, 0);
     int issued = 0;
     while (e == cudaSuccess) {
-      e = cudaGraphLaunch(gexec, st);
+      e = cudaGraphLaunch(gexec[issued < S ? issued / 2 : nblk - 1], st);
       issued += 2;
       if (e == cudaSuccess) e = launch_count_running(d_sc_check, ni, run_count, st);
       if (e == cudaSuccess) e = cudaMemcpyAsync(run_count_h, run_count, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -548,8 +595,8 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
     std::vector<MinresDev> sh(ni);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sh.data(), states, sizeof(MinresDev) * ni, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (gexec) cudaGraphExecDestroy(gexec);
-    if (graph) cudaGraphDestroy(graph);
+    for (auto g : gexec)
+      if (g) cudaGraphExecDestroy(g);
     for (void* p : dev_allocs) cudaFree(p);
     if (e != cudaSuccess) { result = BLTT_ERR_CUDA; break; }
     for (int j = 0; j < ni; ++j) {

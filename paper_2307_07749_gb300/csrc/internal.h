@@ -275,6 +275,12 @@ cudaError_t launch_timepass_multi(int prec, const TpItem* items, const long long
 cudaError_t launch_dst_multi(int prec, const DstItem* items, const long long* prefix, int nitems,
                              long long total, cudaStream_t st);
 cudaError_t launch_w_update_multi(const VecItem* items, int nitems, cudaStream_t st);
+struct FoldItem {           // deferred-update fold of one item (its state decides the request)
+  const MinresDev* st;
+  FoldArgs a;
+};
+// kmax: the largest window among the items
+cudaError_t launch_fold_multi(const FoldItem* items, int nitems, int kmax, cudaStream_t st);
 // which: 0 init, 1 delta, 2 gamma, 3 check
 cudaError_t launch_scalar_multi(int which, const ScalItem* items, int nitems, cudaStream_t st);
 cudaError_t launch_count_running(const ScalItem* items, int nitems, int* out, cudaStream_t st);

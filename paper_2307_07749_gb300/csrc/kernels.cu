@@ -615,6 +615,31 @@ __global__ void __launch_bounds__(256, 2) k_fold(const MinresDev* st, FoldArgs a
   else fold_dispatch<3, KMAX>(a, k, cx, co, cc, e, stride);
 }
 
+// the fold of every item of a batched wave, one item after the other, each over the whole grid
+template <int KMAX>
+__global__ void __launch_bounds__(256, 2) k_fold_multi(const FoldItem* __restrict__ items, int ni) {
+  __shared__ double cx[kMaxWin], co[kMaxWin], cc[kMaxWin];
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (int i = 0; i < ni; ++i) {
+    const MinresDev* st = items[i].st;
+    const int req = st->fold_req;
+    const int k = min(st->iter, items[i].a.S);
+    if (!req || k < 1 || k > KMAX) continue;   // the same for every thread of the block
+    __syncthreads();                           // the previous item's coefficients are read
+    if (threadIdx.x < kMaxWin) {
+      cx[threadIdx.x] = st->xi[threadIdx.x];
+      co[threadIdx.x] = st->cwo[threadIdx.x];
+      cc[threadIdx.x] = st->cwc[threadIdx.x];
+    }
+    __syncthreads();
+    const FoldArgs a = items[i].a;
+    if (req == 1) fold_dispatch<1, KMAX>(a, k, cx, co, cc, e, stride);
+    else if (req == 2) fold_dispatch<2, KMAX>(a, k, cx, co, cc, e, stride);
+    else fold_dispatch<3, KMAX>(a, k, cx, co, cc, e, stride);
+  }
+}
+
 __global__ void __launch_bounds__(256) k_sum_partials(const double* p, int np, double* out) {
   __shared__ double red[32];
   double s = reduce_partials(p, np, red);
@@ -1033,6 +1058,16 @@ cudaError_t launch_fold(const MinresDev* s, const FoldArgs& a, cudaStream_t st) 
   else if (a.S <= 4) k_fold<4><<<g, 256, 0, st>>>(s, a);
   else if (a.S <= 8) k_fold<8><<<g, 256, 0, st>>>(s, a);
   else k_fold<16><<<g, 256, 0, st>>>(s, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fold_multi(const FoldItem* items, int nitems, int kmax, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  const int g = 152 * 2;
+  if (kmax <= 2) k_fold_multi<2><<<g, 256, 0, st>>>(items, nitems);
+  else if (kmax <= 4) k_fold_multi<4><<<g, 256, 0, st>>>(items, nitems);
+  else if (kmax <= 8) k_fold_multi<8><<<g, 256, 0, st>>>(items, nitems);
+  else k_fold_multi<16><<<g, 256, 0, st>>>(items, nitems);
   return cudaGetLastError();
 }
 

@@ -157,3 +157,32 @@ def test_batched_workload_sample_vs_stored_oracle(B, form):
             assert info["relres_true"] <= 1e-8
             deltas.append(info["iters"] - golden[(s, r, form["alpha"])])
     assert max(abs(d) for d in deltas) <= 1, deltas
+
+
+@pytest.mark.parametrize("form", [
+    dict(precision=64, matvec_arith=1, alpha=1e-8),
+    dict(precision=32, matvec_arith=2, alpha=1e-2),
+    dict(precision=64, matvec_arith=1, alpha=1.0),
+], ids=["f64", "f32_prec", "f64_P1"])
+def test_batched_deferred_window_matches_per_iteration_update(B, form):
+    """The batched items defer their (w, x) update over the first iterations as single solves do;
+    with the per-iteration update instead (defer_window = -1) every item takes the same iterations
+    and the same solution to rounding, also past the window (alpha = 1: tens of iterations)."""
+    probs = [fractional_problem(2, 127, 256, 0.6), fractional_problem(2, 31, 128, 0.8),
+             fractional_problem(1, 63, 64, 0.4)]
+    fs = [[rhs_uniform(p.n, 70 + 10 * s + r) for r in range(2)] for s, p in enumerate(probs)]
+    fd = [[to_dev(f) for f in row] for row in fs]
+    res = []
+    for win in (0, -1):
+        ud = [[to_dev(np.zeros_like(f)) for f in row] for row in fs]
+        st, infos = B.bltt_solve_batched(probs, fd, ud, alpha=[form["alpha"]] * len(probs),
+                                         tol=1e-8, maxit=300, precision=form["precision"],
+                                         matvec_arith=form["matvec_arith"], defer_window=win)
+        assert st == 0
+        res.append((infos, [to_host(u) for row in ud for u in row]))
+    (i0, u0), (i1, u1) = res
+    assert [i["iters"] for i in i0] == [i["iters"] for i in i1]
+    if form["alpha"] == 1.0:
+        assert min(i["iters"] for i in i0) > 8
+    for a, b in zip(u0, u1):
+        assert rel(a, b) <= 1e-10
