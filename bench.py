@@ -52,8 +52,8 @@ ALPHA_F32X2 = 1e-6        # double-float preconditioner: 2 iterations, as the FP
 # DRAM bytes (read + write) per unknown of one launch, from one ncu capture of the current kernel
 # on the full workload
 NCU_TRAFFIC_PER_UNKNOWN = {
-    "conv_df": (15.35, "ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch "
-                       "(545.5 + 476.9 MB over 66,585,600 unknowns; one pass)"),
+    "conv_df": (15.38, "ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch "
+                       "(547.2 + 477.0 MB over 66,585,600 unknowns; one pass)"),
 }
 # one metric text for both arms (the GPU solve and the CPU oracle), so that their lines compare
 METRIC = "unknown-iterations/s to relres<=1e-8"
