@@ -290,7 +290,7 @@ __device__ __forceinline__ void dst_tile(long long nlines, int m_rt, long long i
         const V z = buf[at((j & 1) ? (j >> 1) : half + (j >> 1), c >> 1)];
         const double val = A::part_sc(z, c & 1, scale);
         out[ix[u]] = val;
-        acc = fma(val, self_dot ? val : dw[u], acc);
+        if (partials) acc = fma(val, self_dot ? val : dw[u], acc);   // FP64 pipe: only if asked
       }
     }
   }
