@@ -127,6 +127,20 @@ typedef struct {
                         rounding.  0: S = 8; 1..16: S (rounded down to a multiple of the graph
                         block, at least one block); -1: off (an update every iteration).  If the
                         extra vectors cannot be allocated the solve runs without the window.      */
+  int refine;        /* mixed-precision iterative refinement, the fallback of the precision forms
+                        (a reduced-precision preconditioner can make MINRES's recurrences drift
+                        from the true residual and stall): 0 off.  k > 0: every MINRES solve runs
+                        at most ceil(maxit / (k + 1)) iterations and ends at a failed
+                        true-residual check instead of resuming; then, up to k times, the
+                        residual r = f - A u is formed by a fresh FP64-accurate product in the
+                        physical basis, A d = r is solved by MINRES to the tolerance that brings
+                        ||f - A u|| / ||f|| to tol, and u += d.  The corrections raise an FP32
+                        preconditioner to double-float; a first FP32 solve that broke down
+                        restarts from u = 0.  maxit covers all solves, info->iters sums them,
+                        info->refinements counts the corrections and info->relres_true is the
+                        final fresh residual.  A solve that converges within its share is
+                        unchanged.  Not for a dense operator or block spectra (the physical
+                        product needs the blocks themselves): BLTT_ERR_UNSUPPORTED there.      */
 } bltt_solve_opts;
 
 typedef struct {
@@ -141,6 +155,7 @@ typedef struct {
   double t_solve_ms;      /* whole solve incl. set-up, device time on the handle's stream      */
   long long kernel_launches; /* kernels issued by the solve                                    */
   int status;             /* bltt_status of the solve                                          */
+  int refinements;        /* outer corrections of bltt_solve_opts.refine that ran (else 0)     */
 } bltt_solve_info;
 
 /* Create a handle for the BLTT matrix `blocks` with N time steps and M spatial unknowns

@@ -49,7 +49,8 @@ class bltt_solve_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("basis", ctypes.c_int), ("precond", ctypes.c_int),
                 ("sync_every", ctypes.c_int), ("rebuild", ctypes.c_int),
                 ("matvec_arith", ctypes.c_int), ("no_graph", ctypes.c_int),
-                ("single_block", ctypes.c_int), ("defer_window", ctypes.c_int)]
+                ("single_block", ctypes.c_int), ("defer_window", ctypes.c_int),
+                ("refine", ctypes.c_int)]
 
 
 class bltt_solve_info(ctypes.Structure):
@@ -58,7 +59,7 @@ class bltt_solve_info(ctypes.Structure):
                 ("alpha_source", ctypes.c_int), ("precision", ctypes.c_int),
                 ("basis", ctypes.c_int), ("t_setup_ms", ctypes.c_double),
                 ("t_solve_ms", ctypes.c_double), ("kernel_launches", ctypes.c_longlong),
-                ("status", ctypes.c_int)]
+                ("status", ctypes.c_int), ("refinements", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -232,9 +233,10 @@ def bltt_precond_apply(handle, alpha, v, z, precision=PREC_F64):
 
 def bltt_minres_solve_ex(handle, f, alpha, tol, maxit, u, precision=PREC_F64, basis=BASIS_AUTO,
                          precond=PRECOND_ABAC, sync_every=0, raise_on_error=True, rebuild=0,
-                         matvec_arith=ARITH_DEFAULT, no_graph=0, single_block=0, defer_window=0):
+                         matvec_arith=ARITH_DEFAULT, no_graph=0, single_block=0, defer_window=0,
+                         refine=0):
     opts = bltt_solve_opts(precision, basis, precond, sync_every, rebuild, matvec_arith, no_graph,
-                           int(single_block), int(defer_window))
+                           int(single_block), int(defer_window), int(refine))
     info = bltt_solve_info()
     st = lib().bltt_minres_solve_ex(handle, _ptr(f, "f"), float(alpha), float(tol), int(maxit),
                                     ctypes.byref(opts), _ptr(u, "u"), ctypes.byref(info))
@@ -246,12 +248,12 @@ def bltt_minres_solve_ex(handle, f, alpha, tol, maxit, u, precision=PREC_F64, ba
 def bltt_minres_solve_host(handle, f_host, alpha, tol, maxit, u_host, precision=PREC_F64,
                            basis=BASIS_AUTO, precond=PRECOND_ABAC, sync_every=0,
                            raise_on_error=True, rebuild=0, matvec_arith=ARITH_DEFAULT, no_graph=0,
-                           defer_window=0):
+                           defer_window=0, refine=0):
     """bltt_minres_solve_ex with f and u in host memory (pinned for asynchronous copies)."""
     if f_host is u_host:
         raise ValueError("u must not alias f")
     opts = bltt_solve_opts(precision, basis, precond, sync_every, rebuild, matvec_arith, no_graph,
-                           0, int(defer_window))
+                           0, int(defer_window), int(refine))
     info = bltt_solve_info()
     st = lib().bltt_minres_solve_host(handle, _host_ptr(f_host, "f"), float(alpha), float(tol),
                                       int(maxit), ctypes.byref(opts), _host_ptr(u_host, "u"),
@@ -445,22 +447,24 @@ class Solver:
 
     def solve(self, f, alpha=1e-8, tol=1e-8, maxit=200, precision=PREC_F64, basis=BASIS_AUTO,
               precond=PRECOND_ABAC, u=None, sync_every=0, raise_on_error=True, rebuild=False,
-              matvec_arith=ARITH_DEFAULT, graph=True, single_block=False, defer_window=0):
+              matvec_arith=ARITH_DEFAULT, graph=True, single_block=False, defer_window=0,
+              refine=0):
         """single_block: the whole solve in one launch of one block (small problems, FP64).
-        defer_window: iterations whose (w, x) update is deferred (0: 8, -1: none)."""
+        defer_window: iterations whose (w, x) update is deferred (0: 8, -1: none).
+        refine: outer iterative-refinement corrections allowed (0: none)."""
         import torch
         u = torch.empty_like(f) if u is None else u
         st, info = bltt_minres_solve_ex(self.handle, f, alpha, tol, maxit, u, precision, basis,
                                         precond, sync_every, raise_on_error, int(rebuild),
                                         matvec_arith, 0 if graph else 1, int(single_block),
-                                        int(defer_window))
+                                        int(defer_window), int(refine))
         info["status_name"] = STATUS_NAMES.get(st, st)
         return u, info
 
     def solve_host(self, f_host, alpha=1e-8, tol=1e-8, maxit=200, precision=PREC_F64,
                    basis=BASIS_AUTO, precond=PRECOND_ABAC, u_host=None, sync_every=0,
                    raise_on_error=True, rebuild=False, matvec_arith=ARITH_DEFAULT, graph=True,
-                   defer_window=0):
+                   defer_window=0, refine=0):
         """solve() with f and u in host memory; u_host defaults to a pinned tensor."""
         import torch
         if u_host is None:
@@ -468,6 +472,6 @@ class Solver:
         st, info = bltt_minres_solve_host(self.handle, f_host, alpha, tol, maxit, u_host,
                                           precision, basis, precond, sync_every, raise_on_error,
                                           int(rebuild), matvec_arith, 0 if graph else 1,
-                                          int(defer_window))
+                                          int(defer_window), int(refine))
         info["status_name"] = STATUS_NAMES.get(st, st)
         return u_host, info

@@ -151,6 +151,9 @@ struct bltt_ctx {
   // host-buffer solves: device staging of f and u, a copy stream and its event
   double* io_f = nullptr;
   double* io_u = nullptr;
+  // iterative refinement: the residual and the correction
+  double* ir_r = nullptr;
+  double* ir_d = nullptr;
   cudaStream_t io_stream = nullptr;
   cudaEvent_t io_ev = nullptr;
   cudaEvent_t io_chunk_ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -1134,7 +1137,9 @@ struct HostIn {
 
 bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol, int maxit,
                        const bltt_solve_opts* opts, double* u, bltt_solve_info* info,
-                       const HostOut* hout, const HostIn* hin = nullptr);
+                       const HostOut* hout, const HostIn* hin = nullptr, bool inner = false);
+bltt_status refine_solve(bltt_handle h, const double* f, double alpha, double tol, int maxit,
+                         const bltt_solve_opts* opts, double* u, bltt_solve_info* info);
 }  // namespace
 
 extern "C" {
@@ -1142,6 +1147,7 @@ extern "C" {
 bltt_status bltt_minres_solve_ex(bltt_handle h, const double* f, double alpha, double tol,
                                  int maxit, const bltt_solve_opts* opts, double* u,
                                  bltt_solve_info* info) {
+  if (opts && opts->refine > 0) return refine_solve(h, f, alpha, tol, maxit, opts, u, info);
   return solve_impl(h, f, alpha, tol, maxit, opts, u, info, nullptr);
 }
 
@@ -1192,7 +1198,7 @@ bltt_status dst_entry_chunked(bltt_ctx* h, const OpTables& op, const double* f_h
 
 bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol, int maxit,
                        const bltt_solve_opts* opts, double* u, bltt_solve_info* info,
-                       const HostOut* hout, const HostIn* hin) {
+                       const HostOut* hout, const HostIn* hin, bool inner) {
   if (!h) return BLTT_ERR_INVALID_ARG;
   if (info) { std::memset(info, 0, sizeof *info); info->status = BLTT_ERR_INVALID_ARG; }
   if (!f || !u) return fail(h, BLTT_ERR_INVALID_ARG, "null vector");
@@ -1263,6 +1269,7 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
   sh->maxit = maxit;
   sh->phase = PH_RUN;
   sh->win = S;
+  sh->stopfail = inner ? 1 : 0;
   CK(h, cudaMemcpyAsync(h->state, sh, sizeof *sh, cudaMemcpyHostToDevice, st), "state upload");
   int* phase = &h->state->phase;
   // the end of every solve: timings, status and statistics
@@ -1601,7 +1608,9 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
       sh->status = (relres_phys <= tol) ? 0 : 6;
       break;
     }
-    if (sh->iter >= maxit) { sh->phase = PH_MAXIT; sh->status = 6; break; }
+    // an inner solve of refinement ends at a failed check: the outer loop corrects from the
+    // true residual instead
+    if (sh->iter >= maxit || inner) { sh->phase = PH_MAXIT; sh->status = 6; break; }
     // resume: direct launches from iteration sh->iter (a replayed graph could be stopped
     // mid-block); u may still be on its way to the host.  At the window's end the iterations
     // after it need the w vectors, which the fold at the stop left out
@@ -1619,6 +1628,97 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
   }
   return finish(relres_phys);
 }
+
+// Mixed-precision iterative refinement around MINRES (the fallback of the precision forms): an
+// inner solve that fails a true-residual check ends there; the outer loop forms r = f - A u by a
+// fresh FP64-accurate product in the physical basis, solves A d = r in the same form to the
+// tolerance that brings ||f - A u|| / ||f|| to tol, and adds d to u.
+bltt_status refine_solve(bltt_handle h, const double* f, double alpha, double tol, int maxit,
+                         const bltt_solve_opts* opts, double* u, bltt_solve_info* info) {
+  if (!h) return BLTT_ERR_INVALID_ARG;
+  if (info) { std::memset(info, 0, sizeof *info); info->status = BLTT_ERR_INVALID_ARG; }
+  if (h->dense) return fail(h, BLTT_ERR_UNSUPPORTED, "refinement needs the blocks' physical product");
+  if (!f || !u || f == u) return fail(h, BLTT_ERR_INVALID_ARG, "null or aliased vector");
+  bltt_solve_opts o = *opts;
+  const int R = o.refine;
+  o.refine = 0;
+  // every inner solve gets at most an equal share of the budget: a MINRES run whose recurrences
+  // have drifted stagnates rather than failing a check, and the share ends it
+  const int cap = std::max(1, (maxit + R) / (R + 1));
+  bltt_solve_info in{};
+  bltt_status s = solve_impl(h, f, alpha, tol, std::min(cap, maxit), &o, u, &in, nullptr, nullptr,
+                             true);
+  bltt_solve_info tot = in;
+  tot.refinements = 0;
+  auto out = [&](bltt_status r) {
+    tot.status = r;
+    if (info) *info = tot;
+    return r;
+  };
+  // a first solve that broke down (a P^{-1} that is no longer positive definite in the reduced
+  // precision) restarts from u = 0 in the corrections' precision
+  if (s == BLTT_ERR_NUMERIC && o.precision == 32)
+    CK(h, cudaMemsetAsync(u, 0, (size_t)h->n * sizeof(double), h->stream), "restart");
+  else if (s != BLTT_ERR_NOT_CONVERGED)
+    return out(s);
+  if (!h->ir_r) {
+    CK(h, h->alloc(&h->ir_r, (size_t)h->n), "refinement residual");
+    CK(h, h->alloc(&h->ir_d, (size_t)h->n), "refinement correction");
+  }
+  OpTables op = h->op;
+  if (o.matvec_arith == BLTT_ARITH_F64) op.mv_arith = 0;
+  if (o.matvec_arith == BLTT_ARITH_F32X2 || o.matvec_arith == BLTT_ARITH_TC) op.mv_arith = 1;
+  cudaStream_t st = h->stream;
+  const long long n = h->n;
+  double* tmp = vec(h, 9);
+  // ||x||^2 of a vector, and r = f - A u with ||r||^2, synchronously
+  auto sum_to_host = [&](int np) -> double {
+    if (launch_sum_partials(h->partials[0], np, h->scal, st) != cudaSuccess) return NAN;
+    if (cudaMemcpyAsync(h->scal_host, h->scal, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return NAN;
+    return h->scal_host[0];
+  };
+  int np = 0;
+  CK(h, launch_norm2(f, n, h->partials[0], &np, st), "norm");
+  const double nf = std::sqrt(sum_to_host(np));
+  auto residual = [&]() -> double {
+    int nr = 0;
+    if (launch_matvec(op, 0, u, nullptr, h->ir_r, 0, MV_RESID, f, h->partials[0], &nr, nullptr,
+                      tmp, st) != cudaSuccess)
+      return NAN;
+    tot.kernel_launches += (op.b_kind == 1 && op.ntaps == 0) ? 3 : 2;
+    return std::sqrt(sum_to_host(nr));
+  };
+  double rel = residual() / nf;
+  bltt_status res = BLTT_ERR_NOT_CONVERGED;
+  // the corrections run with the FP32 preconditioner raised to double-float: a correction is only
+  // needed where the FP32 rounding, amplified by kappa(D_alpha), has stalled the first solve
+  if (o.precision == 32) o.precision = 96;
+  for (int k = 0; k < R; ++k) {
+    tot.relres_true = rel;
+    if (!std::isfinite(rel)) return out(fail(h, BLTT_ERR_NUMERIC, "non-finite residual in refinement"));
+    if (rel <= tol) { res = BLTT_OK; break; }
+    if (tot.iters >= maxit) break;
+    // A d = r to ||r - A d|| <= tol ||f||
+    bltt_solve_info ik{};
+    s = solve_impl(h, h->ir_r, alpha, tol / rel, std::min(cap, maxit - tot.iters), &o, h->ir_d,
+                   &ik, nullptr, nullptr, true);
+    if (s != BLTT_OK && s != BLTT_ERR_NOT_CONVERGED) return out(s);   // u as before this step
+    CK(h, launch_axpy(u, h->ir_d, n, st), "refinement update");
+    tot.iters += ik.iters;
+    tot.kernel_launches += ik.kernel_launches + 1;
+    tot.t_setup_ms += ik.t_setup_ms;
+    tot.t_solve_ms += ik.t_solve_ms;
+    tot.relres_est = ik.relres_est;
+    tot.refinements = k + 1;
+    rel = residual() / nf;
+  }
+  if (rel <= tol) res = BLTT_OK;
+  tot.relres_true = rel;
+  if (res != BLTT_OK) h->err = "refinement ended before the residual reached tol";
+  return out(res);
+}
 }  // namespace
 
 extern "C" {
@@ -1635,6 +1735,15 @@ bltt_status bltt_minres_solve_host(bltt_handle h, const double* f_host, double a
     CK(h, h->alloc(&h->io_u, (size_t)h->n), "staging of u");
     CK(h, cudaStreamCreateWithFlags(&h->io_stream, cudaStreamNonBlocking), "copy stream");
     CK(h, cudaEventCreateWithFlags(&h->io_ev, cudaEventDisableTiming), "copy event");
+  }
+  if (opts && opts->refine > 0) {
+    // refinement: f in, the device-buffer solve with its outer corrections, u out
+    const size_t bytes = (size_t)h->n * sizeof(double);
+    CK(h, cudaMemcpyAsync(h->io_f, f_host, bytes, cudaMemcpyHostToDevice, h->stream), "copy f to the device");
+    const bltt_status sr = refine_solve(h, h->io_f, alpha, tol, maxit, opts, h->io_u, info);
+    CK(h, cudaMemcpyAsync(u_host, h->io_u, bytes, cudaMemcpyDeviceToHost, h->stream), "copy u to the host");
+    CK(h, cudaStreamSynchronize(h->stream), "sync");
+    return sr;
   }
   const HostOut hout{u_host};
   const HostIn hin{f_host};

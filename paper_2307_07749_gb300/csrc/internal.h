@@ -28,7 +28,8 @@ struct MinresDev {
   double w_cz, w_cwp, w_cw;   // w_{j+1} = w_cz z_j + w_cwp w_{j-1} + w_cw w_j (folded coefficients)
   double normb, relres_est, relres_true, tol;
   double gamma_new;
-  int iter, maxit, phase, status, wpending, pad;
+  int iter, maxit, phase, status, wpending;
+  int stopfail;          // a failed true-residual check ends the solve (inner solves of refinement)
   // deferred solution update over the first `win` iterations: their w vectors and x are kept as
   // coefficients over the stored z_0 .. z_{win-1} (xi: x, cwo / cwc: the two latest w), and
   // k_fold forms the vectors only when needed.  fold_req: bit 0 x, bit 1 the two w vectors.
@@ -205,6 +206,10 @@ cudaError_t launch_solve_one(const OneSolve& s, bool chosen, cudaStream_t st);
 cudaError_t launch_w_update(MinresDev* s, const double* z, double* w_prev, const double* w,
                             double* x, long long n, cudaStream_t st);
 cudaError_t launch_fold(const MinresDev* s, const FoldArgs& a, cudaStream_t st);
+// u += d (FP64) and partial sums of ||x||^2 (iterative refinement)
+cudaError_t launch_axpy(double* u, const double* d, long long n, cudaStream_t st);
+cudaError_t launch_norm2(const double* x, long long n, double* partials, int* nparts,
+                         cudaStream_t st);
 cudaError_t launch_copy_scaled_check(const double* src, double* dst, long long n, cudaStream_t st);
 cudaError_t launch_sum_partials(const double* partials, int np, double* out, cudaStream_t st);
 

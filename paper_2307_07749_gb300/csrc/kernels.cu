@@ -440,6 +440,8 @@ __device__ __forceinline__ void scalar_check(MinresDev* st, const double* p, int
     st->phase = PH_DONE; st->status = (rr <= st->tol) ? 0 : 6;
   } else if (st->iter >= st->maxit) {
     st->phase = PH_MAXIT; st->status = 6;
+  } else if (st->stopfail) {
+    st->phase = PH_MAXIT; st->status = 6;   // an inner solve of refinement ends here
   } else {
     st->phase = PH_RUN;
     // the check failed at the last deferred iteration: the iterations after it need the w vectors
@@ -638,6 +640,21 @@ __global__ void __launch_bounds__(256, 2) k_fold_multi(const FoldItem* __restric
     else if (req == 2) fold_dispatch<2, KMAX>(a, k, cx, co, cc, e, stride);
     else fold_dispatch<3, KMAX>(a, k, cx, co, cc, e, stride);
   }
+}
+
+__global__ void __launch_bounds__(256) k_axpy(double* u, const double* d, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    u[e] += d[e];
+}
+__global__ void __launch_bounds__(256) k_norm2(const double* x, long long n, double* partials) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    acc = fma(x[e], x[e], acc);
+  const double s = block_sum<256>(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
 __global__ void __launch_bounds__(256) k_sum_partials(const double* p, int np, double* out) {
@@ -1068,6 +1085,18 @@ cudaError_t launch_fold_multi(const FoldItem* items, int nitems, int kmax, cudaS
   else if (kmax <= 4) k_fold_multi<4><<<g, 256, 0, st>>>(items, nitems);
   else if (kmax <= 8) k_fold_multi<8><<<g, 256, 0, st>>>(items, nitems);
   else k_fold_multi<16><<<g, 256, 0, st>>>(items, nitems);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy(double* u, const double* d, long long n, cudaStream_t st) {
+  k_axpy<<<grid_stream(n, 256), 256, 0, st>>>(u, d, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_norm2(const double* x, long long n, double* partials, int* nparts,
+                         cudaStream_t st) {
+  const int g = grid_stream(n, 256);
+  if (nparts) *nparts = g;
+  k_norm2<<<g, 256, 0, st>>>(x, n, partials);
   return cudaGetLastError();
 }
 
