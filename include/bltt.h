@@ -347,6 +347,18 @@ bltt_status bltt_profile_enable(bltt_handle h, int enable);
  * number of kernel families recorded (may exceed max_entries), or -1 for a NULL handle. */
 int bltt_profile_read(bltt_handle h, bltt_kernel_stat* out, int max_entries);
 
+/* Guard bands, a substitute for a memory checker (no counterpart in the paper).  With
+ * BLTT_GUARD_BANDS=1 in the environment when h first allocates its solve workspace, every
+ * workspace vector and every deferred-update slot sits between bands of 256 doubles that hold a
+ * fixed NaN bit pattern no kernel writes.  bltt_check_guards synchronises h's stream, reads every
+ * band back and returns BLTT_ERR_CUDA (with the band and element in bltt_last_error) if one was
+ * overwritten, else BLTT_OK; *bands_checked (may be NULL) receives the number of bands read (0
+ * without guard bands).  bltt_guard_poke writes one element of workspace band `band` from the
+ * host (0 <= band <= 10): a hook for the tests of the check itself; BLTT_ERR_INVALID_ARG without
+ * guard bands or for another band. */
+bltt_status bltt_check_guards(bltt_handle h, int* bands_checked);
+bltt_status bltt_guard_poke(bltt_handle h, int band);
+
 /* Relative true residual ||f - A u||_2 / ||f||_2 of a candidate solution u of A u = f (and, if
  * r_dev is not NULL, the residual vector r = f - A u), with neither a handle nor any allocation.
  * The paper has no counterpart: this entry point exists for callers that cannot allocate memory

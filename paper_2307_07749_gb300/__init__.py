@@ -96,6 +96,8 @@ _SIGS = {
                                               ctypes.POINTER(bltt_solve_info)]),
     "bltt_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "bltt_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(bltt_kernel_stat), ctypes.c_int]),
+    "bltt_check_guards": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "bltt_guard_poke": (ctypes.c_int, [_P, ctypes.c_int]),
     "bltt_residual_noalloc": (ctypes.c_int, [ctypes.POINTER(bltt_blocks), ctypes.c_int,
                                              ctypes.c_longlong, _P, _P, _P, _P,
                                              ctypes.POINTER(ctypes.c_double)]),
@@ -282,6 +284,17 @@ def bltt_profile_read(handle):
         raise BlttError(1, "null handle")
     return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms, arr[i].active_launches,
                                    arr[i].active_ms) for i in range(min(k, 64))}
+
+
+def bltt_check_guards(handle):
+    """Number of guard bands read; raises BlttError if one was overwritten."""
+    n = ctypes.c_int(0)
+    _check(lib().bltt_check_guards(handle, ctypes.byref(n)), handle)
+    return n.value
+
+
+def bltt_guard_poke(handle, band):
+    _check(lib().bltt_guard_poke(handle, int(band)), handle)
 
 
 def bltt_residual_noalloc(a, b, N, ndim, m, h, u, f, r=None, stream=None):

@@ -23,6 +23,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 
 using namespace bltt;
@@ -287,7 +289,10 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
     return BLTT_ERR_OOM;
   }
 
+  const nvtxRangeId_t span_all = nvtxRangeStartA("bltt_solve_batched");
   for (const auto& wave : waves) {
+    const nvtxRangeId_t span_wave = nvtxRangeStartA("batched wave");
+    struct EndSpan { nvtxRangeId_t id; ~EndSpan() { nvtxRangeEnd(id); } } end_wave{span_wave};
     const int ni = (int)wave.size();
     size_t off = 0;
     auto carve = [&](size_t nbytes) {
@@ -621,6 +626,7 @@ extern "C" bltt_status bltt_solve_batched(int nsys, const bltt_blocks* sys, cons
       }
     }
   }
+  nvtxRangeEnd(span_all);
   cudaEventRecord(ev1, st);
   cudaEventSynchronize(ev1);
   float ms = 0.f;

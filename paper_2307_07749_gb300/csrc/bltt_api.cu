@@ -6,6 +6,7 @@
 #include <complex>
 #include <cstdio>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -14,6 +15,7 @@
 
 #include <cublas_v2.h>
 #include <cusolverDn.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "internal.h"
 
@@ -140,6 +142,7 @@ struct bltt_ctx {
   // the window's z slots beyond the two of the workspace (S - 1 vectors of n doubles)
   double* win_ws = nullptr;
   int win_vectors = 0;
+  size_t guard = 0;   // doubles of each guard band (0: none)
   bool capturing = false;
   // per-launch profiling
   bool prof = false;
@@ -196,6 +199,18 @@ struct bltt_ctx {
 };
 
 namespace {
+
+// NVTX ranges of a solve's phases (visible under nsys / ncu; free when no tool is attached): a
+// range started by start() ends at end() or when the holder goes out of scope
+struct NvtxSpan {
+  nvtxRangeId_t id = 0;
+  bool open = false;
+  NvtxSpan() = default;
+  explicit NvtxSpan(const char* name) { start(name); }
+  void start(const char* name) { end(); id = nvtxRangeStartA(name); open = true; }
+  void end() { if (open) { nvtxRangeEnd(id); open = false; } }
+  ~NvtxSpan() { end(); }
+};
 
 bltt_status fail(bltt_ctx* h, bltt_status s, const std::string& msg) {
   if (h) h->err = msg; else g_create_error = msg;
@@ -303,11 +318,37 @@ bltt_status eigen_transform(bltt_ctx* h, const double* in, double* out, bool to_
   return BLTT_OK;
 }
 
+// guard bands (BLTT_GUARD_BANDS=1 in the environment when the workspace is first allocated): a
+// band of kGuard doubles with a fixed bit pattern before, between and after the workspace vectors
+// and the window slots; bltt_check_guards reports a band that a kernel wrote into
+constexpr size_t kGuard = 256;                        // 2 KB: vectors stay 16-byte aligned
+constexpr uint64_t kGuardBits = 0x7FF4C0FFEEC0FFEEull;  // a NaN no kernel writes
+size_t guard_of(bltt_ctx* h) {
+  if (!h->ws && !h->win_ws) {
+    const char* e = std::getenv("BLTT_GUARD_BANDS");
+    h->guard = (e && std::atoi(e) > 0) ? kGuard : 0;
+  }
+  return h->guard;
+}
+// fill the nvec + 1 bands of a region of nvec vectors
+cudaError_t fill_guards(bltt_ctx* h, double* base, size_t nvec) {
+  if (!h->guard) return cudaSuccess;
+  std::vector<uint64_t> pat(h->guard, kGuardBits);
+  for (size_t k = 0; k <= nvec; ++k) {
+    cudaError_t e = cudaMemcpy(base + k * (h->n + h->guard), pat.data(), h->guard * 8,
+                               cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // ensure the solve workspace: 10 vectors of n doubles, partial sums, device scalar state
 bltt_status ensure_workspace(bltt_ctx* h) {
   if (h->ws) return BLTT_OK;
   const size_t nv = 10;
-  CK(h, h->alloc(&h->ws, nv * (size_t)h->n + 2), "workspace allocation");
+  const size_t g = guard_of(h);
+  CK(h, h->alloc(&h->ws, nv * ((size_t)h->n + g) + g + 2), "workspace allocation");
+  CK(h, fill_guards(h, h->ws, nv), "guard bands");
   h->ws_vectors = nv;
   CK(h, h->alloc(&h->partials[0], (size_t)kMaxPartials), "partials");
   CK(h, h->alloc(&h->partials[1], (size_t)kMaxPartials), "partials");
@@ -318,7 +359,11 @@ bltt_status ensure_workspace(bltt_ctx* h) {
   return BLTT_OK;
 }
 
-double* vec(bltt_ctx* h, int k) { return h->ws + (size_t)k * h->n; }
+double* vec(bltt_ctx* h, int k) { return h->ws + h->guard + (size_t)k * ((size_t)h->n + h->guard); }
+// window slot j (0 .. win_vectors - 1)
+double* win_vec(bltt_ctx* h, int j) {
+  return h->win_ws + h->guard + (size_t)j * ((size_t)h->n + h->guard);
+}
 
 // every cached graph of the iterations (their kernel arguments changed, or their key did)
 void drop_graphs(bltt_ctx* h) {
@@ -343,7 +388,9 @@ bltt_status ensure_window(bltt_ctx* h, int S) {
     h->win_vectors = 0;
   }
   drop_graphs(h);
-  CK(h, h->alloc(&h->win_ws, (size_t)(S - 1) * (size_t)h->n), "deferred-update slots");
+  const size_t g = guard_of(h);
+  CK(h, h->alloc(&h->win_ws, (size_t)(S - 1) * ((size_t)h->n + g) + g), "deferred-update slots");
+  CK(h, fill_guards(h, h->win_ws, (size_t)(S - 1)), "guard bands");
   h->win_vectors = S - 1;
   return BLTT_OK;
 }
@@ -1199,6 +1246,8 @@ bltt_status dst_entry_chunked(bltt_ctx* h, const OpTables& op, const double* f_h
 bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol, int maxit,
                        const bltt_solve_opts* opts, double* u, bltt_solve_info* info,
                        const HostOut* hout, const HostIn* hin, bool inner) {
+  NvtxSpan span_solve(inner ? "bltt inner solve" : "bltt_minres_solve");
+  NvtxSpan span;
   if (!h) return BLTT_ERR_INVALID_ARG;
   if (info) { std::memset(info, 0, sizeof *info); info->status = BLTT_ERR_INVALID_ARG; }
   if (!f || !u) return fail(h, BLTT_ERR_INVALID_ARG, "null vector");
@@ -1239,6 +1288,7 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
   cudaStream_t st = h->stream;
   CK(h, cudaEventRecord(h->ev[0], st), "event");
   if (o.rebuild) h->pc_alpha = -1.0;
+  span.start("preconditioner set-up");
   if (!none) {
     s = prepare_precond(h, alpha, o.precision);
     if (s != BLTT_OK) return s;
@@ -1356,6 +1406,7 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
   }
 
   // b = Y f (spectral: Y (I (x) U) f) with ||b||^2
+  span.start("entry transform");
   int nb = 0, nzv = 0, np = 0;
   if (spectral && h->dense) {
     // b = Y (I (x) U^T) f: one FP64 GEMM into the scratch vector, then the flip with ||b||^2
@@ -1384,7 +1435,7 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
   // alternate between two vectors each, starting from slot S (z_S) and the w vectors the fold
   // formed (wc = w_{S-1}, wo = w_{S-2})
   double* Zs[kMaxWin + 1] = {vec(h, 3), vec(h, 4)};
-  for (int k = 2; k <= S; ++k) Zs[k] = h->win_ws + (size_t)(k - 2) * (size_t)n;
+  for (int k = 2; k <= S; ++k) Zs[k] = win_vec(h, k - 2);
   double* const Zc[2] = {S ? Zs[S] : vec(h, 3), S ? Zs[S - 1] : vec(h, 4)};
   double* const Wc[2] = {vec(h, 5), vec(h, 6)};
   double* const V0[2] = {vbuf[0], vbuf[1]};
@@ -1491,6 +1542,7 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
     return BLTT_OK;
   };
   for (;;) {
+    span.start("MINRES iterations");
     if (graph_mode && !resumed) {
       const void* key[14] = {(const void*)(intptr_t)spectral, (const void*)(intptr_t)o.precision,
                              (const void*)(intptr_t)op.mv_arith, (const void*)(intptr_t)none,
@@ -1552,6 +1604,7 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
         }
       }
     }
+    span.start("exit transform and true residual");
     // a window solve forms x at every stop on the device; not when it failed before its fold,
     // nor when it took no iteration (x = 0)
     if (S > 0 && sh->iter == 0) {
@@ -1635,6 +1688,7 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
 // tolerance that brings ||f - A u|| / ||f|| to tol, and adds d to u.
 bltt_status refine_solve(bltt_handle h, const double* f, double alpha, double tol, int maxit,
                          const bltt_solve_opts* opts, double* u, bltt_solve_info* info) {
+  NvtxSpan span_refine("bltt_minres_solve (refinement)");
   if (!h) return BLTT_ERR_INVALID_ARG;
   if (info) { std::memset(info, 0, sizeof *info); info->status = BLTT_ERR_INVALID_ARG; }
   if (h->dense) return fail(h, BLTT_ERR_UNSUPPORTED, "refinement needs the blocks' physical product");
@@ -1779,6 +1833,39 @@ int bltt_profile_read(bltt_handle h, bltt_kernel_stat* out, int max_entries) {
     ++k;
   }
   return k;
+}
+
+bltt_status bltt_check_guards(bltt_handle h, int* bands_checked) {
+  if (!h) return BLTT_ERR_INVALID_ARG;
+  if (bands_checked) *bands_checked = 0;
+  if (!h->guard) return BLTT_OK;
+  CK(h, cudaStreamSynchronize(h->stream), "sync");
+  std::vector<uint64_t> got(h->guard);
+  auto check = [&](double* base, size_t nvec, const char* what) -> bltt_status {
+    for (size_t k = 0; base && k <= nvec; ++k) {
+      CK(h, cudaMemcpy(got.data(), base + k * (h->n + h->guard), h->guard * 8,
+                       cudaMemcpyDeviceToHost), "guard band read");
+      for (size_t i = 0; i < h->guard; ++i)
+        if (got[i] != kGuardBits)
+          return fail(h, BLTT_ERR_CUDA, std::string("guard band ") + std::to_string(k) + " of the " +
+                                            what + " was overwritten (element " + std::to_string(i) + ")");
+      if (bands_checked) ++*bands_checked;
+    }
+    return BLTT_OK;
+  };
+  bltt_status s = check(h->ws, h->ws ? h->ws_vectors : 0, "workspace");
+  if (s == BLTT_OK) s = check(h->win_ws, h->win_ws ? (size_t)h->win_vectors : 0, "window slots");
+  return s;
+}
+
+bltt_status bltt_guard_poke(bltt_handle h, int band) {
+  if (!h) return BLTT_ERR_INVALID_ARG;
+  if (!h->guard || !h->ws || band < 0 || (size_t)band > h->ws_vectors)
+    return fail(h, BLTT_ERR_INVALID_ARG, "no such guard band");
+  const double v = 1.0;
+  CK(h, cudaMemcpy(h->ws + (size_t)band * (h->n + h->guard) + h->guard / 2, &v, sizeof v,
+                   cudaMemcpyHostToDevice), "guard band write");
+  return BLTT_OK;
 }
 
 bltt_status bltt_minres_solve(bltt_handle h, const double* f, double alpha, double tol, int maxit,
