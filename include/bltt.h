@@ -103,7 +103,10 @@ typedef struct {
   int precision;     /* BLTT_PREC_F64 (default when 0) or BLTT_PREC_F32                        */
   int basis;         /* BLTT_BASIS_*                                                            */
   int precond;       /* BLTT_PRECOND_*                                                          */
-  int sync_every;    /* iterations issued between host checks of the device state (0: 2)        */
+  int sync_every;    /* iterations issued between host checks of the device state (0: 2); in
+                        graph replay the first check of a solve comes after as many blocks of
+                        them as the previous solve on the handle needed (at most 8): iterations
+                        past the stop return at once on the device                              */
   int rebuild;       /* 1: rebuild the per-alpha preconditioner tables even if cached            */
   int matvec_arith;  /* BLTT_ARITH_*                                                             */
   int no_graph;      /* 1: launch every kernel directly; 0: capture sync_every (rounded up to even)

@@ -143,6 +143,7 @@ struct bltt_ctx {
   double* win_ws = nullptr;
   int win_vectors = 0;
   size_t guard = 0;   // doubles of each guard band (0: none)
+  int ahead_blocks = 0;   // graph blocks the last solve needed: the next one's first burst
   bool capturing = false;
   // per-launch profiling
   bool prof = false;
@@ -1324,6 +1325,7 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
   int* phase = &h->state->phase;
   // the end of every solve: timings, status and statistics
   auto finish = [&](double relres_phys) -> bltt_status {
+    h->ahead_blocks = (sh->iter + G - 1) / G;   // the next solve's first burst
     CK(h, cudaEventRecord(h->ev[2], st), "event");
     CK(h, cudaStreamSynchronize(st), "sync");
     prof_harvest(h);
@@ -1576,19 +1578,29 @@ bltt_status solve_impl(bltt_handle h, const double* f, double alpha, double tol,
         CK(h, ce, "graph instantiate");
         return BLTT_OK;
       };
+      // the first look at the device state comes after as many blocks as the last solve on this
+      // handle needed (at most 8; blocks past the stop return at once on the device), later ones
+      // after every block; with profiling on, after every block (a graph's event nodes hold
+      // its last replay only)
+      int burst = h->prof ? 1 : std::max(1, std::min(8, h->ahead_blocks));
       for (;;) {
-        const bool in_win = issued < S;
-        const int b = issued / G;
-        cudaGraphExec_t& ex = in_win ? h->win_graphs[b].exec : h->gexec;
-        std::vector<bltt_ctx::Pending>& gp = in_win ? h->win_graphs[b].prof : h->graph_prof;
-        s = graph_for(in_win ? issued : S, ex, gp);
-        if (s != BLTT_OK) return s;
-        CK(h, cudaGraphLaunch(ex, st), "graph launch");
-        for (int i = 0; i < G; ++i) h->launches += launches_of(issued + i);
-        issued += G;
+        std::vector<bltt_ctx::Pending>* gp_last = nullptr;
+        for (int bb = 0; bb < burst && issued < maxit; ++bb) {
+          const bool in_win = issued < S;
+          const int b = issued / G;
+          cudaGraphExec_t& ex = in_win ? h->win_graphs[b].exec : h->gexec;
+          std::vector<bltt_ctx::Pending>& gp = in_win ? h->win_graphs[b].prof : h->graph_prof;
+          s = graph_for(in_win ? issued : S, ex, gp);
+          if (s != BLTT_OK) return s;
+          CK(h, cudaGraphLaunch(ex, st), "graph launch");
+          for (int i = 0; i < G; ++i) h->launches += launches_of(issued + i);
+          issued += G;
+          gp_last = &gp;
+        }
+        burst = 1;
         CK(h, cudaMemcpyAsync(sh, h->state, sizeof *sh, cudaMemcpyDeviceToHost, st), "state download");
         CK(h, cudaStreamSynchronize(st), "sync");
-        if (h->prof) prof_harvest_graph(h, gp);
+        if (h->prof && gp_last) prof_harvest_graph(h, *gp_last);
         if (sh->phase != PH_RUN || issued >= maxit) break;
       }
     } else {
