@@ -150,7 +150,9 @@ struct bltt_ctx {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<Pending> pending;
-  struct Stat { long long launches = 0; double ms = 0; long long act = 0; double act_ms = 0; double max_ms = 0; };
+  // per kernel family: every launch's duration, so that "active" (longer than a quarter of the
+  // family's longest launch) is decided against the final maximum when the counters are read
+  struct Stat { long long launches = 0; double ms = 0; double max_ms = 0; std::vector<float> each; };
   std::map<std::string, Stat> stats;
   // host-buffer solves: device staging of f and u, a copy stream and its event
   double* io_f = nullptr;
@@ -666,7 +668,7 @@ void prof_harvest_graph(bltt_ctx* h, const std::vector<bltt_ctx::Pending>& gp) {
     st.launches += 1;
     st.ms += ms[i];
     st.max_ms = std::max(st.max_ms, (double)ms[i]);
-    if (ms[i] > 0.25 * st.max_ms) { st.act += 1; st.act_ms += ms[i]; }
+    st.each.push_back(ms[i]);
   }
   (void)cudaGetLastError();   // a failed timing query must not surface at the next launch check
 }
@@ -675,24 +677,15 @@ void prof_harvest(bltt_ctx* h) {
   if (h->pending.empty()) { h->ev_used = 0; return; }
   cudaStreamSynchronize(h->stream);
   std::vector<float> ms(h->pending.size(), 0.f);
-  std::map<std::string, float> mx;
-  for (size_t i = 0; i < h->pending.size(); ++i) {
+  for (size_t i = 0; i < h->pending.size(); ++i)
     if (cudaEventElapsedTime(&ms[i], h->pending[i].a, h->pending[i].b) != cudaSuccess) ms[i] = -1.f;
-    float& m = mx[h->pending[i].name];
-    m = std::max(m, ms[i]);
-  }
   for (size_t i = 0; i < h->pending.size(); ++i) {
     if (ms[i] < 0.f) continue;
     auto& st = h->stats[h->pending[i].name];
     st.launches += 1;
     st.ms += ms[i];
     st.max_ms = std::max(st.max_ms, (double)ms[i]);
-  }
-  // a launch is active when it took more than 1/4 of its family's longest launch
-  for (size_t i = 0; i < h->pending.size(); ++i) {
-    if (ms[i] < 0.f) continue;
-    auto& st = h->stats[h->pending[i].name];
-    if (ms[i] > 0.25 * st.max_ms) { st.act += 1; st.act_ms += ms[i]; }
+    st.each.push_back(ms[i]);
   }
   h->pending.clear();
   h->ev_used = 0;
@@ -1839,8 +1832,9 @@ int bltt_profile_read(bltt_handle h, bltt_kernel_stat* out, int max_entries) {
       std::strncpy(out[k].name, kv.first.c_str(), sizeof out[k].name - 1);
       out[k].launches = kv.second.launches;
       out[k].total_ms = kv.second.ms;
-      out[k].active_launches = kv.second.act;
-      out[k].active_ms = kv.second.act_ms;
+      // a launch is active when it took more than 1/4 of its family's longest launch
+      for (float m : kv.second.each)
+        if (m > 0.25 * kv.second.max_ms) { out[k].active_launches += 1; out[k].active_ms += m; }
     }
     ++k;
   }
