@@ -292,8 +292,9 @@ bltt_status bltt_minres_solve_host(bltt_handle h, const double* f_host, double a
  *   (system-major), each a vector of that system's N*M doubles, u not aliasing f.
  *   alpha: host array of nsys values in (0,1], or NULL for the default rule (1e-8; 1e-2 for the
  *   FP32 preconditioner and 1e-6 for the double-float one, where their rounding costs no
- *   iteration against FP64 at the same alpha).  opts: precision and matvec_arith as for bltt_minres_solve_ex (basis
- *   is always the DST basis); may be NULL.  info: host array of sum(nrhs) entries or NULL;
+ *   iteration against FP64 at the same alpha).  opts: precision, matvec_arith and defer_window
+ *   as for bltt_minres_solve_ex (basis is always the DST basis; refine is not applied); may be
+ *   NULL.  info: host array of sum(nrhs) entries or NULL;
  *   relres_true is the true residual of the DST-basis system (equal to the physical one up to
  *   the rounding of the exit DST).
  * Returns BLTT_OK when every item converged, else the first failing item's status.  Systems whose

@@ -1741,6 +1741,7 @@ bltt_status refine_solve(bltt_handle h, const double* f, double alpha, double to
   int np = 0;
   CK(h, launch_norm2(f, n, h->partials[0], &np, st), "norm");
   const double nf = std::sqrt(sum_to_host(np));
+  tot.kernel_launches += 2;
   auto residual = [&]() -> double {
     int nr = 0;
     if (launch_matvec(op, 0, u, nullptr, h->ir_r, 0, MV_RESID, f, h->partials[0], &nr, nullptr,
