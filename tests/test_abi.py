@@ -79,6 +79,17 @@ def test_null_handle_calls(lib):
     assert L.bltt_set_matvec_arith(None, 1) == 1
     assert L.bltt_set_variable_coefficient(None, None, 1.0) == 1
     assert L.bltt_set_dense_operator(None, None) == 1
+    # guard bands and the refinement path refuse a null handle before touching the device
+    import ctypes
+    n = ctypes.c_int(-1)
+    assert L.bltt_check_guards(None, ctypes.byref(n)) == 1
+    assert L.bltt_guard_poke(None, 0) == 1
+    opts = B.bltt_solve_opts(32, 1, 0, 0, 0, 2, 0, 0, 0, 4)
+    info = B.bltt_solve_info()
+    assert L.bltt_minres_solve_ex(None, None, 1e-2, 1e-8, 10, ctypes.byref(opts), None,
+                                  ctypes.byref(info)) == 1
+    assert L.bltt_minres_solve_host(None, None, 1e-2, 1e-8, 10, ctypes.byref(opts), None,
+                                    ctypes.byref(info)) == 1
 
 
 def test_alpha_label_rule(lib):
